@@ -1,0 +1,123 @@
+"""Oracle pins (CPU only): the FP32 oracle against hand-derived cases, a float64
+restatement, invariances and closed-form statistics.  See tests/pins.py."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import flock_inputs as fi
+import oracle
+import pins
+
+
+@pytest.mark.parametrize("path", pins.golden_cases(), ids=os.path.basename)
+def test_golden(path):
+    pins.check_golden(path)
+
+
+def test_golden_present():
+    assert len(pins.golden_cases()) >= 7
+
+
+@pytest.mark.parametrize("over", [
+    {},
+    {"fov": fi.FULL_FOV},
+    {"num_segments": 5},
+    {"num_segments": 1, "fov": fi.FULL_FOV},
+    {"num_segments": 16, "fov": float(np.float32(math.radians(120)))},
+    {"agent_radius": 0.0},
+], ids=lambda d: ",".join("%s=%s" % kv for kv in d.items()) or "default")
+def test_fp64_reevaluation(over):
+    n = 600
+    side = fi.side_for(n, 0.3)  # denser than the benchmark: more pairs per agent
+    p, st, act = pins.random_case(n, side, 21, **over)
+    frac = pins.check_fp64(p, st, act)
+    assert frac > 0.8
+
+
+def test_fp64_reevaluation_small_side():
+    # a square only just wider than 2 d_v: many pairs wrap
+    p, st, act = pins.random_case(200, 11.0, 4)
+    pins.check_fp64(p, st, act)
+
+
+def test_translation_invariance():
+    pins.check_translation()
+
+
+def test_permutation_equivariance():
+    pins.check_permutation()
+
+
+def test_statistics_uniform():
+    pins.check_statistics(threads=0)
+
+
+def test_statistics_full_circle():
+    pins.check_statistics(fov=fi.FULL_FOV, seed=12, threads=0)
+
+
+def test_sincos_accuracy():
+    pins.check_sincos()
+
+
+def test_diamond_pseudo_angle():
+    # quadrant anchors and monotonicity against the true angle
+    assert oracle.diamond(1.0, 0.0) == 0.0
+    assert oracle.diamond(1.0, 1.0) == 0.5
+    assert oracle.diamond(0.0, 1.0) == 1.0
+    assert oracle.diamond(-1.0, 0.0) == 2.0
+    assert oracle.diamond(0.0, -1.0) == 3.0
+    ang = np.linspace(0, 2 * math.pi, 2001)[:-1]
+    vals = [oracle.diamond(float(np.float32(math.cos(a))), float(np.float32(math.sin(a))))
+            for a in ang]
+    assert all(b >= a for a, b in zip(vals, vals[1:]))
+
+
+def test_derived_constants_full_circle():
+    p = fi.default_params(100.0, fov=fi.FULL_FOV)
+    d = oracle.derive(p)
+    assert d["full"] == 1 and d["CF"] == -1.0 and d["SF"] == 0.0
+    # edges every 45 degrees: pseudo-angles 0.5, 1, ..., 3.5
+    assert d["T"][:7] == [0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5]
+    assert d["K"] == 46 and d["PK"] == 2 ** 46
+    assert d["RV2"] == 25.0 and d["RC2"] == 1.0 and d["INV_SPAN"] == 0.25
+
+
+def test_empty_and_single():
+    p = fi.default_params(100.0)
+    st, obs, rew, coll, flags = oracle.step(p, np.zeros((0, 4), np.float32),
+                                            np.zeros(0, np.int32))
+    assert obs.shape == (0, 18) and flags == 0
+    one = np.array([[10.0, 20.0, 1.0, 0.5]], np.float32)
+    st, obs, rew, coll, flags = oracle.step(p, one, np.array([4], np.int32))
+    assert rew[0] == 0.0 and coll[0] == 0
+    assert np.all(obs[0, 0:16:2] == 5.0) and np.all(obs[0, 1:16:2] == 0.0)
+
+
+def test_invalid_action_flag():
+    p = fi.default_params(100.0)
+    st = fi.initial_state(10, 100.0, 0)
+    a = np.full(10, 4, np.int32)
+    a[3] = 9
+    a[5] = -1
+    s1, _, _, _, flags = oracle.step(p, st, a)
+    s2, _, _, _, flags2 = oracle.step(p, st, np.full(10, 4, np.int32))
+    assert flags == oracle.FLAG_ACTION and flags2 == 0
+    np.testing.assert_array_equal(s1, s2)
+
+
+def test_state_range_flag():
+    p = fi.default_params(100.0)
+    st = fi.initial_state(4, 100.0, 0)
+    st[2, 0] = 100.0  # x == L is outside [0, L)
+    _, _, _, _, flags = oracle.step(p, st, None)
+    assert flags == oracle.FLAG_STATE
+
+
+def test_invalid_params():
+    for bad in ({"view_radius": 0.0}, {"agent_radius": 3.0}, {"num_segments": 0},
+                {"num_segments": 129}, {"fov": 7.0}, {"side": 9.0}, {"speed_max": -1.0}):
+        assert not oracle.params_ok(dict(fi.default_params(100.0), **bad)), bad
+    assert oracle.params_ok(fi.default_params(100.0))
