@@ -1,0 +1,329 @@
+"""Benchmark of the flock environment step on GB300.
+
+Default (one GPU): the plain single-instance step at 50,000 agents (side
+707.1, density 0.1, view radius 5, 8 sectors, field of view 250 degrees,
+uniform random actions), W warm-up steps then K timed steps, each timed with
+CUDA events on the library's stream, with L2 flushed (a 512 MiB write)
+between timed steps.  Prints one JSON line: agent-steps/s, p50/p99 step
+latency, the roofline of the dominant kernel (the neighbour scan), the same
+metric end to end through host buffers, GPU clocks sampled during the timed
+region, and the CPU oracle timed on this host as a reported baseline.
+
+--gpus N (under torchrun): every rank runs its own 50,000-agent instance
+(instances are independent, no collective on the data path); the value is
+the agent-steps of all ranks over the slowest rank's time.
+
+--impl reference: times the CPU oracle (the reference arm of this project:
+the plain O(N^2) statement of the step) on this host's cores."""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import flock_inputs as fi  # noqa: E402
+
+METRIC = "flock agent-steps/sec at 50k agents, batched vs plain; p99 step latency"
+UNIT = "agent-steps/s"
+N_AGENTS = 50000
+BYTES_PER_AGENT_STEP = 116  # state in 16 + action 4 + state out 16 + obs 72 + reward 4 + coll 4
+NEIGH_BYTES_PER_AGENT = 96  # neighbour scan: reads the state (16), writes obs, reward, coll (80)
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(n=N_AGENTS, steps=2, seed=0):
+    """The oracle, as it stands, on this host's cores: full O(N^2) steps of
+    the same workload (a bounded sample of `steps` steps)."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle
+    side = fi.side_for(n)
+    p = fi.default_params(side)
+    st = fi.initial_state(n, side, seed)
+    acts = fi.random_actions(n, steps, seed)
+    cores = os.cpu_count() or 1
+    oracle.step(p, st, None, threads=cores)  # page in / warm
+    t0 = time.perf_counter()
+    for a in acts:
+        st = oracle.step(p, st, a, threads=cores)[0]
+    dt = time.perf_counter() - t0
+    return {"value": n * steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d full O(N^2) steps of the %d-agent workload (seed %d), %d OpenMP threads"
+                      % (steps, n, seed, cores), "seconds": dt}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle as it stands, on all host cores.  Each
+    step applies the actions of all agents and observes a bounded sample of
+    them (rotating through the agents), sized so that the whole run takes
+    about two minutes; the rate is sampled agent-steps per second."""
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle
+    n = N_AGENTS
+    side = fi.side_for(n)
+    p = fi.default_params(side)
+    st = fi.initial_state(n, side, 0)
+    total = args.steps + args.warmup
+    acts = fi.random_actions(n, total, 0)
+    cores = os.cpu_count() or 1
+    # size the per-step sample from one probe of 512 rows
+    probe = np.arange(512, dtype=np.int32)
+    t0 = time.perf_counter()
+    oracle.observe_rows(p, st, probe, threads=cores)
+    per_row = (time.perf_counter() - t0) / len(probe)
+    budget = 120.0 / max(total, 1)
+    m = int(max(256, min(n, budget / max(per_row, 1e-9))))
+    times = []
+    off = 0
+    for k in range(total):
+        rows = (np.arange(m, dtype=np.int64) + off) % n
+        off = (off + m) % n
+        t0 = time.perf_counter()
+        st, _ = oracle.apply(p, st, acts[k])
+        oracle.observe_rows(p, st, rows.astype(np.int32), threads=cores)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    val = m * len(times) / tot
+    sample = ("each step: actions applied to all %d agents, observation of %d of them "
+              "(rotating), O(N) candidates per observed agent, %d OpenMP threads" % (n, m, cores))
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "plain flock step, 1 instance, 50000 agents, side 707.1, "
+                                   "density 0.1, view radius 5, 8 sectors, fov 250 deg, uniform "
+                                   "random actions (CPU oracle, sampled rows)",
+                       "agents": n, "parallelism": "none"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--agents", type=int, default=N_AGENTS)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    import torch
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    import paper_2207_03945_gb300 as F
+
+    n = args.agents
+    side = fi.side_for(n)
+    p = fi.default_params(side)
+    seed = 1000 * rank
+    st0 = fi.initial_state(n, side, seed)
+    total = args.warmup + args.steps
+    acts_h = fi.random_actions(n, total, seed)
+    acts = torch.from_numpy(acts_h).to(dev)
+    act_buf = torch.empty(n, dtype=torch.int32, device=dev)  # fixed pointer: one graph capture
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream(device=dev)
+    env = F.FlockEnv(p, n, device=dev, stream=stream)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        env.reset(torch.from_numpy(st0).to(dev))
+    F.env_set_timing(env.env, True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(total)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(total)]
+    phase = []
+    stream.synchronize()
+    for k in range(args.warmup):
+        with torch.cuda.stream(stream):
+            act_buf.copy_(acts[k])
+            flush.zero_()
+            starts[k].record(stream)
+            env.step(act_buf)
+            ends[k].record(stream)
+        F.env_get_phase_times(env.env)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.warmup, total):
+            with torch.cuda.stream(stream):
+                act_buf.copy_(acts[k])
+                flush.zero_()  # L2 flush between timed steps (outside the events)
+                starts[k].record(stream)
+                env.step(act_buf)
+                ends[k].record(stream)
+            phase.append(F.env_get_phase_times(env.env))
+        torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    step_ms = [starts[k].elapsed_time(ends[k]) for k in range(args.warmup, total)]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    err = env.error()
+    assert err == 0, "device error bits %d" % err
+    value = world * n * args.steps / (tot_ms * 1e-3)
+    ph = np.array(phase)
+    neigh_ms = float(ph[:, 3].mean())
+    peak, peak_kind = peaks()
+    achieved = NEIGH_BYTES_PER_AGENT * n / (neigh_ms * 1e-3) / 1e9
+    step_gbs = BYTES_PER_AGENT_STEP * n / (tot_ms / args.steps * 1e-3) / 1e9
+
+    # end to end through host buffers (pinned): actions in, outputs out
+    act_h = torch.from_numpy(acts_h[args.warmup]).pin_memory()
+    obs_h = torch.empty((n, env.obs_dim), dtype=torch.float32).pin_memory()
+    rew_h = torch.empty(n, dtype=torch.float32).pin_memory()
+    coll_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    F.env_set_timing(env.env, False)
+    for _ in range(3):
+        F.env_step_host(env.env, act_h, obs_h, rew_h, coll_h)
+    e2e_steps = max(10, min(args.steps, 100))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        F.env_step_host(env.env, act_h, obs_h, rew_h, coll_h)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * n * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": n * 4, "d2h_bytes_per_step": n * (env.obs_dim + 2) * 4,
+           "call": "env_step_host (pinned host buffers, synchronous)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "plain flock step, 1 instance, %d agents, side %.1f, density "
+                                   "0.1, view radius 5, 8 sectors, fov 250 deg, uniform random "
+                                   "actions, CUDA graph of 4 kernels" % (n, side),
+                       "agents": n, "l2": "flushed (512 MiB write) between timed steps",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "step_hbm_gbs": step_gbs,
+            "phase_ms": {"apply_bin": float(ph[:, 0].mean()), "scan": float(ph[:, 1].mean()),
+                         "scatter": float(ph[:, 2].mean()), "neighbours": neigh_ms},
+            "roofline": {"bound": "hbm", "kernel": "k_neighbours", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": peak_kind, "traffic": None,
+                         "bytes_per_agent": NEIGH_BYTES_PER_AGENT},
+            "e2e": e2e,
+            "clocks": clk.summary(),
+            "gpu_launches": 4 * args.steps,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line))
+    env.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * flock.h -- C ABI of the GB300 flock environment step.
+ *
+ * The library advances the flock multi-agent environment of arXiv 2207.03945
+ * ("High Performance Simulation for Scalable Multi-Agent Reinforcement
+ * Learning", Section 4.1) on one GPU.  One step applies every agent's action
+ * (accelerate within [s_min, s_max], rotate, move on the periodic square),
+ * then, with the new positions, gives every agent its sector-vision
+ * observation (Section 4 and Fig. 3), its collision count (Fig. 4) and its
+ * reward r_i = sum_j f(d_ij) over d_ij < d_v (Eq. 1).
+ *
+ * Memory: the caller owns every device buffer, including the workspace the
+ * library carves its scratch from (query its size first).  The library never
+ * allocates device memory; it owns only small host structs and, for graph
+ * replay, a CUDA stream and graph of its own.  All pointers named *_dev are
+ * device pointers; *_host are host pointers (pinned memory gives true
+ * asynchronous copies).  Buffers must not overlap.
+ *
+ * Streams: every call enqueues work on the stream given at create time (a
+ * cudaStream_t passed as void*; NULL is the legacy default stream) and
+ * returns without waiting, except where stated.  One handle per stream; a
+ * handle is not safe for concurrent use from several host threads.
+ *
+ * Errors: calls return FLOCK_OK (0) or a negative FLOCK_E* code.  Conditions
+ * found on the device (bad action values, bad state values, a timed-out
+ * grid barrier, reward accumulator overflow) are latched as FLOCK_ERR_* bits
+ * and read, then cleared, by env_get_error / env_batch_get_error.  Device
+ * code never traps.
+ *
+ * Layouts (row-major, no padding):
+ *   state       n x 4 float : (x, y, theta, s), x, y in [0, side), theta in
+ *                             [0, (float)2pi), s in [speed_min, speed_max]
+ *   actions     n int32     : a in [0, 9): turn = a / 3 picks {-turn_step, 0,
+ *                             +turn_step}, speed change = a % 3 picks
+ *                             {-speed_step, 0, +speed_step}; a = 4 is "keep"
+ *   obs         n x (2v+2) float : for sector k = 0..v-1, (distance to the
+ *                             nearest agent in sector k, or view_radius when
+ *                             empty; number of agents in sector k), then
+ *                             (s, theta).  Sectors split the field of view
+ *                             (centred on the heading) into v equal angles,
+ *                             numbered counter-clockwise from its right edge.
+ *   reward      n float, coll n int32 (collisions: pairs closer than
+ *                             2 * agent_radius)
+ * Row i of every output belongs to agent i of the state (never reordered).
+ */
+#ifndef FLOCK_H
+#define FLOCK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define FLOCK_OK 0
+#define FLOCK_EINVAL (-1)   /* bad argument, parameter or size */
+#define FLOCK_ENOSPACE (-2) /* workspace too small or not 256-byte aligned */
+#define FLOCK_ECUDA (-3)    /* a CUDA runtime call failed (see flock_last_cuda_error) */
+
+/* ---- device-side condition bits (env_get_error) ---- */
+#define FLOCK_ERR_ACTION 1u   /* an action outside [0, 9) was read; it acted as 4 */
+#define FLOCK_ERR_STATE 2u    /* an input state value was non-finite or out of range */
+#define FLOCK_ERR_TIMEOUT 4u  /* a grid barrier of the batched kernel gave up waiting */
+#define FLOCK_ERR_OVERFLOW 8u /* an agent had more in-range neighbours than the exact
+                                 reward sum holds (see flock_derived.nmax) */
+
+#define FLOCK_MAX_SEGMENTS 128
+
+/* Model parameters (Section 4.1; readings of the paper in parentheses). */
+typedef struct flock_params {
+  float side;              /* L: the periodic square [0, L)^2 */
+  float view_radius;       /* d_v: neighbours at distance < d_v are seen (Eq. 1) */
+  float fov;               /* field of view, radians, in (0, (float)2pi];
+                              (float)2pi means the full circle */
+  float agent_radius;      /* d_r: a pair collides when closer than 2 d_r (Fig. 4) */
+  float collision_penalty; /* P: reward contribution of a colliding pair is -P */
+  float speed_min, speed_max; /* speed clamp (the printed min/max are swapped) */
+  float speed_step;        /* speed change of an accelerate/decelerate action */
+  float turn_step;         /* heading change of a rotate action, radians */
+  int num_segments;        /* v: sectors of the field of view, 1..128 */
+} flock_params;
+
+/* Launch shape of the neighbour scan.  Every field may be 0 (library
+ * choice).  Results are identical for every valid setting. */
+typedef struct flock_tuning {
+  int stencil; /* 1: cells of width >= d_v, 3 x 3 stencil; 2: width >= d_v/2, 5 x 5 */
+  int tile_w;  /* cells per tile along x, 1..64 */
+  int tile_h;  /* cells per tile along y, 1..8 */
+  int block;   /* threads per block, multiple of 32 in 64..512 */
+} flock_tuning;
+
+/* Constants the library derives from flock_params (host, double precision
+ * where a transcendental is involved, rounded once to float). */
+typedef struct flock_derived {
+  float side, half_side, view_radius, rv2, rc2, inv_span, two_pi, cos_half_fov,
+      sin_half_fov, speed_min, speed_max;
+  float turn[3], accel[3];
+  float edge[FLOCK_MAX_SEGMENTS + 1]; /* edge[m], m = 1..v: pseudo-angle of sector edge m */
+  int v, full_circle, k_exp;          /* reward sum resolution 2^-k_exp */
+  int64_t penalty_fixed;              /* P * 2^k_exp */
+  int64_t nmax;                       /* in-range neighbours the exact sum holds */
+  int cells_per_side, stencil;        /* cell list geometry */
+  float inv_cell_width;
+} flock_derived;
+
+typedef struct flock_env flock_env;
+typedef struct flock_batch flock_batch;
+
+/* Fills *out with this library's defaults for a square of side `side`:
+ * d_v = 5, d_r = 0.5, P = 1, s in [0, 1], speed_step 0.25, turn_step pi/8,
+ * v = 8, fov = 250 degrees.  Returns FLOCK_EINVAL for a NULL out. */
+int flock_default_params(float side, flock_params *out);
+
+/* 2v + 2 for valid params, else FLOCK_EINVAL. */
+int flock_obs_dim(const flock_params *params);
+
+/* Device workspace (bytes) that env_create needs for n_agents agents. */
+int flock_workspace_bytes(const flock_params *params, const flock_tuning *tuning_or_null,
+                          int n_agents, size_t *bytes_out);
+
+/* The derived constants and cell geometry env_create would use (no GPU
+ * needed).  tuning_or_null selects the stencil. */
+int flock_derive(const flock_params *params, const flock_tuning *tuning_or_null,
+                 flock_derived *out);
+
+/* Creates an environment of n_agents (>= 0) agents.  workspace_dev: caller
+ * buffer of at least flock_workspace_bytes, 256-byte aligned, owned by the
+ * caller until env_destroy; the agent state lives in it.  stream: the
+ * cudaStream_t all calls enqueue on.  No kernel runs; the workspace is
+ * cleared with cudaMemsetAsync. */
+int env_create(const flock_params *params, const flock_tuning *tuning_or_null, int n_agents,
+               void *workspace_dev, size_t workspace_bytes, void *stream, flock_env **out);
+
+/* Loads state0_dev (n x 4) as the current state and writes the initial
+ * observation, rewards and collisions of that state (no action applied). */
+int env_reset(flock_env *env, const float *state0_dev, float *obs_dev, float *reward_dev,
+              int32_t *coll_dev);
+
+/* One step (the hot path): applies actions_dev, then observes.  Enqueues a
+ * CUDA graph of the binning and neighbour-scan kernels (captured on the
+ * first call and again whenever an output pointer changes). */
+int env_step(flock_env *env, const int32_t *actions_dev, float *obs_dev, float *reward_dev,
+             int32_t *coll_dev);
+
+/* env_step from and to host memory: copies the actions in, steps, copies the
+ * outputs out, and waits for the stream.  Returns after the outputs are in
+ * the host buffers. */
+int env_step_host(flock_env *env, const int32_t *actions_host, float *obs_host,
+                  float *reward_host, int32_t *coll_host);
+
+/* Copies the current state (n x 4) out of / into the workspace. */
+int env_get_state(flock_env *env, float *state_dev);
+int env_set_state(flock_env *env, const float *state_dev);
+
+/* Waits for the stream, returns the latched FLOCK_ERR_* bits in *bits_out and
+ * clears them. */
+int env_get_error(flock_env *env, uint32_t *bits_out);
+
+/* The library's derived constants and the tuning in use. */
+int env_get_derived(const flock_env *env, flock_derived *out);
+int env_get_tuning(const flock_env *env, flock_tuning *out);
+
+/* Kernel timing.  With enable != 0 the step graph is re-captured with a CUDA
+ * event around each of its four kernels (apply+bin, scan, scatter,
+ * neighbour scan); env_get_phase_times waits for the stream and returns the
+ * last step's kernel durations in milliseconds.  Off by default. */
+int env_set_timing(flock_env *env, int enable);
+int env_get_phase_times(flock_env *env, float ms_out[4]);
+
+/* Frees the host handle and the library's graph and stream; frees nothing
+ * the caller owns.  Waits for the stream first. */
+void env_destroy(flock_env *env);
+
+/* Last CUDA error string seen by the library in this process (or ""). */
+const char *flock_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLOCK_H */

@@ -1,0 +1,252 @@
+"""GB300 flock environment step (arXiv 2207.03945, Section 4.1).
+
+Thin Python binding of ``libflock.so`` (C ABI declared in include/flock.h):
+the functions below carry the C names and only marshal arguments -- tensors
+become device pointers, dicts become ``flock_params`` -- so every step of the
+environment runs in the library's CUDA kernels.  PyTorch supplies device
+memory and streams.  There is no CPU fallback: importing this package raises
+if the library has not been built (``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _abi
+from ._abi import (FLOCK_ERR_ACTION, FLOCK_ERR_OVERFLOW, FLOCK_ERR_STATE, FLOCK_ERR_TIMEOUT,
+                   FlockError)
+
+__all__ = [
+    "FlockError", "FLOCK_ERR_ACTION", "FLOCK_ERR_STATE", "FLOCK_ERR_TIMEOUT",
+    "FLOCK_ERR_OVERFLOW", "flock_default_params", "flock_obs_dim", "flock_workspace_bytes",
+    "flock_derive",
+    "env_create", "env_reset", "env_step", "env_step_host", "env_get_state", "env_set_state",
+    "env_get_error", "env_get_derived", "env_get_tuning", "env_set_timing",
+    "env_get_phase_times", "env_destroy", "FlockEnv", "lib_path",
+]
+
+lib_path = _abi.LIB_PATH
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t, dtype, shape=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor of the given dtype/shape."""
+    torch = _torch()
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise FlockError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise FlockError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise FlockError("%s must be contiguous" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise FlockError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def flock_default_params(side: float) -> dict:
+    p = _abi.FlockParams()
+    _abi.check(_abi.lib.flock_default_params(ctypes.c_float(side), ctypes.byref(p)))
+    return _abi.params_to_dict(p)
+
+
+def flock_obs_dim(params: dict) -> int:
+    r = _abi.lib.flock_obs_dim(ctypes.byref(_abi.params_from_dict(params)))
+    _abi.check(min(r, 0))
+    return r
+
+
+def flock_workspace_bytes(params: dict, n_agents: int, tuning: dict | None = None) -> int:
+    out = ctypes.c_size_t(0)
+    t = _abi.tuning_from_dict(tuning)
+    _abi.check(_abi.lib.flock_workspace_bytes(ctypes.byref(_abi.params_from_dict(params)),
+                                              ctypes.byref(t) if t is not None else None,
+                                              int(n_agents), ctypes.byref(out)))
+    return int(out.value)
+
+
+def flock_derive(params: dict, tuning: dict | None = None) -> dict:
+    d = _abi.FlockDerived()
+    t = _abi.tuning_from_dict(tuning)
+    _abi.check(_abi.lib.flock_derive(ctypes.byref(_abi.params_from_dict(params)),
+                                     ctypes.byref(t) if t is not None else None, ctypes.byref(d)))
+    return _abi.derived_to_dict(d)
+
+
+class _Env:
+    """Opaque handle (holds the workspace tensor alive)."""
+
+    def __init__(self, handle, n, obs_dim, workspace):
+        self.handle = handle
+        self.n = n
+        self.obs_dim = obs_dim
+        self.workspace = workspace
+
+
+def env_create(params: dict, n_agents: int, workspace, stream=None, tuning: dict | None = None):
+    torch = _torch()
+    if not isinstance(workspace, torch.Tensor) or workspace.dtype != torch.uint8:
+        raise FlockError("workspace must be a uint8 CUDA tensor")
+    h = ctypes.c_void_p()
+    t = _abi.tuning_from_dict(tuning)
+    _abi.check(_abi.lib.env_create(ctypes.byref(_abi.params_from_dict(params)),
+                                   ctypes.byref(t) if t is not None else None, int(n_agents),
+                                   _ptr(workspace, torch.uint8, name="workspace"),
+                                   ctypes.c_size_t(workspace.numel()), _stream(stream),
+                                   ctypes.byref(h)))
+    return _Env(h, int(n_agents), flock_obs_dim(params), workspace)
+
+
+def _outs(env, obs, reward, coll):
+    torch = _torch()
+    return (_ptr(obs, torch.float32, (env.n, env.obs_dim), "obs"),
+            _ptr(reward, torch.float32, (env.n,), "reward"),
+            _ptr(coll, torch.int32, (env.n,), "coll"))
+
+
+def env_reset(env, state0, obs, reward, coll):
+    torch = _torch()
+    _abi.check(_abi.lib.env_reset(env.handle, _ptr(state0, torch.float32, (env.n, 4), "state0"),
+                                  *_outs(env, obs, reward, coll)))
+
+
+def env_step(env, actions, obs, reward, coll):
+    torch = _torch()
+    _abi.check(_abi.lib.env_step(env.handle, _ptr(actions, torch.int32, (env.n,), "actions"),
+                                 *_outs(env, obs, reward, coll)))
+
+
+def env_step_host(env, actions, obs, reward, coll):
+    """Host-memory step: numpy arrays or pinned CPU tensors; waits for completion."""
+    import numpy as np
+
+    def hp(a, dtype, shape, name):
+        torch = _torch()
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda or a.dtype != dtype or not a.is_contiguous() or tuple(a.shape) != shape:
+                raise FlockError("%s: bad host tensor" % name)
+            return ctypes.c_void_p(a.data_ptr())
+        if not isinstance(a, np.ndarray) or not a.flags.c_contiguous or a.shape != shape:
+            raise FlockError("%s: bad host array" % name)
+        return ctypes.c_void_p(a.ctypes.data)
+
+    torch = _torch()
+    n, d = env.n, env.obs_dim
+    _abi.check(_abi.lib.env_step_host(env.handle, hp(actions, torch.int32, (n,), "actions"),
+                                      hp(obs, torch.float32, (n, d), "obs"),
+                                      hp(reward, torch.float32, (n,), "reward"),
+                                      hp(coll, torch.int32, (n,), "coll")))
+
+
+def env_get_state(env, state):
+    torch = _torch()
+    _abi.check(_abi.lib.env_get_state(env.handle, _ptr(state, torch.float32, (env.n, 4), "state")))
+
+
+def env_set_state(env, state):
+    torch = _torch()
+    _abi.check(_abi.lib.env_set_state(env.handle, _ptr(state, torch.float32, (env.n, 4), "state")))
+
+
+def env_get_error(env) -> int:
+    bits = ctypes.c_uint32(0)
+    _abi.check(_abi.lib.env_get_error(env.handle, ctypes.byref(bits)))
+    return int(bits.value)
+
+
+def env_get_derived(env) -> dict:
+    d = _abi.FlockDerived()
+    _abi.check(_abi.lib.env_get_derived(env.handle, ctypes.byref(d)))
+    return _abi.derived_to_dict(d)
+
+
+def env_get_tuning(env) -> dict:
+    t = _abi.FlockTuning()
+    _abi.check(_abi.lib.env_get_tuning(env.handle, ctypes.byref(t)))
+    return {k: getattr(t, k) for k, _ in _abi.FlockTuning._fields_}
+
+
+def env_set_timing(env, enable: bool):
+    _abi.check(_abi.lib.env_set_timing(env.handle, 1 if enable else 0))
+
+
+def env_get_phase_times(env) -> list:
+    """Per-kernel milliseconds of the last step: apply+bin, scan, scatter, neighbours."""
+    ms = (ctypes.c_float * 4)()
+    _abi.check(_abi.lib.env_get_phase_times(env.handle, ms))
+    return list(ms)
+
+
+def env_destroy(env):
+    if env is not None and env.handle:
+        _abi.lib.env_destroy(env.handle)
+        env.handle = None
+
+
+class FlockEnv:
+    """Convenience owner of one environment: allocates the workspace and the
+    output tensors with torch and calls the C ABI."""
+
+    def __init__(self, params: dict, n_agents: int, device="cuda", stream=None,
+                 tuning: dict | None = None):
+        torch = _torch()
+        self.params = dict(params)
+        self.n = int(n_agents)
+        self.device = torch.device(device)
+        self.obs_dim = flock_obs_dim(params)
+        nbytes = flock_workspace_bytes(params, self.n, tuning)
+        self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        self.stream = stream
+        self.env = env_create(params, self.n, self.workspace, stream, tuning)
+        self.obs = torch.empty((self.n, self.obs_dim), dtype=torch.float32, device=self.device)
+        self.reward = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        self.coll = torch.empty(self.n, dtype=torch.int32, device=self.device)
+
+    def reset(self, state0):
+        env_reset(self.env, state0, self.obs, self.reward, self.coll)
+        return self.obs, self.reward, self.coll
+
+    def step(self, actions):
+        env_step(self.env, actions, self.obs, self.reward, self.coll)
+        return self.obs, self.reward, self.coll
+
+    def state(self):
+        torch = _torch()
+        s = torch.empty((self.n, 4), dtype=torch.float32, device=self.device)
+        env_get_state(self.env, s)
+        return s
+
+    def set_state(self, s):
+        env_set_state(self.env, s)
+
+    def error(self) -> int:
+        return env_get_error(self.env)
+
+    def derived(self) -> dict:
+        return env_get_derived(self.env)
+
+    def tuning(self) -> dict:
+        return env_get_tuning(self.env)
+
+    def close(self):
+        env_destroy(self.env)
+        self.env = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "env", None) is not None:
+                self.close()
+        except Exception:
+            pass

@@ -1,0 +1,579 @@
+// Kernels and C ABI of the single-instance flock environment step
+// (arXiv 2207.03945, Section 4.1, Eq. 1, Fig. 3, Fig. 4).  See flock.h.
+//
+// A step is four kernels on the caller's stream, replayed as one CUDA graph:
+//   k_apply_bin   phase A   one thread per agent
+//   k_scan        phase B   one block per scan tile of 2048 cells
+//   k_scatter     phase C   grid-stride over agents and cells
+//   k_neighbours  phase D   one block per tile of cells
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "flock_device.cuh"
+#include "flock_host.h"
+
+namespace flock {
+
+__global__ void __launch_bounds__(256) k_apply_bin(const Inst *__restrict__ gI, Bufs B, int reset) {
+  __shared__ Inst sI;
+  load_inst(sI, gI);
+  __syncthreads();
+  unsigned err = 0;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < sI.n) phaseA_agent(sI, i, B.actions + sI.agent_base, reset, B.counts, B.cellrank, err);
+  if (err) atomicOr(B.err, err);
+}
+
+__global__ void __launch_bounds__(256) k_scan(Bufs B) {
+  __shared__ int sm[kScanTile + 34];
+  phaseB_tile(blockIdx.x, B, sm);
+}
+
+__global__ void __launch_bounds__(256) k_scatter(Bufs B) {
+  __shared__ int tp[kMaxScanTiles + 1];
+  __shared__ int wsum[33];
+  tile_prefix(B, tp, wsum);
+  const int stride = gridDim.x * blockDim.x;
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < B.n_total; f += stride)
+    phaseC_agent(f, B, tp);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= B.c_total; c += stride)
+    phaseC_cell(c, B, tp);
+}
+
+template <int H>
+__global__ void k_neighbours(const Inst *__restrict__ gI, Bufs B) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ Inst sI;
+  load_inst(sI, gI);
+  __syncthreads();
+  unsigned err = 0;
+  const int t = blockIdx.x;
+  phaseD_tile<H>(sI, t % sI.tiles_x, t / sI.tiles_x, B, smem, err);
+  if (err) atomicOr(B.err, err);
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static thread_local char g_last_cuda_error[256] = "";
+
+int cuda_fail(cudaError_t e, const char *what) {
+  snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "%s: %s", what, cudaGetErrorString(e));
+  return FLOCK_ECUDA;
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Derived constants, written out from the model definition: validate the
+// parameters, then compute everything a kernel needs in double where a
+// transcendental is involved and round once to float.
+int derive(const flock_params &p, int stencil, Inst &I, flock_derived *D) {
+  memset(&I, 0, sizeof I);
+  const double kPi = 3.14159265358979323846;
+  const float vals[] = {p.side, p.view_radius, p.fov, p.agent_radius, p.collision_penalty,
+                        p.speed_min, p.speed_max, p.speed_step, p.turn_step};
+  for (float x : vals)
+    if (!std::isfinite(x)) return FLOCK_EINVAL;
+  if (p.num_segments < 1 || p.num_segments > FLOCK_MAX_SEGMENTS) return FLOCK_EINVAL;
+  if (!(p.view_radius > 0.0f) || !(p.agent_radius >= 0.0f)) return FLOCK_EINVAL;
+  if (!(2.0f * p.agent_radius < p.view_radius)) return FLOCK_EINVAL;
+  if (!(p.side > 2.0f * p.view_radius)) return FLOCK_EINVAL;
+  if (!(p.speed_min >= 0.0f && p.speed_min <= p.speed_max && p.speed_max < p.side))
+    return FLOCK_EINVAL;
+  if (!(p.collision_penalty >= 0.0f) || !(p.speed_step >= 0.0f)) return FLOCK_EINVAL;
+  if (!(p.turn_step >= 0.0f && p.turn_step < (float)kPi)) return FLOCK_EINVAL;
+  const float two_pi = (float)(2.0 * kPi);
+  if (!(p.fov > 0.0f && p.fov <= two_pi)) return FLOCK_EINVAL;
+
+  I.L = p.side;
+  I.HL = 0.5f * p.side;
+  I.RV = p.view_radius;
+  I.RV2 = p.view_radius * p.view_radius;
+  const float two_dr = 2.0f * p.agent_radius;
+  I.RC2 = two_dr * two_dr;
+  I.INV_SPAN = (float)(1.0 / ((double)p.view_radius - 2.0 * (double)p.agent_radius));
+  I.TWO_PI = two_pi;
+  I.SMIN = p.speed_min;
+  I.SMAX = p.speed_max;
+  I.v = p.num_segments;
+  I.full = p.fov == two_pi;
+  const double fov = I.full ? 2.0 * kPi : (double)p.fov;
+  if (I.full) {
+    I.CF = -1.0f;  // full circle: sector 0 starts straight behind the agent
+    I.SF = 0.0f;
+  } else {
+    I.CF = (float)cos(0.5 * fov);
+    I.SF = (float)sin(0.5 * fov);
+  }
+  auto pseudo = [](double x, double y) {
+    if (y >= 0.0) return x >= 0.0 ? y / (x + y) : 1.0 + (-x) / (-x + y);
+    return x < 0.0 ? 2.0 + (-y) / (-x - y) : 3.0 + x / (x - y);
+  };
+  for (int m = 1; m <= I.v; ++m) {
+    const double phi = (double)m * fov / (double)I.v;
+    I.T[m] = (float)pseudo(cos(phi), sin(phi));
+  }
+  I.DT[0] = -p.turn_step; I.DT[1] = 0.0f; I.DT[2] = p.turn_step;
+  I.DS[0] = -p.speed_step; I.DS[1] = 0.0f; I.DS[2] = p.speed_step;
+  // the strict range test must not admit a distance above d_v
+  if (sqrtf(nextafterf(I.RV2, 0.0f)) > p.view_radius) return FLOCK_EINVAL;
+
+  // resolution of the exact reward sum: every ramp term is a float no smaller
+  // than the one made by the largest float below d_v, so a multiple of
+  // 2^(e - 24) for that float's exponent e; the penalty must be one too
+  const float rv = p.view_radius;
+  const float t_min = (rv - nextafterf(rv, 0.0f)) * I.INV_SPAN;
+  if (!(t_min > 0.0f)) return FLOCK_EINVAL;
+  int e = 0;
+  frexpf(t_min, &e);
+  int K = 24 - e;
+  if (p.collision_penalty > 0.0f) {
+    int ep = 0;
+    frexpf(p.collision_penalty, &ep);
+    K = K > 24 - ep ? K : 24 - ep;
+  }
+  if (K < 0) K = 0;
+  if (K > 60) return FLOCK_EINVAL;
+  const float t_max = (rv - sqrtf(I.RC2)) * I.INV_SPAN;
+  double mt = (double)t_max > (double)p.collision_penalty ? (double)t_max : (double)p.collision_penalty;
+  if (mt < 1.0) mt = 1.0;
+  const double nmax = floor(ldexp(1.0, 62) / ldexp(mt, K));
+  if (nmax < 1.0) return FLOCK_EINVAL;
+  I.NMAX = nmax > 9.0e15 ? (long long)9.0e15 : (long long)nmax;
+  I.K = K;
+  I.scaleK = ldexpf(1.0f, K);
+  I.inv_scaleK = ldexpf(1.0f, -K);
+  const double pk = ldexp((double)p.collision_penalty, K);
+  I.PK = (long long)pk;
+  if ((double)I.PK != pk) return FLOCK_EINVAL;
+
+  // cell list: cells at least d_v (3 x 3 stencil) or d_v / 2 (5 x 5) wide,
+  // widened by a relative 2^-20 and by L * 2^-21 so that the float binning
+  // of x * (nc / L) can never hide an in-range neighbour outside the stencil
+  if (stencil != 1 && stencil != 2) return FLOCK_EINVAL;
+  const double wmin = ((double)rv * (1.0 + ldexp(1.0, -20)) + (double)p.side * ldexp(1.0, -21)) /
+                      (double)stencil;
+  const double ncd = floor((double)p.side / wmin);
+  if (ncd < 2 * stencil + 1 || ncd * ncd > (double)kMaxScanTiles * kScanTile) return FLOCK_EINVAL;
+  I.nc = (int)ncd;
+  I.ncells = I.nc * I.nc;
+  I.halo = stencil;
+  I.invw = (float)((double)I.nc / (double)p.side);
+  I.obs_dim = 2 * I.v + 2;
+
+  if (D) {
+    memset(D, 0, sizeof *D);
+    D->side = I.L; D->half_side = I.HL; D->view_radius = I.RV; D->rv2 = I.RV2; D->rc2 = I.RC2;
+    D->inv_span = I.INV_SPAN; D->two_pi = I.TWO_PI; D->cos_half_fov = I.CF;
+    D->sin_half_fov = I.SF; D->speed_min = I.SMIN; D->speed_max = I.SMAX;
+    for (int k = 0; k < 3; ++k) { D->turn[k] = I.DT[k]; D->accel[k] = I.DS[k]; }
+    for (int m = 0; m <= FLOCK_MAX_SEGMENTS; ++m) D->edge[m] = I.T[m];
+    D->v = I.v; D->full_circle = I.full; D->k_exp = I.K; D->penalty_fixed = I.PK;
+    D->nmax = I.NMAX; D->cells_per_side = I.nc; D->stencil = stencil; D->inv_cell_width = I.invw;
+  }
+  return FLOCK_OK;
+}
+
+// Fill in the launch shape.  Agents per tile aim at 3/4 of the block.
+int choose_tuning(const Inst &I, int n, const flock_tuning *req, flock_tuning &t) {
+  flock_tuning r{};
+  if (req) r = *req;
+  t.stencil = I.halo;
+  t.block = r.block ? r.block : 128;
+  if (t.block < 64 || t.block > 512 || t.block % 32) return FLOCK_EINVAL;
+  const double w = (double)I.L / I.nc;
+  const double per_cell = n > 0 ? (double)n / ((double)I.L * I.L) * w * w : 1.0;
+  t.tile_h = r.tile_h ? r.tile_h : 2;
+  if (t.tile_h < 1 || t.tile_h > kMaxTileH) return FLOCK_EINVAL;
+  if (r.tile_w) {
+    t.tile_w = r.tile_w;
+  } else {
+    double tw = 0.75 * t.block / (per_cell * t.tile_h);
+    t.tile_w = (int)(tw < 1 ? 1 : (tw > kMaxTileW ? kMaxTileW : tw));
+  }
+  if (t.tile_w < 1 || t.tile_w > kMaxTileW) return FLOCK_EINVAL;
+  if (t.tile_w > I.nc) t.tile_w = I.nc;
+  if (t.tile_h > I.nc) t.tile_h = I.nc;
+  return FLOCK_OK;
+}
+
+// Geometry of the tiles and the shared-memory staging capacity.
+void set_tiles(Inst &I, int n, const flock_tuning &t) {
+  I.tile_w = t.tile_w;
+  I.tile_h = t.tile_h;
+  I.tiles_x = (I.nc + t.tile_w - 1) / t.tile_w;
+  I.tiles_y = (I.nc + t.tile_h - 1) / t.tile_h;
+  const double w = (double)I.L / I.nc;
+  const double per_cell = n > 0 ? (double)n / ((double)I.L * I.L) * w * w : 0.0;
+  const double staged = (t.tile_w + 2.0 * I.halo) * (t.tile_h + 2.0 * I.halo) * per_cell;
+  int cap = (int)(4.0 * staged) + 256;
+  cap = cap < 512 ? 512 : (cap > 4096 ? 4096 : cap);
+  I.cap = cap;
+}
+
+static std::once_flag g_attr_once;
+static cudaError_t g_attr_err = cudaSuccess;
+
+cudaError_t set_kernel_attrs() {
+  std::call_once(g_attr_once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int maxsm = 0;
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int want = maxsm - (int)sizeof(Inst) - 1024;
+    cudaError_t e1 = cudaFuncSetAttribute(k_neighbours<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+    cudaError_t e2 = cudaFuncSetAttribute(k_neighbours<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+    g_attr_err = e1 != cudaSuccess ? e1 : e2;
+  });
+  return g_attr_err;
+}
+
+}  // namespace flock
+
+using namespace flock;
+
+struct Layout {
+  size_t state, cellrank, counts, local, cell_start, tile_sum, sxy, sidx, inst, err, h_act, h_obs,
+      h_rew, h_coll, total;
+};
+
+static Layout make_layout(int n, int C, int D) {
+  Layout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+  const int nT = (C + kScanTile - 1) / kScanTile;
+  L.state = take((size_t)n * 16);
+  L.cellrank = take((size_t)n * 16);
+  L.counts = take((size_t)C * 4);
+  L.local = take((size_t)C * 4);
+  L.cell_start = take((size_t)(C + 1) * 4);
+  L.tile_sum = take((size_t)(nT + 1) * 4);
+  L.sxy = take((size_t)n * 8);
+  L.sidx = take((size_t)n * 4);
+  L.inst = take(sizeof(Inst));
+  L.err = take(64);
+  L.h_act = take((size_t)n * 4);
+  L.h_obs = take((size_t)n * D * 4);
+  L.h_rew = take((size_t)n * 4);
+  L.h_coll = take((size_t)n * 4);
+  L.total = o;
+  return L;
+}
+
+struct flock_env {
+  flock_params params;
+  flock_tuning tuning;
+  flock_derived derived;
+  Inst inst;  // host copy
+  int n;
+  char *ws;
+  Layout lay;
+  cudaStream_t stream;
+  cudaStream_t cap_stream;
+  cudaGraphExec_t graph;
+  const void *g_act, *g_obs, *g_rew, *g_coll;
+  Bufs bufs;
+  int n_scan_tiles;
+  int scatter_grid;
+  size_t smemD;
+  int timing;
+  cudaEvent_t ev[5];
+};
+
+extern "C" const char *flock_last_cuda_error(void) { return g_last_cuda_error; }
+
+extern "C" int flock_default_params(float side, flock_params *out) {
+  if (!out) return FLOCK_EINVAL;
+  const double kPi = 3.14159265358979323846;
+  out->side = side;
+  out->view_radius = 5.0f;
+  out->fov = (float)(250.0 * kPi / 180.0);
+  out->agent_radius = 0.5f;
+  out->collision_penalty = 1.0f;
+  out->speed_min = 0.0f;
+  out->speed_max = 1.0f;
+  out->speed_step = 0.25f;
+  out->turn_step = (float)(kPi / 8.0);
+  out->num_segments = 8;
+  return FLOCK_OK;
+}
+
+extern "C" int flock_obs_dim(const flock_params *p) {
+  if (!p || p->num_segments < 1 || p->num_segments > FLOCK_MAX_SEGMENTS) return FLOCK_EINVAL;
+  return 2 * p->num_segments + 2;
+}
+
+static int resolve(const flock_params *p, const flock_tuning *t, int n, Inst &I, flock_tuning &tt,
+                   flock_derived *D) {
+  if (!p || n < 0) return FLOCK_EINVAL;
+  int stencil = (t && t->stencil) ? t->stencil : 1;
+  int rc = derive(*p, stencil, I, D);
+  if (rc) return rc;
+  rc = choose_tuning(I, n, t, tt);
+  if (rc) return rc;
+  I.n = n;
+  set_tiles(I, n, tt);
+  return FLOCK_OK;
+}
+
+extern "C" int flock_workspace_bytes(const flock_params *p, const flock_tuning *t, int n,
+                                     size_t *bytes) {
+  if (!bytes) return FLOCK_EINVAL;
+  Inst I;
+  flock_tuning tt;
+  int rc = resolve(p, t, n, I, tt, nullptr);
+  if (rc) return rc;
+  *bytes = make_layout(n, I.ncells, I.obs_dim).total;
+  return FLOCK_OK;
+}
+
+extern "C" int flock_derive(const flock_params *p, const flock_tuning *t, flock_derived *out) {
+  if (!p || !out) return FLOCK_EINVAL;
+  Inst I;
+  return derive(*p, (t && t->stencil) ? t->stencil : 1, I, out);
+}
+
+extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, void *ws,
+                          size_t ws_bytes, void *stream, flock_env **out) {
+  if (!out) return FLOCK_EINVAL;
+  *out = nullptr;
+  flock_env *e = new (std::nothrow) flock_env();
+  if (!e) return FLOCK_EINVAL;
+  int rc = resolve(p, t, n, e->inst, e->tuning, &e->derived);
+  if (rc) { delete e; return rc; }
+  e->params = *p;
+  e->n = n;
+  e->lay = make_layout(n, e->inst.ncells, e->inst.obs_dim);
+  if (!ws || ((uintptr_t)ws & 255) || ws_bytes < e->lay.total) { delete e; return FLOCK_ENOSPACE; }
+  e->ws = (char *)ws;
+  e->stream = (cudaStream_t)stream;
+  cudaError_t ce = set_kernel_attrs();
+  if (ce != cudaSuccess) { delete e; return cuda_fail(ce, "cudaFuncSetAttribute"); }
+  ce = cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking);
+  if (ce != cudaSuccess) { delete e; return cuda_fail(ce, "cudaStreamCreate"); }
+  const Layout &L = e->lay;
+  e->inst.state = (float4 *)(e->ws + L.state);
+  e->inst.agent_base = 0;
+  e->inst.cell_base = 0;
+  e->inst.obs_base = 0;
+  Bufs &B = e->bufs;
+  B.cellrank = (int4 *)(e->ws + L.cellrank);
+  B.counts = (int *)(e->ws + L.counts);
+  B.local = (int *)(e->ws + L.local);
+  B.cell_start = (int *)(e->ws + L.cell_start);
+  B.tile_sum = (int *)(e->ws + L.tile_sum);
+  B.sxy = (float2 *)(e->ws + L.sxy);
+  B.sidx = (int *)(e->ws + L.sidx);
+  B.err = (unsigned *)(e->ws + L.err);
+  B.bar = B.err + 4;
+  B.n_total = n;
+  B.c_total = e->inst.ncells;
+  e->n_scan_tiles = (e->inst.ncells + kScanTile - 1) / kScanTile;
+  B.n_scan_tiles = e->n_scan_tiles;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int g = (n + 255) / 256;
+  e->scatter_grid = g < 1 ? 1 : (g > 4 * sms ? 4 * sms : g);
+  e->smemD = phaseD_smem_bytes(e->inst.cap, e->inst.v, e->tuning.block);
+  // descriptor and cleared scratch, in stream order
+  cudaStream_t s = e->stream;
+  cudaError_t c1 = cudaMemcpyAsync(e->ws + L.inst, &e->inst, sizeof(Inst), cudaMemcpyHostToDevice, s);
+  cudaError_t c2 = cudaMemsetAsync(e->ws + L.counts, 0, (size_t)e->inst.ncells * 4, s);
+  cudaError_t c3 = cudaMemsetAsync(e->ws + L.err, 0, 64, s);
+  if (c1 != cudaSuccess || c2 != cudaSuccess || c3 != cudaSuccess) {
+    cudaStreamDestroy(e->cap_stream);
+    delete e;
+    return cuda_fail(c1 != cudaSuccess ? c1 : (c2 != cudaSuccess ? c2 : c3), "env_create copies");
+  }
+  // the host descriptor copy is pageable memory: the copy above has been
+  // staged by the time it returns, so e->inst may change afterwards
+  *out = e;
+  return FLOCK_OK;
+}
+
+static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, float *obs, float *rew,
+                        int32_t *coll, int reset) {
+  Bufs B = e->bufs;
+  B.actions = act;
+  B.obs = obs;
+  B.reward = rew;
+  B.coll = coll;
+  const Inst *gI = (const Inst *)(e->ws + e->lay.inst);
+  const int n = e->n;
+  const bool tm = e->timing != 0;
+  if (tm) CK(cudaEventRecord(e->ev[0], s));
+  if (n > 0) {
+    k_apply_bin<<<(n + 255) / 256, 256, 0, s>>>(gI, B, reset);
+    CK(cudaGetLastError());
+  }
+  if (tm) CK(cudaEventRecord(e->ev[1], s));
+  k_scan<<<e->n_scan_tiles, 256, 0, s>>>(B);
+  CK(cudaGetLastError());
+  if (tm) CK(cudaEventRecord(e->ev[2], s));
+  k_scatter<<<e->scatter_grid, 256, 0, s>>>(B);
+  CK(cudaGetLastError());
+  if (tm) CK(cudaEventRecord(e->ev[3], s));
+  if (n > 0) {
+    const int tiles = e->inst.tiles_x * e->inst.tiles_y;
+    if (e->inst.halo == 1)
+      k_neighbours<1><<<tiles, e->tuning.block, e->smemD, s>>>(gI, B);
+    else
+      k_neighbours<2><<<tiles, e->tuning.block, e->smemD, s>>>(gI, B);
+    CK(cudaGetLastError());
+  }
+  if (tm) CK(cudaEventRecord(e->ev[4], s));
+  return FLOCK_OK;
+}
+
+static bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p % a) == 0; }
+
+static int check_out(const flock_env *e, const float *obs, const float *rew, const int32_t *coll) {
+  if (e->n == 0) return FLOCK_OK;
+  if (!obs || !rew || !coll || !aligned(obs, 8) || !aligned(rew, 4) || !aligned(coll, 4))
+    return FLOCK_EINVAL;
+  return FLOCK_OK;
+}
+
+extern "C" int env_reset(flock_env *e, const float *state0, float *obs, float *rew, int32_t *coll) {
+  if (!e || (e->n > 0 && !state0)) return FLOCK_EINVAL;
+  int rc = check_out(e, obs, rew, coll);
+  if (rc) return rc;
+  if (e->n > 0)
+    CK(cudaMemcpyAsync(e->ws + e->lay.state, state0, (size_t)e->n * 16, cudaMemcpyDeviceToDevice,
+                       e->stream));
+  return enqueue_step(e, e->stream, nullptr, obs, rew, coll, 1);
+}
+
+extern "C" int env_step(flock_env *e, const int32_t *act, float *obs, float *rew, int32_t *coll) {
+  if (!e || (e->n > 0 && !act)) return FLOCK_EINVAL;
+  int rc = check_out(e, obs, rew, coll);
+  if (rc) return rc;
+  if (!e->graph || e->g_act != act || e->g_obs != obs || e->g_rew != rew || e->g_coll != coll) {
+    if (e->graph) {
+      CK(cudaStreamSynchronize(e->stream));  // the old graph may still be running
+      cudaGraphExecDestroy(e->graph);
+      e->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
+    rc = enqueue_step(e, e->cap_stream, act, obs, rew, coll, 0);
+    cudaError_t ce = cudaStreamEndCapture(e->cap_stream, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+    ce = cudaGraphInstantiate(&e->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+      e->graph = nullptr;
+      return cuda_fail(ce, "cudaGraphInstantiate");
+    }
+    e->g_act = act;
+    e->g_obs = obs;
+    e->g_rew = rew;
+    e->g_coll = coll;
+  }
+  CK(cudaGraphLaunch(e->graph, e->stream));
+  return FLOCK_OK;
+}
+
+extern "C" int env_step_host(flock_env *e, const int32_t *act_h, float *obs_h, float *rew_h,
+                             int32_t *coll_h) {
+  if (!e) return FLOCK_EINVAL;
+  const size_t n = (size_t)e->n;
+  if (n > 0 && (!act_h || !obs_h || !rew_h || !coll_h)) return FLOCK_EINVAL;
+  const Layout &L = e->lay;
+  int32_t *act = (int32_t *)(e->ws + L.h_act);
+  float *obs = (float *)(e->ws + L.h_obs);
+  float *rew = (float *)(e->ws + L.h_rew);
+  int32_t *coll = (int32_t *)(e->ws + L.h_coll);
+  if (n > 0) CK(cudaMemcpyAsync(act, act_h, n * 4, cudaMemcpyHostToDevice, e->stream));
+  int rc = env_step(e, act, obs, rew, coll);
+  if (rc) return rc;
+  if (n > 0) {
+    CK(cudaMemcpyAsync(obs_h, obs, n * e->inst.obs_dim * 4, cudaMemcpyDeviceToHost, e->stream));
+    CK(cudaMemcpyAsync(rew_h, rew, n * 4, cudaMemcpyDeviceToHost, e->stream));
+    CK(cudaMemcpyAsync(coll_h, coll, n * 4, cudaMemcpyDeviceToHost, e->stream));
+  }
+  CK(cudaStreamSynchronize(e->stream));
+  return FLOCK_OK;
+}
+
+extern "C" int env_get_state(flock_env *e, float *state) {
+  if (!e || (e->n > 0 && !state)) return FLOCK_EINVAL;
+  if (e->n > 0)
+    CK(cudaMemcpyAsync(state, e->ws + e->lay.state, (size_t)e->n * 16, cudaMemcpyDeviceToDevice,
+                       e->stream));
+  return FLOCK_OK;
+}
+
+extern "C" int env_set_state(flock_env *e, const float *state) {
+  if (!e || (e->n > 0 && !state)) return FLOCK_EINVAL;
+  if (e->n > 0)
+    CK(cudaMemcpyAsync(e->ws + e->lay.state, state, (size_t)e->n * 16, cudaMemcpyDeviceToDevice,
+                       e->stream));
+  return FLOCK_OK;
+}
+
+extern "C" int env_get_error(flock_env *e, uint32_t *bits) {
+  if (!e || !bits) return FLOCK_EINVAL;
+  uint32_t w = 0;
+  CK(cudaMemcpyAsync(&w, e->ws + e->lay.err, 4, cudaMemcpyDeviceToHost, e->stream));
+  CK(cudaMemsetAsync(e->ws + e->lay.err, 0, 4, e->stream));
+  CK(cudaStreamSynchronize(e->stream));
+  *bits = w;
+  return FLOCK_OK;
+}
+
+extern "C" int env_get_derived(const flock_env *e, flock_derived *out) {
+  if (!e || !out) return FLOCK_EINVAL;
+  *out = e->derived;
+  return FLOCK_OK;
+}
+
+extern "C" int env_get_tuning(const flock_env *e, flock_tuning *out) {
+  if (!e || !out) return FLOCK_EINVAL;
+  *out = e->tuning;
+  return FLOCK_OK;
+}
+
+extern "C" int env_set_timing(flock_env *e, int enable) {
+  if (!e) return FLOCK_EINVAL;
+  if (enable && !e->ev[0])
+    for (int k = 0; k < 5; ++k) CK(cudaEventCreate(&e->ev[k]));
+  if ((enable != 0) != (e->timing != 0) && e->graph) {
+    CK(cudaStreamSynchronize(e->stream));
+    cudaGraphExecDestroy(e->graph);
+    e->graph = nullptr;  // re-captured by the next env_step
+  }
+  e->timing = enable != 0;
+  return FLOCK_OK;
+}
+
+extern "C" int env_get_phase_times(flock_env *e, float *ms) {
+  if (!e || !ms || !e->timing) return FLOCK_EINVAL;
+  CK(cudaEventSynchronize(e->ev[4]));
+  for (int k = 0; k < 4; ++k) CK(cudaEventElapsedTime(&ms[k], e->ev[k], e->ev[k + 1]));
+  return FLOCK_OK;
+}
+
+extern "C" void env_destroy(flock_env *e) {
+  if (!e) return;
+  cudaStreamSynchronize(e->stream);
+  for (int k = 0; k < 5; ++k)
+    if (e->ev[k]) cudaEventDestroy(e->ev[k]);
+  if (e->graph) cudaGraphExecDestroy(e->graph);
+  if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
+  delete e;
+}

@@ -1,0 +1,482 @@
+// Device code of the flock environment step (arXiv 2207.03945, Section 4.1).
+//
+// One step is four phases over a uniform cell list on the periodic square:
+//   A  apply actions (Section 4.1: accelerate, rotate, move), compute each
+//      agent's cell, count agents per cell with warp-aggregated atomics;
+//   B  exclusive scan of the cell counts, in tiles of SCAN_TILE cells;
+//   C  scatter positions into cell order (counting sort), finalise cell starts;
+//   D  neighbour scan: per tile of cells, stage the tile plus its halo from
+//      the cell-sorted positions into shared memory, then one thread per agent
+//      visits the stencil cells and fuses observation (Fig. 3), collision
+//      count (Fig. 4) and reward (Eq. 1) into one pass.
+//
+// Every FP32 operation that decides or produces an output is written with an
+// explicit round-to-nearest intrinsic (no contraction, no approximation), so
+// the results are exactly those of the plain O(N^2) definition evaluated
+// with the same formulas.  The reward sum is exact (64-bit fixed point) and
+// therefore independent of the visiting order.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "flock.h"
+
+namespace flock {
+
+constexpr int kMaxV = FLOCK_MAX_SEGMENTS;
+constexpr int kScanTile = 2048;        // cells per scan tile (phase B)
+constexpr int kMaxScanTiles = 4096;    // => at most 8M cells
+constexpr int kMaxTileW = 64, kMaxTileH = 8;
+constexpr int kMaxStagedCells = (kMaxTileH + 4) * (kMaxTileW + 4);
+
+// Per-instance descriptor.  A single environment has one; a batch has one
+// per active instance.  Lives in device memory (the workspace).
+struct Inst {
+  float4 *state;       // resident state (x, y, theta, s), updated in place
+  long long obs_base;  // first float of this instance's obs rows
+  int n, nc, ncells, v;
+  int agent_base, cell_base, tile_base, chunk_base;
+  int tiles_x, tiles_y, tile_w, tile_h;
+  int halo, full, K, reset;
+  int obs_dim, cap, pad0, pad1;  // cap: staged agents that fit in shared memory
+  float L, HL, invw, RV, RV2, RC2, INV_SPAN, SMIN, SMAX, TWO_PI, CF, SF, scaleK, inv_scaleK;
+  float DT[3], DS[3];
+  long long PK, NMAX;
+  float T[kMaxV + 1];
+};
+
+// Scratch and output pointers of one step (flattened over all instances).
+struct Bufs {
+  int4 *cellrank;      // per agent: global cell, rank in cell, x bits, y bits
+  int *counts;         // per cell, zero between steps
+  int *local;          // per cell: exclusive prefix within its scan tile
+  int *cell_start;     // per cell + 1: first sorted position
+  int *tile_sum;       // per scan tile: agents in the tile
+  float2 *sxy;         // cell-sorted positions
+  int *sidx;           // cell-sorted flattened agent index
+  unsigned *err;       // latched FLOCK_ERR_* bits
+  unsigned *bar;       // grid barrier words (count, generation)
+  const int32_t *actions;
+  float *obs;
+  float *reward;
+  int32_t *coll;
+  int n_total, c_total, n_scan_tiles, pad;
+};
+
+// ---------------------------------------------------------------------------
+// Exactly-rounded FP32 arithmetic.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fsqrt(float a) { return __fsqrt_rn(a); }
+
+// Deterministic sine and cosine (used once per agent, never per pair):
+// Cody-Waite reduction by pi/2 with a two-part constant whose high part has 8
+// significant bits (so q * hi is exact for the quadrant counts q <= 4 that
+// headings in [0, 2pi) produce), then the Taylor polynomials of sin to x^9
+// and cos to x^8 in Horner form.  The coefficients are the floats nearest
+// to 1/k!.  Error against the exact functions stays below 2e-7.
+__device__ __forceinline__ void det_sincos(float th, float &c, float &s) {
+  const float kTwoOverPi = 0x1.45f306p-1f;
+  const float kHi = 1.5703125f, kLo = 0x1.fb5444p-12f;
+  const float s1 = -0x1.555556p-3f, s2 = 0x1.111112p-7f, s3 = -0x1.a01a02p-13f,
+              s4 = 0x1.71de3ap-19f;
+  const float c1 = -0.5f, c2 = 0x1.555556p-5f, c3 = -0x1.6c16c2p-10f, c4 = 0x1.a01a02p-16f;
+  int q = __float2int_rn(fmul(th, kTwoOverPi));
+  float qf = (float)q;
+  float r = fsub(fsub(th, fmul(qf, kHi)), fmul(qf, kLo));
+  float r2 = fmul(r, r);
+  float ps = fadd(s3, fmul(r2, s4));
+  ps = fadd(s2, fmul(r2, ps));
+  ps = fadd(s1, fmul(r2, ps));
+  float sr = fadd(r, fmul(fmul(r, r2), ps));
+  float pc = fadd(c3, fmul(r2, c4));
+  pc = fadd(c2, fmul(r2, pc));
+  pc = fadd(c1, fmul(r2, pc));
+  float cr = fadd(1.0f, fmul(r2, pc));
+  switch (q & 3) {
+    case 0: c = cr; s = sr; break;
+    case 1: c = -sr; s = cr; break;
+    case 2: c = -cr; s = -sr; break;
+    default: c = sr; s = -cr; break;
+  }
+}
+
+// Pseudo-angle of direction (x, y) in [0, 4): one unit per quadrant,
+// counter-clockwise from +x, monotone in the true angle.
+__device__ __forceinline__ float pseudo_angle(float x, float y) {
+  if (y >= 0.0f) {
+    if (x >= 0.0f) return fdiv(y, fadd(x, y));
+    return fadd(1.0f, fdiv(-x, fadd(-x, y)));
+  }
+  if (x < 0.0f) return fadd(2.0f, fdiv(-y, fsub(-x, y)));
+  return fadd(3.0f, fdiv(x, fsub(x, y)));
+}
+
+__device__ __forceinline__ float wrap_coord(float x, float L) {
+  if (x >= L) x = fsub(x, L);
+  else if (x < 0.0f) x = fadd(x, L);
+  if (x >= L) x = 0.0f;
+  return x;
+}
+
+__device__ __forceinline__ bool state_ok(const float4 s, const Inst &I) {
+  // NaN fails every comparison; infinities fail the range tests
+  return s.x >= 0.0f && s.x < I.L && s.y >= 0.0f && s.y < I.L && s.z >= 0.0f &&
+         s.z < I.TWO_PI && s.w >= I.SMIN && s.w <= I.SMAX;
+}
+
+// Section 4.1: accelerate (clamped to [s_min, s_max]), rotate (heading kept in
+// [0, 2pi)), then move one step along the new heading on the torus.
+__device__ __forceinline__ float4 apply_action(float4 st, int a, const Inst &I, unsigned &err) {
+  if ((unsigned)a >= 9u) {
+    a = 4;
+    err |= FLOCK_ERR_ACTION;
+  }
+  const int tu = a / 3, su = a - 3 * tu;
+  float s = fadd(st.w, I.DS[su]);
+  if (s < I.SMIN) s = I.SMIN;
+  else if (s > I.SMAX) s = I.SMAX;
+  float th = fadd(st.z, I.DT[tu]);
+  if (th >= I.TWO_PI) th = fsub(th, I.TWO_PI);
+  else if (th < 0.0f) th = fadd(th, I.TWO_PI);
+  if (th >= I.TWO_PI) th = 0.0f;
+  float c, sn;
+  det_sincos(th, c, sn);
+  float x = wrap_coord(fadd(st.x, fmul(s, c)), I.L);
+  float y = wrap_coord(fadd(st.y, fmul(s, sn)), I.L);
+  return make_float4(x, y, th, s);
+}
+
+__device__ __forceinline__ int cell_of(float x, const Inst &I) {
+  int c = __float2int_rz(fmul(x, I.invw));
+  c = c < 0 ? 0 : c;
+  return c >= I.nc ? I.nc - 1 : c;
+}
+
+// ---------------------------------------------------------------------------
+// Phase A: apply + bin one agent (instance-local index i).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void phaseA_agent(const Inst &I, int i, const int32_t *actions_inst,
+                                             int reset, int *counts, int4 *cellrank,
+                                             unsigned &err) {
+  float4 st = I.state[i];
+  if (!state_ok(st, I)) err |= FLOCK_ERR_STATE;
+  if (!reset) {
+    st = apply_action(st, actions_inst[i], I, err);
+    I.state[i] = st;
+  }
+  const int g = I.cell_base + cell_of(st.y, I) * I.nc + cell_of(st.x, I);
+  // warp-aggregated count: one atomic per distinct cell in the warp
+  const unsigned active = __activemask();
+  const unsigned peers = __match_any_sync(active, g);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(&counts[g], __popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  const int rank = base + __popc(peers & ((1u << lane) - 1u));
+  cellrank[I.agent_base + i] = make_int4(g, rank, __float_as_int(st.x), __float_as_int(st.y));
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide exclusive scan helpers (blockDim.x a multiple of 32, <= 1024).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int warp_incl_scan(int v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Exclusive scan of one value per thread; returns the thread's exclusive
+// prefix and writes the block total to *total.  wsum: >= 32 ints of smem.
+__device__ __forceinline__ int block_excl_scan(int v, int *wsum, int *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  int inc = warp_incl_scan(v);
+  __syncthreads();
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < nw ? wsum[lane] : 0;
+    int wi = warp_incl_scan(w);
+    if (lane < nw) wsum[lane] = wi - w;
+    if (lane == nw - 1) wsum[32] = wi;
+  }
+  __syncthreads();
+  int r = wsum[warp] + inc - v;
+  *total = wsum[32];
+  return r;
+}
+
+// In-place exclusive scan of a[0..n) in shared memory; a[n] = total.
+__device__ __forceinline__ void block_excl_scan_inplace(int *a, int n, int *wsum) {
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int lo = threadIdx.x * per;
+  int s = 0;
+  for (int k = 0; k < per; ++k)
+    if (lo + k < n) s += a[lo + k];
+  int total;
+  int run = block_excl_scan(s, wsum, &total);
+  for (int k = 0; k < per; ++k)
+    if (lo + k < n) {
+      int t = a[lo + k];
+      a[lo + k] = run;
+      run += t;
+    }
+  if (threadIdx.x == 0) a[n] = total;
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Phase B: exclusive scan of one tile of kScanTile cells.  Writes the
+// in-tile exclusive prefix to local[], the tile total to tile_sum[t], and
+// zeroes the counts for the next step.  sm: kScanTile + 33 ints.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void phaseB_tile(int t, const Bufs &B, int *sm) {
+  const int c0 = t * kScanTile;
+  const int m = min(kScanTile, B.c_total - c0);
+  int *a = sm;
+  int *wsum = sm + kScanTile + 1;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    a[k] = B.counts[c0 + k];
+    B.counts[c0 + k] = 0;
+  }
+  __syncthreads();
+  block_excl_scan_inplace(a, m, wsum);
+  for (int k = threadIdx.x; k < m; k += blockDim.x) B.local[c0 + k] = a[k];
+  if (threadIdx.x == 0) B.tile_sum[t] = a[m];
+  __syncthreads();
+}
+
+// Prefix over the scan tiles, into smem tp[0..n_scan_tiles].
+__device__ __forceinline__ void tile_prefix(const Bufs &B, int *tp, int *wsum) {
+  for (int k = threadIdx.x; k < B.n_scan_tiles; k += blockDim.x) tp[k] = B.tile_sum[k];
+  __syncthreads();
+  block_excl_scan_inplace(tp, B.n_scan_tiles, wsum);
+}
+
+// Phase C for one flattened agent f: scatter into cell order.
+__device__ __forceinline__ void phaseC_agent(int f, const Bufs &B, const int *tp) {
+  const int4 cr = B.cellrank[f];
+  const int pos = tp[cr.x / kScanTile] + B.local[cr.x] + cr.y;
+  B.sxy[pos] = make_float2(__int_as_float(cr.z), __int_as_float(cr.w));
+  B.sidx[pos] = f;
+}
+
+__device__ __forceinline__ void phaseC_cell(int c, const Bufs &B, const int *tp) {
+  B.cell_start[c] = c == B.c_total ? B.n_total : tp[c / kScanTile] + B.local[c];
+}
+
+// ---------------------------------------------------------------------------
+// Phase D: neighbour scan of one tile of cells.
+// ---------------------------------------------------------------------------
+struct Acc {
+  long long acc;  // reward sum in units of 2^-K
+  int nin, ncoll;
+};
+
+// One candidate pair with its minimum-image offset (dx, dy) from the centre
+// agent.  md/cn: this thread's per-sector minimum d^2 and count (strided by
+// the block size in shared memory).
+__device__ __forceinline__ void pair_core(float dx, float dy, const Inst &I, float ux, float uy,
+                                          Acc &a, float *md, int *cn, int stride,
+                                          const float *T) {
+  const float d2 = fadd(fmul(dx, dx), fmul(dy, dy));
+  if (!(d2 < I.RV2)) return;  // Eq. 1: d_ij < d_v
+  a.nin++;
+  if (d2 < I.RC2) {  // Fig. 4: collision below 2 d_r
+    a.ncoll++;
+    a.acc -= I.PK;
+  } else {
+    const float t = fmul(fsub(I.RV, fsqrt(d2)), I.INV_SPAN);
+    a.acc += __float2ll_rn(fmul(t, I.scaleK));  // exact: t is a multiple of 2^-K
+  }
+  // direction in the frame of the field of view's start edge
+  const float lx = fadd(fmul(dx, ux), fmul(dy, uy));
+  const float ly = fsub(fmul(dy, ux), fmul(dx, uy));
+  if (lx == 0.0f && ly == 0.0f) return;
+  float p = pseudo_angle(lx, ly);
+  if (p >= 4.0f) p = 0.0f;
+  if (!I.full && p >= T[I.v]) return;
+  // k = number of edges T[1..v-1] at or below p (T is non-decreasing)
+  int lo = 0, hi = I.v - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p >= T[mid]) lo = mid;
+    else hi = mid - 1;
+  }
+  float *m = md + lo * stride;
+  if (d2 < *m) *m = d2;
+  cn[lo * stride] += 1;
+}
+
+// Cooperative copy of a descriptor into shared memory (call, then sync).
+__device__ __forceinline__ void load_inst(Inst &dst, const Inst *src) {
+  const int *s = reinterpret_cast<const int *>(src);
+  int *d = reinterpret_cast<int *>(&dst);
+  for (int k = threadIdx.x; k < (int)(sizeof(Inst) / 4); k += blockDim.x) d[k] = s[k];
+}
+
+__device__ __forceinline__ int wrapi(int c, int nc) { return c < 0 ? c + nc : (c >= nc ? c - nc : c); }
+
+// Shared memory of phase D (dynamic).  Layout, in bytes from the base:
+//   float4 stg[cap]                      staged candidates (x, y, shift_x, shift_y)
+//   int    cs[kMaxStagedCells + 1]       staged-cell prefix (row-major)
+//   int    wsum[33]
+//   float  md[v * blockDim]; int cn[v * blockDim]
+// I must be the block's shared-memory copy of the instance descriptor.
+__host__ __device__ inline size_t phaseD_smem_bytes(int cap, int v, int block) {
+  return (size_t)cap * 16 + (size_t)(kMaxStagedCells + 1) * 4 + 33 * 4 + (size_t)v * block * 8;
+}
+
+template <int H>
+__device__ void phaseD_tile(const Inst &I, int tx, int ty, const Bufs &B, char *smem,
+                            unsigned &err) {
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  float4 *stg = reinterpret_cast<float4 *>(smem);
+  int *cs = reinterpret_cast<int *>(smem + (size_t)I.cap * 16);
+  int *wsum = cs + kMaxStagedCells + 1;
+  float *md = reinterpret_cast<float *>(wsum + 33);
+  int *cn = reinterpret_cast<int *>(md + (size_t)I.v * nthr);
+  const float *T = I.T;
+  const int nc = I.nc;
+  const int c0 = tx * I.tile_w, c1 = min(c0 + I.tile_w, nc);
+  const int r0 = ty * I.tile_h, r1 = min(r0 + I.tile_h, nc);
+  const int tw = c1 - c0, th = r1 - r0;
+  const int nsc = tw + 2 * H, nsr = th + 2 * H, ncell = nsc * nsr;
+  const int *cst = B.cell_start;
+
+  // staged-cell counts, row-major over (staged row, staged column)
+  for (int e = tid; e < ncell; e += nthr) {
+    const int sr = e / nsc, sc = e - sr * nsc;
+    const int g = I.cell_base + wrapi(r0 - H + sr, nc) * nc + wrapi(c0 - H + sc, nc);
+    cs[e] = cst[g + 1] - cst[g];
+  }
+  __syncthreads();
+  block_excl_scan_inplace(cs, ncell, wsum);
+  const int staged = cs[ncell];
+  const bool use_smem = staged <= I.cap;
+
+  if (use_smem) {
+    // copy: each staged row is at most three contiguous runs of sorted
+    // positions (left halo across the boundary, interior, right halo)
+    for (int sr = 0; sr < nsr; ++sr) {
+      const int vr = r0 - H + sr;
+      const float sy = vr < 0 ? -I.L : (vr >= nc ? I.L : 0.0f);
+      const int rowg = I.cell_base + wrapi(vr, nc) * nc;
+      const int vlo = c0 - H, vhi = c1 + H;
+#pragma unroll
+      for (int part = 0; part < 3; ++part) {
+        int a, b, off;
+        float sx;
+        if (part == 0) { a = vlo; b = min(0, vhi); off = nc; sx = -I.L; }
+        else if (part == 1) { a = max(vlo, 0); b = min(vhi, nc); off = 0; sx = 0.0f; }
+        else { a = max(vlo, nc); b = vhi; off = -nc; sx = I.L; }
+        if (a >= b) continue;
+        const int gs = cst[rowg + a + off], ge = cst[rowg + b - 1 + off + 1];
+        const int ss = cs[sr * nsc + (a - vlo)];
+        for (int q = tid; q < ge - gs; q += nthr) {
+          const float2 pxy = B.sxy[gs + q];
+          stg[ss + q] = make_float4(pxy.x, pxy.y, sx, sy);
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // centre agents: the tile's own cells, row by row
+  int ncent = 0;
+  for (int r = 0; r < th; ++r) {
+    const int rg = I.cell_base + (r0 + r) * nc;
+    ncent += cst[rg + c1] - cst[rg + c0];
+  }
+  for (int a0 = 0; a0 < ncent; a0 += nthr) {
+    const int a = a0 + tid;
+    if (a < ncent) {
+      int r = 0, al = a, rg = 0, rlen = 0;
+      for (;; ++r) {
+        rg = I.cell_base + (r0 + r) * nc;
+        rlen = cst[rg + c1] - cst[rg + c0];
+        if (al < rlen) break;
+        al -= rlen;
+      }
+      const int gp = cst[rg + c0] + al;  // global sorted position
+      const int f = B.sidx[gp];
+      const int i = f - I.agent_base;
+      const float4 me = I.state[i];
+      const float xi = me.x, yi = me.y;
+      float c, sn;
+      det_sincos(me.z, c, sn);
+      const float ux = fadd(fmul(c, I.CF), fmul(sn, I.SF));
+      const float uy = fsub(fmul(sn, I.CF), fmul(c, I.SF));
+      const int cx = cell_of(xi, I);
+      float *mdt = md + tid;
+      int *cnt = cn + tid;
+      for (int k = 0; k < I.v; ++k) {
+        mdt[k * nthr] = __int_as_float(0x7f800000);
+        cnt[k * nthr] = 0;
+      }
+      Acc acc{0, 0, 0};
+      if (use_smem) {
+        const int sr = r + H, lc = cx - c0 + H;
+        // the centre agent's own staged slot: the interior run of its row
+        // holds the row's tile cells in sorted order
+        const int q = cs[sr * nsc + H] + al;
+        for (int dr = -H; dr <= H; ++dr) {
+          const int srow = sr + dr;
+          const int qa = cs[srow * nsc + lc - H], qb = cs[srow * nsc + lc + H + 1];
+          for (int qq = qa; qq < qb; ++qq) {
+            if (qq == q) continue;
+            const float4 e = stg[qq];
+            const float dx = fadd(fsub(e.x, xi), e.z);
+            const float dy = fadd(fsub(e.y, yi), e.w);
+            pair_core(dx, dy, I, ux, uy, acc, mdt, cnt, nthr, T);
+          }
+        }
+      } else {
+        // dense tile: read candidates straight from the sorted arrays
+        const int cy = r0 + r;
+        for (int dr = -H; dr <= H; ++dr) {
+          const int vr = cy + dr;
+          const float sy = vr < 0 ? -I.L : (vr >= nc ? I.L : 0.0f);
+          const int rowg = I.cell_base + wrapi(vr, nc) * nc;
+          for (int dc = -H; dc <= H; ++dc) {
+            const int vc = cx + dc;
+            const float sx = vc < 0 ? -I.L : (vc >= nc ? I.L : 0.0f);
+            const int g = rowg + wrapi(vc, nc);
+            const int ga = cst[g], gb = cst[g + 1];
+            for (int gq = ga; gq < gb; ++gq) {
+              if (gq == gp) continue;
+              const float2 pxy = B.sxy[gq];
+              const float dx = fadd(fsub(pxy.x, xi), sx);
+              const float dy = fadd(fsub(pxy.y, yi), sy);
+              pair_core(dx, dy, I, ux, uy, acc, mdt, cnt, nthr, T);
+            }
+          }
+        }
+      }
+      // outputs at the agent's own row
+      float *o = B.obs + I.obs_base + (long long)i * I.obs_dim;
+      for (int k = 0; k < I.v; ++k) {
+        const int ck = cnt[k * nthr];
+        const float dk = ck ? fsqrt(mdt[k * nthr]) : I.RV;
+        *reinterpret_cast<float2 *>(o + 2 * k) = make_float2(dk, (float)ck);
+      }
+      *reinterpret_cast<float2 *>(o + 2 * I.v) = make_float2(me.w, me.z);
+      B.reward[I.agent_base + i] = fmul(__ll2float_rn(acc.acc), I.inv_scaleK);
+      B.coll[I.agent_base + i] = acc.ncoll;
+      if ((long long)acc.nin > I.NMAX) err |= FLOCK_ERR_OVERFLOW;
+    }
+  }
+  __syncthreads();  // smem is reused by the next tile
+}
+
+}  // namespace flock

@@ -1,0 +1,99 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+include/flock.h declares, validates parameters, and derives the same
+constants as the oracle (each side computes its own)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import flock_inputs as fi
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    import paper_2207_03945_gb300 as F
+    return F
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*([a-z_][a-z0-9_]*)\s*\(",
+                             text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol():
+    F = _lib()
+    lib = ctypes.CDLL(F.lib_path)
+    names = declared_functions()
+    assert "env_step" in names and "env_create" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_default_params_match_inputs_module():
+    F = _lib()
+    assert F.flock_default_params(100.0) == fi.default_params(100.0)
+
+
+def test_obs_dim_and_workspace():
+    F = _lib()
+    p = fi.default_params(fi.side_for(50000))
+    assert F.flock_obs_dim(p) == 18
+    b = F.flock_workspace_bytes(p, 50000)
+    assert 50000 * 36 < b < 50000 * 200
+    assert F.flock_workspace_bytes(p, 0) > 0
+
+
+def test_invalid_params_rejected():
+    F = _lib()
+    for bad in ({"view_radius": 0.0}, {"agent_radius": 3.0}, {"num_segments": 0},
+                {"num_segments": 129}, {"fov": 7.0}, {"side": 9.0}, {"speed_max": -1.0},
+                {"side": float("nan")}):
+        with pytest.raises(F.FlockError):
+            F.flock_derive(dict(fi.default_params(100.0), **bad))
+    with pytest.raises(F.FlockError):
+        F.flock_workspace_bytes(fi.default_params(100.0), -1)
+    with pytest.raises(F.FlockError):  # 5 x 5 stencil needs 5 cells per side
+        F.flock_derive(fi.default_params(11.0), {"stencil": 2})
+    with pytest.raises(F.FlockError):
+        F.flock_workspace_bytes(fi.default_params(100.0), 10, {"block": 48})
+
+
+@pytest.mark.parametrize("over", [{}, {"fov": fi.FULL_FOV}, {"num_segments": 5},
+                                  {"num_segments": 128, "fov": 3.0}, {"agent_radius": 0.0},
+                                  {"collision_penalty": 0.375}, {"view_radius": 7.3}])
+def test_derived_constants_equal_oracle(over):
+    F = _lib()
+    p = fi.default_params(fi.side_for(5000), **over)
+    a = F.flock_derive(p)
+    b = oracle.derive(p)
+    pairs = [("side", "L"), ("half_side", "HL"), ("view_radius", "RV"), ("rv2", "RV2"),
+             ("rc2", "RC2"), ("inv_span", "INV_SPAN"), ("two_pi", "TWO_PI"),
+             ("cos_half_fov", "CF"), ("sin_half_fov", "SF"), ("speed_min", "SMIN"),
+             ("speed_max", "SMAX"), ("turn", "DT"), ("accel", "DS"), ("edge", "T"),
+             ("v", "v"), ("full_circle", "full"), ("k_exp", "K"), ("penalty_fixed", "PK"),
+             ("nmax", "NMAX")]
+    for ka, kb in pairs:
+        assert a[ka] == b[kb], (ka, a[ka], b[kb])
+
+
+def test_cell_geometry():
+    F = _lib()
+    for n, nc in ((1000, 19), (5000, 44), (50000, 141), (100000, 199)):
+        d = F.flock_derive(fi.default_params(fi.side_for(n)))
+        assert d["cells_per_side"] == nc
+        # cells are at least the view radius wide
+        assert d["side"] / d["cells_per_side"] >= 5.0
+    d2 = F.flock_derive(fi.default_params(fi.side_for(50000)), {"stencil": 2})
+    assert d2["cells_per_side"] == 282 and d2["stencil"] == 2
