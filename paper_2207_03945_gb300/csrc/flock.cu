@@ -162,8 +162,12 @@ int derive(const flock_params &p, int stencil, Inst &I, flock_derived *D) {
   if (stencil != 1 && stencil != 2) return FLOCK_EINVAL;
   const double wmin = ((double)rv * (1.0 + ldexp(1.0, -20)) + (double)p.side * ldexp(1.0, -21)) /
                       (double)stencil;
+  // Fewer than 2h+1 cells per side is fine: a stencil then visits some cell
+  // twice under different periodic shifts, but with L > 2 d_v at most one
+  // image of a neighbour can lie within d_v, so nothing is counted twice.
+  // The halo wraps by one period only, which needs nc >= h.
   const double ncd = floor((double)p.side / wmin);
-  if (ncd < 2 * stencil + 1 || ncd * ncd > (double)kMaxScanTiles * kScanTile) return FLOCK_EINVAL;
+  if (ncd < stencil || ncd * ncd > (double)kMaxScanTiles * kScanTile) return FLOCK_EINVAL;
   I.nc = (int)ncd;
   I.ncells = I.nc * I.nc;
   I.halo = stencil;
@@ -385,6 +389,13 @@ extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, v
   int g = (n + 255) / 256;
   e->scatter_grid = g < 1 ? 1 : (g > 4 * sms ? 4 * sms : g);
   e->smemD = phaseD_smem_bytes(e->inst.cap, e->inst.v, e->tuning.block);
+  int smem_max = 0;
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e->smemD + sizeof(Inst) + 1024 > (size_t)smem_max) {
+    cudaStreamDestroy(e->cap_stream);
+    delete e;
+    return FLOCK_EINVAL;  // launch shape too large for this many sectors
+  }
   // descriptor and cleared scratch, in stream order
   cudaStream_t s = e->stream;
   cudaError_t c1 = cudaMemcpyAsync(e->ws + L.inst, &e->inst, sizeof(Inst), cudaMemcpyHostToDevice, s);
@@ -411,18 +422,18 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, float 
   const Inst *gI = (const Inst *)(e->ws + e->lay.inst);
   const int n = e->n;
   const bool tm = e->timing != 0;
-  if (tm) CK(cudaEventRecord(e->ev[0], s));
+  if (tm) CK(cudaEventRecordWithFlags(e->ev[0], s, cudaEventRecordExternal));
   if (n > 0) {
     k_apply_bin<<<(n + 255) / 256, 256, 0, s>>>(gI, B, reset);
     CK(cudaGetLastError());
   }
-  if (tm) CK(cudaEventRecord(e->ev[1], s));
+  if (tm) CK(cudaEventRecordWithFlags(e->ev[1], s, cudaEventRecordExternal));
   k_scan<<<e->n_scan_tiles, 256, 0, s>>>(B);
   CK(cudaGetLastError());
-  if (tm) CK(cudaEventRecord(e->ev[2], s));
+  if (tm) CK(cudaEventRecordWithFlags(e->ev[2], s, cudaEventRecordExternal));
   k_scatter<<<e->scatter_grid, 256, 0, s>>>(B);
   CK(cudaGetLastError());
-  if (tm) CK(cudaEventRecord(e->ev[3], s));
+  if (tm) CK(cudaEventRecordWithFlags(e->ev[3], s, cudaEventRecordExternal));
   if (n > 0) {
     const int tiles = e->inst.tiles_x * e->inst.tiles_y;
     if (e->inst.halo == 1)
@@ -431,7 +442,7 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, float 
       k_neighbours<2><<<tiles, e->tuning.block, e->smemD, s>>>(gI, B);
     CK(cudaGetLastError());
   }
-  if (tm) CK(cudaEventRecord(e->ev[4], s));
+  if (tm) CK(cudaEventRecordWithFlags(e->ev[4], s, cudaEventRecordExternal));
   return FLOCK_OK;
 }
 

@@ -277,46 +277,86 @@ __device__ __forceinline__ void phaseC_cell(int c, const Bufs &B, const int *tp)
 
 // ---------------------------------------------------------------------------
 // Phase D: neighbour scan of one tile of cells.
+//
+// Layout of one tile: the block stages the tile's cells plus an H-cell halo
+// (H = 1 for the 3 x 3 stencil, 2 for 5 x 5) from the cell-sorted positions
+// into shared memory, row by row, each staged row being at most three
+// contiguous runs of the sorted array (left halo across the periodic
+// boundary, interior, right halo).  Every staged agent carries the periodic
+// shift (0 or +-L per axis) that places its cell next to the tile.
+//
+// The tile's own agents are split evenly over the warps.  A warp takes up to
+// 32 of them (one per lane) and
+//   1. scans the candidates: each lane walks its 2H+1 stencil rows (each a
+//      contiguous staged range), computes the minimum-image offset and d^2,
+//      and appends in-range pairs (dx, dy, d^2, owner lane) to a per-warp
+//      queue in shared memory (ballot compaction);
+//   2. drains the queue 32 pairs at a time with every lane busy: collision
+//      test, reward term, direction in the field-of-view frame, pseudo-angle
+//      and sector; the pairs of one owner (and of one owner's sector) are
+//      combined with __match_any_sync / __reduce_*_sync and a single lane
+//      updates the owner's accumulators -- no atomics;
+//   3. writes each agent's observation, reward and collision count at the
+//      agent's own row.
+// A tile whose staged agents exceed the shared buffer (a dense cluster) is
+// processed by the direct per-thread path, reading the sorted arrays.
 // ---------------------------------------------------------------------------
-struct Acc {
-  long long acc;  // reward sum in units of 2^-K
-  int nin, ncoll;
-};
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kQueue = 128;  // queued pairs per warp
 
-// One candidate pair with its minimum-image offset (dx, dy) from the centre
-// agent.  md/cn: this thread's per-sector minimum d^2 and count (strided by
-// the block size in shared memory).
-__device__ __forceinline__ void pair_core(float dx, float dy, const Inst &I, float ux, float uy,
-                                          Acc &a, float *md, int *cn, int stride,
-                                          const float *T) {
-  const float d2 = fadd(fmul(dx, dx), fmul(dy, dy));
-  if (!(d2 < I.RV2)) return;  // Eq. 1: d_ij < d_v
-  a.nin++;
-  if (d2 < I.RC2) {  // Fig. 4: collision below 2 d_r
-    a.ncoll++;
-    a.acc -= I.PK;
-  } else {
-    const float t = fmul(fsub(I.RV, fsqrt(d2)), I.INV_SPAN);
-    a.acc += __float2ll_rn(fmul(t, I.scaleK));  // exact: t is a multiple of 2^-K
-  }
-  // direction in the frame of the field of view's start edge
-  const float lx = fadd(fmul(dx, ux), fmul(dy, uy));
-  const float ly = fsub(fmul(dy, ux), fmul(dx, uy));
-  if (lx == 0.0f && ly == 0.0f) return;
-  float p = pseudo_angle(lx, ly);
-  if (p >= 4.0f) p = 0.0f;
-  if (!I.full && p >= T[I.v]) return;
-  // k = number of edges T[1..v-1] at or below p (T is non-decreasing)
-  int lo = 0, hi = I.v - 1;
+// x is an integer-valued float in [2^23, 2^62) or 0: its value as an
+// integer, with 32-bit integer operations only (a float -> int64 conversion
+// would run on the FP64 pipe).
+__device__ __forceinline__ unsigned long long float_int_u64(float x) {
+  const unsigned u = __float_as_uint(x);
+  if (u == 0u) return 0ull;
+  const unsigned m = (u & 0x7fffffu) | 0x800000u;
+  return (unsigned long long)m << ((int)(u >> 23) - 150);
+}
+
+// Sector of pseudo-angle p: number of edges T[1..v-1] at or below p.
+__device__ __forceinline__ int sector_of(float p, const float *T, int v) {
+  int lo = 0, hi = v - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (p >= T[mid]) lo = mid;
     else hi = mid - 1;
   }
-  float *m = md + lo * stride;
-  if (d2 < *m) *m = d2;
-  cn[lo * stride] += 1;
+  return lo;
 }
+
+struct Acc {
+  unsigned long long acc;  // sum of ramp terms in units of 2^-K
+  int nin, ncoll;
+};
+
+// Direct path: one candidate pair with its minimum-image offset (dx, dy).
+// md/cn: this thread's per-sector minimum d^2 (as bits) and count, strided.
+__device__ __forceinline__ void pair_core(float dx, float dy, const Inst &I, float ux, float uy,
+                                          Acc &a, unsigned *md, int *cn, int stride) {
+  const float d2 = fadd(fmul(dx, dx), fmul(dy, dy));
+  if (!(d2 < I.RV2)) return;  // Eq. 1: d_ij < d_v
+  a.nin++;
+  if (d2 < I.RC2) {  // Fig. 4: collision below 2 d_r
+    a.ncoll++;
+  } else {
+    const float t = fmul(fsub(I.RV, fsqrt(d2)), I.INV_SPAN);
+    a.acc += float_int_u64(fmul(t, I.scaleK));  // exact: t is a multiple of 2^-K
+  }
+  const float lx = fadd(fmul(dx, ux), fmul(dy, uy));
+  const float ly = fsub(fmul(dy, ux), fmul(dx, uy));
+  if (lx == 0.0f && ly == 0.0f) return;  // coincident: no direction
+  float p = pseudo_angle(lx, ly);
+  if (p >= 4.0f) p = 0.0f;
+  if (!I.full && p >= I.T[I.v]) return;  // outside the field of view
+  const int k = sector_of(p, I.T, I.v);
+  unsigned *m = md + k * stride;
+  const unsigned db = __float_as_uint(d2);
+  if (db < *m) *m = db;
+  cn[k * stride] += 1;
+}
+
+__device__ __forceinline__ int wrapi(int c, int nc) { return c < 0 ? c + nc : (c >= nc ? c - nc : c); }
 
 // Cooperative copy of a descriptor into shared memory (call, then sync).
 __device__ __forceinline__ void load_inst(Inst &dst, const Inst *src) {
@@ -325,29 +365,153 @@ __device__ __forceinline__ void load_inst(Inst &dst, const Inst *src) {
   for (int k = threadIdx.x; k < (int)(sizeof(Inst) / 4); k += blockDim.x) d[k] = s[k];
 }
 
-__device__ __forceinline__ int wrapi(int c, int nc) { return c < 0 ? c + nc : (c >= nc ? c - nc : c); }
+// Output of one agent from its accumulators.
+__device__ __forceinline__ void write_agent(const Inst &I, const Bufs &B, int i, float s,
+                                           float th, unsigned long long acc, int ncoll, int nin,
+                                           const unsigned *md, const int *cn, int stride,
+                                           unsigned &err) {
+  float *o = B.obs + I.obs_base + (long long)i * I.obs_dim;
+  for (int k = 0; k < I.v; ++k) {
+    const int ck = cn[k * stride];
+    const float dk = ck ? fsqrt(__uint_as_float(md[k * stride])) : I.RV;
+    *reinterpret_cast<float2 *>(o + 2 * k) = make_float2(dk, (float)ck);
+  }
+  *reinterpret_cast<float2 *>(o + 2 * I.v) = make_float2(s, th);
+  const long long total = (long long)acc - (long long)ncoll * I.PK;
+  B.reward[I.agent_base + i] = fmul(__ll2float_rn(total), I.inv_scaleK);
+  B.coll[I.agent_base + i] = ncoll;
+  if ((long long)nin > I.NMAX) err |= FLOCK_ERR_OVERFLOW;
+}
 
-// Shared memory of phase D (dynamic).  Layout, in bytes from the base:
+// Shared memory of phase D (dynamic), in bytes from the base:
 //   float4 stg[cap]                      staged candidates (x, y, shift_x, shift_y)
 //   int    cs[kMaxStagedCells + 1]       staged-cell prefix (row-major)
-//   int    wsum[33]
-//   float  md[v * blockDim]; int cn[v * blockDim]
+//   int    wsum[36]
+//   per warp: float4 queue[kQueue]; u64 acc[32]; int ncoll[32], nin[32];
+//             u32 md[32 * v]; int cn[32 * v]
 // I must be the block's shared-memory copy of the instance descriptor.
+__host__ __device__ inline size_t phaseD_warp_bytes(int v) {
+  return (size_t)kQueue * 16 + 32 * 8 + 32 * 4 * 2 + (size_t)32 * v * 8;
+}
+// bytes of the staged-cell prefix plus the scan scratch, rounded to 16
+constexpr size_t kCsBytes = (((size_t)(kMaxStagedCells + 1) * 4 + 36 * 4) + 15) & ~(size_t)15;
 __host__ __device__ inline size_t phaseD_smem_bytes(int cap, int v, int block) {
-  return (size_t)cap * 16 + (size_t)(kMaxStagedCells + 1) * 4 + 33 * 4 + (size_t)v * block * 8;
+  return (size_t)cap * 16 + kCsBytes + (size_t)(block / 32) * phaseD_warp_bytes(v);
+}
+
+struct WarpArea {
+  float4 *queue;
+  unsigned long long *acc;
+  int *ncoll, *nin;
+  unsigned *md;
+  int *cn;
+};
+
+// Drain `count` queued pairs (warp-uniform); ux/uy: this lane's own agent.
+__device__ __forceinline__ void drain(const Inst &I, const WarpArea &W, int count, float ux,
+                                     float uy) {
+  const int lane = threadIdx.x & 31;
+  const int v = I.v;
+  for (int e0 = 0; e0 < count; e0 += 32) {
+    const int e = e0 + lane;
+    const bool valid = e < count;
+    float4 E = valid ? W.queue[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int o = valid ? __float_as_int(E.w) : lane;
+    const float uxo = __shfl_sync(kFull, ux, o), uyo = __shfl_sync(kFull, uy, o);
+    const float dx = E.x, dy = E.y, d2 = E.z;
+    const bool coll = valid && d2 < I.RC2;
+    unsigned long long tv = 0ull;
+    if (valid && !coll) {
+      const float t = fmul(fsub(I.RV, fsqrt(d2)), I.INV_SPAN);
+      tv = float_int_u64(fmul(t, I.scaleK));
+    }
+    int key = -1;
+    if (valid) {
+      const float lx = fadd(fmul(dx, uxo), fmul(dy, uyo));
+      const float ly = fsub(fmul(dy, uxo), fmul(dx, uyo));
+      if (lx != 0.0f || ly != 0.0f) {
+        float p = pseudo_angle(lx, ly);
+        if (p >= 4.0f) p = 0.0f;
+        if (I.full || p < I.T[v]) key = sector_of(p, I.T, v);
+      }
+    }
+    // reward, collisions and in-range count: one group per owner
+    const unsigned mo = __match_any_sync(kFull, valid ? o : 64 + lane);
+    const unsigned s0 = __reduce_add_sync(mo, (unsigned)(tv & 0xffffffull));
+    const unsigned s1 = __reduce_add_sync(mo, (unsigned)((tv >> 24) & 0xffffffull));
+    const unsigned s2 = __reduce_add_sync(mo, (unsigned)(tv >> 48));
+    const unsigned sc = __reduce_add_sync(mo, coll ? 1u : 0u);
+    if (valid && lane == __ffs(mo) - 1) {
+      W.acc[o] += (unsigned long long)s0 + ((unsigned long long)s1 << 24) +
+                  ((unsigned long long)s2 << 48);
+      W.ncoll[o] += (int)sc;
+      W.nin[o] += __popc(mo);
+    }
+    // sector minimum and count: one group per (owner, sector)
+    const bool seen = key >= 0;
+    const unsigned mk = __match_any_sync(kFull, seen ? (o << 8) | key : (1 << 20) + lane);
+    const unsigned mn = __reduce_min_sync(mk, __float_as_uint(d2));
+    if (seen && lane == __ffs(mk) - 1) {
+      unsigned *m = W.md + o * v + key;
+      if (mn < *m) *m = mn;
+      W.cn[o * v + key] += __popc(mk);
+    }
+    __syncwarp();
+  }
+}
+
+// Candidate scan of one lane's stencil rows (smem ranges [ra[r], ra[r]+rn[r])),
+// appending in-range pairs to the warp queue; drains when nearly full.
+template <int H, bool WRAP>
+__device__ __forceinline__ void scan_rows(const Inst &I, const WarpArea &W, const float4 *stg,
+                                          const int *ra, const int *rn, int self, float xi,
+                                          float yi, float ux, float uy) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  int qn = 0;
+#pragma unroll
+  for (int r = 0; r < 2 * H + 1; ++r) {
+    const int n = rn[r];
+    const int maxn = __reduce_max_sync(kFull, (unsigned)n);
+    for (int j = 0; j < maxn; ++j) {
+      const int q = ra[r] + j;
+      bool inr = false;
+      float dx = 0.f, dy = 0.f, d2 = 0.f;
+      if (j < n && q != self) {
+        const float4 e = stg[q];
+        dx = fsub(e.x, xi);
+        dy = fsub(e.y, yi);
+        if (WRAP) {
+          dx = fadd(dx, e.z);
+          dy = fadd(dy, e.w);
+        }
+        d2 = fadd(fmul(dx, dx), fmul(dy, dy));
+        inr = d2 < I.RV2;  // Eq. 1: d_ij < d_v
+      }
+      const unsigned m = __ballot_sync(kFull, inr);
+      if (inr) W.queue[qn + __popc(m & lt)] = make_float4(dx, dy, d2, __int_as_float(lane));
+      qn += __popc(m);
+      if (qn > kQueue - 32) {
+        __syncwarp();
+        drain(I, W, qn, ux, uy);
+        qn = 0;
+      }
+    }
+  }
+  __syncwarp();
+  drain(I, W, qn, ux, uy);
 }
 
 template <int H>
 __device__ void phaseD_tile(const Inst &I, int tx, int ty, const Bufs &B, char *smem,
                             unsigned &err) {
   const int tid = threadIdx.x, nthr = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
   float4 *stg = reinterpret_cast<float4 *>(smem);
   int *cs = reinterpret_cast<int *>(smem + (size_t)I.cap * 16);
   int *wsum = cs + kMaxStagedCells + 1;
-  float *md = reinterpret_cast<float *>(wsum + 33);
-  int *cn = reinterpret_cast<int *>(md + (size_t)I.v * nthr);
-  const float *T = I.T;
-  const int nc = I.nc;
+  char *wbase = smem + (size_t)I.cap * 16 + kCsBytes;  // 16-byte aligned
+  const int nc = I.nc, v = I.v;
   const int c0 = tx * I.tile_w, c1 = min(c0 + I.tile_w, nc);
   const int r0 = ty * I.tile_h, r1 = min(r0 + I.tile_h, nc);
   const int tw = c1 - c0, th = r1 - r0;
@@ -364,11 +528,11 @@ __device__ void phaseD_tile(const Inst &I, int tx, int ty, const Bufs &B, char *
   block_excl_scan_inplace(cs, ncell, wsum);
   const int staged = cs[ncell];
   const bool use_smem = staged <= I.cap;
+  const bool wraps = c0 - H < 0 || c1 + H > nc || r0 - H < 0 || r1 + H > nc;
 
   if (use_smem) {
-    // copy: each staged row is at most three contiguous runs of sorted
-    // positions (left halo across the boundary, interior, right halo)
-    for (int sr = 0; sr < nsr; ++sr) {
+    // one warp per staged row; a row is at most three contiguous runs
+    for (int sr = warp; sr < nsr; sr += nwarps) {
       const int vr = r0 - H + sr;
       const float sy = vr < 0 ? -I.L : (vr >= nc ? I.L : 0.0f);
       const int rowg = I.cell_base + wrapi(vr, nc) * nc;
@@ -381,9 +545,9 @@ __device__ void phaseD_tile(const Inst &I, int tx, int ty, const Bufs &B, char *
         else if (part == 1) { a = max(vlo, 0); b = min(vhi, nc); off = 0; sx = 0.0f; }
         else { a = max(vlo, nc); b = vhi; off = -nc; sx = I.L; }
         if (a >= b) continue;
-        const int gs = cst[rowg + a + off], ge = cst[rowg + b - 1 + off + 1];
+        const int gs = cst[rowg + a + off], ge = cst[rowg + b + off];
         const int ss = cs[sr * nsc + (a - vlo)];
-        for (int q = tid; q < ge - gs; q += nthr) {
+        for (int q = lane; q < ge - gs; q += 32) {
           const float2 pxy = B.sxy[gs + q];
           stg[ss + q] = make_float4(pxy.x, pxy.y, sx, sy);
         }
@@ -392,15 +556,86 @@ __device__ void phaseD_tile(const Inst &I, int tx, int ty, const Bufs &B, char *
   }
   __syncthreads();
 
-  // centre agents: the tile's own cells, row by row
+  // the tile's own agents, counted row by row
   int ncent = 0;
   for (int r = 0; r < th; ++r) {
     const int rg = I.cell_base + (r0 + r) * nc;
     ncent += cst[rg + c1] - cst[rg + c0];
   }
-  for (int a0 = 0; a0 < ncent; a0 += nthr) {
-    const int a = a0 + tid;
-    if (a < ncent) {
+
+  if (use_smem) {
+    WarpArea W;
+    char *wp = wbase + (size_t)warp * phaseD_warp_bytes(v);
+    W.queue = reinterpret_cast<float4 *>(wp);
+    W.acc = reinterpret_cast<unsigned long long *>(wp + kQueue * 16);
+    W.ncoll = reinterpret_cast<int *>(wp + kQueue * 16 + 32 * 8);
+    W.nin = W.ncoll + 32;
+    W.md = reinterpret_cast<unsigned *>(W.nin + 32);
+    W.cn = reinterpret_cast<int *>(W.md + 32 * v);
+    // contiguous, even share of the tile's agents per warp
+    const int per = (ncent + nwarps - 1) / nwarps;
+    const int wa0 = warp * per, wa1 = min(wa0 + per, ncent);
+    for (int b0 = wa0; b0 < wa1; b0 += 32) {
+      const int a = b0 + lane;
+      const bool have = a < wa1;
+      int self = -1, i = 0, sr = 0, lc = 0;
+      float4 me = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (have) {
+        int r = 0, al = a, rg = 0, rlen = 0;
+        for (;; ++r) {
+          rg = I.cell_base + (r0 + r) * nc;
+          rlen = cst[rg + c1] - cst[rg + c0];
+          if (al < rlen) break;
+          al -= rlen;
+        }
+        sr = r + H;
+        self = cs[sr * nsc + H] + al;  // interior run of the row, in sorted order
+        i = B.sidx[cst[rg + c0] + al] - I.agent_base;
+        me = I.state[i];
+        lc = cell_of(me.x, I) - c0 + H;
+      }
+      float c = 1.f, sn = 0.f;
+      det_sincos(me.z, c, sn);
+      const float ux = fadd(fmul(c, I.CF), fmul(sn, I.SF));
+      const float uy = fsub(fmul(sn, I.CF), fmul(c, I.SF));
+      W.acc[lane] = 0ull;
+      W.ncoll[lane] = 0;
+      W.nin[lane] = 0;
+      for (int k = 0; k < v; ++k) {
+        W.md[lane * v + k] = 0x7f800000u;
+        W.cn[lane * v + k] = 0;
+      }
+      int ra[2 * H + 1], rn[2 * H + 1];
+#pragma unroll
+      for (int r = 0; r < 2 * H + 1; ++r) {
+        if (have) {
+          const int row = sr - H + r;
+          ra[r] = cs[row * nsc + lc - H];
+          rn[r] = cs[row * nsc + lc + H + 1] - ra[r];
+        } else {
+          ra[r] = 0;
+          rn[r] = 0;
+        }
+      }
+      __syncwarp();
+      if (wraps)
+        scan_rows<H, true>(I, W, stg, ra, rn, self, me.x, me.y, ux, uy);
+      else
+        scan_rows<H, false>(I, W, stg, ra, rn, self, me.x, me.y, ux, uy);
+      __syncwarp();
+      if (have)
+        write_agent(I, B, i, me.w, me.z, W.acc[lane], W.ncoll[lane], W.nin[lane],
+                    W.md + lane * v, W.cn + lane * v, 1, err);
+      __syncwarp();
+    }
+  } else {
+    // dense tile: per-thread scan straight from the sorted arrays, with the
+    // per-sector accumulators strided by the block size
+    unsigned *md = reinterpret_cast<unsigned *>(wbase);
+    int *cn = reinterpret_cast<int *>(md + (size_t)v * nthr);
+    for (int a0 = 0; a0 < ncent; a0 += nthr) {
+      const int a = a0 + tid;
+      if (a >= ncent) continue;
       int r = 0, al = a, rg = 0, rlen = 0;
       for (;; ++r) {
         rg = I.cell_base + (r0 + r) * nc;
@@ -408,72 +643,40 @@ __device__ void phaseD_tile(const Inst &I, int tx, int ty, const Bufs &B, char *
         if (al < rlen) break;
         al -= rlen;
       }
-      const int gp = cst[rg + c0] + al;  // global sorted position
-      const int f = B.sidx[gp];
-      const int i = f - I.agent_base;
+      const int gp = cst[rg + c0] + al;
+      const int i = B.sidx[gp] - I.agent_base;
       const float4 me = I.state[i];
-      const float xi = me.x, yi = me.y;
       float c, sn;
       det_sincos(me.z, c, sn);
       const float ux = fadd(fmul(c, I.CF), fmul(sn, I.SF));
       const float uy = fsub(fmul(sn, I.CF), fmul(c, I.SF));
-      const int cx = cell_of(xi, I);
-      float *mdt = md + tid;
-      int *cnt = cn + tid;
-      for (int k = 0; k < I.v; ++k) {
-        mdt[k * nthr] = __int_as_float(0x7f800000);
-        cnt[k * nthr] = 0;
+      const int cx = cell_of(me.x, I);
+      for (int k = 0; k < v; ++k) {
+        md[k * nthr + tid] = 0x7f800000u;
+        cn[k * nthr + tid] = 0;
       }
-      Acc acc{0, 0, 0};
-      if (use_smem) {
-        const int sr = r + H, lc = cx - c0 + H;
-        // the centre agent's own staged slot: the interior run of its row
-        // holds the row's tile cells in sorted order
-        const int q = cs[sr * nsc + H] + al;
-        for (int dr = -H; dr <= H; ++dr) {
-          const int srow = sr + dr;
-          const int qa = cs[srow * nsc + lc - H], qb = cs[srow * nsc + lc + H + 1];
-          for (int qq = qa; qq < qb; ++qq) {
-            if (qq == q) continue;
-            const float4 e = stg[qq];
-            const float dx = fadd(fsub(e.x, xi), e.z);
-            const float dy = fadd(fsub(e.y, yi), e.w);
-            pair_core(dx, dy, I, ux, uy, acc, mdt, cnt, nthr, T);
-          }
-        }
-      } else {
-        // dense tile: read candidates straight from the sorted arrays
-        const int cy = r0 + r;
-        for (int dr = -H; dr <= H; ++dr) {
-          const int vr = cy + dr;
-          const float sy = vr < 0 ? -I.L : (vr >= nc ? I.L : 0.0f);
-          const int rowg = I.cell_base + wrapi(vr, nc) * nc;
-          for (int dc = -H; dc <= H; ++dc) {
-            const int vc = cx + dc;
-            const float sx = vc < 0 ? -I.L : (vc >= nc ? I.L : 0.0f);
-            const int g = rowg + wrapi(vc, nc);
-            const int ga = cst[g], gb = cst[g + 1];
-            for (int gq = ga; gq < gb; ++gq) {
-              if (gq == gp) continue;
-              const float2 pxy = B.sxy[gq];
-              const float dx = fadd(fsub(pxy.x, xi), sx);
-              const float dy = fadd(fsub(pxy.y, yi), sy);
-              pair_core(dx, dy, I, ux, uy, acc, mdt, cnt, nthr, T);
-            }
+      Acc acc{0ull, 0, 0};
+      const int cy = r0 + r;
+      for (int dr = -H; dr <= H; ++dr) {
+        const int vr = cy + dr;
+        const float sy = vr < 0 ? -I.L : (vr >= nc ? I.L : 0.0f);
+        const int rowg = I.cell_base + wrapi(vr, nc) * nc;
+        for (int dc = -H; dc <= H; ++dc) {
+          const int vc = cx + dc;
+          const float sx = vc < 0 ? -I.L : (vc >= nc ? I.L : 0.0f);
+          const int g = rowg + wrapi(vc, nc);
+          const int ga = cst[g], gb = cst[g + 1];
+          for (int gq = ga; gq < gb; ++gq) {
+            if (gq == gp) continue;
+            const float2 pxy = B.sxy[gq];
+            const float dx = fadd(fsub(pxy.x, me.x), sx);
+            const float dy = fadd(fsub(pxy.y, me.y), sy);
+            pair_core(dx, dy, I, ux, uy, acc, md + tid, cn + tid, nthr);
           }
         }
       }
-      // outputs at the agent's own row
-      float *o = B.obs + I.obs_base + (long long)i * I.obs_dim;
-      for (int k = 0; k < I.v; ++k) {
-        const int ck = cnt[k * nthr];
-        const float dk = ck ? fsqrt(mdt[k * nthr]) : I.RV;
-        *reinterpret_cast<float2 *>(o + 2 * k) = make_float2(dk, (float)ck);
-      }
-      *reinterpret_cast<float2 *>(o + 2 * I.v) = make_float2(me.w, me.z);
-      B.reward[I.agent_base + i] = fmul(__ll2float_rn(acc.acc), I.inv_scaleK);
-      B.coll[I.agent_base + i] = acc.ncoll;
-      if ((long long)acc.nin > I.NMAX) err |= FLOCK_ERR_OVERFLOW;
+      write_agent(I, B, i, me.w, me.z, acc.acc, acc.ncoll, acc.nin, md + tid, cn + tid, nthr,
+                  err);
     }
   }
   __syncthreads();  // smem is reused by the next tile

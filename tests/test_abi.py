@@ -64,8 +64,11 @@ def test_invalid_params_rejected():
             F.flock_derive(dict(fi.default_params(100.0), **bad))
     with pytest.raises(F.FlockError):
         F.flock_workspace_bytes(fi.default_params(100.0), -1)
-    with pytest.raises(F.FlockError):  # 5 x 5 stencil needs 5 cells per side
-        F.flock_derive(fi.default_params(11.0), {"stencil": 2})
+    with pytest.raises(F.FlockError):
+        F.flock_derive(fi.default_params(100.0), {"stencil": 3})
+    # a square just over 2 d_v wide still has a cell list (one or two cells per side)
+    assert F.flock_derive(fi.default_params(10.5))["cells_per_side"] == 2
+    assert F.flock_derive(fi.default_params(10.5), {"stencil": 2})["cells_per_side"] == 4
     with pytest.raises(F.FlockError):
         F.flock_workspace_bytes(fi.default_params(100.0), 10, {"block": 48})
 

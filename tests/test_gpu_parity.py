@@ -162,15 +162,17 @@ def test_launch_shapes_are_bit_identical(tuning):
     assert_same(g, o, str(tuning))
 
 
-def test_small_square_wraps_everywhere():
-    # side 11 with d_v 5: three cells per axis, every stencil wraps
+@pytest.mark.parametrize("side,stencil", [(11.0, 1), (10.5, 1), (10.5, 2), (16.0, 1), (26.0, 2)])
+def test_small_square_wraps_everywhere(side, stencil):
+    # squares only just wider than 2 d_v: one to five cells per axis, every
+    # stencil wraps and some visit a cell twice under different shifts
     n, steps = 60, 10
-    p = fi.default_params(11.0)
-    st0 = fi.initial_state(n, 11.0, 5)
+    p = fi.default_params(side)
+    st0 = fi.initial_state(n, side, 5)
     acts = fi.random_actions(n, steps, 5)
-    g, _, _ = gpu_run(p, st0, acts)
+    g, _, _ = gpu_run(p, st0, acts, {"stencil": stencil})
     o, _ = oracle_run(p, st0, acts)
-    assert_same(g, o, "side 11")
+    assert_same(g, o, "side %g" % side)
 
 
 def test_dense_cluster_exceeds_shared_memory():
