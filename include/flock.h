@@ -86,9 +86,12 @@ typedef struct flock_params {
  * choice).  Results are identical for every valid setting. */
 typedef struct flock_tuning {
   int stencil; /* 1: cells of width >= d_v, 3 x 3 stencil; 2: width >= d_v/2, 5 x 5 */
-  int tile_w;  /* cells per tile along x, 1..64 */
-  int tile_h;  /* cells per tile along y, 1..8 */
+  int tile_w;  /* mode 1: cells per tile along x, 1..64 */
+  int tile_h;  /* mode 1: cells per tile along y, 1..8 */
   int block;   /* threads per block, multiple of 32 in 64..512 */
+  int mode;    /* neighbour scan: 1 = tiles of cells staged in shared memory,
+                  2 = each warp takes 32 consecutive cell-sorted agents and
+                  reads their stencil cells through the L1 cache */
 } flock_tuning;
 
 /* Constants the library derives from flock_params (host, double precision

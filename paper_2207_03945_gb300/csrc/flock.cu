@@ -32,13 +32,14 @@ __global__ void __launch_bounds__(256) k_scan(Bufs B) {
   phaseB_tile(blockIdx.x, B, sm);
 }
 
-__global__ void __launch_bounds__(256) k_scatter(Bufs B) {
+__global__ void __launch_bounds__(256) k_scatter(const Inst *__restrict__ gI, Bufs B) {
   __shared__ int tp[kMaxScanTiles + 1];
   __shared__ int wsum[33];
   tile_prefix(B, tp, wsum);
+  const float4 *state = gI->state;
   const int stride = gridDim.x * blockDim.x;
   for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < B.n_total; f += stride)
-    phaseC_agent(f, B, tp);
+    phaseC_agent(f, state + f, B, tp);
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= B.c_total; c += stride)
     phaseC_cell(c, B, tp);
 }
@@ -52,6 +53,22 @@ __global__ void k_neighbours(const Inst *__restrict__ gI, Bufs B) {
   unsigned err = 0;
   const int t = blockIdx.x;
   phaseD_tile<H>(sI, t % sI.tiles_x, t / sI.tiles_x, B, smem, err);
+  if (err) atomicOr(B.err, err);
+}
+
+template <int H>
+__global__ void k_neighbours_direct(const Inst *__restrict__ gI, Bufs B) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ Inst sI;
+  load_inst(sI, gI);
+  __syncthreads();
+  unsigned err = 0;
+  const int warp = threadIdx.x >> 5;
+  const int gp0 = (blockIdx.x * (blockDim.x >> 5) + warp) * 32;
+  if (gp0 < sI.n) {
+    const DirectArea W = direct_area(smem + (size_t)warp * direct_warp_bytes(sI.v), sI.v);
+    phaseD_direct<H>(sI, gp0, min(gp0 + 32, sI.n), B, W, err);
+  }
   if (err) atomicOr(B.err, err);
 }
 
@@ -192,6 +209,8 @@ int choose_tuning(const Inst &I, int n, const flock_tuning *req, flock_tuning &t
   flock_tuning r{};
   if (req) r = *req;
   t.stencil = I.halo;
+  t.mode = r.mode ? r.mode : 2;
+  if (t.mode != 1 && t.mode != 2) return FLOCK_EINVAL;
   t.block = r.block ? r.block : 128;
   if (t.block < 64 || t.block > 512 || t.block % 32) return FLOCK_EINVAL;
   const double w = (double)I.L / I.nc;
@@ -219,8 +238,8 @@ void set_tiles(Inst &I, int n, const flock_tuning &t) {
   const double w = (double)I.L / I.nc;
   const double per_cell = n > 0 ? (double)n / ((double)I.L * I.L) * w * w : 0.0;
   const double staged = (t.tile_w + 2.0 * I.halo) * (t.tile_h + 2.0 * I.halo) * per_cell;
-  int cap = (int)(4.0 * staged) + 256;
-  cap = cap < 512 ? 512 : (cap > 4096 ? 4096 : cap);
+  int cap = (int)(2.0 * staged) + 128;
+  cap = cap < 256 ? 256 : (cap > 4096 ? 4096 : cap);
   I.cap = cap;
 }
 
@@ -236,7 +255,9 @@ cudaError_t set_kernel_attrs() {
     const int want = maxsm - (int)sizeof(Inst) - 1024;
     cudaError_t e1 = cudaFuncSetAttribute(k_neighbours<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
     cudaError_t e2 = cudaFuncSetAttribute(k_neighbours<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
-    g_attr_err = e1 != cudaSuccess ? e1 : e2;
+    cudaError_t e3 = cudaFuncSetAttribute(k_neighbours_direct<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+    cudaError_t e4 = cudaFuncSetAttribute(k_neighbours_direct<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+    g_attr_err = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : e4));
   });
   return g_attr_err;
 }
@@ -246,7 +267,7 @@ cudaError_t set_kernel_attrs() {
 using namespace flock;
 
 struct Layout {
-  size_t state, cellrank, counts, local, cell_start, tile_sum, sxy, sidx, inst, err, h_act, h_obs,
+  size_t state, cellrank, counts, local, cell_start, tile_sum, sxy, sts, sidx, inst, err, h_act, h_obs,
       h_rew, h_coll, total;
 };
 
@@ -256,12 +277,13 @@ static Layout make_layout(int n, int C, int D) {
   auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
   const int nT = (C + kScanTile - 1) / kScanTile;
   L.state = take((size_t)n * 16);
-  L.cellrank = take((size_t)n * 16);
+  L.cellrank = take((size_t)n * 8);
   L.counts = take((size_t)C * 4);
   L.local = take((size_t)C * 4);
   L.cell_start = take((size_t)(C + 1) * 4);
   L.tile_sum = take((size_t)(nT + 1) * 4);
   L.sxy = take((size_t)n * 8);
+  L.sts = take((size_t)n * 8);
   L.sidx = take((size_t)n * 4);
   L.inst = take(sizeof(Inst));
   L.err = take(64);
@@ -370,12 +392,13 @@ extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, v
   e->inst.cell_base = 0;
   e->inst.obs_base = 0;
   Bufs &B = e->bufs;
-  B.cellrank = (int4 *)(e->ws + L.cellrank);
+  B.cellrank = (int2 *)(e->ws + L.cellrank);
   B.counts = (int *)(e->ws + L.counts);
   B.local = (int *)(e->ws + L.local);
   B.cell_start = (int *)(e->ws + L.cell_start);
   B.tile_sum = (int *)(e->ws + L.tile_sum);
   B.sxy = (float2 *)(e->ws + L.sxy);
+  B.sts = (float2 *)(e->ws + L.sts);
   B.sidx = (int *)(e->ws + L.sidx);
   B.err = (unsigned *)(e->ws + L.err);
   B.bar = B.err + 4;
@@ -388,7 +411,9 @@ extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, v
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int g = (n + 255) / 256;
   e->scatter_grid = g < 1 ? 1 : (g > 4 * sms ? 4 * sms : g);
-  e->smemD = phaseD_smem_bytes(e->inst.cap, e->inst.v, e->tuning.block);
+  e->smemD = e->tuning.mode == 1
+                 ? phaseD_smem_bytes(e->inst.cap, e->inst.v, e->tuning.block)
+                 : (size_t)(e->tuning.block / 32) * direct_warp_bytes(e->inst.v);
   int smem_max = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e->smemD + sizeof(Inst) + 1024 > (size_t)smem_max) {
@@ -431,15 +456,24 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, float 
   k_scan<<<e->n_scan_tiles, 256, 0, s>>>(B);
   CK(cudaGetLastError());
   if (tm) CK(cudaEventRecordWithFlags(e->ev[2], s, cudaEventRecordExternal));
-  k_scatter<<<e->scatter_grid, 256, 0, s>>>(B);
+  k_scatter<<<e->scatter_grid, 256, 0, s>>>(gI, B);
   CK(cudaGetLastError());
   if (tm) CK(cudaEventRecordWithFlags(e->ev[3], s, cudaEventRecordExternal));
   if (n > 0) {
-    const int tiles = e->inst.tiles_x * e->inst.tiles_y;
-    if (e->inst.halo == 1)
-      k_neighbours<1><<<tiles, e->tuning.block, e->smemD, s>>>(gI, B);
-    else
-      k_neighbours<2><<<tiles, e->tuning.block, e->smemD, s>>>(gI, B);
+    if (e->tuning.mode == 1) {
+      const int tiles = e->inst.tiles_x * e->inst.tiles_y;
+      if (e->inst.halo == 1)
+        k_neighbours<1><<<tiles, e->tuning.block, e->smemD, s>>>(gI, B);
+      else
+        k_neighbours<2><<<tiles, e->tuning.block, e->smemD, s>>>(gI, B);
+    } else {
+      const int per_block = e->tuning.block;  // one agent per thread
+      const int blocks = (n + per_block - 1) / per_block;
+      if (e->inst.halo == 1)
+        k_neighbours_direct<1><<<blocks, e->tuning.block, e->smemD, s>>>(gI, B);
+      else
+        k_neighbours_direct<2><<<blocks, e->tuning.block, e->smemD, s>>>(gI, B);
+    }
     CK(cudaGetLastError());
   }
   if (tm) CK(cudaEventRecordWithFlags(e->ev[4], s, cudaEventRecordExternal));

@@ -48,12 +48,13 @@ struct Inst {
 
 // Scratch and output pointers of one step (flattened over all instances).
 struct Bufs {
-  int4 *cellrank;      // per agent: global cell, rank in cell, x bits, y bits
+  int2 *cellrank;      // per agent: global cell, rank in cell
   int *counts;         // per cell, zero between steps
   int *local;          // per cell: exclusive prefix within its scan tile
   int *cell_start;     // per cell + 1: first sorted position
   int *tile_sum;       // per scan tile: agents in the tile
-  float2 *sxy;         // cell-sorted positions
+  float2 *sxy;         // cell-sorted positions (x, y)
+  float2 *sts;         // cell-sorted (theta, s)
   int *sidx;           // cell-sorted flattened agent index
   unsigned *err;       // latched FLOCK_ERR_* bits
   unsigned *bar;       // grid barrier words (count, generation)
@@ -106,14 +107,17 @@ __device__ __forceinline__ void det_sincos(float th, float &c, float &s) {
 }
 
 // Pseudo-angle of direction (x, y) in [0, 4): one unit per quadrant,
-// counter-clockwise from +x, monotone in the true angle.
+// counter-clockwise from +x, monotone in the true angle.  Per quadrant q it
+// is q + n / d with d = |x| + |y| in all four quadrants and n = |y| (q even)
+// or |x| (q odd); written with one division and no branch, it gives the
+// same bits as the case-by-case form y/(x+y), 1+(-x)/(-x+y), 2+(-y)/(-x-y),
+// 3+x/(x-y).
 __device__ __forceinline__ float pseudo_angle(float x, float y) {
-  if (y >= 0.0f) {
-    if (x >= 0.0f) return fdiv(y, fadd(x, y));
-    return fadd(1.0f, fdiv(-x, fadd(-x, y)));
-  }
-  if (x < 0.0f) return fadd(2.0f, fdiv(-y, fsub(-x, y)));
-  return fadd(3.0f, fdiv(x, fsub(x, y)));
+  const bool yp = y >= 0.0f, xp = x >= 0.0f;
+  const int q = yp ? (xp ? 0 : 1) : (xp ? 3 : 2);
+  const float ax = fabsf(x), ay = fabsf(y);
+  const float num = (q & 1) ? ax : ay;
+  return fadd((float)q, fdiv(num, fadd(ax, ay)));
 }
 
 __device__ __forceinline__ float wrap_coord(float x, float L) {
@@ -161,7 +165,7 @@ __device__ __forceinline__ int cell_of(float x, const Inst &I) {
 // Phase A: apply + bin one agent (instance-local index i).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void phaseA_agent(const Inst &I, int i, const int32_t *actions_inst,
-                                             int reset, int *counts, int4 *cellrank,
+                                             int reset, int *counts, int2 *cellrank,
                                              unsigned &err) {
   float4 st = I.state[i];
   if (!state_ok(st, I)) err |= FLOCK_ERR_STATE;
@@ -179,7 +183,7 @@ __device__ __forceinline__ void phaseA_agent(const Inst &I, int i, const int32_t
   if (lane == leader) base = atomicAdd(&counts[g], __popc(peers));
   base = __shfl_sync(peers, base, leader);
   const int rank = base + __popc(peers & ((1u << lane) - 1u));
-  cellrank[I.agent_base + i] = make_int4(g, rank, __float_as_int(st.x), __float_as_int(st.y));
+  cellrank[I.agent_base + i] = make_int2(g, rank);
 }
 
 // ---------------------------------------------------------------------------
@@ -263,11 +267,15 @@ __device__ __forceinline__ void tile_prefix(const Bufs &B, int *tp, int *wsum) {
   block_excl_scan_inplace(tp, B.n_scan_tiles, wsum);
 }
 
-// Phase C for one flattened agent f: scatter into cell order.
-__device__ __forceinline__ void phaseC_agent(int f, const Bufs &B, const int *tp) {
-  const int4 cr = B.cellrank[f];
+// Phase C for one agent (flattened index f, local index i of instance I):
+// counting-sort scatter of its state into cell order.
+__device__ __forceinline__ void phaseC_agent(int f, const float4 *state_i, const Bufs &B,
+                                             const int *tp) {
+  const int2 cr = B.cellrank[f];
+  const float4 st = *state_i;
   const int pos = tp[cr.x / kScanTile] + B.local[cr.x] + cr.y;
-  B.sxy[pos] = make_float2(__int_as_float(cr.z), __int_as_float(cr.w));
+  B.sxy[pos] = make_float2(st.x, st.y);
+  B.sts[pos] = make_float2(st.z, st.w);
   B.sidx[pos] = f;
 }
 
@@ -386,7 +394,7 @@ __device__ __forceinline__ void write_agent(const Inst &I, const Bufs &B, int i,
 // Shared memory of phase D (dynamic), in bytes from the base:
 //   float4 stg[cap]                      staged candidates (x, y, shift_x, shift_y)
 //   int    cs[kMaxStagedCells + 1]       staged-cell prefix (row-major)
-//   int    wsum[36]
+//   int    wsum[33], rs[kMaxTileH], rl[kMaxTileH]   scan scratch, the tile's rows
 //   per warp: float4 queue[kQueue]; u64 acc[32]; int ncoll[32], nin[32];
 //             u32 md[32 * v]; int cn[32 * v]
 // I must be the block's shared-memory copy of the instance descriptor.
@@ -394,7 +402,8 @@ __host__ __device__ inline size_t phaseD_warp_bytes(int v) {
   return (size_t)kQueue * 16 + 32 * 8 + 32 * 4 * 2 + (size_t)32 * v * 8;
 }
 // bytes of the staged-cell prefix plus the scan scratch, rounded to 16
-constexpr size_t kCsBytes = (((size_t)(kMaxStagedCells + 1) * 4 + 36 * 4) + 15) & ~(size_t)15;
+constexpr size_t kCsBytes =
+    (((size_t)(kMaxStagedCells + 1) * 4 + (33 + 2 * kMaxTileH) * 4) + 15) & ~(size_t)15;
 __host__ __device__ inline size_t phaseD_smem_bytes(int cap, int v, int block) {
   return (size_t)cap * 16 + kCsBytes + (size_t)(block / 32) * phaseD_warp_bytes(v);
 }
@@ -408,6 +417,11 @@ struct WarpArea {
 };
 
 // Drain `count` queued pairs (warp-uniform); ux/uy: this lane's own agent.
+// Every lane takes one pair per round whatever its owner; the owner's
+// accumulators are updated with shared-memory atomics (a round holds pairs of
+// many owners, so they rarely collide).  In this path an agent has at most
+// `cap` <= 4096 in-range neighbours, so in-range and collision counts share
+// one 32-bit word (low and high 16 bits).
 __device__ __forceinline__ void drain(const Inst &I, const WarpArea &W, int count, float ux,
                                      float uy) {
   const int lane = threadIdx.x & 31;
@@ -418,46 +432,29 @@ __device__ __forceinline__ void drain(const Inst &I, const WarpArea &W, int coun
     float4 E = valid ? W.queue[e] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int o = valid ? __float_as_int(E.w) : lane;
     const float uxo = __shfl_sync(kFull, ux, o), uyo = __shfl_sync(kFull, uy, o);
-    const float dx = E.x, dy = E.y, d2 = E.z;
-    const bool coll = valid && d2 < I.RC2;
-    unsigned long long tv = 0ull;
-    if (valid && !coll) {
-      const float t = fmul(fsub(I.RV, fsqrt(d2)), I.INV_SPAN);
-      tv = float_int_u64(fmul(t, I.scaleK));
-    }
-    int key = -1;
     if (valid) {
+      const float dx = E.x, dy = E.y, d2 = E.z;
+      const bool coll = d2 < I.RC2;
+      if (!coll) {
+        const float t = fmul(fsub(I.RV, fsqrt(d2)), I.INV_SPAN);
+        const unsigned long long tv = float_int_u64(fmul(t, I.scaleK));
+        if (tv) atomicAdd(&W.acc[o], tv);
+      }
+      atomicAdd(reinterpret_cast<unsigned *>(&W.ncoll[o]), coll ? 0x10001u : 1u);
       const float lx = fadd(fmul(dx, uxo), fmul(dy, uyo));
       const float ly = fsub(fmul(dy, uxo), fmul(dx, uyo));
       if (lx != 0.0f || ly != 0.0f) {
         float p = pseudo_angle(lx, ly);
         if (p >= 4.0f) p = 0.0f;
-        if (I.full || p < I.T[v]) key = sector_of(p, I.T, v);
+        if (I.full || p < I.T[v]) {
+          const int key = sector_of(p, I.T, v);
+          atomicMin(&W.md[o * v + key], __float_as_uint(d2));
+          atomicAdd(&W.cn[o * v + key], 1);
+        }
       }
     }
-    // reward, collisions and in-range count: one group per owner
-    const unsigned mo = __match_any_sync(kFull, valid ? o : 64 + lane);
-    const unsigned s0 = __reduce_add_sync(mo, (unsigned)(tv & 0xffffffull));
-    const unsigned s1 = __reduce_add_sync(mo, (unsigned)((tv >> 24) & 0xffffffull));
-    const unsigned s2 = __reduce_add_sync(mo, (unsigned)(tv >> 48));
-    const unsigned sc = __reduce_add_sync(mo, coll ? 1u : 0u);
-    if (valid && lane == __ffs(mo) - 1) {
-      W.acc[o] += (unsigned long long)s0 + ((unsigned long long)s1 << 24) +
-                  ((unsigned long long)s2 << 48);
-      W.ncoll[o] += (int)sc;
-      W.nin[o] += __popc(mo);
-    }
-    // sector minimum and count: one group per (owner, sector)
-    const bool seen = key >= 0;
-    const unsigned mk = __match_any_sync(kFull, seen ? (o << 8) | key : (1 << 20) + lane);
-    const unsigned mn = __reduce_min_sync(mk, __float_as_uint(d2));
-    if (seen && lane == __ffs(mk) - 1) {
-      unsigned *m = W.md + o * v + key;
-      if (mn < *m) *m = mn;
-      W.cn[o * v + key] += __popc(mk);
-    }
-    __syncwarp();
   }
+  __syncwarp();
 }
 
 // Candidate scan of one lane's stencil rows (smem ranges [ra[r], ra[r]+rn[r])),
@@ -518,7 +515,14 @@ __device__ void phaseD_tile(const Inst &I, int tx, int ty, const Bufs &B, char *
   const int nsc = tw + 2 * H, nsr = th + 2 * H, ncell = nsc * nsr;
   const int *cst = B.cell_start;
 
-  // staged-cell counts, row-major over (staged row, staged column)
+  // the tile's own rows in the sorted order, and the staged-cell counts
+  // (row-major over staged row, staged column)
+  int *rs = wsum + 33, *rl = rs + kMaxTileH;
+  if (tid < th) {
+    const int rg = I.cell_base + (r0 + tid) * nc;
+    rs[tid] = cst[rg + c0];
+    rl[tid] = cst[rg + c1] - rs[tid];
+  }
   for (int e = tid; e < ncell; e += nthr) {
     const int sr = e / nsc, sc = e - sr * nsc;
     const int g = I.cell_base + wrapi(r0 - H + sr, nc) * nc + wrapi(c0 - H + sc, nc);
@@ -556,12 +560,10 @@ __device__ void phaseD_tile(const Inst &I, int tx, int ty, const Bufs &B, char *
   }
   __syncthreads();
 
-  // the tile's own agents, counted row by row
+  // the tile's own agents: row r (0..th-1) holds sorted positions
+  // [rs[r], rs[r] + rl[r]); rs/rl were filled during staging
   int ncent = 0;
-  for (int r = 0; r < th; ++r) {
-    const int rg = I.cell_base + (r0 + r) * nc;
-    ncent += cst[rg + c1] - cst[rg + c0];
-  }
+  for (int r = 0; r < th; ++r) ncent += rl[r];
 
   if (use_smem) {
     WarpArea W;
@@ -572,35 +574,43 @@ __device__ void phaseD_tile(const Inst &I, int tx, int ty, const Bufs &B, char *
     W.nin = W.ncoll + 32;
     W.md = reinterpret_cast<unsigned *>(W.nin + 32);
     W.cn = reinterpret_cast<int *>(W.md + 32 * v);
+    // output rows are written cooperatively: P float2 per row, rpi rows per
+    // pass of the warp (lane -> row lane / P, element lane % P)
+    const int P = v + 1;
+    const int rpi = P <= 32 ? 32 / P : 1;
+    const int my_r = P <= 32 ? lane / P : 0, my_e = P <= 32 ? lane % P : lane;
     // contiguous, even share of the tile's agents per warp
     const int per = (ncent + nwarps - 1) / nwarps;
     const int wa0 = warp * per, wa1 = min(wa0 + per, ncent);
     for (int b0 = wa0; b0 < wa1; b0 += 32) {
       const int a = b0 + lane;
+      const int nb = min(32, wa1 - b0);
       const bool have = a < wa1;
       int self = -1, i = 0, sr = 0, lc = 0;
-      float4 me = make_float4(0.f, 0.f, 0.f, 0.f);
+      float xi = 0.f, yi = 0.f;
+      float2 ts = make_float2(0.f, 0.f);
       if (have) {
-        int r = 0, al = a, rg = 0, rlen = 0;
-        for (;; ++r) {
-          rg = I.cell_base + (r0 + r) * nc;
-          rlen = cst[rg + c1] - cst[rg + c0];
-          if (al < rlen) break;
-          al -= rlen;
+        int r = 0, al = a;
+        while (al >= rl[r]) {
+          al -= rl[r];
+          ++r;
         }
         sr = r + H;
         self = cs[sr * nsc + H] + al;  // interior run of the row, in sorted order
-        i = B.sidx[cst[rg + c0] + al] - I.agent_base;
-        me = I.state[i];
-        lc = cell_of(me.x, I) - c0 + H;
+        const int gp = rs[r] + al;
+        i = B.sidx[gp] - I.agent_base;
+        ts = B.sts[gp];
+        const float4 e = stg[self];
+        xi = e.x;
+        yi = e.y;
+        lc = cell_of(xi, I) - c0 + H;
       }
       float c = 1.f, sn = 0.f;
-      det_sincos(me.z, c, sn);
+      det_sincos(ts.x, c, sn);
       const float ux = fadd(fmul(c, I.CF), fmul(sn, I.SF));
       const float uy = fsub(fmul(sn, I.CF), fmul(c, I.SF));
       W.acc[lane] = 0ull;
       W.ncoll[lane] = 0;
-      W.nin[lane] = 0;
       for (int k = 0; k < v; ++k) {
         W.md[lane * v + k] = 0x7f800000u;
         W.cn[lane * v + k] = 0;
@@ -619,13 +629,38 @@ __device__ void phaseD_tile(const Inst &I, int tx, int ty, const Bufs &B, char *
       }
       __syncwarp();
       if (wraps)
-        scan_rows<H, true>(I, W, stg, ra, rn, self, me.x, me.y, ux, uy);
+        scan_rows<H, true>(I, W, stg, ra, rn, self, xi, yi, ux, uy);
       else
-        scan_rows<H, false>(I, W, stg, ra, rn, self, me.x, me.y, ux, uy);
+        scan_rows<H, false>(I, W, stg, ra, rn, self, xi, yi, ux, uy);
       __syncwarp();
-      if (have)
-        write_agent(I, B, i, me.w, me.z, W.acc[lane], W.ncoll[lane], W.nin[lane],
-                    W.md + lane * v, W.cn + lane * v, 1, err);
+      // reward and collisions: one value per agent
+      if (have) {
+        const unsigned packed = (unsigned)W.ncoll[lane];  // in-range | collisions << 16
+        const int ncoll = (int)(packed >> 16);
+        const long long total = (long long)W.acc[lane] - (long long)ncoll * I.PK;
+        B.reward[I.agent_base + i] = fmul(__ll2float_rn(total), I.inv_scaleK);
+        B.coll[I.agent_base + i] = ncoll;
+        if ((long long)(packed & 0xffffu) > I.NMAX) err |= FLOCK_ERR_OVERFLOW;
+      }
+      // observation rows, written whole and contiguous
+      float *obs = B.obs + I.obs_base;
+      for (int rb = 0; rb < nb; rb += rpi) {
+        const int r = min(rb + my_r, 31);
+        const int ir = __shfl_sync(kFull, i, r);
+        const float sr_ = __shfl_sync(kFull, ts.y, r), tr = __shfl_sync(kFull, ts.x, r);
+        if (rb + my_r < nb && my_r < rpi) {
+          for (int e = my_e; e < P; e += 32) {
+            float2 val;
+            if (e < v) {
+              const int ck = W.cn[r * v + e];
+              val = make_float2(ck ? fsqrt(__uint_as_float(W.md[r * v + e])) : I.RV, (float)ck);
+            } else {
+              val = make_float2(sr_, tr);
+            }
+            *reinterpret_cast<float2 *>(obs + (long long)ir * I.obs_dim + 2 * e) = val;
+          }
+        }
+      }
       __syncwarp();
     }
   } else {
@@ -680,6 +715,224 @@ __device__ void phaseD_tile(const Inst &I, int tx, int ty, const Bufs &B, char *
     }
   }
   __syncthreads();  // smem is reused by the next tile
+}
+
+
+// ---------------------------------------------------------------------------
+// Phase D, direct form: one warp handles up to 32 consecutive cell-sorted
+// agents of one instance (sorted positions [gp0, gp1)), with no block-level
+// staging.  Neighbouring lanes are in the same or adjacent cells, so their
+// stencil rows overlap and the candidate reads hit L1; nothing waits on
+// other warps.  Per stencil row a lane's candidates are at most three
+// contiguous runs of the sorted array (cells across the left boundary, the
+// cells inside, cells across the right boundary), each with its own
+// periodic shift.  Pair processing (queue, drain) and the output are the
+// same as in the staged form.  smem: this warp's WarpArea.
+// ---------------------------------------------------------------------------
+struct DirectArea {
+  float4 *queue;
+  unsigned long long *acc;
+  int *nin, *ncoll;
+  unsigned *md;
+  int *cn;
+};
+
+__host__ __device__ inline size_t direct_warp_bytes(int v) {
+  return (size_t)kQueue * 16 + 32 * 8 + 32 * 4 * 2 + (size_t)32 * v * 8;
+}
+
+__device__ __forceinline__ DirectArea direct_area(char *base, int v) {
+  DirectArea W;
+  W.queue = reinterpret_cast<float4 *>(base);
+  W.acc = reinterpret_cast<unsigned long long *>(base + kQueue * 16);
+  W.nin = reinterpret_cast<int *>(base + kQueue * 16 + 32 * 8);
+  W.ncoll = W.nin + 32;
+  W.md = reinterpret_cast<unsigned *>(W.ncoll + 32);
+  W.cn = reinterpret_cast<int *>(W.md + 32 * v);
+  return W;
+}
+
+// Drain for the direct form: separate in-range and collision counters (an
+// agent may have any number of neighbours here).
+__device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W, int count,
+                                            float ux, float uy) {
+  const int lane = threadIdx.x & 31;
+  const int v = I.v;
+  for (int e0 = 0; e0 < count; e0 += 32) {
+    const int e = e0 + lane;
+    const bool valid = e < count;
+    float4 E = valid ? W.queue[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int o = valid ? __float_as_int(E.w) : lane;
+    const float uxo = __shfl_sync(kFull, ux, o), uyo = __shfl_sync(kFull, uy, o);
+    if (valid) {
+      const float dx = E.x, dy = E.y, d2 = E.z;
+      atomicAdd(&W.nin[o], 1);
+      if (d2 < I.RC2) {  // Fig. 4: collision below 2 d_r
+        atomicAdd(&W.ncoll[o], 1);
+      } else {
+        const float t = fmul(fsub(I.RV, fsqrt(d2)), I.INV_SPAN);
+        const unsigned long long tv = float_int_u64(fmul(t, I.scaleK));
+        if (tv) atomicAdd(&W.acc[o], tv);
+      }
+      const float lx = fadd(fmul(dx, uxo), fmul(dy, uyo));
+      const float ly = fsub(fmul(dy, uxo), fmul(dx, uyo));
+      if (lx != 0.0f || ly != 0.0f) {
+        float p = pseudo_angle(lx, ly);
+        if (p >= 4.0f) p = 0.0f;
+        if (I.full || p < I.T[v]) {
+          const int key = sector_of(p, I.T, v);
+          atomicMin(&W.md[o * v + key], __float_as_uint(d2));
+          atomicAdd(&W.cn[o * v + key], 1);
+        }
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// One run of candidates [a, a + n) with shifts (sx, sy); appends in-range
+// pairs to the queue (warp-uniform loop), draining when nearly full.
+template <bool SHIFT>
+__device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, const float2 *sxy,
+                                           int a, int n, int self, float sx, float sy, float xi,
+                                           float yi, float ux, float uy, int &qn) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int maxn = __reduce_max_sync(kFull, (unsigned)n);
+  for (int j = 0; j < maxn; ++j) {
+    const int q = a + j;
+    bool inr = false;
+    float dx = 0.f, dy = 0.f, d2 = 0.f;
+    if (j < n && q != self) {
+      const float2 p = __ldg(sxy + q);
+      dx = fsub(p.x, xi);
+      dy = fsub(p.y, yi);
+      if (SHIFT) {
+        dx = fadd(dx, sx);
+        dy = fadd(dy, sy);
+      }
+      d2 = fadd(fmul(dx, dx), fmul(dy, dy));
+      inr = d2 < I.RV2;  // Eq. 1: d_ij < d_v
+    }
+    const unsigned m = __ballot_sync(kFull, inr);
+    if (inr) W.queue[qn + __popc(m & lt)] = make_float4(dx, dy, d2, __int_as_float(lane));
+    qn += __popc(m);
+    if (qn > kQueue - 32) {
+      __syncwarp();
+      drain_direct(I, W, qn, ux, uy);
+      qn = 0;
+    }
+  }
+}
+
+template <int H>
+__device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
+                              const DirectArea &W, unsigned &err) {
+  const int lane = threadIdx.x & 31;
+  const int nc = I.nc, v = I.v;
+  const int gp = gp0 + lane;
+  const bool have = gp < gp1;
+  const int nb = gp1 - gp0;
+  float xi = 0.f, yi = 0.f;
+  float2 ts = make_float2(0.f, 0.f);
+  int i = 0, cx = 0, cy = 0;
+  if (have) {
+    const float2 p = B.sxy[gp];
+    xi = p.x;
+    yi = p.y;
+    ts = B.sts[gp];
+    i = B.sidx[gp] - I.agent_base;
+    cx = cell_of(xi, I);
+    cy = cell_of(yi, I);
+  }
+  float c = 1.f, sn = 0.f;
+  det_sincos(ts.x, c, sn);
+  const float ux = fadd(fmul(c, I.CF), fmul(sn, I.SF));
+  const float uy = fsub(fmul(sn, I.CF), fmul(c, I.SF));
+  W.acc[lane] = 0ull;
+  W.nin[lane] = 0;
+  W.ncoll[lane] = 0;
+  for (int k = 0; k < v; ++k) {
+    W.md[lane * v + k] = 0x7f800000u;
+    W.cn[lane * v + k] = 0;
+  }
+  // stencil columns [cx - H, cx + H] split into runs that do not wrap
+  const int vlo = cx - H, vhi = cx + H + 1;
+  const int ma = max(vlo, 0), mb = min(vhi, nc);  // interior run
+  const bool lw = vlo < 0, rw = vhi > nc;         // left / right boundary runs
+  const bool wrap_any = __any_sync(kFull, have && (lw || rw || cy - H < 0 || cy + H >= nc));
+  const int *cst = B.cell_start;
+  int ra[2 * H + 1], rn[2 * H + 1];
+#pragma unroll
+  for (int r = 0; r < 2 * H + 1; ++r) {
+    const int rowg = I.cell_base + wrapi(cy - H + r, nc) * nc;
+    ra[r] = have ? cst[rowg + ma] : 0;
+    rn[r] = have ? cst[rowg + mb] - ra[r] : 0;
+  }
+  __syncwarp();
+  int qn = 0;
+  const int self = have ? gp : -1;
+  if (!wrap_any) {
+#pragma unroll
+    for (int r = 0; r < 2 * H + 1; ++r)
+      direct_run<false>(I, W, B.sxy, ra[r], rn[r], self, 0.f, 0.f, xi, yi, ux, uy, qn);
+  } else {
+#pragma unroll
+    for (int r = 0; r < 2 * H + 1; ++r) {
+      const int vr = cy - H + r;
+      const float sy = vr < 0 ? -I.L : (vr >= nc ? I.L : 0.0f);
+      const int rowg = I.cell_base + wrapi(vr, nc) * nc;
+      direct_run<true>(I, W, B.sxy, ra[r], rn[r], self, 0.f, sy, xi, yi, ux, uy, qn);
+      // cells across the left boundary: virtual columns [vlo, 0) -> [vlo + nc, nc)
+      int a = 0, n = 0;
+      if (have && lw) {
+        a = cst[rowg + vlo + nc];
+        n = cst[rowg + nc] - a;
+      }
+      direct_run<true>(I, W, B.sxy, a, n, self, -I.L, sy, xi, yi, ux, uy, qn);
+      // cells across the right boundary: virtual columns [nc, vhi) -> [0, vhi - nc)
+      a = 0;
+      n = 0;
+      if (have && rw) {
+        a = cst[rowg];
+        n = cst[rowg + vhi - nc] - a;
+      }
+      direct_run<true>(I, W, B.sxy, a, n, self, I.L, sy, xi, yi, ux, uy, qn);
+    }
+  }
+  __syncwarp();
+  drain_direct(I, W, qn, ux, uy);
+  // reward and collisions
+  if (have) {
+    const int ncoll = W.ncoll[lane];
+    const long long total = (long long)W.acc[lane] - (long long)ncoll * I.PK;
+    B.reward[I.agent_base + i] = fmul(__ll2float_rn(total), I.inv_scaleK);
+    B.coll[I.agent_base + i] = ncoll;
+    if ((long long)W.nin[lane] > I.NMAX) err |= FLOCK_ERR_OVERFLOW;
+  }
+  // observation rows, written whole and contiguous
+  const int P = v + 1;
+  const int rpi = P <= 32 ? 32 / P : 1;
+  const int my_r = P <= 32 ? lane / P : 0, my_e = P <= 32 ? lane % P : lane;
+  float *obs = B.obs + I.obs_base;
+  for (int rb = 0; rb < nb; rb += rpi) {
+    const int r = min(rb + my_r, 31);
+    const int ir = __shfl_sync(kFull, i, r);
+    const float sr_ = __shfl_sync(kFull, ts.y, r), tr = __shfl_sync(kFull, ts.x, r);
+    if (rb + my_r < nb && my_r < rpi) {
+      for (int e = my_e; e < P; e += 32) {
+        float2 val;
+        if (e < v) {
+          const int ck = W.cn[r * v + e];
+          val = make_float2(ck ? fsqrt(__uint_as_float(W.md[r * v + e])) : I.RV, (float)ck);
+        } else {
+          val = make_float2(sr_, tr);
+        }
+        *reinterpret_cast<float2 *>(obs + (long long)ir * I.obs_dim + 2 * e) = val;
+      }
+    }
+  }
+  __syncwarp();
 }
 
 }  // namespace flock

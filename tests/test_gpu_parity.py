@@ -108,7 +108,8 @@ def test_trajectory_5k_20_steps():
     assert err == 0
 
 
-def test_50k_full_size_3_steps():
+@pytest.mark.parametrize("mode", [1, 2])
+def test_50k_full_size_3_steps(mode):
     """The benchmark's 50,000-agent configuration (side 707.1) in the launch
     shape the benchmark uses: three steps, all outputs, bit-exact."""
     n, steps = 50000, 3
@@ -116,7 +117,7 @@ def test_50k_full_size_3_steps():
     p = fi.default_params(side)
     st0 = fi.initial_state(n, side, 2)
     acts = fi.random_actions(n, steps, 2)
-    g, err, _ = gpu_run(p, st0, acts)
+    g, err, _ = gpu_run(p, st0, acts, {"mode": mode})
     o, _ = oracle_run(p, st0, acts)
     assert_same(g, o, "50k")
     assert err == 0
@@ -143,12 +144,17 @@ def test_parameter_variants(over):
 
 
 @pytest.mark.parametrize("tuning", [
-    {"stencil": 1, "tile_w": 1, "tile_h": 1, "block": 64},
-    {"stencil": 1, "tile_w": 64, "tile_h": 8, "block": 512},
-    {"stencil": 1, "tile_w": 7, "tile_h": 3, "block": 96},
-    {"stencil": 2, "tile_w": 16, "tile_h": 4, "block": 128},
-    {"stencil": 2, "tile_w": 64, "tile_h": 1, "block": 256},
-], ids=lambda d: "s%d-%dx%d-b%d" % (d["stencil"], d["tile_w"], d["tile_h"], d["block"]))
+    {"mode": 1, "stencil": 1, "tile_w": 1, "tile_h": 1, "block": 64},
+    {"mode": 1, "stencil": 1, "tile_w": 64, "tile_h": 8, "block": 512},
+    {"mode": 1, "stencil": 1, "tile_w": 7, "tile_h": 3, "block": 96},
+    {"mode": 1, "stencil": 2, "tile_w": 16, "tile_h": 4, "block": 128},
+    {"mode": 1, "stencil": 2, "tile_w": 64, "tile_h": 1, "block": 256},
+    {"mode": 2, "stencil": 1, "tile_w": 0, "tile_h": 0, "block": 64},
+    {"mode": 2, "stencil": 1, "tile_w": 0, "tile_h": 0, "block": 512},
+    {"mode": 2, "stencil": 2, "tile_w": 0, "tile_h": 0, "block": 128},
+    {"mode": 2, "stencil": 2, "tile_w": 0, "tile_h": 0, "block": 256},
+], ids=lambda d: "m%d-s%d-%dx%d-b%d" % (d["mode"], d["stencil"], d["tile_w"], d["tile_h"],
+                                         d["block"]))
 def test_launch_shapes_are_bit_identical(tuning):
     """Every tuning the autotuner may pick gives the same bits."""
     n, steps = 4000, 3
@@ -157,27 +163,30 @@ def test_launch_shapes_are_bit_identical(tuning):
     st0 = fi.initial_state(n, side, 4)
     acts = fi.random_actions(n, steps, 4)
     g, _, tun = gpu_run(p, st0, acts, tuning)
-    assert tun["stencil"] == tuning["stencil"]
+    assert tun["stencil"] == tuning["stencil"] and tun["mode"] == tuning["mode"]
     o, _ = oracle_run(p, st0, acts)
     assert_same(g, o, str(tuning))
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("side,stencil", [(11.0, 1), (10.5, 1), (10.5, 2), (16.0, 1), (26.0, 2)])
-def test_small_square_wraps_everywhere(side, stencil):
+def test_small_square_wraps_everywhere(side, stencil, mode):
     # squares only just wider than 2 d_v: one to five cells per axis, every
     # stencil wraps and some visit a cell twice under different shifts
     n, steps = 60, 10
     p = fi.default_params(side)
     st0 = fi.initial_state(n, side, 5)
     acts = fi.random_actions(n, steps, 5)
-    g, _, _ = gpu_run(p, st0, acts, {"stencil": stencil})
+    g, _, _ = gpu_run(p, st0, acts, {"stencil": stencil, "mode": mode})
     o, _ = oracle_run(p, st0, acts)
     assert_same(g, o, "side %g" % side)
 
 
-def test_dense_cluster_exceeds_shared_memory():
-    """6,000 agents packed into a 20 x 20 patch: tiles overflow the shared
-    staging buffer and take the direct-read path."""
+@pytest.mark.parametrize("mode", [1, 2])
+def test_dense_cluster_exceeds_shared_memory(mode):
+    """6,000 agents packed into a 20 x 20 patch: in mode 1 tiles overflow the
+    shared staging buffer and take the per-thread path; in mode 2 warps see
+    hundreds of in-range neighbours per agent."""
     n = 6000
     rng = np.random.Generator(np.random.PCG64(6))
     st0 = fi.initial_state(n, 100.0, 6)
@@ -185,7 +194,7 @@ def test_dense_cluster_exceeds_shared_memory():
     st0[:, 1] = (40.0 + 20.0 * rng.random(n)).astype(np.float32)
     p = fi.default_params(100.0)
     acts = fi.random_actions(n, 2, 6)
-    g, err, _ = gpu_run(p, st0, acts)
+    g, err, _ = gpu_run(p, st0, acts, {"mode": mode})
     o, flags = oracle_run(p, st0, acts)
     assert_same(g, o, "cluster")
     assert err == flags == 0
