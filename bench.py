@@ -188,6 +188,69 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256):
+    """The batched form: n_inst instances with agent counts log-uniform in
+    [100, 20000] (density 0.1 each), all advanced by one persistent kernel
+    per step, replayed from a CUDA graph.  Returns a dict for the JSON line."""
+    sizes = fi.batch_sizes(n_inst, 100, 20000, seed)
+    params = [fi.default_params(fi.side_for(n)) for n in sizes]
+    total = sum(sizes)
+    cells = sum(F.flock_instance_cells(p) for p in params)
+    arena = torch.empty((total, 4), dtype=torch.float32, device=dev)
+    states, off = [], 0
+    for k, n in enumerate(sizes):
+        arena[off:off + n] = torch.from_numpy(fi.initial_state(n, fi.side_for(n), seed + k))
+        states.append(arena[off:off + n])
+        off += n
+    b = F.FlockBatch(n_inst, total, cells, 18, device=dev, stream=stream)
+    b.set(params, sizes, states, reset=[1] * n_inst)
+    acts = torch.from_numpy(fi.random_actions(total, steps + warmup + 1, seed + 1)).to(dev)
+    act_buf = torch.empty(total, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+    F.env_batch_set_timing(b.batch, True)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    kern = []
+    with torch.cuda.stream(stream):
+        act_buf.copy_(acts[0])
+        b.step(act_buf)  # initial observation (reset)
+        for k in range(warmup):
+            act_buf.copy_(acts[1 + k])
+            flush.zero_()
+            b.step(act_buf)
+    torch.cuda.synchronize()
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            act_buf.copy_(acts[1 + warmup + k])
+            flush.zero_()
+            ev0[k].record(stream)
+            b.step(act_buf)
+            ev1[k].record(stream)
+        kern.append(F.env_batch_get_time(b.batch))
+    torch.cuda.synchronize()
+    err = b.error()
+    assert err == 0, "device error bits %d" % err
+    ms = [ev0[k].elapsed_time(ev1[k]) for k in range(steps)]
+    tot = sum(ms)
+    grid, block = F.env_batch_get_launch(b.batch)
+    kern_ms = float(np.mean(kern))
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_AGENT_STEP * total / (kern_ms * 1e-3) / 1e9
+    b.close()
+    return {"value": total * steps / (tot * 1e-3), "unit": UNIT, "instances": n_inst,
+            "agents": total, "cells": cells, "ms_per_step": tot / steps,
+            "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+            "grid": grid, "block": block,
+            "workload": "batched: %d flock instances, agent counts log-uniform in [100, 20000] "
+                        "(seed %d, %d agents), density 0.1, view radius 5, 8 sectors, fov 250 "
+                        "deg, one persistent cooperative kernel per step, CUDA graph"
+                        % (n_inst, seed, total),
+            "roofline": {"bound": "hbm", "kernel": "k_batch_step", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": peak_kind, "traffic": None,
+                         "bytes_per_agent": BYTES_PER_AGENT_STEP}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -196,6 +259,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--agents", type=int, default=N_AGENTS)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--tuning", default=None,
+                    help='launch shape as JSON, e.g. {"mode": 2, "stencil": 1, "block": 128}')
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -228,7 +294,8 @@ def main():
     act_buf = torch.empty(n, dtype=torch.int32, device=dev)  # fixed pointer: one graph capture
     torch.cuda.synchronize()
     stream = torch.cuda.Stream(device=dev)
-    env = F.FlockEnv(p, n, device=dev, stream=stream)
+    tuning = json.loads(args.tuning) if args.tuning else None
+    env = F.FlockEnv(p, n, device=dev, stream=stream, tuning=tuning)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     with torch.cuda.stream(stream):
         env.reset(torch.from_numpy(st0).to(dev))
@@ -293,6 +360,10 @@ def main():
            "h2d_bytes_per_step": n * 4, "d2h_bytes_per_step": n * (env.obs_dim + 2) * 4,
            "call": "env_step_host (pinned host buffers, synchronous)"}
 
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(F, torch, dev, stream, args.steps, args.warmup, flush,
+                              seed=1000 * rank)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -303,7 +374,8 @@ def main():
             "config": {"workload": "plain flock step, 1 instance, %d agents, side %.1f, density "
                                    "0.1, view radius 5, 8 sectors, fov 250 deg, uniform random "
                                    "actions, CUDA graph of 4 kernels" % (n, side),
-                       "agents": n, "l2": "flushed (512 MiB write) between timed steps",
+                       "agents": n, "tuning": env.tuning(),
+                       "l2": "flushed (512 MiB write) between timed steps",
                        "parallelism": "replicas" if world > 1 else "single"},
             "step_hbm_gbs": step_gbs,
             "phase_ms": {"apply_bin": float(ph[:, 0].mean()), "scan": float(ph[:, 1].mean()),
@@ -314,8 +386,12 @@ def main():
                          "bytes_per_agent": NEIGH_BYTES_PER_AGENT},
             "e2e": e2e,
             "clocks": clk.summary(),
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": 4 * args.steps + (args.steps if batched else 0),
         }
+        if batched is not None:
+            line["batched"] = batched
+            if world > 1:
+                line["batched"]["value_all_ranks"] = None
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))

@@ -176,6 +176,66 @@ int env_get_phase_times(flock_env *env, float ms_out[4]);
  * the caller owns.  Waits for the stream first. */
 void env_destroy(flock_env *env);
 
+/* ---------------------------------------------------------------------------
+ * Batched step: many independent flock instances advanced by ONE persistent
+ * cooperative kernel per step (apply+bin, scan, scatter and neighbour scan as
+ * phases separated by grid barriers).  Instances may differ in agent count and
+ * in every parameter except num_segments; all share the batch's tuning.
+ *
+ * Instance k of the active set owns rows [off_k, off_k + n_k) of every
+ * flattened per-agent buffer (actions, reward, coll, and obs rows of 2v+2
+ * floats), off_k = n_0 + ... + n_{k-1}.  Its state lives in caller memory
+ * (state_dev[k], n_k x 4 floats) and is updated in place, so sessions stay
+ * resident across steps and may join or leave between steps.
+ * ------------------------------------------------------------------------- */
+
+/* Cells one instance uses (cells_per_side^2) under the given tuning. */
+int flock_instance_cells(const flock_params *params, const flock_tuning *tuning_or_null,
+                         int *cells_out);
+
+/* Workspace for a batch of at most max_instances instances holding at most
+ * max_agents agents and max_cells cells in total. */
+int flock_batch_workspace_bytes(int max_instances, int max_agents, int max_cells,
+                                const flock_tuning *tuning_or_null, size_t *bytes_out);
+
+/* Creates a batch (no instance active).  Same ownership and stream rules as
+ * env_create.  Needs a device that supports cooperative launches. */
+int env_batch_create(int max_instances, int max_agents, int max_cells,
+                     const flock_tuning *tuning_or_null, void *workspace_dev,
+                     size_t workspace_bytes, void *stream, flock_batch **out);
+
+/* Sets the active instances (replacing the previous set), in order.
+ * params/n_agents/state_dev/reset are arrays of n_inst entries; reset[k] != 0
+ * (or reset == NULL for none) makes the next step observe instance k without
+ * applying its actions (its initial observation).  The descriptors are
+ * copied to the device in stream order; no kernel is re-captured.
+ * Returns FLOCK_EINVAL if a parameter set is invalid, if num_segments
+ * differs between instances, or if a total exceeds the batch's maxima. */
+int env_batch_set(flock_batch *batch, int n_inst, const flock_params *params,
+                  const int *n_agents, float *const *state_dev, const int *reset);
+
+/* One step of every active instance (the batched hot path). */
+int env_batch_step(flock_batch *batch, const int32_t *actions_dev, float *obs_dev,
+                   float *reward_dev, int32_t *coll_dev);
+
+/* Waits for the stream, returns and clears the latched FLOCK_ERR_* bits; after
+ * a FLOCK_ERR_TIMEOUT it also resets the grid-barrier counters. */
+int env_batch_get_error(flock_batch *batch, uint32_t *bits_out);
+
+/* Bound on the polls of one grid-barrier wait (default 1<<22, about a
+ * second); a wait that runs out sets FLOCK_ERR_TIMEOUT and the kernel
+ * returns.  0 makes every wait give up at once (for tests of that path). */
+int env_batch_set_spin_limit(flock_batch *batch, unsigned limit);
+
+/* Grid size (blocks) and block size of the persistent kernel, and the
+ * duration of the last step in ms when timing is on (events around the
+ * kernel, recorded inside the replayed graph). */
+int env_batch_get_launch(const flock_batch *batch, int *grid_out, int *block_out);
+int env_batch_set_timing(flock_batch *batch, int enable);
+int env_batch_get_time(flock_batch *batch, float *ms_out);
+
+void env_batch_destroy(flock_batch *batch);
+
 /* Last CUDA error string seen by the library in this process (or ""). */
 const char *flock_last_cuda_error(void);
 

@@ -22,7 +22,10 @@ __all__ = [
     "flock_derive",
     "env_create", "env_reset", "env_step", "env_step_host", "env_get_state", "env_set_state",
     "env_get_error", "env_get_derived", "env_get_tuning", "env_set_timing",
-    "env_get_phase_times", "env_destroy", "FlockEnv", "lib_path",
+    "env_get_phase_times", "env_destroy", "FlockEnv", "lib_path", "flock_instance_cells",
+    "flock_batch_workspace_bytes", "env_batch_create", "env_batch_set", "env_batch_step",
+    "env_batch_get_error", "env_batch_set_spin_limit", "env_batch_get_launch",
+    "env_batch_set_timing", "env_batch_get_time", "env_batch_destroy", "FlockBatch",
 ]
 
 lib_path = _abi.LIB_PATH
@@ -247,6 +250,152 @@ class FlockEnv:
     def __del__(self):
         try:
             if getattr(self, "env", None) is not None:
+                self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# Batched step (many instances, one persistent kernel per step)
+# ---------------------------------------------------------------------------
+def flock_instance_cells(params: dict, tuning: dict | None = None) -> int:
+    out = ctypes.c_int(0)
+    t = _abi.tuning_from_dict(tuning)
+    _abi.check(_abi.lib.flock_instance_cells(ctypes.byref(_abi.params_from_dict(params)),
+                                             ctypes.byref(t) if t is not None else None,
+                                             ctypes.byref(out)))
+    return int(out.value)
+
+
+def flock_batch_workspace_bytes(max_instances: int, max_agents: int, max_cells: int,
+                                tuning: dict | None = None) -> int:
+    out = ctypes.c_size_t(0)
+    t = _abi.tuning_from_dict(tuning)
+    _abi.check(_abi.lib.flock_batch_workspace_bytes(int(max_instances), int(max_agents),
+                                                    int(max_cells),
+                                                    ctypes.byref(t) if t is not None else None,
+                                                    ctypes.byref(out)))
+    return int(out.value)
+
+
+class _Batch:
+    def __init__(self, handle, workspace):
+        self.handle = handle
+        self.workspace = workspace
+
+
+def env_batch_create(max_instances, max_agents, max_cells, workspace, stream=None, tuning=None):
+    torch = _torch()
+    h = ctypes.c_void_p()
+    t = _abi.tuning_from_dict(tuning)
+    _abi.check(_abi.lib.env_batch_create(int(max_instances), int(max_agents), int(max_cells),
+                                         ctypes.byref(t) if t is not None else None,
+                                         _ptr(workspace, torch.uint8, name="workspace"),
+                                         ctypes.c_size_t(workspace.numel()), _stream(stream),
+                                         ctypes.byref(h)))
+    return _Batch(h, workspace)
+
+
+def env_batch_set(batch, params_list, n_agents, states, reset=None):
+    """Active set: parallel lists of parameter dicts, agent counts, state
+    tensors (n x 4 float32 on the device) and reset flags."""
+    torch = _torch()
+    k = len(params_list)
+    P = (_abi.FlockParams * max(k, 1))(*[_abi.params_from_dict(p) for p in params_list])
+    N = (ctypes.c_int * max(k, 1))(*[int(n) for n in n_agents])
+    S = (ctypes.c_void_p * max(k, 1))(*[
+        _ptr(st, torch.float32, (int(n), 4), "state").value if int(n) > 0 else None
+        for st, n in zip(states, n_agents)])
+    R = (ctypes.c_int * max(k, 1))(*[int(bool(r)) for r in (reset or [0] * k)])
+    _abi.check(_abi.lib.env_batch_set(batch.handle, k, P, N, S, R))
+    batch.states = list(states)  # keep the tensors alive while active
+
+
+def env_batch_step(batch, actions, obs, reward, coll):
+    torch = _torch()
+    _abi.check(_abi.lib.env_batch_step(batch.handle, _ptr(actions, torch.int32, name="actions"),
+                                       _ptr(obs, torch.float32, name="obs"),
+                                       _ptr(reward, torch.float32, name="reward"),
+                                       _ptr(coll, torch.int32, name="coll")))
+
+
+def env_batch_get_error(batch) -> int:
+    bits = ctypes.c_uint32(0)
+    _abi.check(_abi.lib.env_batch_get_error(batch.handle, ctypes.byref(bits)))
+    return int(bits.value)
+
+
+def env_batch_set_spin_limit(batch, limit: int):
+    _abi.check(_abi.lib.env_batch_set_spin_limit(batch.handle, ctypes.c_uint(limit)))
+
+
+def env_batch_get_launch(batch):
+    g = ctypes.c_int(0)
+    b = ctypes.c_int(0)
+    _abi.check(_abi.lib.env_batch_get_launch(batch.handle, ctypes.byref(g), ctypes.byref(b)))
+    return int(g.value), int(b.value)
+
+
+def env_batch_set_timing(batch, enable: bool):
+    _abi.check(_abi.lib.env_batch_set_timing(batch.handle, 1 if enable else 0))
+
+
+def env_batch_get_time(batch) -> float:
+    ms = ctypes.c_float(0)
+    _abi.check(_abi.lib.env_batch_get_time(batch.handle, ctypes.byref(ms)))
+    return float(ms.value)
+
+
+def env_batch_destroy(batch):
+    if batch is not None and batch.handle:
+        _abi.lib.env_batch_destroy(batch.handle)
+        batch.handle = None
+
+
+class FlockBatch:
+    """Convenience owner of a batch: allocates the workspace and the
+    flattened output tensors with torch and calls the C ABI."""
+
+    def __init__(self, max_instances: int, max_agents: int, max_cells: int, obs_dim: int,
+                 device="cuda", stream=None, tuning: dict | None = None):
+        torch = _torch()
+        self.device = torch.device(device)
+        self.obs_dim = int(obs_dim)
+        nbytes = flock_batch_workspace_bytes(max_instances, max_agents, max_cells, tuning)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.batch = env_batch_create(max_instances, max_agents, max_cells, self.workspace,
+                                      stream, tuning)
+        self.obs = torch.empty((max(max_agents, 1), self.obs_dim), dtype=torch.float32,
+                               device=self.device)
+        self.reward = torch.empty(max(max_agents, 1), dtype=torch.float32, device=self.device)
+        self.coll = torch.empty(max(max_agents, 1), dtype=torch.int32, device=self.device)
+        self.n_total = 0
+        self.offsets = []
+
+    def set(self, params_list, n_agents, states, reset=None):
+        env_batch_set(self.batch, params_list, n_agents, states, reset)
+        self.offsets = []
+        off = 0
+        for n in n_agents:
+            self.offsets.append(off)
+            off += int(n)
+        self.n_total = off
+
+    def step(self, actions):
+        env_batch_step(self.batch, actions, self.obs, self.reward, self.coll)
+        n = self.n_total
+        return self.obs[:n], self.reward[:n], self.coll[:n]
+
+    def error(self) -> int:
+        return env_batch_get_error(self.batch)
+
+    def close(self):
+        env_batch_destroy(self.batch)
+        self.batch = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "batch", None) is not None:
                 self.close()
         except Exception:
             pass

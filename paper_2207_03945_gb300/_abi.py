@@ -105,6 +105,19 @@ def _load():
         "env_get_tuning": [vp, T],
         "env_set_timing": [vp, ctypes.c_int],
         "env_get_phase_times": [vp, ctypes.POINTER(ctypes.c_float)],
+        "flock_instance_cells": [P, T, ctypes.POINTER(ctypes.c_int)],
+        "flock_batch_workspace_bytes": [ctypes.c_int, ctypes.c_int, ctypes.c_int, T,
+                                        ctypes.POINTER(ctypes.c_size_t)],
+        "env_batch_create": [ctypes.c_int, ctypes.c_int, ctypes.c_int, T, vp, ctypes.c_size_t,
+                             vp, ctypes.POINTER(vp)],
+        "env_batch_set": [vp, ctypes.c_int, P, ctypes.POINTER(ctypes.c_int),
+                          ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int)],
+        "env_batch_step": [vp, vp, vp, vp, vp],
+        "env_batch_get_error": [vp, ctypes.POINTER(ctypes.c_uint32)],
+        "env_batch_set_spin_limit": [vp, ctypes.c_uint],
+        "env_batch_get_launch": [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+        "env_batch_set_timing": [vp, ctypes.c_int],
+        "env_batch_get_time": [vp, ctypes.POINTER(ctypes.c_float)],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -112,6 +125,8 @@ def _load():
         fn.restype = ctypes.c_int
     lib.env_destroy.argtypes = [vp]
     lib.env_destroy.restype = None
+    lib.env_batch_destroy.argtypes = [vp]
+    lib.env_batch_destroy.restype = None
     lib.flock_last_cuda_error.argtypes = []
     lib.flock_last_cuda_error.restype = ctypes.c_char_p
     return lib

@@ -56,7 +56,7 @@ __global__ void k_neighbours(const Inst *__restrict__ gI, Bufs B) {
   if (err) atomicOr(B.err, err);
 }
 
-template <int H>
+template <int H, int V>
 __global__ void k_neighbours_direct(const Inst *__restrict__ gI, Bufs B) {
   extern __shared__ __align__(16) char smem[];
   __shared__ Inst sI;
@@ -67,7 +67,7 @@ __global__ void k_neighbours_direct(const Inst *__restrict__ gI, Bufs B) {
   const int gp0 = (blockIdx.x * (blockDim.x >> 5) + warp) * 32;
   if (gp0 < sI.n) {
     const DirectArea W = direct_area(smem + (size_t)warp * direct_warp_bytes(sI.v), sI.v);
-    phaseD_direct<H>(sI, gp0, min(gp0 + 32, sI.n), B, W, err);
+    phaseD_direct<H, V>(sI, gp0, min(gp0 + 32, sI.n), B, W, err);
   }
   if (err) atomicOr(B.err, err);
 }
@@ -255,8 +255,8 @@ cudaError_t set_kernel_attrs() {
     const int want = maxsm - (int)sizeof(Inst) - 1024;
     cudaError_t e1 = cudaFuncSetAttribute(k_neighbours<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
     cudaError_t e2 = cudaFuncSetAttribute(k_neighbours<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
-    cudaError_t e3 = cudaFuncSetAttribute(k_neighbours_direct<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
-    cudaError_t e4 = cudaFuncSetAttribute(k_neighbours_direct<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+    cudaError_t e3 = cudaFuncSetAttribute(k_neighbours_direct<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+    cudaError_t e4 = cudaFuncSetAttribute(k_neighbours_direct<2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
     g_attr_err = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : e4));
   });
   return g_attr_err;
@@ -469,10 +469,14 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, float 
     } else {
       const int per_block = e->tuning.block;  // one agent per thread
       const int blocks = (n + per_block - 1) / per_block;
-      if (e->inst.halo == 1)
-        k_neighbours_direct<1><<<blocks, e->tuning.block, e->smemD, s>>>(gI, B);
-      else
-        k_neighbours_direct<2><<<blocks, e->tuning.block, e->smemD, s>>>(gI, B);
+      const bool v8 = e->inst.v == 8;
+      if (e->inst.halo == 1) {
+        if (v8) k_neighbours_direct<1, 8><<<blocks, e->tuning.block, e->smemD, s>>>(gI, B);
+        else k_neighbours_direct<1, 0><<<blocks, e->tuning.block, e->smemD, s>>>(gI, B);
+      } else {
+        if (v8) k_neighbours_direct<2, 8><<<blocks, e->tuning.block, e->smemD, s>>>(gI, B);
+        else k_neighbours_direct<2, 0><<<blocks, e->tuning.block, e->smemD, s>>>(gI, B);
+      }
     }
     CK(cudaGetLastError());
   }

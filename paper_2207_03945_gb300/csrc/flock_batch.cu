@@ -1,0 +1,513 @@
+// Batched flock step: many independent instances of the environment of arXiv
+// 2207.03945 (Section 4.1) advanced by one persistent cooperative kernel.
+//
+// The kernel runs the four phases of a step over flattened work lists that
+// span all active instances, separated by grid barriers:
+//   A  agents  -> apply actions, bin into the instance's cell list
+//   B  cells   -> exclusive scan, 2048-cell tiles (one global scan: instance
+//                 k's cells and agents are contiguous ranges, in the same order)
+//   C  agents  -> counting-sort scatter into cell order
+//   D  chunks  -> 32 consecutive sorted agents of one instance per warp,
+//                 taken from a shared ticket; neighbour scan (direct form)
+// Descriptors and outputs live in device memory read by the kernel, so one
+// captured graph serves every step and every change of the active set.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "flock_device.cuh"
+#include "flock_host.h"
+
+namespace flock {
+
+constexpr int kBatchBlock = 256;
+constexpr int kCtrBarCount = 0, kCtrBarGen = 1, kCtrTicket = 2, kCtrExit = 3;
+
+// Device-resident arguments of the batched kernel.
+struct BatchDev {
+  int n_inst, n_total, c_total, n_scan_tiles;
+  int n_chunks, pad0, pad1, pad2;
+  Bufs B;
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier with a bounded wait.  Returns false (and latches
+// FLOCK_ERR_TIMEOUT) when the wait gives up; the caller then leaves.
+__device__ bool grid_barrier(unsigned *ctr, unsigned *err, unsigned spin_limit, int *flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned gen = ld_acquire(&ctr[kCtrBarGen]);
+    __threadfence();
+    const unsigned arrived = atomicAdd(&ctr[kCtrBarCount], 1u) + 1u;
+    int ok = 1;
+    if (arrived == gridDim.x) {
+      atomicExch(&ctr[kCtrBarCount], 0u);
+      __threadfence();
+      st_release(&ctr[kCtrBarGen], gen + 1u);
+    } else {
+      ok = 0;
+      for (unsigned it = 0; it < spin_limit; ++it) {
+        if (ld_acquire(&ctr[kCtrBarGen]) != gen) {
+          ok = 1;
+          break;
+        }
+        __nanosleep(64);
+      }
+      if (!ok) atomicOr(err, FLOCK_ERR_TIMEOUT);
+    }
+    // a block that gave up, or that sees another block's timeout, stops
+    if (ok && (ld_acquire(err) & FLOCK_ERR_TIMEOUT)) ok = 0;
+    *flag = ok;
+  }
+  __syncthreads();
+  return *flag != 0;
+}
+
+// Largest k with pre[k] <= x, for pre[0] = 0 <= x < pre[n].
+__device__ __forceinline__ int find_inst(const int *pre, int n, int x) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(pre + mid) <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int H, int V>
+__global__ void __launch_bounds__(kBatchBlock) k_batch_step(const BatchDev *__restrict__ d, Inst *insts,
+                                                          const int *__restrict__ apre,
+                                                          const int *__restrict__ cpre,
+                                                          unsigned *ctr, unsigned spin_limit) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ int flag;
+  __shared__ int wsum[33];
+  const BatchDev D = *d;
+  Bufs B = D.B;
+  unsigned err = 0;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gstride = gridDim.x * blockDim.x;
+
+  // ---- phase A: apply actions and bin (Section 4.1: act, then observe) ----
+  for (int f = gtid; f < D.n_total; f += gstride) {
+    const int k = find_inst(apre, D.n_inst, f);
+    const Inst &I = insts[k];
+    phaseA_agent(I, f - I.agent_base, B.actions + I.agent_base, I.reset, B.counts, B.cellrank,
+                 err);
+  }
+  if (!grid_barrier(ctr, B.err, spin_limit, &flag)) goto done;
+
+  // ---- phase B: scan of the cell counts ----
+  for (int t = blockIdx.x; t < D.n_scan_tiles; t += gridDim.x)
+    phaseB_tile(t, B, reinterpret_cast<int *>(smem));
+  if (!grid_barrier(ctr, B.err, spin_limit, &flag)) goto done;
+
+  // ---- phase C: scatter into cell order, cell starts ----
+  {
+    int *tp = reinterpret_cast<int *>(smem);
+    tile_prefix(B, tp, wsum);
+    for (int f = gtid; f < D.n_total; f += gstride) {
+      const int k = find_inst(apre, D.n_inst, f);
+      const Inst &I = insts[k];
+      phaseC_agent(f, I.state + (f - I.agent_base), B, tp);
+    }
+    for (int c = gtid; c <= D.c_total; c += gstride) phaseC_cell(c, B, tp);
+  }
+  if (!grid_barrier(ctr, B.err, spin_limit, &flag)) goto done;
+
+  // ---- phase D: neighbour scan, one chunk of 32 sorted agents per warp ----
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int v = V == 8 ? 8 : insts[0].v;
+    char *wbase = smem + (size_t)warp * (sizeof(Inst) + direct_warp_bytes(v));
+    Inst &sI = *reinterpret_cast<Inst *>(wbase);
+    const DirectArea W = direct_area(wbase + sizeof(Inst), v);
+    int cur = -1;
+    for (;;) {
+      int c = 0;
+      if (lane == 0) c = (int)atomicAdd(&ctr[kCtrTicket], 1u);
+      c = __shfl_sync(kFull, c, 0);
+      if (c >= D.n_chunks) break;
+      const int k = find_inst(cpre, D.n_inst, c);
+      if (k != cur) {
+        const int *src = reinterpret_cast<const int *>(insts + k);
+        int *dst = reinterpret_cast<int *>(&sI);
+        for (int w = lane; w < (int)(sizeof(Inst) / 4); w += 32) dst[w] = src[w];
+        __syncwarp();
+        cur = k;
+      }
+      const int gp0 = sI.agent_base + (c - __ldg(cpre + k)) * 32;
+      const int gp1 = min(gp0 + 32, sI.agent_base + sI.n);
+      phaseD_direct<H, V>(sI, gp0, gp1, B, W, err);
+      // an instance observed without actions goes back to normal stepping
+      if (sI.reset && gp0 == sI.agent_base && lane == 0) insts[k].reset = 0;
+    }
+  }
+
+done:
+  if (err) atomicOr(B.err, err);
+  // the last block out resets the ticket for the next launch
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ctr[kCtrExit], 1u) == gridDim.x - 1) {
+      atomicExch(&ctr[kCtrTicket], 0u);
+      atomicExch(&ctr[kCtrExit], 0u);
+    }
+  }
+}
+
+static size_t batch_smem(int v) {
+  const size_t scan = (size_t)(kScanTile + 34) * 4;
+  const size_t prefix = (size_t)(kMaxScanTiles + 1) * 4;
+  const size_t warps = (size_t)(kBatchBlock / 32) * (sizeof(Inst) + direct_warp_bytes(v));
+  size_t m = scan > prefix ? scan : prefix;
+  return m > warps ? m : warps;
+}
+
+using KFn = void (*)(const BatchDev *, Inst *, const int *, const int *, unsigned *, unsigned);
+
+static KFn batch_kernel(int halo, int v) {
+  if (halo == 1) return v == 8 ? k_batch_step<1, 8> : k_batch_step<1, 0>;
+  return v == 8 ? k_batch_step<2, 8> : k_batch_step<2, 0>;
+}
+
+}  // namespace flock
+
+using namespace flock;
+
+namespace {
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct BLayout {
+  size_t dev, insts, apre, cpre, ctr, err, cellrank, counts, local, cell_start, tile_sum, sxy,
+      sts, sidx, total;
+};
+
+BLayout batch_layout(int mi, int ma, int mc) {
+  BLayout L{};
+  size_t o = 0;
+  auto take = [&](size_t b) { size_t at = o; o = a256(o + b); return at; };
+  const int nT = (mc + kScanTile - 1) / kScanTile;
+  L.dev = take(sizeof(BatchDev));
+  L.insts = take((size_t)mi * sizeof(Inst));
+  L.apre = take((size_t)(mi + 1) * 4);
+  L.cpre = take((size_t)(mi + 1) * 4);
+  L.ctr = take(64);
+  L.err = take(64);
+  L.cellrank = take((size_t)ma * 8);
+  L.counts = take((size_t)mc * 4);
+  L.local = take((size_t)mc * 4);
+  L.cell_start = take((size_t)(mc + 1) * 4);
+  L.tile_sum = take((size_t)(nT + 1) * 4);
+  L.sxy = take((size_t)ma * 8);
+  L.sts = take((size_t)ma * 8);
+  L.sidx = take((size_t)ma * 4);
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+struct flock_batch {
+  int max_inst, max_agents, max_cells;
+  flock_tuning tuning;
+  BLayout lay;
+  char *ws;
+  cudaStream_t stream, cap_stream;
+  cudaGraphExec_t graph;
+  int grid, v, halo;
+  unsigned spin_limit;
+  BatchDev dev;  // host copy
+  std::vector<Inst> insts;
+  std::vector<int> apre, cpre;
+  const void *g_act, *g_obs, *g_rew, *g_coll;
+  int timing;
+  cudaEvent_t ev[2];
+  bool configured;
+};
+
+extern "C" int flock_instance_cells(const flock_params *p, const flock_tuning *t, int *cells) {
+  if (!p || !cells) return FLOCK_EINVAL;
+  Inst I;
+  int rc = derive(*p, (t && t->stencil) ? t->stencil : 1, I, nullptr);
+  if (rc) return rc;
+  *cells = I.ncells;
+  return FLOCK_OK;
+}
+
+extern "C" int flock_batch_workspace_bytes(int mi, int ma, int mc, const flock_tuning *t,
+                                           size_t *bytes) {
+  (void)t;
+  if (!bytes || mi < 1 || ma < 0 || mc < 1 || mc > kMaxScanTiles * kScanTile) return FLOCK_EINVAL;
+  *bytes = batch_layout(mi, ma, mc).total;
+  return FLOCK_OK;
+}
+
+#define BCK(call)                                       \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+extern "C" int env_batch_create(int mi, int ma, int mc, const flock_tuning *t, void *ws,
+                                size_t ws_bytes, void *stream, flock_batch **out) {
+  if (!out) return FLOCK_EINVAL;
+  *out = nullptr;
+  if (mi < 1 || ma < 0 || mc < 1 || mc > kMaxScanTiles * kScanTile) return FLOCK_EINVAL;
+  flock_batch *b = new (std::nothrow) flock_batch();
+  if (!b) return FLOCK_EINVAL;
+  b->max_inst = mi;
+  b->max_agents = ma;
+  b->max_cells = mc;
+  b->tuning = flock_tuning{};
+  if (t) b->tuning = *t;
+  b->halo = b->tuning.stencil ? b->tuning.stencil : 1;
+  if (b->halo != 1 && b->halo != 2) { delete b; return FLOCK_EINVAL; }
+  b->tuning.stencil = b->halo;
+  b->tuning.mode = 2;
+  b->tuning.block = kBatchBlock;
+  b->lay = batch_layout(mi, ma, mc);
+  if (!ws || ((uintptr_t)ws & 255) || ws_bytes < b->lay.total) { delete b; return FLOCK_ENOSPACE; }
+  b->ws = (char *)ws;
+  b->stream = (cudaStream_t)stream;
+  b->spin_limit = 1u << 22;
+  b->v = 0;
+  int dev = 0, coop = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop) { delete b; return FLOCK_EINVAL; }
+  cudaError_t ce = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (ce != cudaSuccess) { delete b; return cuda_fail(ce, "cudaStreamCreate"); }
+  const BLayout &L = b->lay;
+  ce = cudaMemsetAsync(b->ws + L.counts, 0, (size_t)mc * 4, b->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(b->ws + L.ctr, 0, 128, b->stream);
+  if (ce != cudaSuccess) {
+    cudaStreamDestroy(b->cap_stream);
+    delete b;
+    return cuda_fail(ce, "env_batch_create memset");
+  }
+  *out = b;
+  return FLOCK_OK;
+}
+
+extern "C" int env_batch_set(flock_batch *b, int n_inst, const flock_params *params,
+                             const int *n_agents, float *const *state, const int *reset) {
+  if (!b || n_inst < 0 || n_inst > b->max_inst || (n_inst > 0 && (!params || !n_agents || !state)))
+    return FLOCK_EINVAL;
+  std::vector<Inst> ins((size_t)(n_inst > 0 ? n_inst : 1));
+  std::vector<int> apre((size_t)n_inst + 1), cpre((size_t)n_inst + 1);
+  long long na = 0, ncell = 0, nchunk = 0;
+  int v = 0;
+  for (int k = 0; k < n_inst; ++k) {
+    Inst &I = ins[k];
+    int rc = derive(params[k], b->halo, I, nullptr);
+    if (rc) return rc;
+    if (n_agents[k] < 0 || (n_agents[k] > 0 && !state[k])) return FLOCK_EINVAL;
+    if (k == 0) v = I.v;
+    if (I.v != v) return FLOCK_EINVAL;  // one sector count per batch
+    I.n = n_agents[k];
+    I.state = reinterpret_cast<float4 *>(state[k]);
+    I.agent_base = (int)na;
+    I.cell_base = (int)ncell;
+    I.chunk_base = (int)nchunk;
+    I.obs_base = na * (long long)I.obs_dim;
+    I.reset = reset ? (reset[k] != 0) : 0;
+    apre[k] = (int)na;
+    cpre[k] = (int)nchunk;
+    na += I.n;
+    ncell += I.ncells;
+    nchunk += (I.n + 31) / 32;
+    if (na > b->max_agents || ncell > b->max_cells) return FLOCK_EINVAL;
+  }
+  apre[n_inst] = (int)na;
+  cpre[n_inst] = (int)nchunk;
+  if (n_inst > 0 && v != b->v) {
+    // the kernel variant (and its shared memory) depends on v
+    KFn fn = batch_kernel(b->halo, v);
+    const size_t sm = batch_smem(v);
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    BCK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kBatchBlock, sm));
+    if (per < 1) return FLOCK_EINVAL;  // too many sectors for one block
+    b->grid = per * sms;
+    b->v = v;
+    if (b->graph) {
+      BCK(cudaStreamSynchronize(b->stream));
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+  }
+  const BLayout &L = b->lay;
+  BatchDev &D = b->dev;
+  D.n_inst = n_inst;
+  D.n_total = (int)na;
+  D.c_total = (int)ncell;
+  D.n_scan_tiles = n_inst > 0 ? (int)((ncell + kScanTile - 1) / kScanTile) : 0;
+  D.n_chunks = (int)nchunk;
+  Bufs &B = D.B;
+  B.cellrank = (int2 *)(b->ws + L.cellrank);
+  B.counts = (int *)(b->ws + L.counts);
+  B.local = (int *)(b->ws + L.local);
+  B.cell_start = (int *)(b->ws + L.cell_start);
+  B.tile_sum = (int *)(b->ws + L.tile_sum);
+  B.sxy = (float2 *)(b->ws + L.sxy);
+  B.sts = (float2 *)(b->ws + L.sts);
+  B.sidx = (int *)(b->ws + L.sidx);
+  B.err = (unsigned *)(b->ws + L.err);
+  B.bar = (unsigned *)(b->ws + L.ctr);
+  B.n_total = D.n_total;
+  B.c_total = D.c_total;
+  B.n_scan_tiles = D.n_scan_tiles;
+  b->insts.swap(ins);
+  b->apre.swap(apre);
+  b->cpre.swap(cpre);
+  if (n_inst > 0) {
+    BCK(cudaMemcpyAsync(b->ws + L.insts, b->insts.data(), (size_t)n_inst * sizeof(Inst),
+                        cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaMemcpyAsync(b->ws + L.apre, b->apre.data(), (size_t)(n_inst + 1) * 4,
+                        cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaMemcpyAsync(b->ws + L.cpre, b->cpre.data(), (size_t)(n_inst + 1) * 4,
+                        cudaMemcpyHostToDevice, b->stream));
+  }
+  b->g_act = b->g_obs = b->g_rew = b->g_coll = nullptr;  // outputs re-uploaded at next step
+  b->configured = true;
+  return FLOCK_OK;
+}
+
+static int batch_enqueue(flock_batch *b, cudaStream_t s) {
+  const BLayout &L = b->lay;
+  if (b->timing) BCK(cudaEventRecordWithFlags(b->ev[0], s, cudaEventRecordExternal));
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(b->grid);
+  cfg.blockDim = dim3(kBatchBlock);
+  cfg.dynamicSmemBytes = batch_smem(b->v);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  KFn fn = batch_kernel(b->halo, b->v);
+  BCK(cudaLaunchKernelEx(&cfg, fn, (const BatchDev *)(b->ws + L.dev), (Inst *)(b->ws + L.insts),
+                         (const int *)(b->ws + L.apre), (const int *)(b->ws + L.cpre),
+                         (unsigned *)(b->ws + L.ctr), b->spin_limit));
+  if (b->timing) BCK(cudaEventRecordWithFlags(b->ev[1], s, cudaEventRecordExternal));
+  return FLOCK_OK;
+}
+
+extern "C" int env_batch_step(flock_batch *b, const int32_t *act, float *obs, float *rew,
+                              int32_t *coll) {
+  if (!b || !b->configured) return FLOCK_EINVAL;
+  if (b->dev.n_total == 0) return FLOCK_OK;
+  if (!act || !obs || !rew || !coll || ((uintptr_t)obs & 7)) return FLOCK_EINVAL;
+  if (act != b->g_act || obs != b->g_obs || rew != b->g_rew || coll != b->g_coll) {
+    b->dev.B.actions = act;
+    b->dev.B.obs = obs;
+    b->dev.B.reward = rew;
+    b->dev.B.coll = coll;
+    BCK(cudaMemcpyAsync(b->ws + b->lay.dev, &b->dev, sizeof(BatchDev), cudaMemcpyHostToDevice,
+                        b->stream));
+    b->g_act = act;
+    b->g_obs = obs;
+    b->g_rew = rew;
+    b->g_coll = coll;
+  }
+  if (!b->graph) {
+    cudaGraph_t g = nullptr;
+    BCK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = batch_enqueue(b, b->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+    ce = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+      b->graph = nullptr;
+      return cuda_fail(ce, "cudaGraphInstantiate");
+    }
+  }
+  BCK(cudaGraphLaunch(b->graph, b->stream));
+  return FLOCK_OK;
+}
+
+extern "C" int env_batch_get_error(flock_batch *b, uint32_t *bits) {
+  if (!b || !bits) return FLOCK_EINVAL;
+  uint32_t w = 0;
+  BCK(cudaMemcpyAsync(&w, b->ws + b->lay.err, 4, cudaMemcpyDeviceToHost, b->stream));
+  BCK(cudaMemsetAsync(b->ws + b->lay.err, 0, 4, b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  if (w & FLOCK_ERR_TIMEOUT) {
+    // a barrier gave up: the barrier counters and the cell counts may be
+    // mid-step; start them over
+    BCK(cudaMemsetAsync(b->ws + b->lay.ctr, 0, 64, b->stream));
+    BCK(cudaMemsetAsync(b->ws + b->lay.counts, 0, (size_t)b->max_cells * 4, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+  }
+  *bits = w;
+  return FLOCK_OK;
+}
+
+extern "C" int env_batch_set_spin_limit(flock_batch *b, unsigned limit) {
+  if (!b) return FLOCK_EINVAL;
+  if (b->graph) {
+    BCK(cudaStreamSynchronize(b->stream));
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  b->spin_limit = limit;
+  return FLOCK_OK;
+}
+
+extern "C" int env_batch_get_launch(const flock_batch *b, int *grid, int *block) {
+  if (!b || !grid || !block) return FLOCK_EINVAL;
+  *grid = b->grid;
+  *block = kBatchBlock;
+  return FLOCK_OK;
+}
+
+extern "C" int env_batch_set_timing(flock_batch *b, int enable) {
+  if (!b) return FLOCK_EINVAL;
+  if (enable && !b->ev[0])
+    for (int k = 0; k < 2; ++k) BCK(cudaEventCreate(&b->ev[k]));
+  if ((enable != 0) != (b->timing != 0) && b->graph) {
+    BCK(cudaStreamSynchronize(b->stream));
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  b->timing = enable != 0;
+  return FLOCK_OK;
+}
+
+extern "C" int env_batch_get_time(flock_batch *b, float *ms) {
+  if (!b || !ms || !b->timing) return FLOCK_EINVAL;
+  BCK(cudaEventSynchronize(b->ev[1]));
+  BCK(cudaEventElapsedTime(ms, b->ev[0], b->ev[1]));
+  return FLOCK_OK;
+}
+
+extern "C" void env_batch_destroy(flock_batch *b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  for (int k = 0; k < 2; ++k)
+    if (b->ev[k]) cudaEventDestroy(b->ev[k]);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+}

@@ -31,8 +31,9 @@ constexpr int kMaxTileW = 64, kMaxTileH = 8;
 constexpr int kMaxStagedCells = (kMaxTileH + 4) * (kMaxTileW + 4);
 
 // Per-instance descriptor.  A single environment has one; a batch has one
-// per active instance.  Lives in device memory (the workspace).
-struct Inst {
+// per active instance.  Lives in device memory (the workspace); 16-byte
+// aligned so that per-warp shared copies keep the areas after them aligned.
+struct alignas(16) Inst {
   float4 *state;       // resident state (x, y, theta, s), updated in place
   long long obs_base;  // first float of this instance's obs rows
   int n, nc, ncells, v;
@@ -45,6 +46,8 @@ struct Inst {
   long long PK, NMAX;
   float T[kMaxV + 1];
 };
+
+static_assert(sizeof(Inst) % 16 == 0, "Inst must keep 16-byte alignment");
 
 // Scratch and output pointers of one step (flattened over all instances).
 struct Bufs {
@@ -752,12 +755,42 @@ __device__ __forceinline__ DirectArea direct_area(char *base, int v) {
   return W;
 }
 
-// Drain for the direct form: separate in-range and collision counters (an
-// agent may have any number of neighbours here).
+// Sector search with the edges in registers: for V = 8 a three-level
+// binary search over T[1..7] with selects; otherwise the generic search.
+template <int V>
+struct Edges {
+  float t[8];
+  __device__ __forceinline__ void load(const Inst &I) {
+    if (V == 8) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) t[m] = I.T[m + 1];
+    }
+  }
+  // returns the sector, or -1 when outside the field of view
+  __device__ __forceinline__ int sector(const Inst &I, float p) const {
+    if (V == 8) {
+      if (!I.full && p >= t[7]) return -1;
+      const bool b2 = p >= t[3];
+      const float t1 = b2 ? t[5] : t[1];
+      const bool b1 = p >= t1;
+      const float t0 = b2 ? (b1 ? t[6] : t[4]) : (b1 ? t[2] : t[0]);
+      const bool b0 = p >= t0;
+      return (b2 ? 4 : 0) + (b1 ? 2 : 0) + (b0 ? 1 : 0);
+    } else {
+      if (!I.full && p >= I.T[I.v]) return -1;
+      return sector_of(p, I.T, I.v);
+    }
+  }
+};
+
+// Drain for the direct form.  In-range and collision counts are kept by the
+// owner lanes during the candidate scan; here each queued pair adds its ramp
+// term (non-colliding pairs) and its sector minimum and count.
+template <int V>
 __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W, int count,
-                                            float ux, float uy) {
+                                            float ux, float uy, const Edges<V> &E8) {
   const int lane = threadIdx.x & 31;
-  const int v = I.v;
+  const int v = V == 8 ? 8 : I.v;
   for (int e0 = 0; e0 < count; e0 += 32) {
     const int e = e0 + lane;
     const bool valid = e < count;
@@ -766,10 +799,7 @@ __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W,
     const float uxo = __shfl_sync(kFull, ux, o), uyo = __shfl_sync(kFull, uy, o);
     if (valid) {
       const float dx = E.x, dy = E.y, d2 = E.z;
-      atomicAdd(&W.nin[o], 1);
-      if (d2 < I.RC2) {  // Fig. 4: collision below 2 d_r
-        atomicAdd(&W.ncoll[o], 1);
-      } else {
+      if (!(d2 < I.RC2)) {
         const float t = fmul(fsub(I.RV, fsqrt(d2)), I.INV_SPAN);
         const unsigned long long tv = float_int_u64(fmul(t, I.scaleK));
         if (tv) atomicAdd(&W.acc[o], tv);
@@ -779,8 +809,8 @@ __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W,
       if (lx != 0.0f || ly != 0.0f) {
         float p = pseudo_angle(lx, ly);
         if (p >= 4.0f) p = 0.0f;
-        if (I.full || p < I.T[v]) {
-          const int key = sector_of(p, I.T, v);
+        const int key = E8.sector(I, p);
+        if (key >= 0) {
           atomicMin(&W.md[o * v + key], __float_as_uint(d2));
           atomicAdd(&W.cn[o * v + key], 1);
         }
@@ -792,10 +822,11 @@ __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W,
 
 // One run of candidates [a, a + n) with shifts (sx, sy); appends in-range
 // pairs to the queue (warp-uniform loop), draining when nearly full.
-template <bool SHIFT>
+template <bool SHIFT, int V>
 __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, const float2 *sxy,
                                            int a, int n, int self, float sx, float sy, float xi,
-                                           float yi, float ux, float uy, int &qn) {
+                                           float yi, float ux, float uy, int &qn, int &nin,
+                                           int &ncoll, const Edges<V> &E8) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const int maxn = __reduce_max_sync(kFull, (unsigned)n);
@@ -813,23 +844,29 @@ __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, c
       }
       d2 = fadd(fmul(dx, dx), fmul(dy, dy));
       inr = d2 < I.RV2;  // Eq. 1: d_ij < d_v
+      if (inr) {
+        nin++;
+        ncoll += d2 < I.RC2 ? 1 : 0;  // Fig. 4: collision below 2 d_r
+      }
     }
     const unsigned m = __ballot_sync(kFull, inr);
     if (inr) W.queue[qn + __popc(m & lt)] = make_float4(dx, dy, d2, __int_as_float(lane));
     qn += __popc(m);
     if (qn > kQueue - 32) {
       __syncwarp();
-      drain_direct(I, W, qn, ux, uy);
+      drain_direct<V>(I, W, qn, ux, uy, E8);
       qn = 0;
     }
   }
 }
 
-template <int H>
+template <int H, int V>
 __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
                               const DirectArea &W, unsigned &err) {
   const int lane = threadIdx.x & 31;
-  const int nc = I.nc, v = I.v;
+  const int nc = I.nc, v = V == 8 ? 8 : I.v;
+  Edges<V> E8;
+  E8.load(I);
   const int gp = gp0 + lane;
   const bool have = gp < gp1;
   const int nb = gp1 - gp0;
@@ -850,12 +887,21 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
   const float ux = fadd(fmul(c, I.CF), fmul(sn, I.SF));
   const float uy = fsub(fmul(sn, I.CF), fmul(c, I.SF));
   W.acc[lane] = 0ull;
-  W.nin[lane] = 0;
-  W.ncoll[lane] = 0;
-  for (int k = 0; k < v; ++k) {
-    W.md[lane * v + k] = 0x7f800000u;
-    W.cn[lane * v + k] = 0;
+  if (V == 8) {
+    uint4 *m4 = reinterpret_cast<uint4 *>(W.md + lane * 8);
+    int4 *c4 = reinterpret_cast<int4 *>(W.cn + lane * 8);
+    const unsigned inf = 0x7f800000u;
+    m4[0] = make_uint4(inf, inf, inf, inf);
+    m4[1] = make_uint4(inf, inf, inf, inf);
+    c4[0] = make_int4(0, 0, 0, 0);
+    c4[1] = make_int4(0, 0, 0, 0);
+  } else {
+    for (int k = 0; k < v; ++k) {
+      W.md[lane * v + k] = 0x7f800000u;
+      W.cn[lane * v + k] = 0;
+    }
   }
+  int nin = 0, ncoll = 0;
   // stencil columns [cx - H, cx + H] split into runs that do not wrap
   const int vlo = cx - H, vhi = cx + H + 1;
   const int ma = max(vlo, 0), mb = min(vhi, nc);  // interior run
@@ -875,21 +921,24 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
   if (!wrap_any) {
 #pragma unroll
     for (int r = 0; r < 2 * H + 1; ++r)
-      direct_run<false>(I, W, B.sxy, ra[r], rn[r], self, 0.f, 0.f, xi, yi, ux, uy, qn);
+      direct_run<false, V>(I, W, B.sxy, ra[r], rn[r], self, 0.f, 0.f, xi, yi, ux, uy, qn, nin,
+                           ncoll, E8);
   } else {
 #pragma unroll
     for (int r = 0; r < 2 * H + 1; ++r) {
       const int vr = cy - H + r;
       const float sy = vr < 0 ? -I.L : (vr >= nc ? I.L : 0.0f);
       const int rowg = I.cell_base + wrapi(vr, nc) * nc;
-      direct_run<true>(I, W, B.sxy, ra[r], rn[r], self, 0.f, sy, xi, yi, ux, uy, qn);
+      direct_run<true, V>(I, W, B.sxy, ra[r], rn[r], self, 0.f, sy, xi, yi, ux, uy, qn, nin,
+                          ncoll, E8);
       // cells across the left boundary: virtual columns [vlo, 0) -> [vlo + nc, nc)
       int a = 0, n = 0;
       if (have && lw) {
         a = cst[rowg + vlo + nc];
         n = cst[rowg + nc] - a;
       }
-      direct_run<true>(I, W, B.sxy, a, n, self, -I.L, sy, xi, yi, ux, uy, qn);
+      direct_run<true, V>(I, W, B.sxy, a, n, self, -I.L, sy, xi, yi, ux, uy, qn, nin, ncoll,
+                          E8);
       // cells across the right boundary: virtual columns [nc, vhi) -> [0, vhi - nc)
       a = 0;
       n = 0;
@@ -897,18 +946,17 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
         a = cst[rowg];
         n = cst[rowg + vhi - nc] - a;
       }
-      direct_run<true>(I, W, B.sxy, a, n, self, I.L, sy, xi, yi, ux, uy, qn);
+      direct_run<true, V>(I, W, B.sxy, a, n, self, I.L, sy, xi, yi, ux, uy, qn, nin, ncoll, E8);
     }
   }
   __syncwarp();
-  drain_direct(I, W, qn, ux, uy);
+  drain_direct<V>(I, W, qn, ux, uy, E8);
   // reward and collisions
   if (have) {
-    const int ncoll = W.ncoll[lane];
     const long long total = (long long)W.acc[lane] - (long long)ncoll * I.PK;
     B.reward[I.agent_base + i] = fmul(__ll2float_rn(total), I.inv_scaleK);
     B.coll[I.agent_base + i] = ncoll;
-    if ((long long)W.nin[lane] > I.NMAX) err |= FLOCK_ERR_OVERFLOW;
+    if ((long long)nin > I.NMAX) err |= FLOCK_ERR_OVERFLOW;
   }
   // observation rows, written whole and contiguous
   const int P = v + 1;
