@@ -253,11 +253,16 @@ cudaError_t set_kernel_attrs() {
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int want = maxsm - (int)sizeof(Inst) - 1024;
-    cudaError_t e1 = cudaFuncSetAttribute(k_neighbours<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
-    cudaError_t e2 = cudaFuncSetAttribute(k_neighbours<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
-    cudaError_t e3 = cudaFuncSetAttribute(k_neighbours_direct<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
-    cudaError_t e4 = cudaFuncSetAttribute(k_neighbours_direct<2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
-    g_attr_err = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : e4));
+    const void *fns[] = {(const void *)k_neighbours<1>, (const void *)k_neighbours<2>,
+                         (const void *)k_neighbours_direct<1, 0>,
+                         (const void *)k_neighbours_direct<2, 0>,
+                         (const void *)k_neighbours_direct<1, 8>,
+                         (const void *)k_neighbours_direct<2, 8>};
+    g_attr_err = cudaSuccess;
+    for (const void *f : fns) {
+      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+      if (e != cudaSuccess && g_attr_err == cudaSuccess) g_attr_err = e;
+    }
   });
   return g_attr_err;
 }

@@ -22,7 +22,7 @@
 namespace flock {
 
 constexpr int kBatchBlock = 256;
-constexpr int kCtrBarCount = 0, kCtrBarGen = 1, kCtrTicket = 2, kCtrExit = 3;
+constexpr int kCtrBarCount = 0, kCtrBarGen = 1, kCtrTicket = 2, kCtrExit = 3, kCtrAbort = 4;
 
 // Device-resident arguments of the batched kernel.
 struct BatchDev {
@@ -63,10 +63,13 @@ __device__ bool grid_barrier(unsigned *ctr, unsigned *err, unsigned spin_limit, 
         }
         __nanosleep(64);
       }
-      if (!ok) atomicOr(err, FLOCK_ERR_TIMEOUT);
+      if (!ok) {
+        atomicOr(err, FLOCK_ERR_TIMEOUT);
+        atomicExch(&ctr[kCtrAbort], 1u);
+      }
     }
-    // a block that gave up, or that sees another block's timeout, stops
-    if (ok && (ld_acquire(err) & FLOCK_ERR_TIMEOUT)) ok = 0;
+    // a block that gave up, or that sees that another one did, stops
+    if (ok && ld_acquire(&ctr[kCtrAbort])) ok = 0;
     *flag = ok;
   }
   __syncthreads();
@@ -156,12 +159,25 @@ __global__ void __launch_bounds__(kBatchBlock) k_batch_step(const BatchDev *__re
 
 done:
   if (err) atomicOr(B.err, err);
-  // the last block out resets the ticket for the next launch
+  // The last block out restores the counters for the next launch.  After an
+  // abort the barrier count and the cell counts may be mid-step; the cell
+  // counts are cleared here so that no later step scatters with them.
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    if (atomicAdd(&ctr[kCtrExit], 1u) == gridDim.x - 1) {
+    const bool last = atomicAdd(&ctr[kCtrExit], 1u) == gridDim.x - 1;
+    flag = last ? (ld_acquire(&ctr[kCtrAbort]) ? 2 : 1) : 0;
+  }
+  __syncthreads();
+  if (flag == 2)
+    for (int c = threadIdx.x; c < D.c_total; c += blockDim.x) B.counts[c] = 0;
+  if (flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicExch(&ctr[kCtrBarCount], 0u);
       atomicExch(&ctr[kCtrTicket], 0u);
+      atomicExch(&ctr[kCtrAbort], 0u);
       atomicExch(&ctr[kCtrExit], 0u);
     }
   }
@@ -292,7 +308,8 @@ extern "C" int env_batch_create(int mi, int ma, int mc, const flock_tuning *t, v
   if (ce != cudaSuccess) { delete b; return cuda_fail(ce, "cudaStreamCreate"); }
   const BLayout &L = b->lay;
   ce = cudaMemsetAsync(b->ws + L.counts, 0, (size_t)mc * 4, b->stream);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(b->ws + L.ctr, 0, 128, b->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(b->ws + L.ctr, 0, 64, b->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(b->ws + L.err, 0, 64, b->stream);
   if (ce != cudaSuccess) {
     cudaStreamDestroy(b->cap_stream);
     delete b;
@@ -454,8 +471,8 @@ extern "C" int env_batch_get_error(flock_batch *b, uint32_t *bits) {
   BCK(cudaMemsetAsync(b->ws + b->lay.err, 0, 4, b->stream));
   BCK(cudaStreamSynchronize(b->stream));
   if (w & FLOCK_ERR_TIMEOUT) {
-    // a barrier gave up: the barrier counters and the cell counts may be
-    // mid-step; start them over
+    // the kernel restored its counters on the way out; clear them once more
+    // from the host in case the step was cut short in an unforeseen place
     BCK(cudaMemsetAsync(b->ws + b->lay.ctr, 0, 64, b->stream));
     BCK(cudaMemsetAsync(b->ws + b->lay.counts, 0, (size_t)b->max_cells * 4, b->stream));
     BCK(cudaStreamSynchronize(b->stream));

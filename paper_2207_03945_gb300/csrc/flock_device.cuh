@@ -277,6 +277,10 @@ __device__ __forceinline__ void phaseC_agent(int f, const float4 *state_i, const
   const int2 cr = B.cellrank[f];
   const float4 st = *state_i;
   const int pos = tp[cr.x / kScanTile] + B.local[cr.x] + cr.y;
+  if ((unsigned)pos >= (unsigned)B.n_total) {  // inconsistent counts: never write out of range
+    atomicOr(B.err, FLOCK_ERR_STATE);
+    return;
+  }
   B.sxy[pos] = make_float2(st.x, st.y);
   B.sts[pos] = make_float2(st.z, st.w);
   B.sidx[pos] = f;
