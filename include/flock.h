@@ -236,6 +236,41 @@ int env_batch_get_time(flock_batch *batch, float *ms_out);
 
 void env_batch_destroy(flock_batch *batch);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free step.  (The paper has no counterpart: this entry point exists
+ * for callers of this library that cannot allocate device memory -- code in a
+ * host callback or real-time loop where cudaMalloc may block or is not
+ * allowed, or a plugin whose host application owns all device memory.)
+ *
+ * One step of a flock environment of n_agents agents, with every scratch
+ * buffer taken from a fixed array of FLOCK_STATIC_SCRATCH_BYTES bytes that
+ * the library declares in device memory.  Each GPU that loads the library
+ * holds that array until the process exits.  The caller passes only:
+ *   state_dev    n x 4 floats, read and updated in place;
+ *   actions_dev  n int32, or NULL to observe the state without moving it;
+ *   obs_dev, reward_dev, coll_dev  the outputs, as for env_step.
+ * The call enqueues on `stream` and returns; with error_bits_out non-NULL it
+ * waits for the stream and stores the FLOCK_ERR_* bits of this call.
+ *
+ * Limits: at most FLOCK_STATIC_MAX_AGENTS agents and a cell list of at most
+ * FLOCK_STATIC_MAX_CELLS cells (cells_per_side^2 of flock_derive with the
+ * default 3 x 3 stencil); larger sizes return FLOCK_EINVAL.  The call does
+ * no cudaMalloc or cudaFree and calls no allocating library routine.
+ *
+ * Every call on a device uses the same array, which keeps the previous
+ * call's contents; the call clears what must start at zero itself.  Calls
+ * whose work overlaps on the GPU (different streams, or threads without
+ * ordering) race on the array: order them on one stream.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) for that
+ * device; make that first call before any stream capture is in progress.
+ * ------------------------------------------------------------------------- */
+#define FLOCK_STATIC_MAX_AGENTS 65536
+#define FLOCK_STATIC_MAX_CELLS 32768
+#define FLOCK_STATIC_SCRATCH_BYTES 2229760
+int flock_step_static(const flock_params *params, int n_agents, float *state_dev,
+                      const int32_t *actions_dev, float *obs_dev, float *reward_dev,
+                      int32_t *coll_dev, void *stream, uint32_t *error_bits_out);
+
 /* Last CUDA error string seen by the library in this process (or ""). */
 const char *flock_last_cuda_error(void);
 

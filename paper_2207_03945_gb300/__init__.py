@@ -26,6 +26,7 @@ __all__ = [
     "flock_batch_workspace_bytes", "env_batch_create", "env_batch_set", "env_batch_step",
     "env_batch_get_error", "env_batch_set_spin_limit", "env_batch_get_launch",
     "env_batch_set_timing", "env_batch_get_time", "env_batch_destroy", "FlockBatch",
+    "flock_step_static",
 ]
 
 lib_path = _abi.LIB_PATH
@@ -399,3 +400,26 @@ class FlockBatch:
                 self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# Allocation-free step
+# ---------------------------------------------------------------------------
+def flock_step_static(params: dict, state, actions, obs, reward, coll, stream=None,
+                      wait: bool = True):
+    """One step whose scratch lives in the library's fixed device array, for
+    callers that cannot allocate device memory (see flock.h).  state (n x 4)
+    is updated in place; actions None observes without moving.  With wait,
+    returns the step's FLOCK_ERR_* bits after the stream has finished."""
+    torch = _torch()
+    n = int(state.shape[0])
+    d = 2 * int(params["num_segments"]) + 2
+    bits = ctypes.c_uint32(0)
+    _abi.check(_abi.lib.flock_step_static(
+        ctypes.byref(_abi.params_from_dict(params)), n,
+        _ptr(state, torch.float32, (n, 4), "state"),
+        _ptr(actions, torch.int32, (n,), "actions") if actions is not None else None,
+        _ptr(obs, torch.float32, (n, d), "obs"), _ptr(reward, torch.float32, (n,), "reward"),
+        _ptr(coll, torch.int32, (n,), "coll"), _stream(stream),
+        ctypes.byref(bits) if wait else None))
+    return int(bits.value) if wait else None

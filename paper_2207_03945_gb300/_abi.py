@@ -18,6 +18,8 @@ FLOCK_ERR_STATE = 2
 FLOCK_ERR_TIMEOUT = 4
 FLOCK_ERR_OVERFLOW = 8
 MAX_SEGMENTS = 128
+STATIC_MAX_AGENTS = 65536
+STATIC_MAX_CELLS = 32768
 
 _NAMES = {FLOCK_EINVAL: "FLOCK_EINVAL", FLOCK_ENOSPACE: "FLOCK_ENOSPACE",
           FLOCK_ECUDA: "FLOCK_ECUDA"}
@@ -118,6 +120,8 @@ def _load():
         "env_batch_get_launch": [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "env_batch_set_timing": [vp, ctypes.c_int],
         "env_batch_get_time": [vp, ctypes.POINTER(ctypes.c_float)],
+        "flock_step_static": [P, ctypes.c_int, vp, vp, vp, vp, vp, vp,
+                              ctypes.POINTER(ctypes.c_uint32)],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)

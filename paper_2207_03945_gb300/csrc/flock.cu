@@ -631,3 +631,150 @@ extern "C" void env_destroy(flock_env *e) {
   if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
   delete e;
 }
+
+
+// ---------------------------------------------------------------------------
+// Allocation-free step.
+//
+// Some callers cannot allocate device memory at all: code that runs inside a
+// host callback or a real-time loop where cudaMalloc may block or is
+// forbidden, plugins whose host application owns every allocation, and
+// processes that must not touch a caching allocator they do not control.
+// flock_step_static serves them: the caller passes only the state, the
+// actions and the outputs; everything else the step needs (cell counts,
+// offsets, sorted copies, the parameter descriptor, the error word) lives in
+// the fixed device array below, which every GPU that loads this library
+// holds for the lifetime of the process.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kStaticMaxAgents = FLOCK_STATIC_MAX_AGENTS;
+constexpr int kStaticMaxCells = FLOCK_STATIC_MAX_CELLS;
+constexpr int kStaticScanTiles = (kStaticMaxCells + kScanTile - 1) / kScanTile;
+
+// Byte offsets inside the array (each 256-byte aligned).
+constexpr size_t sa(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t kSInst = 0;
+constexpr size_t kSErr = sa(kSInst + sizeof(Inst));
+constexpr size_t kSCellrank = sa(kSErr + 64);
+constexpr size_t kSCounts = sa(kSCellrank + (size_t)kStaticMaxAgents * 8);
+constexpr size_t kSLocal = sa(kSCounts + (size_t)kStaticMaxCells * 4);
+constexpr size_t kSCellStart = sa(kSLocal + (size_t)kStaticMaxCells * 4);
+constexpr size_t kSTileSum = sa(kSCellStart + (size_t)(kStaticMaxCells + 1) * 4);
+constexpr size_t kSSxy = sa(kSTileSum + (size_t)(kStaticScanTiles + 1) * 4);
+constexpr size_t kSSts = sa(kSSxy + (size_t)kStaticMaxAgents * 8);
+constexpr size_t kSSidx = sa(kSSts + (size_t)kStaticMaxAgents * 8);
+constexpr size_t kSBytes = sa(kSSidx + (size_t)kStaticMaxAgents * 4);
+static_assert(kSBytes == FLOCK_STATIC_SCRATCH_BYTES, "flock.h states the scratch size");
+
+}  // namespace
+
+// The scratch of flock_step_static: one per device, shared by every call.
+static __device__ __align__(256) char g_flock_static_scratch[kSBytes];
+
+namespace {
+
+std::mutex g_static_mu;
+char *g_static_ptr[256];  // device address of the array, per device ordinal
+
+// Device address of the scratch array on the current device (set up on the
+// first call for that device).  In host code the array's name is only a
+// host-side stand-in, so the address must come from cudaGetSymbolAddress.
+int static_scratch(char **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 256) return FLOCK_EINVAL;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_flock_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+    g_static_ptr[dev] = (char *)p;
+  }
+  *out = g_static_ptr[dev];
+  return FLOCK_OK;
+}
+
+}  // namespace
+
+extern "C" int flock_step_static(const flock_params *p, int n, float *state_dev,
+                                 const int32_t *actions_dev, float *obs_dev, float *reward_dev,
+                                 int32_t *coll_dev, void *stream, uint32_t *error_bits_out) {
+  if (!p || n < 0) return FLOCK_EINVAL;
+  if (n > kStaticMaxAgents) return FLOCK_EINVAL;  // more agents than the fixed scratch holds
+  Inst I;
+  int rc = derive(*p, 1, I, nullptr);
+  if (rc) return rc;
+  if (I.ncells > kStaticMaxCells) return FLOCK_EINVAL;  // cell list larger than the scratch
+  if (n > 0 && (!state_dev || !obs_dev || !reward_dev || !coll_dev || ((uintptr_t)obs_dev & 7)))
+    return FLOCK_EINVAL;
+  char *sp = nullptr;
+  rc = static_scratch(&sp);
+  if (rc) return rc;
+  cudaError_t ce = set_kernel_attrs();
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaFuncSetAttribute");
+  flock_tuning t{};
+  t.stencil = 1;
+  t.mode = 2;
+  t.block = 128;
+  I.n = n;
+  I.state = reinterpret_cast<float4 *>(state_dev);
+  I.agent_base = 0;
+  I.cell_base = 0;
+  I.obs_base = 0;
+  set_tiles(I, n, t);
+  cudaStream_t s = (cudaStream_t)stream;
+  Bufs B{};
+  B.cellrank = (int2 *)(sp + kSCellrank);
+  B.counts = (int *)(sp + kSCounts);
+  B.local = (int *)(sp + kSLocal);
+  B.cell_start = (int *)(sp + kSCellStart);
+  B.tile_sum = (int *)(sp + kSTileSum);
+  B.sxy = (float2 *)(sp + kSSxy);
+  B.sts = (float2 *)(sp + kSSts);
+  B.sidx = (int *)(sp + kSSidx);
+  B.err = (unsigned *)(sp + kSErr);
+  B.bar = B.err + 4;
+  B.actions = actions_dev;
+  B.obs = obs_dev;
+  B.reward = reward_dev;
+  B.coll = coll_dev;
+  B.n_total = n;
+  B.c_total = I.ncells;
+  B.n_scan_tiles = (I.ncells + kScanTile - 1) / kScanTile;
+  // the array keeps the previous call's contents: start the counts and the
+  // error word from zero, and load this call's descriptor
+  CK(cudaMemsetAsync(sp + kSCounts, 0, (size_t)I.ncells * 4, s));
+  CK(cudaMemsetAsync(sp + kSErr, 0, 64, s));
+  CK(cudaMemcpyAsync(sp + kSInst, &I, sizeof(Inst), cudaMemcpyHostToDevice, s));
+  const Inst *gI = (const Inst *)(sp + kSInst);
+  const int reset = actions_dev ? 0 : 1;
+  if (n > 0) {
+    k_apply_bin<<<(n + 255) / 256, 256, 0, s>>>(gI, B, reset);
+    CK(cudaGetLastError());
+  }
+  k_scan<<<B.n_scan_tiles, 256, 0, s>>>(B);
+  CK(cudaGetLastError());
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int g = (n + 255) / 256;
+  g = g < 1 ? 1 : (g > 4 * sms ? 4 * sms : g);
+  k_scatter<<<g, 256, 0, s>>>(gI, B);
+  CK(cudaGetLastError());
+  if (n > 0) {
+    const size_t smem = (size_t)(t.block / 32) * direct_warp_bytes(I.v);
+    const int blocks = (n + t.block - 1) / t.block;
+    if (I.v == 8) k_neighbours_direct<1, 8><<<blocks, t.block, smem, s>>>(gI, B);
+    else k_neighbours_direct<1, 0><<<blocks, t.block, smem, s>>>(gI, B);
+    CK(cudaGetLastError());
+  }
+  if (error_bits_out) {
+    uint32_t w = 0;
+    CK(cudaMemcpyAsync(&w, sp + kSErr, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *error_bits_out = w;
+  }
+  return FLOCK_OK;
+}
