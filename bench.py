@@ -188,11 +188,14 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256):
+def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256, sizes=None):
     """The batched form: n_inst instances with agent counts log-uniform in
     [100, 20000] (density 0.1 each), all advanced by one persistent kernel
-    per step, replayed from a CUDA graph.  Returns a dict for the JSON line."""
-    sizes = fi.batch_sizes(n_inst, 100, 20000, seed)
+    per step, replayed from a CUDA graph.  With `sizes`, those instances
+    instead.  Returns a dict for the JSON line."""
+    if sizes is None:
+        sizes = fi.batch_sizes(n_inst, 100, 20000, seed)
+    n_inst = len(sizes)
     params = [fi.default_params(fi.side_for(n)) for n in sizes]
     total = sum(sizes)
     cells = sum(F.flock_instance_cells(p) for p in params)
@@ -207,10 +210,8 @@ def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256)
     acts = torch.from_numpy(fi.random_actions(total, steps + warmup + 1, seed + 1)).to(dev)
     act_buf = torch.empty(total, dtype=torch.int32, device=dev)
     torch.cuda.synchronize()
-    F.env_batch_set_timing(b.batch, True)
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    kern = []
     with torch.cuda.stream(stream):
         act_buf.copy_(acts[0])
         b.step(act_buf)  # initial observation (reset)
@@ -226,7 +227,17 @@ def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256)
             ev0[k].record(stream)
             b.step(act_buf)
             ev1[k].record(stream)
+    torch.cuda.synchronize()
+    # kernel duration from events recorded inside the step graph
+    F.env_batch_set_timing(b.batch, True)
+    kern = []
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            act_buf.copy_(acts[1 + warmup + k])
+            flush.zero_()
+            b.step(act_buf)
         kern.append(F.env_batch_get_time(b.batch))
+    F.env_batch_set_timing(b.batch, False)
     torch.cuda.synchronize()
     err = b.error()
     assert err == 0, "device error bits %d" % err
@@ -241,14 +252,63 @@ def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256)
             "agents": total, "cells": cells, "ms_per_step": tot / steps,
             "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
             "grid": grid, "block": block,
-            "workload": "batched: %d flock instances, agent counts log-uniform in [100, 20000] "
-                        "(seed %d, %d agents), density 0.1, view radius 5, 8 sectors, fov 250 "
-                        "deg, one persistent cooperative kernel per step, CUDA graph"
-                        % (n_inst, seed, total),
+            "workload": "batched: %d flock instances, agent counts %s (seed %d, %d agents), "
+                        "density 0.1, view radius 5, 8 sectors, fov 250 deg, one persistent "
+                        "cooperative kernel per step, CUDA graph"
+                        % (n_inst, "log-uniform in [100, 20000]" if n_inst > 1 else str(sizes),
+                           seed, total),
             "roofline": {"bound": "hbm", "kernel": "k_batch_step", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_kind, "traffic": None,
                          "bytes_per_agent": BYTES_PER_AGENT_STEP}}
+
+
+POLICY_BYTES_PER_AGENT = 48  # state 16 in + 16 out, action 4 in + 4 out, reward 4, coll 4
+
+
+def run_policy(F, torch, dev, stream, steps, warmup, flush, n=100000, seed=0):
+    """Step + fused policy at 100,000 agents (side 1000): the greedy actions
+    of each step drive the next; observations stay on chip."""
+    side = fi.side_for(n)
+    p = fi.default_params(side)
+    env = F.FlockEnv(p, n, device=dev, stream=stream)
+    w = fi.policy_weights(seed)
+    blob = torch.from_numpy(w["blob"].view(np.int16)).to(dev)
+    act = torch.from_numpy(fi.random_actions(n, 1, seed)[0]).to(dev)
+    rew = torch.empty(n, dtype=torch.float32, device=dev)
+    coll = torch.empty(n, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        env.reset(torch.from_numpy(fi.initial_state(n, side, seed)).to(dev))
+        for _ in range(warmup):
+            flush.zero_()
+            F.env_step_policy(env.env, blob, act, rew, coll)
+    torch.cuda.synchronize()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev0[k].record(stream)
+            F.env_step_policy(env.env, blob, act, rew, coll)
+            ev1[k].record(stream)
+    torch.cuda.synchronize()
+    assert env.error() == 0
+    ms = [ev0[k].elapsed_time(ev1[k]) for k in range(steps)]
+    tot = sum(ms)
+    env.close()
+    peak, peak_kind = peaks()
+    achieved = POLICY_BYTES_PER_AGENT * n / (tot / steps * 1e-3) / 1e9
+    return {"value": n * steps / (tot * 1e-3), "unit": UNIT, "agents": n,
+            "ms_per_step": tot / steps, "p50_ms": float(np.percentile(ms, 50)),
+            "p99_ms": float(np.percentile(ms, 99)),
+            "workload": "step + fused policy: %d agents, side %.0f, MLP 18-64-64-9 tanh, BF16 "
+                        "weights N(0, 0.1) and activations on tensor cores (mma.sync), FP32 "
+                        "accumulate, greedy actions feed the next step" % (n, side),
+            "roofline": {"bound": "hbm", "kernel": "whole step (4 kernels)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                         "bytes_per_agent": POLICY_BYTES_PER_AGENT}}
 
 
 def main():
@@ -260,6 +320,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--agents", type=int, default=N_AGENTS)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-policy", action="store_true")
     ap.add_argument("--tuning", default=None,
                     help='launch shape as JSON, e.g. {"mode": 2, "stencil": 1, "block": 128}')
     args = ap.parse_args()
@@ -299,10 +360,8 @@ def main():
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     with torch.cuda.stream(stream):
         env.reset(torch.from_numpy(st0).to(dev))
-    F.env_set_timing(env.env, True)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(total)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(total)]
-    phase = []
     stream.synchronize()
     for k in range(args.warmup):
         with torch.cuda.stream(stream):
@@ -311,10 +370,11 @@ def main():
             starts[k].record(stream)
             env.step(act_buf)
             ends[k].record(stream)
-        F.env_get_phase_times(env.env)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
+    # timed region: K steps, each bracketed by events on the library's
+    # stream, the L2 flush and the action copy outside the events
     with ClockSampler(local) as clk:
         for k in range(args.warmup, total):
             with torch.cuda.stream(stream):
@@ -323,10 +383,20 @@ def main():
                 starts[k].record(stream)
                 env.step(act_buf)
                 ends[k].record(stream)
-            phase.append(F.env_get_phase_times(env.env))
         torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
+    # second pass, same workload: CUDA events recorded inside the step graph
+    # around each kernel give the per-kernel durations for the roofline
+    F.env_set_timing(env.env, True)
+    phase = []
+    for k in range(args.warmup, total):
+        with torch.cuda.stream(stream):
+            act_buf.copy_(acts[k])
+            flush.zero_()
+            env.step(act_buf)
+        phase.append(F.env_get_phase_times(env.env))
+    F.env_set_timing(env.env, False)
     step_ms = [starts[k].elapsed_time(ends[k]) for k in range(args.warmup, total)]
     tot_ms = sum(step_ms)
     if world > 1:
@@ -348,7 +418,6 @@ def main():
     obs_h = torch.empty((n, env.obs_dim), dtype=torch.float32).pin_memory()
     rew_h = torch.empty(n, dtype=torch.float32).pin_memory()
     coll_h = torch.empty(n, dtype=torch.int32).pin_memory()
-    F.env_set_timing(env.env, False)
     for _ in range(3):
         F.env_step_host(env.env, act_h, obs_h, rew_h, coll_h)
     e2e_steps = max(10, min(args.steps, 100))
@@ -360,10 +429,17 @@ def main():
            "h2d_bytes_per_step": n * 4, "d2h_bytes_per_step": n * (env.obs_dim + 2) * 4,
            "call": "env_step_host (pinned host buffers, synchronous)"}
 
-    batched = None
+    batched = single_fused = None
     if not args.no_batched:
         batched = run_batched(F, torch, dev, stream, args.steps, args.warmup, flush,
                               seed=1000 * rank)
+        # the same 50,000-agent instance as the headline, as a batch of one
+        single_fused = run_batched(F, torch, dev, stream, args.steps, args.warmup, flush,
+                                   seed=1000 * rank, sizes=[n])
+    policy = None
+    if not args.no_policy:
+        policy = run_policy(F, torch, dev, stream, args.steps, args.warmup, flush,
+                            seed=1000 * rank)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -386,10 +462,14 @@ def main():
                          "bytes_per_agent": NEIGH_BYTES_PER_AGENT},
             "e2e": e2e,
             "clocks": clk.summary(),
-            "gpu_launches": 4 * args.steps + (args.steps if batched else 0),
+            # kernels of this library launched inside the timed region (four per step)
+            "gpu_launches": 4 * args.steps,
         }
         if batched is not None:
             line["batched"] = batched
+            line["single_instance_persistent"] = single_fused
+        if policy is not None:
+            line["policy"] = policy
             if world > 1:
                 line["batched"]["value_all_ranks"] = None
         if not args.no_cpu_baseline and world == 1:

@@ -147,6 +147,20 @@ int env_reset(flock_env *env, const float *state0_dev, float *obs_dev, float *re
 int env_step(flock_env *env, const int32_t *actions_dev, float *obs_dev, float *reward_dev,
              int32_t *coll_dev);
 
+/* One step whose next actions come from the fused policy: applies
+ * actions_inout_dev, observes, and feeds each agent's observation through the
+ * shared policy network on chip (the learners' shared MLP of Section 4.3,
+ * here 18 -> 64 -> 64 -> 9 with tanh, as the 18-value observation needs;
+ * needs num_segments == 8), then overwrites actions_inout_dev with the greedy
+ * actions (largest logit, lowest index on ties) for the next step.
+ * weights_bf16_dev: 5,961 bfloat16 values, W1[64][18] b1[64] W2[64][64]
+ * b2[64] W3[9][64] b3[9], each W row-major [out][in].  Operands are BF16 on
+ * the tensor cores, accumulation FP32, tanh the hardware approximation.
+ * logits_dev (n x 9 floats) and obs_dev (n x 18) may be NULL; with NULL obs
+ * the observations never reach device memory. */
+int env_step_policy(flock_env *env, const uint16_t *weights_bf16_dev, int32_t *actions_inout_dev,
+                    float *reward_dev, int32_t *coll_dev, float *logits_dev, float *obs_dev);
+
 /* env_step from and to host memory: copies the actions in, steps, copies the
  * outputs out, and waits for the stream.  Returns after the outputs are in
  * the host buffers. */

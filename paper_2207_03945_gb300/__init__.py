@@ -23,6 +23,7 @@ __all__ = [
     "env_create", "env_reset", "env_step", "env_step_host", "env_get_state", "env_set_state",
     "env_get_error", "env_get_derived", "env_get_tuning", "env_set_timing",
     "env_get_phase_times", "env_destroy", "FlockEnv", "lib_path", "flock_instance_cells",
+    "env_step_policy",
     "flock_batch_workspace_bytes", "env_batch_create", "env_batch_set", "env_batch_step",
     "env_batch_get_error", "env_batch_set_spin_limit", "env_batch_get_launch",
     "env_batch_set_timing", "env_batch_get_time", "env_batch_destroy", "FlockBatch",
@@ -130,6 +131,22 @@ def env_step(env, actions, obs, reward, coll):
     torch = _torch()
     _abi.check(_abi.lib.env_step(env.handle, _ptr(actions, torch.int32, (env.n,), "actions"),
                                  *_outs(env, obs, reward, coll)))
+
+
+def env_step_policy(env, weights_bf16, actions, reward, coll, logits=None, obs=None):
+    """Step whose next actions come from the fused BF16 policy MLP; actions
+    (int32, n) are read, then overwritten with the greedy actions.
+    weights_bf16: 5,961 bf16 values (torch.bfloat16, or int16/uint16 bits)."""
+    torch = _torch()
+    w = weights_bf16
+    if not (isinstance(w, torch.Tensor) and w.is_cuda and w.numel() == 5961 and
+            w.element_size() == 2 and w.is_contiguous()):
+        raise FlockError("weights must be 5961 contiguous 16-bit values on the device")
+    _abi.check(_abi.lib.env_step_policy(
+        env.handle, ctypes.c_void_p(w.data_ptr()), _ptr(actions, torch.int32, (env.n,), "actions"),
+        _ptr(reward, torch.float32, (env.n,), "reward"), _ptr(coll, torch.int32, (env.n,), "coll"),
+        _ptr(logits, torch.float32, (env.n, 9), "logits") if logits is not None else None,
+        _ptr(obs, torch.float32, (env.n, env.obs_dim), "obs") if obs is not None else None))
 
 
 def env_step_host(env, actions, obs, reward, coll):

@@ -100,6 +100,7 @@ def _load():
         "env_reset": [vp, vp, vp, vp, vp],
         "env_step": [vp, vp, vp, vp, vp],
         "env_step_host": [vp, vp, vp, vp, vp],
+        "env_step_policy": [vp, vp, vp, vp, vp, vp, vp],
         "env_get_state": [vp, vp],
         "env_set_state": [vp, vp],
         "env_get_error": [vp, ctypes.POINTER(ctypes.c_uint32)],

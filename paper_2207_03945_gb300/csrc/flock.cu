@@ -72,6 +72,32 @@ __global__ void k_neighbours_direct(const Inst *__restrict__ gI, Bufs B) {
   if (err) atomicOr(B.err, err);
 }
 
+// Neighbour scan with the fused policy (v = 8): observations go through the
+// MLP on chip; greedy actions (and optionally logits and observations) out.
+template <int H>
+__global__ void k_neighbours_policy(const Inst *__restrict__ gI, Bufs B,
+                                    const unsigned short *__restrict__ wblob, int32_t *actions,
+                                    float *logits) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ Inst sI;
+  load_inst(sI, gI);
+  load_policy(wblob, smem);
+  __syncthreads();
+  unsigned err = 0;
+  const int warp = threadIdx.x >> 5;
+  const int gp0 = (blockIdx.x * (blockDim.x >> 5) + warp) * 32;
+  if (gp0 < sI.n) {
+    char *wp = smem + kPolicyBytes + (size_t)warp * (direct_warp_bytes(8) + kTileBytes);
+    const DirectArea W = direct_area(wp, 8);
+    PolicyCtx pc = policy_ctx(smem);
+    pc.tile = reinterpret_cast<unsigned short *>(wp + direct_warp_bytes(8));
+    pc.actions = actions;
+    pc.logits = logits;
+    phaseD_direct<H, 8, true>(sI, gp0, min(gp0 + 32, sI.n), B, W, err, &pc);
+  }
+  if (err) atomicOr(B.err, err);
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -253,7 +279,9 @@ cudaError_t set_kernel_attrs() {
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int want = maxsm - (int)sizeof(Inst) - 1024;
-    const void *fns[] = {(const void *)k_neighbours<1>, (const void *)k_neighbours<2>,
+    const void *fns[] = {(const void *)k_neighbours_policy<1>,
+                         (const void *)k_neighbours_policy<2>,
+                         (const void *)k_neighbours<1>, (const void *)k_neighbours<2>,
                          (const void *)k_neighbours_direct<1, 0>,
                          (const void *)k_neighbours_direct<2, 0>,
                          (const void *)k_neighbours_direct<1, 8>,
@@ -318,6 +346,8 @@ struct flock_env {
   size_t smemD;
   int timing;
   cudaEvent_t ev[5];
+  cudaGraphExec_t pgraph;  // step with the fused policy
+  const void *p_w, *p_act, *p_rew, *p_coll, *p_log, *p_obs;
 };
 
 extern "C" const char *flock_last_cuda_error(void) { return g_last_cuda_error; }
@@ -489,6 +519,37 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, float 
   return FLOCK_OK;
 }
 
+static int enqueue_policy_step(flock_env *e, cudaStream_t s, const unsigned short *w,
+                               int32_t *act, float *rew, int32_t *coll, float *logits,
+                               float *obs) {
+  Bufs B = e->bufs;
+  B.actions = act;
+  B.obs = obs;
+  B.reward = rew;
+  B.coll = coll;
+  const Inst *gI = (const Inst *)(e->ws + e->lay.inst);
+  const int n = e->n;
+  if (n > 0) {
+    k_apply_bin<<<(n + 255) / 256, 256, 0, s>>>(gI, B, 0);
+    CK(cudaGetLastError());
+  }
+  k_scan<<<e->n_scan_tiles, 256, 0, s>>>(B);
+  CK(cudaGetLastError());
+  k_scatter<<<e->scatter_grid, 256, 0, s>>>(gI, B);
+  CK(cudaGetLastError());
+  if (n > 0) {
+    const int block = e->tuning.block;
+    const size_t smem = kPolicyBytes + (size_t)(block / 32) * (direct_warp_bytes(8) + kTileBytes);
+    const int blocks = (n + block - 1) / block;
+    if (e->inst.halo == 1)
+      k_neighbours_policy<1><<<blocks, block, smem, s>>>(gI, B, w, act, logits);
+    else
+      k_neighbours_policy<2><<<blocks, block, smem, s>>>(gI, B, w, act, logits);
+    CK(cudaGetLastError());
+  }
+  return FLOCK_OK;
+}
+
 static bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p % a) == 0; }
 
 static int check_out(const flock_env *e, const float *obs, const float *rew, const int32_t *coll) {
@@ -539,6 +600,51 @@ extern "C" int env_step(flock_env *e, const int32_t *act, float *obs, float *rew
     e->g_coll = coll;
   }
   CK(cudaGraphLaunch(e->graph, e->stream));
+  return FLOCK_OK;
+}
+
+extern "C" int env_step_policy(flock_env *e, const uint16_t *weights, int32_t *act, float *rew,
+                               int32_t *coll, float *logits, float *obs) {
+  if (!e || e->inst.v != 8) return FLOCK_EINVAL;
+  if (e->n > 0 && (!weights || !act || !rew || !coll || !aligned(weights, 4) ||
+                   (obs && !aligned(obs, 8))))
+    return FLOCK_EINVAL;
+  const size_t smem = kPolicyBytes + (size_t)(e->tuning.block / 32) * (direct_warp_bytes(8) + kTileBytes);
+  int dev = 0, smem_max = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem + sizeof(Inst) + 1024 > (size_t)smem_max) return FLOCK_EINVAL;
+  if (!e->pgraph || e->p_w != weights || e->p_act != act || e->p_rew != rew ||
+      e->p_coll != coll || e->p_log != logits || e->p_obs != obs) {
+    if (e->pgraph) {
+      CK(cudaStreamSynchronize(e->stream));
+      cudaGraphExecDestroy(e->pgraph);
+      e->pgraph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_policy_step(e, e->cap_stream, (const unsigned short *)weights, act, rew, coll,
+                                 logits, obs);
+    cudaError_t ce = cudaStreamEndCapture(e->cap_stream, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+    ce = cudaGraphInstantiate(&e->pgraph, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+      e->pgraph = nullptr;
+      return cuda_fail(ce, "cudaGraphInstantiate");
+    }
+    e->p_w = weights;
+    e->p_act = act;
+    e->p_rew = rew;
+    e->p_coll = coll;
+    e->p_log = logits;
+    e->p_obs = obs;
+  }
+  CK(cudaGraphLaunch(e->pgraph, e->stream));
   return FLOCK_OK;
 }
 
@@ -628,6 +734,7 @@ extern "C" void env_destroy(flock_env *e) {
   for (int k = 0; k < 5; ++k)
     if (e->ev[k]) cudaEventDestroy(e->ev[k]);
   if (e->graph) cudaGraphExecDestroy(e->graph);
+  if (e->pgraph) cudaGraphExecDestroy(e->pgraph);
   if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
   delete e;
 }

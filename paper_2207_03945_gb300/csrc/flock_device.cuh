@@ -18,6 +18,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "flock.h"
@@ -864,9 +865,204 @@ __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, c
   }
 }
 
-template <int H, int V>
+// ---------------------------------------------------------------------------
+// Fused policy: the shared MLP of the learners (Section 4.3; two hidden
+// layers of 64 with tanh, here 18 -> 64 -> 64 -> 9 on the 18-value
+// observation) applied to the observations while they are still on chip.
+// BF16 operands on the tensor cores (mma.sync m16n8k16), FP32 accumulate;
+// the greedy action (largest logit, lowest index on ties) is written back.
+// A warp holds its 32 agents' observations as a BF16 tile [32][kTileS];
+// each layer's accumulators, passed through tanh and rounded to BF16, are
+// the next layer's A fragments without leaving the registers.
+// ---------------------------------------------------------------------------
+constexpr int kW1S = 40, kW2S = 72, kW3S = 72, kTileS = 40;  // padded row strides (bf16)
+constexpr size_t kPolicyBytes = (size_t)(64 * kW1S + 64 * kW2S + 16 * kW3S) * 2 + (64 + 64 + 16) * 4;
+constexpr size_t kTileBytes = (size_t)32 * kTileS * 2;
+static_assert(kPolicyBytes % 16 == 0 && kTileBytes % 16 == 0, "policy smem alignment");
+// offsets in the 5,961-value BF16 blob: W1[64][18] b1[64] W2[64][64] b2[64] W3[9][64] b3[9]
+constexpr int kOffB1 = 64 * 18, kOffW2 = kOffB1 + 64, kOffB2 = kOffW2 + 64 * 64,
+              kOffW3 = kOffB2 + 64, kOffB3 = kOffW3 + 9 * 64, kBlobLen = kOffB3 + 9;
+
+struct PolicyCtx {
+  const unsigned short *W1, *W2, *W3;  // shared memory, bf16 bits, padded rows
+  const float *b1, *b2, *b3;
+  unsigned short *tile;                 // this warp's observation tile
+  int32_t *actions;                     // greedy actions out (agent rows)
+  float *logits;                        // optional: logits out, 9 per agent
+};
+
+__device__ __forceinline__ float bf16_bits_to_float(unsigned short b) {
+  return __uint_as_float((unsigned)b << 16);
+}
+
+// Block-cooperative load of the blob into the padded shared layout (call,
+// then __syncthreads).  Padding columns and rows are zero.
+__device__ __forceinline__ void load_policy(const unsigned short *__restrict__ blob, char *base) {
+  unsigned short *W1 = reinterpret_cast<unsigned short *>(base);
+  unsigned short *W2 = W1 + 64 * kW1S;
+  unsigned short *W3 = W2 + 64 * kW2S;
+  float *b1 = reinterpret_cast<float *>(W3 + 16 * kW3S);
+  float *b2 = b1 + 64, *b3 = b2 + 64;
+  for (int e = threadIdx.x; e < 64 * kW1S; e += blockDim.x) {
+    const int n = e / kW1S, k = e - n * kW1S;
+    W1[e] = k < 18 ? blob[n * 18 + k] : (unsigned short)0;
+  }
+  for (int e = threadIdx.x; e < 64 * kW2S; e += blockDim.x) {
+    const int n = e / kW2S, k = e - n * kW2S;
+    W2[e] = k < 64 ? blob[kOffW2 + n * 64 + k] : (unsigned short)0;
+  }
+  for (int e = threadIdx.x; e < 16 * kW3S; e += blockDim.x) {
+    const int n = e / kW3S, k = e - n * kW3S;
+    W3[e] = (n < 9 && k < 64) ? blob[kOffW3 + n * 64 + k] : (unsigned short)0;
+  }
+  for (int e = threadIdx.x; e < 64; e += blockDim.x) {
+    b1[e] = bf16_bits_to_float(blob[kOffB1 + e]);
+    b2[e] = bf16_bits_to_float(blob[kOffB2 + e]);
+  }
+  for (int e = threadIdx.x; e < 16; e += blockDim.x)
+    b3[e] = e < 9 ? bf16_bits_to_float(blob[kOffB3 + e]) : 0.0f;
+}
+
+__device__ __forceinline__ PolicyCtx policy_ctx(char *base) {
+  PolicyCtx P;
+  P.W1 = reinterpret_cast<const unsigned short *>(base);
+  P.W2 = P.W1 + 64 * kW1S;
+  P.W3 = P.W2 + 64 * kW2S;
+  P.b1 = reinterpret_cast<const float *>(P.W3 + 16 * kW3S);
+  P.b2 = P.b1 + 64;
+  P.b3 = P.b2 + 64;
+  P.tile = nullptr;
+  P.actions = nullptr;
+  P.logits = nullptr;
+  return P;
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const unsigned (&a)[4], unsigned b0,
+                                               unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// round-to-nearest-even pair of floats to packed bf16 (lo in the low half)
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const unsigned *>(&v);
+}
+
+__device__ __forceinline__ unsigned lds32(const unsigned short *p) {
+  return *reinterpret_cast<const unsigned *>(p);
+}
+
+// Forward pass of one m-tile (16 rows, row0 = 0 or 16) of the warp's tile.
+// Returns, for this thread, the greedy action and the 4 logit columns it
+// holds for rows row0 + g and row0 + g + 8 (g = lane / 4).
+__device__ __forceinline__ void policy_mtile(const PolicyCtx &P, int row0, int &act_lo,
+                                             int &act_hi, float (&lg)[2][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  // layer 1: [16 x 32] x W1^T -> [16 x 64]
+  float acc[8][4];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const float c0 = P.b1[8 * nt + 2 * t], c1 = P.b1[8 * nt + 2 * t + 1];
+    acc[nt][0] = c0; acc[nt][1] = c1; acc[nt][2] = c0; acc[nt][3] = c1;
+  }
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+    const unsigned short *r0 = P.tile + (row0 + g) * kTileS + 16 * kk + 2 * t;
+    const unsigned short *r1 = r0 + 8 * kTileS;
+    const unsigned a[4] = {lds32(r0), lds32(r1), lds32(r0 + 8), lds32(r1 + 8)};
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const unsigned short *w = P.W1 + (8 * nt + g) * kW1S + 16 * kk + 2 * t;
+      mma_bf16_16816(acc[nt], a, lds32(w), lds32(w + 8));
+    }
+  }
+  unsigned a2[4][4];
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    a2[kk][0] = pack_bf16(tanh_fast(acc[2 * kk][0]), tanh_fast(acc[2 * kk][1]));
+    a2[kk][1] = pack_bf16(tanh_fast(acc[2 * kk][2]), tanh_fast(acc[2 * kk][3]));
+    a2[kk][2] = pack_bf16(tanh_fast(acc[2 * kk + 1][0]), tanh_fast(acc[2 * kk + 1][1]));
+    a2[kk][3] = pack_bf16(tanh_fast(acc[2 * kk + 1][2]), tanh_fast(acc[2 * kk + 1][3]));
+  }
+  // layer 2: [16 x 64] x W2^T -> [16 x 64]
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const float c0 = P.b2[8 * nt + 2 * t], c1 = P.b2[8 * nt + 2 * t + 1];
+    acc[nt][0] = c0; acc[nt][1] = c1; acc[nt][2] = c0; acc[nt][3] = c1;
+  }
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const unsigned short *w = P.W2 + (8 * nt + g) * kW2S + 16 * kk + 2 * t;
+      mma_bf16_16816(acc[nt], a2[kk], lds32(w), lds32(w + 8));
+    }
+  }
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    a2[kk][0] = pack_bf16(tanh_fast(acc[2 * kk][0]), tanh_fast(acc[2 * kk][1]));
+    a2[kk][1] = pack_bf16(tanh_fast(acc[2 * kk][2]), tanh_fast(acc[2 * kk][3]));
+    a2[kk][2] = pack_bf16(tanh_fast(acc[2 * kk + 1][0]), tanh_fast(acc[2 * kk + 1][1]));
+    a2[kk][3] = pack_bf16(tanh_fast(acc[2 * kk + 1][2]), tanh_fast(acc[2 * kk + 1][3]));
+  }
+  // layer 3: [16 x 64] x W3^T -> [16 x 16] (9 logits + padding)
+  float o[2][4];
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt) {
+    const float c0 = P.b3[8 * nt + 2 * t], c1 = P.b3[8 * nt + 2 * t + 1];
+    o[nt][0] = c0; o[nt][1] = c1; o[nt][2] = c0; o[nt][3] = c1;
+  }
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const unsigned short *w = P.W3 + (8 * nt + g) * kW3S + 16 * kk + 2 * t;
+      mma_bf16_16816(o[nt], a2[kk], lds32(w), lds32(w + 8));
+    }
+  }
+  // greedy action per row: this thread holds columns 2t, 2t+1, 8+2t, 9+2t
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float v4[4] = {o[0][2 * h], o[0][2 * h + 1], o[1][2 * h], o[1][2 * h + 1]};
+    const int c4[4] = {2 * t, 2 * t + 1, 8 + 2 * t, 9 + 2 * t};
+    float best = -__int_as_float(0x7f800000);
+    int bi = 16;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      lg[h][j] = v4[j];
+      if (c4[j] < 9 && (v4[j] > best || (v4[j] == best && c4[j] < bi))) {
+        best = v4[j];
+        bi = c4[j];
+      }
+    }
+#pragma unroll
+    for (int m = 1; m <= 2; m <<= 1) {
+      const float ob = __shfl_xor_sync(kFull, best, m);
+      const int oi = __shfl_xor_sync(kFull, bi, m);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    if (h == 0) act_lo = bi;
+    else act_hi = bi;
+  }
+}
+
+template <int H, int V, bool POL = false>
 __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
-                              const DirectArea &W, unsigned &err) {
+                              const DirectArea &W, unsigned &err,
+                              const PolicyCtx *pc = nullptr) {
   const int lane = threadIdx.x & 31;
   const int nc = I.nc, v = V == 8 ? 8 : I.v;
   Edges<V> E8;
@@ -962,11 +1158,19 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
     B.coll[I.agent_base + i] = ncoll;
     if ((long long)nin > I.NMAX) err |= FLOCK_ERR_OVERFLOW;
   }
-  // observation rows, written whole and contiguous
+  // observation rows, written whole and contiguous (and, with the policy,
+  // also as BF16 rows of the warp's tile)
   const int P = v + 1;
   const int rpi = P <= 32 ? 32 / P : 1;
   const int my_r = P <= 32 ? lane / P : 0, my_e = P <= 32 ? lane % P : lane;
-  float *obs = B.obs + I.obs_base;
+  float *obs = B.obs ? B.obs + I.obs_base : nullptr;
+  if (POL) {
+    // padding columns 18..31 of every row, and whole rows past the chunk
+    unsigned *row = reinterpret_cast<unsigned *>(pc->tile + lane * kTileS);
+#pragma unroll
+    for (int w2 = 0; w2 < kTileS / 2; ++w2)
+      if (w2 >= 9 || lane >= nb) row[w2] = 0u;
+  }
   for (int rb = 0; rb < nb; rb += rpi) {
     const int r = min(rb + my_r, 31);
     const int ir = __shfl_sync(kFull, i, r);
@@ -980,11 +1184,39 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
         } else {
           val = make_float2(sr_, tr);
         }
-        *reinterpret_cast<float2 *>(obs + (long long)ir * I.obs_dim + 2 * e) = val;
+        if (obs) *reinterpret_cast<float2 *>(obs + (long long)ir * I.obs_dim + 2 * e) = val;
+        if (POL)
+          *reinterpret_cast<unsigned *>(pc->tile + r * kTileS + 2 * e) = pack_bf16(val.x, val.y);
       }
     }
   }
   __syncwarp();
+  if (POL) {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      int alo = 0, ahi = 0;
+      float lg[2][4];
+      policy_mtile(*pc, 16 * mt, alo, ahi, lg);
+      const int rlo = 16 * mt + g, rhi = rlo + 8;
+      const int ilo = __shfl_sync(kFull, i, rlo), ihi = __shfl_sync(kFull, i, rhi);
+      if (t == 0) {
+        if (rlo < nb) pc->actions[I.agent_base + ilo] = alo;
+        if (rhi < nb) pc->actions[I.agent_base + ihi] = ahi;
+      }
+      if (pc->logits) {
+        const int c4[4] = {2 * t, 2 * t + 1, 8 + 2 * t, 9 + 2 * t};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (c4[j] < 9) {
+            if (rlo < nb) pc->logits[(long long)(I.agent_base + ilo) * 9 + c4[j]] = lg[0][j];
+            if (rhi < nb) pc->logits[(long long)(I.agent_base + ihi) * 9 + c4[j]] = lg[1][j];
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
 }
 
 }  // namespace flock
