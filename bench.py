@@ -311,6 +311,32 @@ def run_policy(F, torch, dev, stream, steps, warmup, flush, n=100000, seed=0):
                          "bytes_per_agent": POLICY_BYTES_PER_AGENT}}
 
 
+def run_serving(dev, seconds, seed=0, rate=50.0, budget=100 * 10 ** 9, backlog=0):
+    """Serving loop with continuous batching: Poisson session arrivals, agent
+    counts log-uniform in [500, 50000], episodes of 100..2000 steps, admission
+    by a device-memory budget, all admitted sessions stepped together by the
+    batched kernel each iteration.  backlog > 0 adds that many sessions at
+    t = 0 (saturation)."""
+    from paper_2207_03945_gb300 import serve
+    arrivals = fi.session_stream(rate, seconds, seed)
+    if backlog:
+        rng = np.random.Generator(np.random.PCG64(seed + 99))
+        for k in range(backlog):
+            n = int(round(math.exp(math.log(500) + rng.random() * (math.log(50000) - math.log(500)))))
+            arrivals.append((0.0, n, int(rng.integers(100, 2001)), 10 ** 6 + k))
+    srv = serve.FlockServer(budget, state_fn=lambda s: fi.initial_state(s.n, s.params["side"],
+                                                                         s.seed),
+                            max_slots=512, arena_agents=8_000_000, max_cells=4_000_000,
+                            device=dev)
+    st = srv.run(arrivals, duration=seconds)
+    err = srv.batch.error()
+    assert err == 0, "device error bits %d" % err
+    srv.close()
+    st.update({"rate_per_s": rate, "budget_bytes": budget, "backlog": backlog,
+               "seconds": seconds, "sessions_offered": len(arrivals)})
+    return st
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -321,6 +347,7 @@ def main():
     ap.add_argument("--agents", type=int, default=N_AGENTS)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-policy", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--tuning", default=None,
                     help='launch shape as JSON, e.g. {"mode": 2, "stencil": 1, "block": 128}')
     args = ap.parse_args()
@@ -436,6 +463,16 @@ def main():
         # the same 50,000-agent instance as the headline, as a batch of one
         single_fused = run_batched(F, torch, dev, stream, args.steps, args.warmup, flush,
                                    seed=1000 * rank, sizes=[n])
+    serving = None
+    if args.serve_seconds > 0:
+        serving = {
+            "as_specified": run_serving(dev, args.serve_seconds, seed=1000 * rank),
+            "saturated_small_budget": run_serving(dev, max(5.0, args.serve_seconds / 2),
+                                                  seed=1000 * rank + 1, budget=10 ** 8,
+                                                  backlog=200),
+            "workload": "serving: Poisson arrivals 50/s, agents log-uniform in [500, 50000], "
+                        "episodes uniform in [100, 2000] steps, 100 GB budget, random actions; "
+                        "plus a saturated run (200 sessions queued at t=0, 100 MB budget)"}
     policy = None
     if not args.no_policy:
         policy = run_policy(F, torch, dev, stream, args.steps, args.warmup, flush,
@@ -470,6 +507,8 @@ def main():
             line["single_instance_persistent"] = single_fused
         if policy is not None:
             line["policy"] = policy
+        if serving is not None:
+            line["serving"] = serving
             if world > 1:
                 line["batched"]["value_all_ranks"] = None
         if not args.no_cpu_baseline and world == 1:

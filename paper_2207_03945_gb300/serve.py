@@ -1,0 +1,309 @@
+"""Serving loop with continuous batching for the flock environment.
+
+Sessions (independent flock environments of different agent counts, the
+environments of arXiv 2207.03945 Section 4.1) arrive over time.  The server
+admits a waiting session as soon as a slot and enough of the device-memory
+budget are free, keeps every admitted session's state resident in one device
+arena, and advances ALL admitted sessions together, one step per iteration,
+with the batched kernel (one persistent launch per iteration).  A session
+that arrives while others are running joins at the next iteration; a session
+whose episode is over leaves and frees its slot and memory.  Nothing is
+re-captured when the set changes: only the instance descriptors are
+re-uploaded.
+
+SessionScheduler is the host-side bookkeeping (queue, admission, arena
+ranges) and needs no GPU; FlockServer runs it against the library.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Device bytes a session of n agents and c cells occupies while admitted:
+# resident state (16/agent), the batch's per-agent scratch (cell and rank 8,
+# sorted positions 8, sorted heading and speed 8, sorted index 4), its rows of
+# the flattened actions and outputs (4 + 72 + 4 + 4), per-cell scratch
+# (counts, offsets, starts: 12/cell) and one descriptor.
+BYTES_PER_AGENT = 16 + 8 + 8 + 8 + 4 + 4 + 72 + 4 + 4
+BYTES_PER_CELL = 12
+BYTES_PER_SESSION = 1024
+
+
+def session_bytes(n_agents: int, n_cells: int) -> int:
+    return BYTES_PER_AGENT * n_agents + BYTES_PER_CELL * n_cells + BYTES_PER_SESSION
+
+
+@dataclass
+class Session:
+    sid: int
+    n: int
+    cells: int
+    steps: int
+    seed: int
+    t_arrival: float
+    params: dict = None
+    offset: int = -1          # first agent row of its state in the arena
+    steps_done: int = 0
+    t_admit: float = None
+    t_done: float = None
+    latencies: list = field(default_factory=list)
+    reset: bool = True        # next step observes without moving
+
+    @property
+    def bytes(self):
+        return session_bytes(self.n, self.cells)
+
+
+class SessionScheduler:
+    """Admission control and arena bookkeeping (host only).
+
+    budget_bytes: device memory the admitted sessions may use in total;
+    max_slots: sessions stepped together at most; arena_agents: agent rows of
+    the state arena; max_cells: cells of all admitted sessions at most;
+    queue_limit: waiting sessions beyond which arrivals are rejected."""
+
+    def __init__(self, budget_bytes, max_slots, arena_agents, max_cells, queue_limit=100000):
+        self.budget = int(budget_bytes)
+        self.max_slots = int(max_slots)
+        self.arena_agents = int(arena_agents)
+        self.max_cells = int(max_cells)
+        self.queue_limit = int(queue_limit)
+        self.free = [(0, self.arena_agents)]  # free arena ranges (start, length), sorted
+        self.queue = collections.deque()
+        self.active = []
+        self.used_bytes = 0
+        self.used_cells = 0
+        self.admitted = 0
+        self.rejected = 0
+        self.finished = []
+
+    # -- arena ranges: first fit, coalescing on free --
+    def _alloc(self, n):
+        for k, (s, l) in enumerate(self.free):
+            if l >= n:
+                if l == n:
+                    self.free.pop(k)
+                else:
+                    self.free[k] = (s + n, l - n)
+                return s
+        return -1
+
+    def _release(self, start, n):
+        if n == 0:
+            return
+        self.free.append((start, n))
+        self.free.sort()
+        merged = []
+        for s, l in self.free:
+            if merged and merged[-1][0] + merged[-1][1] == s:
+                merged[-1] = (merged[-1][0], merged[-1][1] + l)
+            else:
+                merged.append((s, l))
+        self.free = merged
+
+    def submit(self, sess: Session) -> bool:
+        """Queue a session; False (rejected) if it can never fit or the queue is full."""
+        if (sess.bytes > self.budget or sess.n > self.arena_agents or sess.cells > self.max_cells
+                or len(self.queue) >= self.queue_limit):
+            self.rejected += 1
+            return False
+        self.queue.append(sess)
+        return True
+
+    def admit(self, now):
+        """Admit waiting sessions in arrival order while a slot, budget, cells
+        and an arena range are free.  Returns the sessions admitted."""
+        out = []
+        while self.queue and len(self.active) < self.max_slots:
+            s = self.queue[0]
+            if (self.used_bytes + s.bytes > self.budget
+                    or self.used_cells + s.cells > self.max_cells):
+                break
+            off = self._alloc(s.n) if s.n > 0 else 0
+            if off < 0:
+                break
+            self.queue.popleft()
+            s.offset = off
+            s.t_admit = now
+            s.reset = True
+            self.used_bytes += s.bytes
+            self.used_cells += s.cells
+            self.active.append(s)
+            self.admitted += 1
+            out.append(s)
+        return out
+
+    def retire(self, now):
+        """Remove sessions whose episode is complete; returns them."""
+        done = [s for s in self.active if s.steps_done >= s.steps]
+        if done:
+            self.active = [s for s in self.active if s.steps_done < s.steps]
+            for s in done:
+                s.t_done = now
+                self._release(s.offset, s.n)
+                self.used_bytes -= s.bytes
+                self.used_cells -= s.cells
+                self.finished.append(s)
+        return done
+
+
+class FlockServer:
+    """Runs a SessionScheduler against the batched kernel on one GPU.
+
+    state_fn(session) -> (n, 4) float32 initial state of a session (host
+    array, the client's data); params_fn(n) -> parameter dict of a session of
+    n agents (default: the library defaults on a square of side
+    sqrt(n / 0.1), i.e. density 0.1); action_fn(session, step, out) fills the
+    session's int32 actions for one step into the device tensor `out`
+    (default: uniform random actions drawn on the device)."""
+
+    def __init__(self, budget_bytes, state_fn, max_slots=256, arena_agents=2_000_000,
+                 max_cells=1_000_000, device="cuda", stream=None, params_fn=None,
+                 action_fn=None, queue_limit=100000, tuning=None):
+        import math
+
+        import torch
+
+        from . import FlockBatch, flock_default_params, flock_instance_cells
+        self.torch = torch
+        self.dev = torch.device(device)
+        self.stream = stream
+        self.tuning = tuning
+        self.params_fn = params_fn or (
+            lambda n: flock_default_params(max(math.sqrt(max(n, 1) / 0.1), 12.0)))
+        self.state_fn = state_fn
+        self.action_fn = action_fn
+        self.cells_fn = lambda p: flock_instance_cells(p, tuning)
+        self.sched = SessionScheduler(budget_bytes, max_slots, arena_agents, max_cells,
+                                      queue_limit)
+        self.arena = torch.empty((arena_agents, 4), dtype=torch.float32, device=self.dev)
+        self.batch = FlockBatch(max_slots, arena_agents, max_cells, 18, device=self.dev,
+                                stream=stream, tuning=tuning)
+        self.actions = torch.empty(arena_agents, dtype=torch.int32, device=self.dev)
+        self.gen = torch.Generator(device=self.dev)
+        self.gen.manual_seed(12345)
+        self.next_sid = 0
+        self.iterations = 0
+        self.agent_steps = 0
+        self.set_changes = 0
+        self._active_ids = None
+        self.on_step = None  # optional callback(session, obs, reward, coll) after each step
+
+    def submit(self, n, steps, seed, t_arrival=None):
+        p = self.params_fn(n)
+        s = Session(self.next_sid, int(n), self.cells_fn(p), int(steps), int(seed),
+                    time.perf_counter() if t_arrival is None else t_arrival, params=p)
+        self.next_sid += 1
+        return s if self.sched.submit(s) else None
+
+    def _sync_set(self):
+        ids = [s.sid for s in self.sched.active]
+        if ids != self._active_ids or any(s.reset for s in self.sched.active):
+            torch = self.torch
+            act = self.sched.active
+            self.batch.set([s.params for s in act], [s.n for s in act],
+                           [self.arena[s.offset:s.offset + s.n] for s in act],
+                           reset=[s.reset for s in act])
+            self._active_ids = ids
+            self.set_changes += 1
+
+    def iteration(self):
+        """Retire, admit, step every admitted session once.  Returns the
+        number of sessions stepped."""
+        with self.torch.cuda.stream(self.stream) if self.stream is not None else _null():
+            return self._iteration()
+
+    def _iteration(self):
+        torch = self.torch
+        now = time.perf_counter()
+        self.sched.retire(now)
+        for s in self.sched.admit(now):
+            st = torch.from_numpy(np.ascontiguousarray(self.state_fn(s), dtype=np.float32))
+            self.arena[s.offset:s.offset + s.n].copy_(st.to(self.dev, non_blocking=False))
+        act = self.sched.active
+        if not act:
+            return 0
+        t0 = time.perf_counter()
+        self._sync_set()
+        off = 0
+        if True:
+            for s in act:
+                view = self.actions[off:off + s.n]
+                if self.action_fn is not None:
+                    self.action_fn(s, s.steps_done, view)
+                off += s.n
+            if self.action_fn is None:
+                self.actions[:off].random_(0, 9, generator=self.gen)
+            obs, rew, coll = self.batch.step(self.actions[:off])
+        if self.stream is not None:
+            self.stream.synchronize()
+        else:
+            torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        off = 0
+        for s in act:
+            if self.on_step is not None:
+                self.on_step(s, obs[off:off + s.n], rew[off:off + s.n], coll[off:off + s.n])
+            s.latencies.append(t1 - t0)
+            s.steps_done += 1
+            s.reset = False
+            off += s.n
+        self.iterations += 1
+        self.agent_steps += off
+        return len(act)
+
+    def run(self, arrivals, duration=None, drain=True):
+        """Replay `arrivals` = [(t, n, steps, seed), ...] in real time (t in
+        seconds from now) and iterate until all sessions are done (or until
+        `duration` seconds, when given).  Returns stats()."""
+        t_start = time.perf_counter()
+        pending = collections.deque(sorted(arrivals))
+        while True:
+            now = time.perf_counter() - t_start
+            while pending and pending[0][0] <= now:
+                t, n, steps, seed = pending.popleft()
+                self.submit(n, steps, seed, t_arrival=t_start + t)
+            if duration is not None and now >= duration:
+                break
+            if not self.sched.active and not self.sched.queue:
+                if not pending:
+                    if drain:
+                        break
+                    break
+                time.sleep(min(0.001, max(0.0, pending[0][0] - now)))
+                continue
+            self.iteration()
+        self.wall = time.perf_counter() - t_start
+        return self.stats()
+
+    def stats(self):
+        lat = [x for s in self.sched.finished + self.sched.active for x in s.latencies]
+        waits = [s.t_admit - s.t_arrival for s in self.sched.finished + self.sched.active
+                 if s.t_admit is not None]
+        wall = getattr(self, "wall", None)
+        return {
+            "sessions_admitted": self.sched.admitted, "sessions_rejected": self.sched.rejected,
+            "sessions_finished": len(self.sched.finished),
+            "sessions_waiting": len(self.sched.queue), "iterations": self.iterations,
+            "agent_steps": self.agent_steps, "set_changes": self.set_changes,
+            "step_latency_p50_ms": 1e3 * float(np.percentile(lat, 50)) if lat else None,
+            "step_latency_p99_ms": 1e3 * float(np.percentile(lat, 99)) if lat else None,
+            "queue_wait_p50_ms": 1e3 * float(np.percentile(waits, 50)) if waits else None,
+            "queue_wait_p99_ms": 1e3 * float(np.percentile(waits, 99)) if waits else None,
+            "agent_steps_per_s": self.agent_steps / wall if wall else None,
+            "wall_s": wall,
+        }
+
+    def close(self):
+        self.batch.close()
+
+
+class _null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
