@@ -48,6 +48,30 @@ def dist_info():
     return rank, world, local
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest x over the ranks of the default process group (x itself when
+    there is none).  NCCL needs a device tensor, gloo a host one."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64,
+                     device=device if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world: int, agents_per_rank: int, steps: int, max_ms: float) -> float:
+    """Whole-job agent-steps per second: every rank advanced its own
+    agents_per_rank agents `steps` times; the job took the slowest rank's time."""
+    return world * agents_per_rank * steps / (max_ms * 1e-3)
+
+
+def rank_seed(rank: int) -> int:
+    """Seed of a rank's replica: ranks run independent instances."""
+    return 1000 * rank
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -188,7 +212,8 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256, sizes=None):
+def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256, sizes=None,
+                world=1, tune=True):
     """The batched form: n_inst instances with agent counts log-uniform in
     [100, 20000] (density 0.1 each), all advanced by one persistent kernel
     per step, replayed from a CUDA graph.  With `sizes`, those instances
@@ -205,7 +230,13 @@ def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256,
         arena[off:off + n] = torch.from_numpy(fi.initial_state(n, fi.side_for(n), seed + k))
         states.append(arena[off:off + n])
         off += n
-    b = F.FlockBatch(n_inst, total, cells, 18, device=dev, stream=stream)
+    tuning = None
+    if tune:
+        from paper_2207_03945_gb300.autotune import autotune_batch
+        host_states = [s_.cpu().numpy() for s_ in states]
+        tuning, _ = autotune_batch(params, sizes, host_states, device=dev)
+    cells = sum(F.flock_instance_cells(p, tuning) for p in params)
+    b = F.FlockBatch(n_inst, total, cells, 18, device=dev, stream=stream, tuning=tuning)
     b.set(params, sizes, states, reset=[1] * n_inst)
     acts = torch.from_numpy(fi.random_actions(total, steps + warmup + 1, seed + 1)).to(dev)
     act_buf = torch.empty(total, dtype=torch.int32, device=dev)
@@ -242,14 +273,15 @@ def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256,
     err = b.error()
     assert err == 0, "device error bits %d" % err
     ms = [ev0[k].elapsed_time(ev1[k]) for k in range(steps)]
-    tot = sum(ms)
+    tot = max_over_ranks(sum(ms), dev)
     grid, block = F.env_batch_get_launch(b.batch)
     kern_ms = float(np.mean(kern))
     peak, peak_kind = peaks()
     achieved = BYTES_PER_AGENT_STEP * total / (kern_ms * 1e-3) / 1e9
     b.close()
-    return {"value": total * steps / (tot * 1e-3), "unit": UNIT, "instances": n_inst,
-            "agents": total, "cells": cells, "ms_per_step": tot / steps,
+    return {"value": weak_scaling_value(world, total, steps, tot), "unit": UNIT,
+            "instances": n_inst, "agents": total, "cells": cells, "ms_per_step": tot / steps,
+            "tuning": tuning,
             "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
             "grid": grid, "block": block,
             "workload": "batched: %d flock instances, agent counts %s (seed %d, %d agents), "
@@ -266,7 +298,7 @@ def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256,
 POLICY_BYTES_PER_AGENT = 48  # state 16 in + 16 out, action 4 in + 4 out, reward 4, coll 4
 
 
-def run_policy(F, torch, dev, stream, steps, warmup, flush, n=100000, seed=0):
+def run_policy(F, torch, dev, stream, steps, warmup, flush, n=100000, seed=0, world=1):
     """Step + fused policy at 100,000 agents (side 1000): the greedy actions
     of each step drive the next; observations stay on chip."""
     side = fi.side_for(n)
@@ -295,11 +327,11 @@ def run_policy(F, torch, dev, stream, steps, warmup, flush, n=100000, seed=0):
     torch.cuda.synchronize()
     assert env.error() == 0
     ms = [ev0[k].elapsed_time(ev1[k]) for k in range(steps)]
-    tot = sum(ms)
+    tot = max_over_ranks(sum(ms), dev)
     env.close()
     peak, peak_kind = peaks()
     achieved = POLICY_BYTES_PER_AGENT * n / (tot / steps * 1e-3) / 1e9
-    return {"value": n * steps / (tot * 1e-3), "unit": UNIT, "agents": n,
+    return {"value": weak_scaling_value(world, n, steps, tot), "unit": UNIT, "agents": n,
             "ms_per_step": tot / steps, "p50_ms": float(np.percentile(ms, 50)),
             "p99_ms": float(np.percentile(ms, 99)),
             "workload": "step + fused policy: %d agents, side %.0f, MLP 18-64-64-9 tanh, BF16 "
@@ -374,7 +406,7 @@ def main():
     n = args.agents
     side = fi.side_for(n)
     p = fi.default_params(side)
-    seed = 1000 * rank
+    seed = rank_seed(rank)
     st0 = fi.initial_state(n, side, seed)
     total = args.warmup + args.steps
     acts_h = fi.random_actions(n, total, seed)
@@ -382,7 +414,13 @@ def main():
     act_buf = torch.empty(n, dtype=torch.int32, device=dev)  # fixed pointer: one graph capture
     torch.cuda.synchronize()
     stream = torch.cuda.Stream(device=dev)
-    tuning = json.loads(args.tuning) if args.tuning else None
+    if args.tuning:
+        tuning = json.loads(args.tuning)
+        tuned_by = "command line"
+    else:
+        from paper_2207_03945_gb300.autotune import autotune
+        tuning, _ = autotune(p, st0, device=dev, use_cache=False)
+        tuned_by = "autotuner (bit-identical candidates, fastest kept)"
     env = F.FlockEnv(p, n, device=dev, stream=stream, tuning=tuning)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     with torch.cuda.stream(stream):
@@ -425,15 +463,10 @@ def main():
         phase.append(F.env_get_phase_times(env.env))
     F.env_set_timing(env.env, False)
     step_ms = [starts[k].elapsed_time(ends[k]) for k in range(args.warmup, total)]
-    tot_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(sum(step_ms), dev)
     err = env.error()
     assert err == 0, "device error bits %d" % err
-    value = world * n * args.steps / (tot_ms * 1e-3)
+    value = weak_scaling_value(world, n, args.steps, tot_ms)
     ph = np.array(phase)
     neigh_ms = float(ph[:, 3].mean())
     peak, peak_kind = peaks()
@@ -459,16 +492,16 @@ def main():
     batched = single_fused = None
     if not args.no_batched:
         batched = run_batched(F, torch, dev, stream, args.steps, args.warmup, flush,
-                              seed=1000 * rank)
+                              seed=rank_seed(rank), world=world)
         # the same 50,000-agent instance as the headline, as a batch of one
         single_fused = run_batched(F, torch, dev, stream, args.steps, args.warmup, flush,
-                                   seed=1000 * rank, sizes=[n])
+                                   seed=rank_seed(rank), sizes=[n], world=world, tune=False)
     serving = None
     if args.serve_seconds > 0:
         serving = {
-            "as_specified": run_serving(dev, args.serve_seconds, seed=1000 * rank),
+            "as_specified": run_serving(dev, args.serve_seconds, seed=rank_seed(rank)),
             "saturated_small_budget": run_serving(dev, max(5.0, args.serve_seconds / 2),
-                                                  seed=1000 * rank + 1, budget=10 ** 8,
+                                                  seed=rank_seed(rank) + 1, budget=10 ** 8,
                                                   backlog=200),
             "workload": "serving: Poisson arrivals 50/s, agents log-uniform in [500, 50000], "
                         "episodes uniform in [100, 2000] steps, 100 GB budget, random actions; "
@@ -476,7 +509,7 @@ def main():
     policy = None
     if not args.no_policy:
         policy = run_policy(F, torch, dev, stream, args.steps, args.warmup, flush,
-                            seed=1000 * rank)
+                            seed=rank_seed(rank), world=world)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -487,7 +520,7 @@ def main():
             "config": {"workload": "plain flock step, 1 instance, %d agents, side %.1f, density "
                                    "0.1, view radius 5, 8 sectors, fov 250 deg, uniform random "
                                    "actions, CUDA graph of 4 kernels" % (n, side),
-                       "agents": n, "tuning": env.tuning(),
+                       "agents": n, "tuning": env.tuning(), "tuned_by": tuned_by,
                        "l2": "flushed (512 MiB write) between timed steps",
                        "parallelism": "replicas" if world > 1 else "single"},
             "step_hbm_gbs": step_gbs,
@@ -509,8 +542,7 @@ def main():
             line["policy"] = policy
         if serving is not None:
             line["serving"] = serving
-            if world > 1:
-                line["batched"]["value_all_ranks"] = None
+
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))

@@ -1,0 +1,159 @@
+"""Autotuner for the launch shape of the flock step.
+
+For a workload (parameters and agent count) it times every candidate launch
+shape -- neighbour-scan form (warp chunks through L1, or shared-memory tiles
+of several sizes), cell size (3 x 3 stencil of cells >= d_v, or 5 x 5 of
+cells >= d_v / 2) and block size -- checks that each candidate gives the
+same bits as the library's default (every shape must), and keeps the
+fastest.  Results are cached in a JSON file keyed by GPU name, agent-count
+bucket (power of two) and sector count.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "flock_gb300_tuning.json")
+
+CANDIDATES = (
+    [{"mode": 2, "stencil": s, "block": b} for s in (1, 2) for b in (64, 128, 256)] +
+    [{"mode": 1, "stencil": 1, "tile_w": w, "tile_h": h, "block": 128}
+     for (w, h) in ((19, 2), (10, 4), (32, 1))] +
+    [{"mode": 1, "stencil": 2, "tile_w": 16, "tile_h": 4, "block": 128}])
+
+BATCH_CANDIDATES = ({"stencil": 1}, {"stencil": 2})
+
+
+def _key(torch, dev, n, params):
+    name = torch.cuda.get_device_name(dev)
+    bucket = 1 << max(0, int(math.ceil(math.log2(max(n, 1)))))
+    return "%s|n<=%d|v=%d" % (name, bucket, int(params["num_segments"]))
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(path, table):
+    d = os.path.dirname(path)
+    if d:
+        os.makedirs(d, exist_ok=True)
+    tmp = path + ".tmp%d" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(table, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def autotune(params, state0, steps=6, warmup=2, device="cuda", cache=DEFAULT_CACHE,
+             candidates=CANDIDATES, use_cache=True):
+    """Best launch shape for one environment of these parameters and this
+    initial state (n x 4 float32 host array).  Returns (tuning, report) where
+    report lists (tuning, ms per step, identical) for every candidate."""
+    import numpy as np
+    import torch
+
+    from . import FlockEnv, FlockError
+    dev = torch.device(device)
+    n = int(state0.shape[0])
+    key = _key(torch, dev, n, params)
+    table = _load(cache) if (cache and use_cache) else {}
+    if key in table:
+        return table[key]["tuning"], table[key].get("report", [])
+    rng = np.random.Generator(np.random.PCG64(17))
+    acts = torch.from_numpy(rng.integers(0, 9, size=(warmup + steps, n), dtype=np.int32)).to(dev)
+    s0 = torch.from_numpy(np.ascontiguousarray(state0, dtype=np.float32)).to(dev)
+    ref = None
+    report = []
+    best = None
+    for cand in [None] + list(candidates):
+        try:
+            env = FlockEnv(params, n, device=dev, tuning=cand)
+        except FlockError:
+            continue  # shape not valid for this workload (e.g. too few cells)
+        env.reset(s0)
+        outs = []
+        for k in range(warmup):
+            o, r, c = env.step(acts[k])
+            outs.append((o.clone(), r.clone(), c.clone()))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(warmup, warmup + steps):
+            env.step(acts[k])
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        tun = env.tuning()
+        env.close()
+        if ref is None:
+            ref = outs
+            same = True
+        else:
+            same = all(torch.equal(a, b) for x, y in zip(outs, ref) for a, b in zip(x, y))
+        if cand is not None:
+            report.append((tun, ms, same))
+            if same and (best is None or ms < best[1]):
+                best = (tun, ms)
+    if best is None:
+        raise FlockError("no valid launch shape")
+    if cache:
+        table = _load(cache)
+        table[key] = {"tuning": best[0], "ms": best[1], "report": report}
+        _store(cache, table)
+    return best[0], report
+
+
+def autotune_batch(params_list, sizes, states, steps=4, warmup=2, device="cuda",
+                   candidates=BATCH_CANDIDATES):
+    """Best cell size (stencil) for a batch: times one persistent launch per
+    step for each candidate and checks the outputs are identical."""
+    import numpy as np
+    import torch
+
+    from . import FlockBatch, FlockError, flock_instance_cells
+    dev = torch.device(device)
+    total = int(sum(sizes))
+    rng = np.random.Generator(np.random.PCG64(19))
+    acts = torch.from_numpy(rng.integers(0, 9, size=(warmup + steps, total),
+                                         dtype=np.int32)).to(dev)
+    ref = None
+    best = None
+    report = []
+    for cand in candidates:
+        try:
+            cells = sum(flock_instance_cells(p, cand) for p in params_list)
+            b = FlockBatch(len(sizes), total, cells, 2 * int(params_list[0]["num_segments"]) + 2,
+                           device=dev, tuning=cand)
+        except FlockError:
+            continue
+        st = [torch.from_numpy(np.ascontiguousarray(s, dtype=np.float32)).to(dev) for s in states]
+        b.set(params_list, sizes, st, reset=[1] * len(sizes))
+        b.step(acts[0])
+        outs = []
+        for k in range(1, warmup):
+            o, r, c = b.step(acts[k])
+            outs.append((o.clone(), r.clone(), c.clone()))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(warmup, warmup + steps):
+            b.step(acts[k])
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        b.close()
+        if ref is None:
+            ref, same = outs, True
+        else:
+            same = all(torch.equal(a, c) for x, y in zip(outs, ref) for a, c in zip(x, y))
+        report.append((dict(cand), ms, same))
+        if same and (best is None or ms < best[1]):
+            best = (dict(cand), ms)
+    return best[0], report
