@@ -193,6 +193,8 @@ int derive(const flock_params &p, int stencil, Inst &I, flock_derived *D) {
   if (nmax < 1.0) return FLOCK_EINVAL;
   I.NMAX = nmax > 9.0e15 ? (long long)9.0e15 : (long long)nmax;
   I.K = K;
+  // a term is below t_max * 2^K; two 24-bit pieces hold it when that is < 2^48
+  I.pieces = ldexp((double)t_max, K) < ldexp(1.0, 48) ? 2 : 3;
   I.scaleK = ldexpf(1.0f, K);
   I.inv_scaleK = ldexpf(1.0f, -K);
   const double pk = ldexp((double)p.collision_penalty, K);

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kBatchBlock) k_batch_step(const BatchDev *__re
       }
       const int gp0 = sI.agent_base + (c - __ldg(cpre + k)) * 32;
       const int gp1 = min(gp0 + 32, sI.agent_base + sI.n);
-      phaseD_direct<H, V>(sI, gp0, gp1, B, W, err);
+      phaseD_direct<H, V, false, false>(sI, gp0, gp1, B, W, err);
       // an instance observed without actions goes back to normal stepping
       if (sI.reset && gp0 == sI.agent_base && lane == 0) insts[k].reset = 0;
     }

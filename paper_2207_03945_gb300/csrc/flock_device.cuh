@@ -41,7 +41,9 @@ struct alignas(16) Inst {
   int agent_base, cell_base, tile_base, chunk_base;
   int tiles_x, tiles_y, tile_w, tile_h;
   int halo, full, K, reset;
-  int obs_dim, cap, pad0, pad1;  // cap: staged agents that fit in shared memory
+  int obs_dim, cap;  // cap: staged agents that fit in shared memory
+  int pieces;        // 32-bit pieces a reward term needs in shared accumulators (2 or 3)
+  int pad1;
   float L, HL, invw, RV, RV2, RC2, INV_SPAN, SMIN, SMAX, TWO_PI, CF, SF, scaleK, inv_scaleK;
   float DT[3], DS[3];
   long long PK, NMAX;
@@ -739,21 +741,23 @@ __device__ void phaseD_tile(const Inst &I, int tx, int ty, const Bufs &B, char *
 // ---------------------------------------------------------------------------
 struct DirectArea {
   float4 *queue;
-  unsigned long long *acc;
+  unsigned long long *acc;  // [32]: each owner lane's reward sum (units of 2^-K)
+  unsigned *accp;           // [3][32]: pieces of the current drain (bits 0-23, 24-47, 48-)
   int *nin, *ncoll;
   unsigned *md;
   int *cn;
 };
 
 __host__ __device__ inline size_t direct_warp_bytes(int v) {
-  return (size_t)kQueue * 16 + 32 * 8 + 32 * 4 * 2 + (size_t)32 * v * 8;
+  return (size_t)kQueue * 16 + 32 * 8 + 3 * 32 * 4 + 32 + 32 * 4 * 2 + (size_t)32 * v * 8;
 }
 
 __device__ __forceinline__ DirectArea direct_area(char *base, int v) {
   DirectArea W;
   W.queue = reinterpret_cast<float4 *>(base);
   W.acc = reinterpret_cast<unsigned long long *>(base + kQueue * 16);
-  W.nin = reinterpret_cast<int *>(base + kQueue * 16 + 32 * 8);
+  W.accp = reinterpret_cast<unsigned *>(base + kQueue * 16 + 32 * 8);
+  W.nin = reinterpret_cast<int *>(base + kQueue * 16 + 32 * 8 + 3 * 32 * 4 + 32);
   W.ncoll = W.nin + 32;
   W.md = reinterpret_cast<unsigned *>(W.ncoll + 32);
   W.cn = reinterpret_cast<int *>(W.md + 32 * v);
@@ -791,7 +795,11 @@ struct Edges {
 // Drain for the direct form.  In-range and collision counts are kept by the
 // owner lanes during the candidate scan; here each queued pair adds its ramp
 // term (non-colliding pairs) and its sector minimum and count.
-template <int V>
+// PIECES: add each term as 24-bit pieces with 32-bit shared atomics and fold
+// them into the 64-bit sums once per drain (64-bit shared atomics are slow);
+// without it, one 64-bit atomic per term (fewer registers, which the batched
+// kernel needs to keep four blocks per SM).  Both sums are exact integers.
+template <int V, bool PIECES>
 __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W, int count,
                                             float ux, float uy, const Edges<V> &E8) {
   const int lane = threadIdx.x & 31;
@@ -807,7 +815,15 @@ __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W,
       if (!(d2 < I.RC2)) {
         const float t = fmul(fsub(I.RV, fsqrt(d2)), I.INV_SPAN);
         const unsigned long long tv = float_int_u64(fmul(t, I.scaleK));
-        if (tv) atomicAdd(&W.acc[o], tv);
+        // a drain holds at most kQueue pairs, so each 32-bit piece sum
+        // stays below 2^24 * kQueue and exact
+        if (PIECES && tv) {
+          atomicAdd(&W.accp[o], (unsigned)tv & 0xffffffu);
+          atomicAdd(&W.accp[32 + o], (unsigned)(tv >> 24) & 0xffffffu);
+          if (I.pieces > 2) atomicAdd(&W.accp[64 + o], (unsigned)(tv >> 48));
+        } else if (tv) {
+          atomicAdd(&W.acc[o], tv);
+        }
       }
       const float lx = fadd(fmul(dx, uxo), fmul(dy, uyo));
       const float ly = fsub(fmul(dy, uxo), fmul(dx, uyo));
@@ -823,11 +839,20 @@ __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W,
     }
   }
   __syncwarp();
+  if (!PIECES) return;
+  // each lane folds its own pieces into its 64-bit sum
+  W.acc[lane] += (unsigned long long)W.accp[lane] +
+                 ((unsigned long long)W.accp[32 + lane] << 24) +
+                 ((unsigned long long)W.accp[64 + lane] << 48);
+  W.accp[lane] = 0u;
+  W.accp[32 + lane] = 0u;
+  W.accp[64 + lane] = 0u;
+  __syncwarp();
 }
 
 // One run of candidates [a, a + n) with shifts (sx, sy); appends in-range
 // pairs to the queue (warp-uniform loop), draining when nearly full.
-template <bool SHIFT, int V>
+template <bool SHIFT, int V, bool PIECES>
 __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, const float2 *sxy,
                                            int a, int n, int self, float sx, float sy, float xi,
                                            float yi, float ux, float uy, int &qn, int &nin,
@@ -859,7 +884,7 @@ __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, c
     qn += __popc(m);
     if (qn > kQueue - 32) {
       __syncwarp();
-      drain_direct<V>(I, W, qn, ux, uy, E8);
+      drain_direct<V, PIECES>(I, W, qn, ux, uy, E8);
       qn = 0;
     }
   }
@@ -1059,7 +1084,7 @@ __device__ __forceinline__ void policy_mtile(const PolicyCtx &P, int row0, int &
   }
 }
 
-template <int H, int V, bool POL = false>
+template <int H, int V, bool POL = false, bool PIECES = true>
 __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
                               const DirectArea &W, unsigned &err,
                               const PolicyCtx *pc = nullptr) {
@@ -1087,6 +1112,11 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
   const float ux = fadd(fmul(c, I.CF), fmul(sn, I.SF));
   const float uy = fsub(fmul(sn, I.CF), fmul(c, I.SF));
   W.acc[lane] = 0ull;
+  if (PIECES) {
+    W.accp[lane] = 0u;
+    W.accp[32 + lane] = 0u;
+    W.accp[64 + lane] = 0u;
+  }
   if (V == 8) {
     uint4 *m4 = reinterpret_cast<uint4 *>(W.md + lane * 8);
     int4 *c4 = reinterpret_cast<int4 *>(W.cn + lane * 8);
@@ -1121,7 +1151,7 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
   if (!wrap_any) {
 #pragma unroll
     for (int r = 0; r < 2 * H + 1; ++r)
-      direct_run<false, V>(I, W, B.sxy, ra[r], rn[r], self, 0.f, 0.f, xi, yi, ux, uy, qn, nin,
+      direct_run<false, V, PIECES>(I, W, B.sxy, ra[r], rn[r], self, 0.f, 0.f, xi, yi, ux, uy, qn, nin,
                            ncoll, E8);
   } else {
 #pragma unroll
@@ -1129,7 +1159,7 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
       const int vr = cy - H + r;
       const float sy = vr < 0 ? -I.L : (vr >= nc ? I.L : 0.0f);
       const int rowg = I.cell_base + wrapi(vr, nc) * nc;
-      direct_run<true, V>(I, W, B.sxy, ra[r], rn[r], self, 0.f, sy, xi, yi, ux, uy, qn, nin,
+      direct_run<true, V, PIECES>(I, W, B.sxy, ra[r], rn[r], self, 0.f, sy, xi, yi, ux, uy, qn, nin,
                           ncoll, E8);
       // cells across the left boundary: virtual columns [vlo, 0) -> [vlo + nc, nc)
       int a = 0, n = 0;
@@ -1137,7 +1167,7 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
         a = cst[rowg + vlo + nc];
         n = cst[rowg + nc] - a;
       }
-      direct_run<true, V>(I, W, B.sxy, a, n, self, -I.L, sy, xi, yi, ux, uy, qn, nin, ncoll,
+      direct_run<true, V, PIECES>(I, W, B.sxy, a, n, self, -I.L, sy, xi, yi, ux, uy, qn, nin, ncoll,
                           E8);
       // cells across the right boundary: virtual columns [nc, vhi) -> [0, vhi - nc)
       a = 0;
@@ -1146,11 +1176,11 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
         a = cst[rowg];
         n = cst[rowg + vhi - nc] - a;
       }
-      direct_run<true, V>(I, W, B.sxy, a, n, self, I.L, sy, xi, yi, ux, uy, qn, nin, ncoll, E8);
+      direct_run<true, V, PIECES>(I, W, B.sxy, a, n, self, I.L, sy, xi, yi, ux, uy, qn, nin, ncoll, E8);
     }
   }
   __syncwarp();
-  drain_direct<V>(I, W, qn, ux, uy, E8);
+  drain_direct<V, PIECES>(I, W, qn, ux, uy, E8);
   // reward and collisions
   if (have) {
     const long long total = (long long)W.acc[lane] - (long long)ncoll * I.PK;
