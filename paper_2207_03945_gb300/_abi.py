@@ -41,7 +41,7 @@ class FlockParams(ctypes.Structure):
 
 class FlockTuning(ctypes.Structure):
     _fields_ = [("stencil", ctypes.c_int), ("tile_w", ctypes.c_int), ("tile_h", ctypes.c_int),
-                ("block", ctypes.c_int), ("mode", ctypes.c_int)]
+                ("block", ctypes.c_int), ("mode", ctypes.c_int), ("lanes", ctypes.c_int)]
 
 
 class FlockDerived(ctypes.Structure):
@@ -71,7 +71,8 @@ def tuning_from_dict(t):
     if t is None:
         return None
     return FlockTuning(int(t.get("stencil", 0)), int(t.get("tile_w", 0)),
-                       int(t.get("tile_h", 0)), int(t.get("block", 0)), int(t.get("mode", 0)))
+                       int(t.get("tile_h", 0)), int(t.get("block", 0)), int(t.get("mode", 0)),
+                       int(t.get("lanes", 0)))
 
 
 def derived_to_dict(d: FlockDerived) -> dict:

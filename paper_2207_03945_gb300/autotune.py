@@ -3,7 +3,7 @@
 For a workload (parameters and agent count) it times every candidate launch
 shape -- neighbour-scan form (warp chunks through L1, or shared-memory tiles
 of several sizes), cell size (3 x 3 stencil of cells >= d_v, or 5 x 5 of
-cells >= d_v / 2) and block size -- checks that each candidate gives the
+cells >= d_v / 2), lanes per agent (1, 2 or 4) and block size -- checks that each candidate gives the
 same bits as the library's default (every shape must), and keeps the
 fastest.  Results are cached in a JSON file keyed by GPU name, agent-count
 bucket (power of two) and sector count.
@@ -17,12 +17,20 @@ import os
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "flock_gb300_tuning.json")
 
 CANDIDATES = (
-    [{"mode": 2, "stencil": s, "block": b} for s in (1, 2) for b in (64, 128, 256)] +
+    [{"mode": 2, "stencil": s, "block": b, "lanes": l}
+     for s in (1, 2) for b in (64, 128, 256) for l in (1, 2, 4)] +
     [{"mode": 1, "stencil": 1, "tile_w": w, "tile_h": h, "block": 128}
      for (w, h) in ((19, 2), (10, 4), (32, 1))] +
     [{"mode": 1, "stencil": 2, "tile_w": 16, "tile_h": 4, "block": 128}])
 
 BATCH_CANDIDATES = ({"stencil": 1}, {"stencil": 2})
+
+
+def _hold(torch):
+    """Keeps the GPU busy for a few milliseconds so that the timed steps are
+    all queued before the first one starts: the events then measure device
+    time, not the host's launch rate (which bounds small workloads)."""
+    torch.cuda._sleep(8_000_000)
 
 
 def _key(torch, dev, n, params):
@@ -83,6 +91,7 @@ def autotune(params, state0, steps=6, warmup=2, device="cuda", cache=DEFAULT_CAC
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        _hold(torch)
         e0.record()
         for k in range(warmup, warmup + steps):
             env.step(acts[k])
@@ -142,6 +151,7 @@ def autotune_batch(params_list, sizes, states, steps=4, warmup=2, device="cuda",
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        _hold(torch)
         e0.record()
         for k in range(warmup, warmup + steps):
             b.step(acts[k])

@@ -17,6 +17,14 @@
 
 namespace flock {
 
+// Programmatic dependent launch: a kernel launched with the programmatic
+// serialization attribute is set up while the kernel before it drains; it
+// waits here until that kernel has finished and its writes are visible.
+// (No early trigger: blocks of the next kernel held resident while this one
+// still runs made the step slower.)  Launched without the attribute, the
+// wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __global__ void __launch_bounds__(256) k_apply_bin(const Inst *__restrict__ gI, Bufs B, int reset) {
   __shared__ Inst sI;
   load_inst(sI, gI);
@@ -29,12 +37,14 @@ __global__ void __launch_bounds__(256) k_apply_bin(const Inst *__restrict__ gI, 
 
 __global__ void __launch_bounds__(256) k_scan(Bufs B) {
   __shared__ int sm[kScanTile + 34];
+  pdl_wait();
   phaseB_tile(blockIdx.x, B, sm);
 }
 
 __global__ void __launch_bounds__(256) k_scatter(const Inst *__restrict__ gI, Bufs B) {
   __shared__ int tp[kMaxScanTiles + 1];
   __shared__ int wsum[33];
+  pdl_wait();
   tile_prefix(B, tp, wsum);
   const float4 *state = gI->state;
   const int stride = gridDim.x * blockDim.x;
@@ -49,6 +59,7 @@ __global__ void k_neighbours(const Inst *__restrict__ gI, Bufs B) {
   extern __shared__ __align__(16) char smem[];
   __shared__ Inst sI;
   load_inst(sI, gI);
+  pdl_wait();
   __syncthreads();
   unsigned err = 0;
   const int t = blockIdx.x;
@@ -56,18 +67,21 @@ __global__ void k_neighbours(const Inst *__restrict__ gI, Bufs B) {
   if (err) atomicOr(B.err, err);
 }
 
-template <int H, int V>
+// LPA lanes per agent: each warp takes 32 / LPA consecutive sorted agents.
+template <int H, int V, int LPA>
 __global__ void k_neighbours_direct(const Inst *__restrict__ gI, Bufs B) {
   extern __shared__ __align__(16) char smem[];
   __shared__ Inst sI;
   load_inst(sI, gI);
+  pdl_wait();
   __syncthreads();
   unsigned err = 0;
   const int warp = threadIdx.x >> 5;
-  const int gp0 = (blockIdx.x * (blockDim.x >> 5) + warp) * 32;
+  constexpr int A = 32 / LPA;
+  const int gp0 = (blockIdx.x * (blockDim.x >> 5) + warp) * A;
   if (gp0 < sI.n) {
     const DirectArea W = direct_area(smem + (size_t)warp * direct_warp_bytes(sI.v), sI.v);
-    phaseD_direct<H, V>(sI, gp0, min(gp0 + 32, sI.n), B, W, err);
+    phaseD_direct<H, V, false, true, LPA>(sI, gp0, min(gp0 + A, sI.n), B, W, err);
   }
   if (err) atomicOr(B.err, err);
 }
@@ -82,6 +96,7 @@ __global__ void k_neighbours_policy(const Inst *__restrict__ gI, Bufs B,
   __shared__ Inst sI;
   load_inst(sI, gI);
   load_policy(wblob, smem);
+  pdl_wait();
   __syncthreads();
   unsigned err = 0;
   const int warp = threadIdx.x >> 5;
@@ -241,6 +256,9 @@ int choose_tuning(const Inst &I, int n, const flock_tuning *req, flock_tuning &t
   if (t.mode != 1 && t.mode != 2) return FLOCK_EINVAL;
   t.block = r.block ? r.block : 128;
   if (t.block < 64 || t.block > 512 || t.block % 32) return FLOCK_EINVAL;
+  t.lanes = r.lanes ? r.lanes : 1;
+  if (t.lanes != 1 && t.lanes != 2 && t.lanes != 4) return FLOCK_EINVAL;
+  if (t.mode == 1) t.lanes = 1;
   const double w = (double)I.L / I.nc;
   const double per_cell = n > 0 ? (double)n / ((double)I.L * I.L) * w * w : 1.0;
   t.tile_h = r.tile_h ? r.tile_h : 2;
@@ -284,10 +302,18 @@ cudaError_t set_kernel_attrs() {
     const void *fns[] = {(const void *)k_neighbours_policy<1>,
                          (const void *)k_neighbours_policy<2>,
                          (const void *)k_neighbours<1>, (const void *)k_neighbours<2>,
-                         (const void *)k_neighbours_direct<1, 0>,
-                         (const void *)k_neighbours_direct<2, 0>,
-                         (const void *)k_neighbours_direct<1, 8>,
-                         (const void *)k_neighbours_direct<2, 8>};
+                         (const void *)k_neighbours_direct<1, 0, 1>,
+                         (const void *)k_neighbours_direct<2, 0, 1>,
+                         (const void *)k_neighbours_direct<1, 8, 1>,
+                         (const void *)k_neighbours_direct<2, 8, 1>,
+                         (const void *)k_neighbours_direct<1, 0, 2>,
+                         (const void *)k_neighbours_direct<2, 0, 2>,
+                         (const void *)k_neighbours_direct<1, 8, 2>,
+                         (const void *)k_neighbours_direct<2, 8, 2>,
+                         (const void *)k_neighbours_direct<1, 0, 4>,
+                         (const void *)k_neighbours_direct<2, 0, 4>,
+                         (const void *)k_neighbours_direct<1, 8, 4>,
+                         (const void *)k_neighbours_direct<2, 8, 4>};
     g_attr_err = cudaSuccess;
     for (const void *f : fns) {
       cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
@@ -474,6 +500,26 @@ extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, v
   return FLOCK_OK;
 }
 
+// Launch with programmatic stream serialization (pdl = true): the kernel's
+// blocks may be scheduled while the previous kernel in the stream finishes,
+// hiding the launch gap; every kernel launched this way waits in pdl_wait()
+// before it reads what the previous one wrote.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch(bool pdl, void (*k)(KArgs...), int grid, int block, size_t smem,
+                         cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, ((KArgs)args)...);
+}
+
 static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, float *obs, float *rew,
                         int32_t *coll, int reset) {
   Bufs B = e->bufs;
@@ -484,38 +530,36 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, float 
   const Inst *gI = (const Inst *)(e->ws + e->lay.inst);
   const int n = e->n;
   const bool tm = e->timing != 0;
+  // with timing events between the kernels, plain stream order
+  const bool pdl = !tm;
   if (tm) CK(cudaEventRecordWithFlags(e->ev[0], s, cudaEventRecordExternal));
-  if (n > 0) {
-    k_apply_bin<<<(n + 255) / 256, 256, 0, s>>>(gI, B, reset);
-    CK(cudaGetLastError());
-  }
+  if (n > 0) CK(launch(false, k_apply_bin, (n + 255) / 256, 256, 0, s, gI, B, reset));
   if (tm) CK(cudaEventRecordWithFlags(e->ev[1], s, cudaEventRecordExternal));
-  k_scan<<<e->n_scan_tiles, 256, 0, s>>>(B);
-  CK(cudaGetLastError());
+  // k_scan follows k_apply_bin only when there was one
+  CK(launch(pdl && n > 0, k_scan, e->n_scan_tiles, 256, 0, s, B));
   if (tm) CK(cudaEventRecordWithFlags(e->ev[2], s, cudaEventRecordExternal));
-  k_scatter<<<e->scatter_grid, 256, 0, s>>>(gI, B);
-  CK(cudaGetLastError());
+  CK(launch(pdl, k_scatter, e->scatter_grid, 256, 0, s, gI, B));
   if (tm) CK(cudaEventRecordWithFlags(e->ev[3], s, cudaEventRecordExternal));
   if (n > 0) {
+    const int blk = e->tuning.block;
+    const size_t sm = e->smemD;
     if (e->tuning.mode == 1) {
       const int tiles = e->inst.tiles_x * e->inst.tiles_y;
-      if (e->inst.halo == 1)
-        k_neighbours<1><<<tiles, e->tuning.block, e->smemD, s>>>(gI, B);
-      else
-        k_neighbours<2><<<tiles, e->tuning.block, e->smemD, s>>>(gI, B);
+      if (e->inst.halo == 1) CK(launch(pdl, k_neighbours<1>, tiles, blk, sm, s, gI, B));
+      else CK(launch(pdl, k_neighbours<2>, tiles, blk, sm, s, gI, B));
     } else {
-      const int per_block = e->tuning.block;  // one agent per thread
+      const int lpa = e->tuning.lanes;
+      const int per_block = blk / lpa;  // agents per block
       const int blocks = (n + per_block - 1) / per_block;
-      const bool v8 = e->inst.v == 8;
-      if (e->inst.halo == 1) {
-        if (v8) k_neighbours_direct<1, 8><<<blocks, e->tuning.block, e->smemD, s>>>(gI, B);
-        else k_neighbours_direct<1, 0><<<blocks, e->tuning.block, e->smemD, s>>>(gI, B);
-      } else {
-        if (v8) k_neighbours_direct<2, 8><<<blocks, e->tuning.block, e->smemD, s>>>(gI, B);
-        else k_neighbours_direct<2, 0><<<blocks, e->tuning.block, e->smemD, s>>>(gI, B);
-      }
+      using KD = void (*)(const Inst *, Bufs);
+      static const KD kd[2][2][3] = {
+          {{k_neighbours_direct<1, 0, 1>, k_neighbours_direct<1, 0, 2>, k_neighbours_direct<1, 0, 4>},
+           {k_neighbours_direct<1, 8, 1>, k_neighbours_direct<1, 8, 2>, k_neighbours_direct<1, 8, 4>}},
+          {{k_neighbours_direct<2, 0, 1>, k_neighbours_direct<2, 0, 2>, k_neighbours_direct<2, 0, 4>},
+           {k_neighbours_direct<2, 8, 1>, k_neighbours_direct<2, 8, 2>, k_neighbours_direct<2, 8, 4>}}};
+      const KD k = kd[e->inst.halo - 1][e->inst.v == 8 ? 1 : 0][lpa == 1 ? 0 : (lpa == 2 ? 1 : 2)];
+      CK(launch(pdl, k, blocks, blk, sm, s, gI, B));
     }
-    CK(cudaGetLastError());
   }
   if (tm) CK(cudaEventRecordWithFlags(e->ev[4], s, cudaEventRecordExternal));
   return FLOCK_OK;
@@ -531,23 +575,17 @@ static int enqueue_policy_step(flock_env *e, cudaStream_t s, const unsigned shor
   B.coll = coll;
   const Inst *gI = (const Inst *)(e->ws + e->lay.inst);
   const int n = e->n;
-  if (n > 0) {
-    k_apply_bin<<<(n + 255) / 256, 256, 0, s>>>(gI, B, 0);
-    CK(cudaGetLastError());
-  }
-  k_scan<<<e->n_scan_tiles, 256, 0, s>>>(B);
-  CK(cudaGetLastError());
-  k_scatter<<<e->scatter_grid, 256, 0, s>>>(gI, B);
-  CK(cudaGetLastError());
+  if (n > 0) CK(launch(false, k_apply_bin, (n + 255) / 256, 256, 0, s, gI, B, 0));
+  CK(launch(n > 0, k_scan, e->n_scan_tiles, 256, 0, s, B));
+  CK(launch(true, k_scatter, e->scatter_grid, 256, 0, s, gI, B));
   if (n > 0) {
     const int block = e->tuning.block;
     const size_t smem = kPolicyBytes + (size_t)(block / 32) * (direct_warp_bytes(8) + kTileBytes);
     const int blocks = (n + block - 1) / block;
     if (e->inst.halo == 1)
-      k_neighbours_policy<1><<<blocks, block, smem, s>>>(gI, B, w, act, logits);
+      CK(launch(true, k_neighbours_policy<1>, blocks, block, smem, s, gI, B, w, act, logits));
     else
-      k_neighbours_policy<2><<<blocks, block, smem, s>>>(gI, B, w, act, logits);
-    CK(cudaGetLastError());
+      CK(launch(true, k_neighbours_policy<2>, blocks, block, smem, s, gI, B, w, act, logits));
   }
   return FLOCK_OK;
 }
@@ -875,8 +913,8 @@ extern "C" int flock_step_static(const flock_params *p, int n, float *state_dev,
   if (n > 0) {
     const size_t smem = (size_t)(t.block / 32) * direct_warp_bytes(I.v);
     const int blocks = (n + t.block - 1) / t.block;
-    if (I.v == 8) k_neighbours_direct<1, 8><<<blocks, t.block, smem, s>>>(gI, B);
-    else k_neighbours_direct<1, 0><<<blocks, t.block, smem, s>>>(gI, B);
+    if (I.v == 8) k_neighbours_direct<1, 8, 1><<<blocks, t.block, smem, s>>>(gI, B);
+    else k_neighbours_direct<1, 0, 1><<<blocks, t.block, smem, s>>>(gI, B);
     CK(cudaGetLastError());
   }
   if (error_bits_out) {

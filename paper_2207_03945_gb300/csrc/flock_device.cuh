@@ -852,15 +852,20 @@ __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W,
 
 // One run of candidates [a, a + n) with shifts (sx, sy); appends in-range
 // pairs to the queue (warp-uniform loop), draining when nearly full.
-template <bool SHIFT, int V, bool PIECES>
+// With LPA lanes per agent, lane l serves agent slot l % (32 / LPA) and
+// takes every LPA-th candidate of the run, starting at l / (32 / LPA).
+template <bool SHIFT, int V, bool PIECES, int LPA>
 __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, const float2 *sxy,
                                            int a, int n, int self, float sx, float sy, float xi,
                                            float yi, float ux, float uy, int &qn, int &nin,
                                            int &ncoll, const Edges<V> &E8) {
+  constexpr int A = 32 / LPA;
   const int lane = threadIdx.x & 31;
+  const int slot = lane & (A - 1), sub = lane / A;
   const unsigned lt = (1u << lane) - 1u;
   const int maxn = __reduce_max_sync(kFull, (unsigned)n);
-  for (int j = 0; j < maxn; ++j) {
+  for (int j0 = 0; j0 < maxn; j0 += LPA) {
+    const int j = j0 + sub;
     const int q = a + j;
     bool inr = false;
     float dx = 0.f, dy = 0.f, d2 = 0.f;
@@ -880,7 +885,7 @@ __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, c
       }
     }
     const unsigned m = __ballot_sync(kFull, inr);
-    if (inr) W.queue[qn + __popc(m & lt)] = make_float4(dx, dy, d2, __int_as_float(lane));
+    if (inr) W.queue[qn + __popc(m & lt)] = make_float4(dx, dy, d2, __int_as_float(slot));
     qn += __popc(m);
     if (qn > kQueue - 32) {
       __syncwarp();
@@ -1084,15 +1089,21 @@ __device__ __forceinline__ void policy_mtile(const PolicyCtx &P, int row0, int &
   }
 }
 
-template <int H, int V, bool POL = false, bool PIECES = true>
+// A warp takes the 32 / LPA consecutive sorted agents [gp0, gp1); LPA lanes
+// share each agent's candidates (LPA = 1, 2 or 4; the policy form uses 1).
+template <int H, int V, bool POL = false, bool PIECES = true, int LPA = 1>
 __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
                               const DirectArea &W, unsigned &err,
                               const PolicyCtx *pc = nullptr) {
+  static_assert(LPA == 1 || LPA == 2 || LPA == 4, "lanes per agent");
+  static_assert(!POL || LPA == 1, "the policy tile holds 32 agents");
+  constexpr int A = 32 / LPA;
   const int lane = threadIdx.x & 31;
+  const int slot = lane & (A - 1);
   const int nc = I.nc, v = V == 8 ? 8 : I.v;
   Edges<V> E8;
   E8.load(I);
-  const int gp = gp0 + lane;
+  const int gp = gp0 + slot;
   const bool have = gp < gp1;
   const int nb = gp1 - gp0;
   float xi = 0.f, yi = 0.f;
@@ -1151,7 +1162,7 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
   if (!wrap_any) {
 #pragma unroll
     for (int r = 0; r < 2 * H + 1; ++r)
-      direct_run<false, V, PIECES>(I, W, B.sxy, ra[r], rn[r], self, 0.f, 0.f, xi, yi, ux, uy, qn, nin,
+      direct_run<false, V, PIECES, LPA>(I, W, B.sxy, ra[r], rn[r], self, 0.f, 0.f, xi, yi, ux, uy, qn, nin,
                            ncoll, E8);
   } else {
 #pragma unroll
@@ -1159,7 +1170,7 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
       const int vr = cy - H + r;
       const float sy = vr < 0 ? -I.L : (vr >= nc ? I.L : 0.0f);
       const int rowg = I.cell_base + wrapi(vr, nc) * nc;
-      direct_run<true, V, PIECES>(I, W, B.sxy, ra[r], rn[r], self, 0.f, sy, xi, yi, ux, uy, qn, nin,
+      direct_run<true, V, PIECES, LPA>(I, W, B.sxy, ra[r], rn[r], self, 0.f, sy, xi, yi, ux, uy, qn, nin,
                           ncoll, E8);
       // cells across the left boundary: virtual columns [vlo, 0) -> [vlo + nc, nc)
       int a = 0, n = 0;
@@ -1167,7 +1178,7 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
         a = cst[rowg + vlo + nc];
         n = cst[rowg + nc] - a;
       }
-      direct_run<true, V, PIECES>(I, W, B.sxy, a, n, self, -I.L, sy, xi, yi, ux, uy, qn, nin, ncoll,
+      direct_run<true, V, PIECES, LPA>(I, W, B.sxy, a, n, self, -I.L, sy, xi, yi, ux, uy, qn, nin, ncoll,
                           E8);
       // cells across the right boundary: virtual columns [nc, vhi) -> [0, vhi - nc)
       a = 0;
@@ -1176,13 +1187,19 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
         a = cst[rowg];
         n = cst[rowg + vhi - nc] - a;
       }
-      direct_run<true, V, PIECES>(I, W, B.sxy, a, n, self, I.L, sy, xi, yi, ux, uy, qn, nin, ncoll, E8);
+      direct_run<true, V, PIECES, LPA>(I, W, B.sxy, a, n, self, I.L, sy, xi, yi, ux, uy, qn, nin, ncoll, E8);
     }
   }
   __syncwarp();
   drain_direct<V, PIECES>(I, W, qn, ux, uy, E8);
+  // the lanes of an agent add up their counts
+#pragma unroll
+  for (int m = A; m < 32; m <<= 1) {
+    nin += __shfl_xor_sync(kFull, nin, m);
+    ncoll += __shfl_xor_sync(kFull, ncoll, m);
+  }
   // reward and collisions
-  if (have) {
+  if (have && lane < A) {
     const long long total = (long long)W.acc[lane] - (long long)ncoll * I.PK;
     B.reward[I.agent_base + i] = fmul(__ll2float_rn(total), I.inv_scaleK);
     B.coll[I.agent_base + i] = ncoll;
