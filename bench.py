@@ -38,7 +38,51 @@ METRIC = "flock agent-steps/sec at 50k agents, batched vs plain; p99 step latenc
 UNIT = "agent-steps/s"
 N_AGENTS = 50000
 BYTES_PER_AGENT_STEP = 116  # state in 16 + action 4 + state out 16 + obs 72 + reward 4 + coll 4
-NEIGH_BYTES_PER_AGENT = 96  # neighbour scan: reads the state (16), writes obs, reward, coll (80)
+# neighbour scan: reads the agent's sorted position (8), heading and speed (8)
+# and index (4); writes its observation (72), reward (4) and collisions (4)
+NEIGH_BYTES_PER_AGENT = 100
+# DRAM traffic per launch from ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum), valid while the kernel sources are unchanged
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+CSRC = os.path.join(ROOT, "paper_2207_03945_gb300", "csrc")
+
+
+def sources_digest() -> str:
+    """SHA-256 over the kernel sources and the public header."""
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h")))
+    for f in files:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    with open(os.path.join(ROOT, "include", "flock.h"), "rb") as fh:
+        h.update(b"flock.h\0" + fh.read())
+    return h.hexdigest()
+
+
+def tuning_tag(t: dict) -> str:
+    """Short name of a launch shape, e.g. m2-s1-b128-l2."""
+    tag = "m%d-s%d-b%d" % (t["mode"], t["stencil"], t["block"])
+    if t["mode"] == 1:
+        return tag + "-t%dx%d" % (t["tile_w"], t["tile_h"])
+    return tag + "-l%d" % t.get("lanes", 1)
+
+
+def measured_traffic(kernel: str, workload: str):
+    """Bytes per launch of `kernel` on `workload` from the committed ncu
+    table, or None when there is no entry or the sources changed since."""
+    try:
+        lines = open(TRAFFIC_FILE).read().splitlines()
+    except OSError:
+        return None
+    digest = sources_digest()
+    for ln in lines:
+        if not ln.strip() or ln.startswith("#"):
+            continue
+        f = [x.strip() for x in ln.split("|")]
+        if len(f) >= 5 and f[0] == kernel and f[1] == workload and f[4] == digest:
+            return int(f[2]) + int(f[3])
+    return None
 
 
 def dist_info():
@@ -275,6 +319,7 @@ def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256,
     ms = [ev0[k].elapsed_time(ev1[k]) for k in range(steps)]
     tot = max_over_ranks(sum(ms), dev)
     grid, block = F.env_batch_get_launch(b.batch)
+    traffic_key = "batched-%d-%d-s%d" % (n_inst, total, (tuning or {}).get("stencil", 1))
     kern_ms = float(np.mean(kern))
     peak, peak_kind = peaks()
     achieved = BYTES_PER_AGENT_STEP * total / (kern_ms * 1e-3) / 1e9
@@ -291,7 +336,8 @@ def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256,
                            seed, total),
             "roofline": {"bound": "hbm", "kernel": "k_batch_step", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_source": peak_kind, "traffic": None,
+                         "peak_source": peak_kind,
+                         "traffic": measured_traffic("k_batch_step", traffic_key),
                          "bytes_per_agent": BYTES_PER_AGENT_STEP}}
 
 
@@ -339,7 +385,8 @@ def run_policy(F, torch, dev, stream, steps, warmup, flush, n=100000, seed=0, wo
                         "accumulate, greedy actions feed the next step" % (n, side),
             "roofline": {"bound": "hbm", "kernel": "whole step (4 kernels)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                         "frac": achieved / peak, "peak_source": peak_kind,
+                         "traffic": measured_traffic("k_neighbours_policy", "policy-%d" % n),
                          "bytes_per_agent": POLICY_BYTES_PER_AGENT}}
 
 
@@ -382,6 +429,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--tuning", default=None,
                     help='launch shape as JSON, e.g. {"mode": 2, "stencil": 1, "block": 128}')
+    ap.add_argument("--autotune", action="store_true",
+                    help="plain step: launch shape from the autotuner instead of the default")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -417,10 +466,13 @@ def main():
     if args.tuning:
         tuning = json.loads(args.tuning)
         tuned_by = "command line"
-    else:
+    elif args.autotune:
         from paper_2207_03945_gb300.autotune import autotune
         tuning, _ = autotune(p, st0, device=dev, use_cache=False)
         tuned_by = "autotuner (bit-identical candidates, fastest kept)"
+    else:
+        tuning = None
+        tuned_by = "library default (direct form, 3 x 3 cells, lanes per agent by agent count)"
     env = F.FlockEnv(p, n, device=dev, stream=stream, tuning=tuning)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     with torch.cuda.stream(stream):
@@ -528,7 +580,9 @@ def main():
                          "scatter": float(ph[:, 2].mean()), "neighbours": neigh_ms},
             "roofline": {"bound": "hbm", "kernel": "k_neighbours", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_source": peak_kind, "traffic": None,
+                         "peak_source": peak_kind,
+                         "traffic": measured_traffic("k_neighbours_direct", "plain-%d-%s" % (
+                             n, tuning_tag(env.tuning()))),
                          "bytes_per_agent": NEIGH_BYTES_PER_AGENT},
             "e2e": e2e,
             "clocks": clk.summary(),

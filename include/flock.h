@@ -92,8 +92,9 @@ typedef struct flock_tuning {
   int mode;    /* neighbour scan: 1 = tiles of cells staged in shared memory,
                   2 = each warp takes 32 / lanes consecutive cell-sorted agents
                   and reads their stencil cells through the L1 cache */
-  int lanes;   /* mode 2: lanes per agent, 1, 2 or 4 (0: 1); the lanes of an
-                  agent share its candidates.  Mode 1 and the policy step use 1. */
+  int lanes;   /* mode 2: lanes per agent, 1, 2 or 4 (0: 4 up to 32,768 agents,
+                  2 up to 524,288, else 1); the lanes of an agent share its
+                  candidates.  Mode 1 and the policy step use 1. */
 } flock_tuning;
 
 /* Constants the library derives from flock_params (host, double precision

@@ -256,7 +256,9 @@ int choose_tuning(const Inst &I, int n, const flock_tuning *req, flock_tuning &t
   if (t.mode != 1 && t.mode != 2) return FLOCK_EINVAL;
   t.block = r.block ? r.block : 128;
   if (t.block < 64 || t.block > 512 || t.block % 32) return FLOCK_EINVAL;
-  t.lanes = r.lanes ? r.lanes : 1;
+  // lanes per agent: more lanes keep more warps in flight when there are
+  // few agents; with many, one lane per agent has the least overhead
+  t.lanes = r.lanes ? r.lanes : (n <= 32768 ? 4 : (n <= 524288 ? 2 : 1));
   if (t.lanes != 1 && t.lanes != 2 && t.lanes != 4) return FLOCK_EINVAL;
   if (t.mode == 1) t.lanes = 1;
   const double w = (double)I.L / I.nc;
@@ -609,16 +611,30 @@ extern "C" int env_reset(flock_env *e, const float *state0, float *obs, float *r
   return enqueue_step(e, e->stream, nullptr, obs, rew, coll, 1);
 }
 
+// Makes `exec` run graph g.  When only kernel arguments differ (new buffer
+// pointers), the executable graph is updated in place: launches already
+// enqueued keep the old arguments, so nothing waits.  Otherwise (first use,
+// or a different topology) it is re-instantiated after the stream drains.
+static cudaError_t install_graph(cudaGraphExec_t &exec, cudaGraph_t g, cudaStream_t s) {
+  if (exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(exec, g, &info) == cudaSuccess) return cudaSuccess;
+    (void)cudaGetLastError();  // the update was refused: rebuild
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    cudaGraphExecDestroy(exec);
+    exec = nullptr;
+  }
+  const cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+  if (e != cudaSuccess) exec = nullptr;
+  return e;
+}
+
 extern "C" int env_step(flock_env *e, const int32_t *act, float *obs, float *rew, int32_t *coll) {
   if (!e || (e->n > 0 && !act)) return FLOCK_EINVAL;
   int rc = check_out(e, obs, rew, coll);
   if (rc) return rc;
   if (!e->graph || e->g_act != act || e->g_obs != obs || e->g_rew != rew || e->g_coll != coll) {
-    if (e->graph) {
-      CK(cudaStreamSynchronize(e->stream));  // the old graph may still be running
-      cudaGraphExecDestroy(e->graph);
-      e->graph = nullptr;
-    }
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
     rc = enqueue_step(e, e->cap_stream, act, obs, rew, coll, 0);
@@ -628,10 +644,10 @@ extern "C" int env_step(flock_env *e, const int32_t *act, float *obs, float *rew
       return rc;
     }
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
-    ce = cudaGraphInstantiate(&e->graph, g, 0);
+    ce = install_graph(e->graph, g, e->stream);
     cudaGraphDestroy(g);
     if (ce != cudaSuccess) {
-      e->graph = nullptr;
+      e->g_act = nullptr;  // force a rebuild next time
       return cuda_fail(ce, "cudaGraphInstantiate");
     }
     e->g_act = act;
@@ -656,11 +672,6 @@ extern "C" int env_step_policy(flock_env *e, const uint16_t *weights, int32_t *a
   if (smem + sizeof(Inst) + 1024 > (size_t)smem_max) return FLOCK_EINVAL;
   if (!e->pgraph || e->p_w != weights || e->p_act != act || e->p_rew != rew ||
       e->p_coll != coll || e->p_log != logits || e->p_obs != obs) {
-    if (e->pgraph) {
-      CK(cudaStreamSynchronize(e->stream));
-      cudaGraphExecDestroy(e->pgraph);
-      e->pgraph = nullptr;
-    }
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = enqueue_policy_step(e, e->cap_stream, (const unsigned short *)weights, act, rew, coll,
@@ -671,10 +682,10 @@ extern "C" int env_step_policy(flock_env *e, const uint16_t *weights, int32_t *a
       return rc;
     }
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
-    ce = cudaGraphInstantiate(&e->pgraph, g, 0);
+    ce = install_graph(e->pgraph, g, e->stream);
     cudaGraphDestroy(g);
     if (ce != cudaSuccess) {
-      e->pgraph = nullptr;
+      e->p_w = nullptr;  // force a rebuild next time
       return cuda_fail(ce, "cudaGraphInstantiate");
     }
     e->p_w = weights;

@@ -314,3 +314,32 @@ def test_statistics_at_benchmark_density():
     assert abs(obs[:, 1:16:2].sum(1).mean() - lam) < 10 * math.sqrt(lam / n)
     assert abs(coll.mean() - rho * math.pi) < 10 * math.sqrt(rho * math.pi / n)
     assert err == 0
+
+
+def test_new_buffers_each_step_without_waiting():
+    """Steps queued back to back, each with other action and output buffers
+    (the step graph is updated in place while earlier steps may still run):
+    the last two steps' outputs and the final state match the oracle."""
+    n, steps = 3000, 8
+    side = fi.side_for(n)
+    p = fi.default_params(side)
+    st0 = fi.initial_state(n, side, 11)
+    acts = fi.random_actions(n, steps, 11)
+    env = F.FlockEnv(p, n, device=DEV)
+    env.reset(torch.from_numpy(st0).to(DEV))
+    acts_d = [torch.from_numpy(np.ascontiguousarray(a)).to(DEV) for a in acts]
+    outs = [(torch.empty((n, env.obs_dim), dtype=torch.float32, device=DEV),
+             torch.empty(n, dtype=torch.float32, device=DEV),
+             torch.empty(n, dtype=torch.int32, device=DEV)) for _ in range(2)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        F.env_step(env.env, acts_d[k], *outs[k % 2])
+    torch.cuda.synchronize()
+    o, _ = oracle_run(p, st0, acts)
+    assert np.array_equal(env.state().cpu().numpy(), o[-1][0])
+    for k in (steps - 2, steps - 1):
+        obs, rew, coll = (t.cpu().numpy() for t in outs[k % 2])
+        assert np.array_equal(obs, o[k + 1][1]) and np.array_equal(rew, o[k + 1][2])
+        assert np.array_equal(coll, o[k + 1][3])
+    assert env.error() == 0
+    env.close()
