@@ -170,7 +170,8 @@ def test_launch_shapes_are_bit_identical(tuning):
     acts = fi.random_actions(n, steps, 4)
     g, _, tun = gpu_run(p, st0, acts, tuning)
     assert tun["stencil"] == tuning["stencil"] and tun["mode"] == tuning["mode"]
-    assert tun["lanes"] == tuning.get("lanes", 1)
+    if "lanes" in tuning or tuning["mode"] == 1:
+        assert tun["lanes"] == tuning.get("lanes", 1)
     o, _ = oracle_run(p, st0, acts)
     assert_same(g, o, str(tuning))
 
