@@ -80,6 +80,29 @@ def random_actions(n: int, steps: int, seed: int) -> np.ndarray:
     return rng.integers(0, 9, size=(steps, n), dtype=np.int32)
 
 
+def paper_params(n_agents: int, **overrides) -> dict:
+    """The paper's own flock variant (Section 4.1 and Section 5): 128 sectors,
+    a view distance of a tenth of the side, field of view 250 degrees, on the
+    square of density 0.1 (side sqrt(n / 0.1)); agent radius, speeds and the
+    action ranges as in default_params.  The paper does not give the density;
+    0.1 keeps the collision rate of the other workloads."""
+    side = side_for(n_agents)
+    p = default_params(side, view_radius=float(np.float32(side / 10.0)), num_segments=128)
+    p.update(overrides)
+    return p
+
+
+def random_cont_actions(n: int, steps: int, seed: int, a_max: float, t_max: float,
+                        over: float = 1.25) -> np.ndarray:
+    """(steps, n, 2) float32 continuous actions (acceleration, rotation),
+    uniform in [-over * a_max, over * a_max] x [-over * t_max, over * t_max];
+    with over > 1 some fall outside the ranges (they are clamped)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 15485863))
+    u = rng.random((steps, n, 2)) * 2.0 - 1.0
+    scale = np.array([a_max, t_max], np.float64) * over
+    return (u * scale).astype(np.float32)
+
+
 def batch_sizes(n_inst: int = 256, lo: int = 100, hi: int = 20000, seed: int = 0) -> list:
     """Agent counts round(exp(U[ln lo, ln hi])) for a batch of instances."""
     rng = np.random.Generator(np.random.PCG64(seed + 104729))

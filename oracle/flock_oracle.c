@@ -55,7 +55,8 @@
 /* Status codes and latched condition bits (same meaning as the product's). */
 #define OR_OK 0
 #define OR_EINVAL (-1)
-#define OR_FLAG_ACTION 1u   /* an action outside [0, 9) was replaced by 4 */
+#define OR_FLAG_ACTION 1u   /* an action outside [0, 9) was replaced by 4, or a
+                               continuous action component was not finite */
 #define OR_FLAG_STATE 2u    /* a state component was non-finite or out of range */
 #define OR_FLAG_OVERFLOW 8u /* more in-range neighbours than the 64-bit sum holds */
 
@@ -243,19 +244,15 @@ static int state_ok(const oracle_derived *d, const float *st) {
          st[2] < d->TWO_PI && st[3] >= d->SMIN && st[3] <= d->SMAX;
 }
 
-/* Action a in [0, 9): turn = a / 3 picks {-Delta, 0, +Delta}, speed = a % 3
- * picks {-a, 0, +a}.  Speed update read as a clamp to [s_min, s_max] (the
- * printed formula has min and max swapped).  Heading wraps into [0, 2pi). */
-static void apply_one(const oracle_derived *d, float *st, int32_t a, uint32_t *flags) {
-  if (a < 0 || a >= 9) {
-    a = 4;
-    *flags |= OR_FLAG_ACTION;
-  }
-  int tu = a / 3, su = a % 3;
-  float s = st[3] + d->DS[su];
+/* Speed change ds and heading change dt of one agent, then the move: the
+ * speed update is read as a clamp to [s_min, s_max] (the printed formula has
+ * min and max swapped), the heading wraps into [0, 2pi) (|dt| < pi, so one
+ * wrap is enough), and the agent moves one step along the new heading. */
+static void move_one(const oracle_derived *d, float *st, float ds, float dt) {
+  float s = st[3] + ds;
   if (s < d->SMIN) s = d->SMIN;
   else if (s > d->SMAX) s = d->SMAX;
-  float th = st[2] + d->DT[tu];
+  float th = st[2] + dt;
   if (th >= d->TWO_PI) th = th - d->TWO_PI;
   else if (th < 0.0f) th = th + d->TWO_PI;
   if (th >= d->TWO_PI) th = 0.0f;
@@ -267,6 +264,41 @@ static void apply_one(const oracle_derived *d, float *st, int32_t a, uint32_t *f
   st[1] = wrap_coord(y, d->L);
   st[2] = th;
   st[3] = s;
+}
+
+/* Discrete action a in [0, 9): turn = a / 3 picks {-Delta, 0, +Delta}, speed
+ * = a % 3 picks {-a, 0, +a}. */
+static void apply_one(const oracle_derived *d, float *st, int32_t a, uint32_t *flags) {
+  if (a < 0 || a >= 9) {
+    a = 4;
+    *flags |= OR_FLAG_ACTION;
+  }
+  int tu = a / 3, su = a % 3;
+  move_one(d, st, d->DS[su], d->DT[tu]);
+}
+
+/* Continuous action (acceleration, rotation), the two-dimensional action
+ * space of the paper's flock (Section 4.1): the acceleration lies in
+ * [-a_max, a_max] and the rotation in [-theta_max, theta_max]; here
+ * a_max = speed_step and theta_max = turn_step, and values outside are
+ * clamped to the range (reading: the ranges bound the action).  A component
+ * that is not finite counts as 0 and raises OR_FLAG_ACTION. */
+static void apply_cont(const oracle_derived *d, float *st, const float *a, uint32_t *flags) {
+  float acc = a[0], rot = a[1];
+  if (!isfinite(acc)) {
+    acc = 0.0f;
+    *flags |= OR_FLAG_ACTION;
+  }
+  if (!isfinite(rot)) {
+    rot = 0.0f;
+    *flags |= OR_FLAG_ACTION;
+  }
+  const float amax = d->DS[2], tmax = d->DT[2];
+  if (acc < -amax) acc = -amax;
+  else if (acc > amax) acc = amax;
+  if (rot < -tmax) rot = -tmax;
+  else if (rot > tmax) rot = tmax;
+  move_one(d, st, acc, rot);
 }
 
 /* ------------------------------------------------------------------ */
@@ -405,6 +437,60 @@ int oracle_apply(const oracle_params *p, int n, float *state, const int32_t *act
   if (rc != OR_OK) return rc;
   uint32_t flags = 0;
   for (int i = 0; i < n; ++i) apply_one(&d, state + 4 * i, actions[i], &flags);
+  if (flags_out) *flags_out = flags;
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* The paper's own flock variant: continuous actions and the view-only */
+/* observation (Section 4.1: the view of v sectors and the speed).     */
+/* ------------------------------------------------------------------ */
+
+/* Observation layouts: 0 = per sector (distance, count), then speed and
+ * heading (2v + 2 values); 1 = per sector the distance, then the speed
+ * (v + 1 values), the 129-value observation of Section 4.1 for v = 128. */
+int oracle_obs_dim(const oracle_params *p, int layout) {
+  return layout == 1 ? p->num_segments + 1 : 2 * p->num_segments + 2;
+}
+
+/* One update with continuous actions.  actions: n x 2 floats (acceleration,
+ * rotation) or NULL for a reset; obs: n x oracle_obs_dim(p, layout). */
+int oracle_step_cont(const oracle_params *p, int n, float *state, const float *actions,
+                     int layout, float *obs, float *reward, int32_t *coll, uint32_t *flags_out,
+                     int threads) {
+  oracle_derived d;
+  int rc = oracle_derive(p, &d);
+  if (rc != OR_OK) return rc;
+  if (n < 0 || (layout != 0 && layout != 1)) return OR_EINVAL;
+  const int v = d.v;
+  const size_t D = (size_t)oracle_obs_dim(p, layout);
+  uint32_t flags = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!state_ok(&d, state + 4 * i)) flags |= OR_FLAG_STATE;
+    if (actions) apply_cont(&d, state + 4 * i, actions + 2 * i, &flags);
+  }
+#ifdef _OPENMP
+  int nt = threads > 0 ? threads : omp_get_max_threads();
+  uint32_t oflags = 0;
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 16) reduction(| : oflags)
+#else
+  (void)threads;
+  uint32_t oflags = 0;
+#endif
+  for (int i = 0; i < n; ++i) {
+    uint32_t f = 0;
+    float row[2 * OR_MAXV + 2];
+    observe_one(&d, n, state, i, row, reward + i, coll + i, &f);
+    float *o = obs + (size_t)i * D;
+    if (layout == 0) {
+      memcpy(o, row, (2 * (size_t)v + 2) * sizeof(float));
+    } else {
+      for (int k = 0; k < v; ++k) o[k] = row[2 * k]; /* distances */
+      o[v] = row[2 * v];                             /* speed */
+    }
+    oflags |= f;
+  }
+  flags |= oflags;
   if (flags_out) *flags_out = flags;
   return OR_OK;
 }

@@ -80,6 +80,8 @@ def _bind(path):
     lib.oracle_observe_rows.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, fp,
                                         ctypes.c_int, ip, fp, fp, ip, ctypes.c_int]
     lib.oracle_apply.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, fp, ip, up]
+    lib.oracle_step_cont.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, fp, fp, ctypes.c_int,
+                                     fp, fp, ip, up, ctypes.c_int]
     lib.oracle_sincos.argtypes = [ctypes.c_float, fp, fp]
     lib.oracle_diamond.argtypes = [ctypes.c_float, ctypes.c_float]
     lib.oracle_diamond.restype = ctypes.c_float
@@ -138,8 +140,11 @@ def _i(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
 
 
-def obs_dim(params: dict) -> int:
-    return 2 * int(params["num_segments"]) + 2
+def obs_dim(params: dict, layout: int = 0) -> int:
+    """Observation length: layout 0 = (distance, count) per sector, speed,
+    heading; layout 1 = distance per sector, speed (the paper's)."""
+    v = int(params["num_segments"])
+    return v + 1 if layout == 1 else 2 * v + 2
 
 
 def derive(params: dict) -> dict:
@@ -186,6 +191,30 @@ def step(params: dict, state: np.ndarray, actions: np.ndarray | None = None, thr
                          ctypes.byref(flags), int(threads))
     if rc != 0:
         raise ValueError("oracle rejected parameters (rc=%d)" % rc)
+    return st, obs, rew, coll, int(flags.value)
+
+
+def step_cont(params: dict, state: np.ndarray, actions: np.ndarray | None = None,
+              layout: int = 1, threads: int = 0):
+    """One update with continuous actions (N, 2) float32 (acceleration,
+    rotation), or None for a reset.  Returns (new_state, obs, reward, coll,
+    flags); obs has obs_dim(params, layout) columns."""
+    lib = _load()
+    st = np.ascontiguousarray(state, dtype=np.float32).copy()
+    n = st.shape[0]
+    obs = np.zeros((n, obs_dim(params, layout)), np.float32)
+    rew = np.zeros(n, np.float32)
+    coll = np.zeros(n, np.int32)
+    flags = ctypes.c_uint32(0)
+    act = None
+    if actions is not None:
+        act = np.ascontiguousarray(actions, dtype=np.float32)
+        assert act.shape == (n, 2)
+    rc = lib.oracle_step_cont(ctypes.byref(_params(params)), n, _f(st),
+                              _f(act) if act is not None else None, int(layout), _f(obs),
+                              _f(rew), _i(coll), ctypes.byref(flags), int(threads))
+    if rc != 0:
+        raise ValueError("oracle rejected the call (rc=%d)" % rc)
     return st, obs, rew, coll, int(flags.value)
 
 

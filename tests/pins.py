@@ -13,6 +13,17 @@ Pins (arXiv 2207.03945, Section 4.1, Eq. 1, Fig. 3, Fig. 4):
 * permutation equivariance (relabelling agents);
 * closed-form statistics of uniform agents (Poisson neighbour counts);
 * the deterministic sine/cosine against the library's float64 sin/cos.
+
+Pins of the paper's own flock variant (continuous two-dimensional actions,
+the view-only observation of Section 4.1):
+* continuous actions equal to the discrete steps {-a, 0, +a} x {-Delta, 0,
+  +Delta} reproduce the pinned discrete update bit for bit;
+* actions outside the ranges act as the clamped ones;
+* one move against the closed form x + s cos(theta), y + s sin(theta) in
+  float64 (to the FP32 rounding of the terms);
+* a non-finite component acts as 0 and is flagged;
+* the view-only layout holds exactly the distance columns and the speed of
+  the pinned (distance, count) layout.
 """
 from __future__ import annotations
 
@@ -172,3 +183,98 @@ def check_sincos():
         worst = max(worst, abs(c - math.cos(float(t))), abs(s - math.sin(float(t))))
     assert worst <= 2e-7, worst
     assert oracle.sincos(0.0) == (1.0, 0.0)
+
+
+def check_cont_reduces_to_discrete(seed=31, n=500):
+    """Continuous actions taken from the nine discrete ones give the discrete
+    update: same state, observation, reward and collisions, bit for bit."""
+    side = fi.side_for(n)
+    p = fi.default_params(side)
+    st = fi.initial_state(n, side, seed)
+    a = fi.random_actions(n, 1, seed)[0]
+    amax, tmax = np.float32(p["speed_step"]), np.float32(p["turn_step"])
+    ds = np.array([-amax, 0.0, amax], np.float32)
+    dt = np.array([-tmax, 0.0, tmax], np.float32)
+    ca = np.stack([ds[a % 3], dt[a // 3]], axis=1).astype(np.float32)
+    s1, o1, r1, c1, f1 = oracle.step(p, st, a, threads=0)
+    s2, o2, r2, c2, f2 = oracle.step_cont(p, st, ca, layout=0, threads=0)
+    for x, y, what in ((s1, s2, "state"), (o1, o2, "obs"), (r1, r2, "reward"), (c1, c2, "coll")):
+        np.testing.assert_array_equal(x, y, err_msg="continuous vs discrete " + what)
+    assert f1 == f2 == 0
+
+
+def check_cont_clamp(seed=37, n=300):
+    """Out-of-range actions act as the clamped ones."""
+    side = fi.side_for(n)
+    p = fi.default_params(side)
+    st = fi.initial_state(n, side, seed)
+    amax, tmax = np.float32(p["speed_step"]), np.float32(p["turn_step"])
+    ca = fi.random_cont_actions(n, 1, seed, float(amax), float(tmax), over=3.0)[0]
+    clipped = np.stack([np.clip(ca[:, 0], -amax, amax), np.clip(ca[:, 1], -tmax, tmax)],
+                       axis=1).astype(np.float32)
+    assert (np.abs(ca[:, 0]) > amax).any() and (np.abs(ca[:, 1]) > tmax).any()
+    a = oracle.step_cont(p, st, ca, layout=1, threads=0)
+    b = oracle.step_cont(p, st, clipped, layout=1, threads=0)
+    for x, y in zip(a[:4], b[:4]):
+        np.testing.assert_array_equal(x, y, err_msg="clamped actions")
+
+
+def check_cont_motion():
+    """One agent, no neighbours: speed and heading change by the action, the
+    agent moves by s' (cos theta', sin theta') (float64 closed form)."""
+    p = fi.default_params(100.0)
+    cases = [((50.0, 50.0, 1.0, 0.5), (0.1, 0.2)),
+             ((99.9, 0.05, 0.05, 0.75), (-0.2, -0.3)),   # heading wraps below 0, x and y wrap
+             ((10.0, 20.0, 6.2, 0.9), (0.25, 0.3))]      # speed clamps at 1, heading wraps above 2 pi
+    for st0, act in cases:
+        st = np.array([st0], np.float32)
+        s2, obs, _, _, flags = oracle.step_cont(p, st, np.array([act], np.float32), layout=1)
+        assert flags == 0
+        s = min(max(float(np.float32(np.float32(st0[3]) + np.float32(act[0]))), 0.0), 1.0)
+        th = float(np.float32(np.float32(st0[2]) + np.float32(act[1])))
+        two_pi = float(np.float32(2 * math.pi))
+        if th < 0:
+            th = float(np.float32(th + two_pi))
+        elif th >= two_pi:
+            th = float(np.float32(th - two_pi))
+        x = (st0[0] + s * math.cos(th)) % 100.0
+        y = (st0[1] + s * math.sin(th)) % 100.0
+        assert abs(float(s2[0, 3]) - s) == 0.0 and abs(float(s2[0, 2]) - th) == 0.0
+        assert abs(float(s2[0, 0]) - x) < 3e-5 and abs(float(s2[0, 1]) - y) < 3e-5, (s2, x, y)
+        # view-only row: every sector empty (distance d_v), then the speed
+        assert np.all(obs[0, :8] == np.float32(p["view_radius"])) and obs[0, 8] == s2[0, 3]
+
+
+def check_cont_nonfinite():
+    """A non-finite component acts as 0 and raises the action flag."""
+    n = 50
+    p = fi.default_params(40.0)
+    st = fi.initial_state(n, 40.0, 41)
+    ca = np.zeros((n, 2), np.float32)
+    bad = ca.copy()
+    bad[3, 0] = np.nan
+    bad[7, 1] = np.inf
+    a = oracle.step_cont(p, st, ca, layout=1)
+    b = oracle.step_cont(p, st, bad, layout=1)
+    for x, y in zip(a[:4], b[:4]):
+        np.testing.assert_array_equal(x, y)
+    assert a[4] == 0 and b[4] == oracle.FLAG_ACTION
+
+
+def check_layout_view_only(seed=43, n=600):
+    """Layout 1 (the paper's 129-value observation for v = 128) holds the
+    distance columns and the speed of layout 0."""
+    p = fi.paper_params(n)
+    st = fi.initial_state(n, p["side"], seed)
+    ca = fi.random_cont_actions(n, 1, seed, p["speed_step"], p["turn_step"])[0]
+    s0, o0, r0, c0, f0 = oracle.step_cont(p, st, ca, layout=0)
+    s1, o1, r1, c1, f1 = oracle.step_cont(p, st, ca, layout=1)
+    v = int(p["num_segments"])
+    assert o1.shape == (n, v + 1) and o0.shape == (n, 2 * v + 2)
+    np.testing.assert_array_equal(o1[:, :v], o0[:, 0:2 * v:2])
+    np.testing.assert_array_equal(o1[:, v], o0[:, 2 * v])
+    np.testing.assert_array_equal(o1[:, v], s1[:, 3])
+    for x, y in ((s0, s1), (r0, r1), (c0, c1)):
+        np.testing.assert_array_equal(x, y)
+    # a tenth of the side: about 0.1 pi (L/10)^2 = pi n / 100 neighbours in range
+    assert (o0[:, 1:2 * v:2].sum(axis=1) > 0).mean() > 0.9

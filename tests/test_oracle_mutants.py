@@ -42,6 +42,14 @@ MUTANTS = {
     "count_includes_self": ("if (j == i) continue;", "if (j == i && 0) continue;"),
     "turn_table_swapped": ("d->DT[0] = -p->turn_step; d->DT[1] = 0.0f; d->DT[2] = p->turn_step;",
                            "d->DT[0] = p->turn_step; d->DT[1] = 0.0f; d->DT[2] = -p->turn_step;"),
+    "cont_clamp_bound_swapped": ("if (acc < -amax) acc = -amax;", "if (acc < -amax) acc = amax;"),
+    "cont_components_swapped": ("move_one(d, st, acc, rot);", "move_one(d, st, rot, acc);"),
+    "cont_rotation_unclamped": ("else if (rot > tmax) rot = tmax;", "else if (0) rot = tmax;"),
+    "cont_nonfinite_kept": ("    acc = 0.0f;\n    *flags |= OR_FLAG_ACTION;", "    *flags |= OR_FLAG_ACTION;"),
+    "layout1_counts_for_distances": ("o[k] = row[2 * k]; /* distances */",
+                                     "o[k] = row[2 * k + 1]; /* distances */"),
+    "layout1_heading_for_speed": ("o[v] = row[2 * v];                             /* speed */",
+                                  "o[v] = row[2 * v + 1];                             /* speed */"),
     "move_before_turn": ("  float c, sn;\n  oracle_sincos(th, &c, &sn);\n  float x = st[0] + s * c;",
                          "  float c, sn;\n  oracle_sincos(st[2], &c, &sn);\n  float x = st[0] + s * c;"),
 }
@@ -56,7 +64,12 @@ def _pins_fail():
                   400, fi.side_for(400, 0.3), 22, fov=fi.FULL_FOV))),
               ("translation", pins.check_translation),
               ("permutation", pins.check_permutation),
-              ("statistics", lambda: pins.check_statistics(n=3000, threads=0))]
+              ("statistics", lambda: pins.check_statistics(n=3000, threads=0)),
+              ("cont_discrete", pins.check_cont_reduces_to_discrete),
+              ("cont_clamp", pins.check_cont_clamp),
+              ("cont_motion", pins.check_cont_motion),
+              ("cont_nonfinite", pins.check_cont_nonfinite),
+              ("layout_view_only", pins.check_layout_view_only)]
     for name, fn in checks:
         try:
             fn()

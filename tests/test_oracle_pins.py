@@ -121,3 +121,23 @@ def test_invalid_params():
                 {"num_segments": 129}, {"fov": 7.0}, {"side": 9.0}, {"speed_max": -1.0}):
         assert not oracle.params_ok(dict(fi.default_params(100.0), **bad)), bad
     assert oracle.params_ok(fi.default_params(100.0))
+
+
+def test_continuous_actions_reduce_to_discrete():
+    pins.check_cont_reduces_to_discrete()
+
+
+def test_continuous_actions_clamp():
+    pins.check_cont_clamp()
+
+
+def test_continuous_motion_closed_form():
+    pins.check_cont_motion()
+
+
+def test_continuous_nonfinite_action():
+    pins.check_cont_nonfinite()
+
+
+def test_view_only_layout():
+    pins.check_layout_view_only()
