@@ -390,6 +390,56 @@ def run_policy(F, torch, dev, stream, steps, warmup, flush, n=100000, seed=0, wo
                          "bytes_per_agent": POLICY_BYTES_PER_AGENT}}
 
 
+def run_paper_variant(F, torch, dev, stream, steps, warmup, flush, n=16000, seed=0, world=1):
+    """The paper's own flock (Section 4.1, Section 5): 16,000 agents (its
+    largest flock run), 128 sectors, view a tenth of the side (side 400, view
+    40: about 500 neighbours in range), field of view 250 degrees, continuous
+    (acceleration, rotation) actions, the 129-value view-only observation."""
+    p = fi.paper_params(n)
+    env = F.FlockEnv(p, n, device=dev, stream=stream)
+    acts = torch.from_numpy(fi.random_cont_actions(n, steps + warmup, seed, p["speed_step"],
+                                                   p["turn_step"])).to(dev)
+    act_buf = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        env.reset(torch.from_numpy(fi.initial_state(n, p["side"], seed)).to(dev))
+        for k in range(warmup):
+            act_buf.copy_(acts[k])
+            flush.zero_()
+            env.step_continuous(act_buf)
+    torch.cuda.synchronize()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            act_buf.copy_(acts[warmup + k])
+            flush.zero_()
+            ev0[k].record(stream)
+            env.step_continuous(act_buf)
+            ev1[k].record(stream)
+    torch.cuda.synchronize()
+    assert env.error() == 0
+    tun = env.tuning()
+    env.close()
+    ms = [ev0[k].elapsed_time(ev1[k]) for k in range(steps)]
+    tot = max_over_ranks(sum(ms), dev)
+    peak, peak_kind = peaks()
+    v = int(p["num_segments"])
+    bpa = 16 + 8 + 16 + 4 * (v + 1) + 4 + 4  # state in, action, state out, obs, reward, coll
+    achieved = bpa * n / (tot / steps * 1e-3) / 1e9
+    return {"value": weak_scaling_value(world, n, steps, tot), "unit": UNIT, "agents": n,
+            "ms_per_step": tot / steps, "p50_ms": float(np.percentile(ms, 50)),
+            "p99_ms": float(np.percentile(ms, 99)), "tuning": tun,
+            "workload": "the paper's flock: %d agents, side %.0f, view %.0f (a tenth of the "
+                        "side), 128 sectors, fov 250 deg, continuous (acceleration, rotation) "
+                        "actions, observation 128 distances + speed" % (n, p["side"],
+                                                                         p["view_radius"]),
+            "roofline": {"bound": "hbm", "kernel": "whole step (4 kernels)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind,
+                         "traffic": None, "bytes_per_agent": bpa}}
+
+
 def run_serving(dev, seconds, seed=0, rate=50.0, budget=100 * 10 ** 9, backlog=0):
     """Serving loop with continuous batching: Poisson session arrivals, agent
     counts log-uniform in [500, 50000], episodes of 100..2000 steps, admission
@@ -426,6 +476,8 @@ def main():
     ap.add_argument("--agents", type=int, default=N_AGENTS)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-policy", action="store_true")
+    ap.add_argument("--no-paper", action="store_true",
+                    help="skip the paper's own flock variant (16,000 agents, 128 sectors)")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--tuning", default=None,
                     help='launch shape as JSON, e.g. {"mode": 2, "stencil": 1, "block": 128}')
@@ -562,6 +614,10 @@ def main():
     if not args.no_policy:
         policy = run_policy(F, torch, dev, stream, args.steps, args.warmup, flush,
                             seed=rank_seed(rank), world=world)
+    paper = None
+    if not args.no_paper:
+        paper = run_paper_variant(F, torch, dev, stream, min(args.steps, 50), args.warmup, flush,
+                                  seed=rank_seed(rank), world=world)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -594,6 +650,8 @@ def main():
             line["single_instance_persistent"] = single_fused
         if policy is not None:
             line["policy"] = policy
+        if paper is not None:
+            line["paper_variant"] = paper
         if serving is not None:
             line["serving"] = serving
 

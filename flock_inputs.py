@@ -46,6 +46,7 @@ def default_params(side: float, **overrides) -> dict:
         "speed_step": 0.25,
         "turn_step": float(np.float32(math.pi / 8.0)),
         "num_segments": 8,
+        "obs_layout": 0,
     }
     for k, v in overrides.items():
         if k not in p:
@@ -82,12 +83,14 @@ def random_actions(n: int, steps: int, seed: int) -> np.ndarray:
 
 def paper_params(n_agents: int, **overrides) -> dict:
     """The paper's own flock variant (Section 4.1 and Section 5): 128 sectors,
-    a view distance of a tenth of the side, field of view 250 degrees, on the
+    a view distance of a tenth of the side, field of view 250 degrees, the
+    view-only observation (obs_layout 1: 128 distances and the speed), on the
     square of density 0.1 (side sqrt(n / 0.1)); agent radius, speeds and the
     action ranges as in default_params.  The paper does not give the density;
     0.1 keeps the collision rate of the other workloads."""
     side = side_for(n_agents)
-    p = default_params(side, view_radius=float(np.float32(side / 10.0)), num_segments=128)
+    p = default_params(side, view_radius=float(np.float32(side / 10.0)), num_segments=128,
+                       obs_layout=1)
     p.update(overrides)
     return p
 

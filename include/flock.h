@@ -33,12 +33,18 @@
  *   actions     n int32     : a in [0, 9): turn = a / 3 picks {-turn_step, 0,
  *                             +turn_step}, speed change = a % 3 picks
  *                             {-speed_step, 0, +speed_step}; a = 4 is "keep"
- *   obs         n x (2v+2) float : for sector k = 0..v-1, (distance to the
+ *   continuous actions  n x 2 float : (acceleration, rotation), the paper's
+ *                             two-dimensional action space (Section 4.1),
+ *                             clamped to [-speed_step, speed_step] x
+ *                             [-turn_step, turn_step] (env_step_continuous)
+ *   obs, layout 0  n x (2v+2) float : for sector k = 0..v-1, (distance to the
  *                             nearest agent in sector k, or view_radius when
  *                             empty; number of agents in sector k), then
  *                             (s, theta).  Sectors split the field of view
  *                             (centred on the heading) into v equal angles,
  *                             numbered counter-clockwise from its right edge.
+ *   obs, layout 1  n x (v+1) float : the distances of the v sectors, then s
+ *                             (the paper's observation: 129 values for v = 128)
  *   reward      n float, coll n int32 (collisions: pairs closer than
  *                             2 * agent_radius)
  * Row i of every output belongs to agent i of the state (never reordered).
@@ -60,7 +66,8 @@ extern "C" {
 #define FLOCK_ECUDA (-3)    /* a CUDA runtime call failed (see flock_last_cuda_error) */
 
 /* ---- device-side condition bits (env_get_error) ---- */
-#define FLOCK_ERR_ACTION 1u   /* an action outside [0, 9) was read; it acted as 4 */
+#define FLOCK_ERR_ACTION 1u   /* an action outside [0, 9) was read (it acted as 4), or a
+                                 continuous action component was not finite (it acted as 0) */
 #define FLOCK_ERR_STATE 2u    /* an input state value was non-finite or out of range */
 #define FLOCK_ERR_TIMEOUT 4u  /* a grid barrier of the batched kernel gave up waiting */
 #define FLOCK_ERR_OVERFLOW 8u /* an agent had more in-range neighbours than the exact
@@ -80,6 +87,8 @@ typedef struct flock_params {
   float speed_step;        /* speed change of an accelerate/decelerate action */
   float turn_step;         /* heading change of a rotate action, radians */
   int num_segments;        /* v: sectors of the field of view, 1..128 */
+  int obs_layout;          /* 0: (distance, count) per sector, speed, heading (2v + 2
+                              values); 1: distance per sector, speed (v + 1 values) */
 } flock_params;
 
 /* Launch shape of the neighbour scan.  Every field may be 0 (library
@@ -150,11 +159,21 @@ int env_reset(flock_env *env, const float *state0_dev, float *obs_dev, float *re
 int env_step(flock_env *env, const int32_t *actions_dev, float *obs_dev, float *reward_dev,
              int32_t *coll_dev);
 
+/* env_step with the paper's continuous actions (Section 4.1): actions2_dev
+ * holds n x 2 floats (acceleration, rotation), 8-byte aligned.  Each is
+ * clamped to [-speed_step, speed_step] and [-turn_step, turn_step]; a
+ * component that is not finite acts as 0 and latches FLOCK_ERR_ACTION.  The
+ * speed clamp, heading wrap, move and observation are those of env_step.
+ * Shares env_step's cached graph (updated in place when the kind of action
+ * or a pointer changes). */
+int env_step_continuous(flock_env *env, const float *actions2_dev, float *obs_dev,
+                        float *reward_dev, int32_t *coll_dev);
+
 /* One step whose next actions come from the fused policy: applies
  * actions_inout_dev, observes, and feeds each agent's observation through the
  * shared policy network on chip (the learners' shared MLP of Section 4.3,
  * here 18 -> 64 -> 64 -> 9 with tanh, as the 18-value observation needs;
- * needs num_segments == 8), then overwrites actions_inout_dev with the greedy
+ * needs num_segments == 8 and obs_layout 0), then overwrites actions_inout_dev with the greedy
  * actions (largest logit, lowest index on ties) for the next step.
  * weights_bf16_dev: 5,961 bfloat16 values, W1[64][18] b1[64] W2[64][64]
  * b2[64] W3[9][64] b3[9], each W row-major [out][in].  Operands are BF16 on
@@ -197,11 +216,12 @@ void env_destroy(flock_env *env);
  * Batched step: many independent flock instances advanced by ONE persistent
  * cooperative kernel per step (apply+bin, scan, scatter and neighbour scan as
  * phases separated by grid barriers).  Instances may differ in agent count and
- * in every parameter except num_segments; all share the batch's tuning.
+ * in every parameter except num_segments and obs_layout; all share the
+ * batch's tuning.  Actions are discrete (int32).
  *
  * Instance k of the active set owns rows [off_k, off_k + n_k) of every
- * flattened per-agent buffer (actions, reward, coll, and obs rows of 2v+2
- * floats), off_k = n_0 + ... + n_{k-1}.  Its state lives in caller memory
+ * flattened per-agent buffer (actions, reward, coll, and obs rows of the
+ * layout's length), off_k = n_0 + ... + n_{k-1}.  Its state lives in caller memory
  * (state_dev[k], n_k x 4 floats) and is updated in place, so sessions stay
  * resident across steps and may join or leave between steps.
  * ------------------------------------------------------------------------- */

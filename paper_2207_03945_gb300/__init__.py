@@ -20,7 +20,7 @@ __all__ = [
     "FlockError", "FLOCK_ERR_ACTION", "FLOCK_ERR_STATE", "FLOCK_ERR_TIMEOUT",
     "FLOCK_ERR_OVERFLOW", "flock_default_params", "flock_obs_dim", "flock_workspace_bytes",
     "flock_derive",
-    "env_create", "env_reset", "env_step", "env_step_host", "env_get_state", "env_set_state",
+    "env_create", "env_reset", "env_step", "env_step_continuous", "env_step_host", "env_get_state", "env_set_state",
     "env_get_error", "env_get_derived", "env_get_tuning", "env_set_timing",
     "env_get_phase_times", "env_destroy", "FlockEnv", "lib_path", "flock_instance_cells",
     "env_step_policy",
@@ -133,6 +133,15 @@ def env_step(env, actions, obs, reward, coll):
                                  *_outs(env, obs, reward, coll)))
 
 
+def env_step_continuous(env, actions2, obs, reward, coll):
+    """Step with continuous actions: actions2 is (n, 2) float32 (acceleration,
+    rotation), clamped to [-speed_step, speed_step] x [-turn_step, turn_step]."""
+    torch = _torch()
+    _abi.check(_abi.lib.env_step_continuous(
+        env.handle, _ptr(actions2, torch.float32, (env.n, 2), "actions2"),
+        *_outs(env, obs, reward, coll)))
+
+
 def env_step_policy(env, weights_bf16, actions, reward, coll, logits=None, obs=None):
     """Step whose next actions come from the fused BF16 policy MLP; actions
     (int32, n) are read, then overwritten with the greedy actions.
@@ -241,6 +250,10 @@ class FlockEnv:
 
     def step(self, actions):
         env_step(self.env, actions, self.obs, self.reward, self.coll)
+        return self.obs, self.reward, self.coll
+
+    def step_continuous(self, actions2):
+        env_step_continuous(self.env, actions2, self.obs, self.reward, self.coll)
         return self.obs, self.reward, self.coll
 
     def state(self):

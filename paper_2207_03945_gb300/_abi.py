@@ -36,7 +36,8 @@ class FlockParams(ctypes.Structure):
                 ("fov", ctypes.c_float), ("agent_radius", ctypes.c_float),
                 ("collision_penalty", ctypes.c_float), ("speed_min", ctypes.c_float),
                 ("speed_max", ctypes.c_float), ("speed_step", ctypes.c_float),
-                ("turn_step", ctypes.c_float), ("num_segments", ctypes.c_int)]
+                ("turn_step", ctypes.c_float), ("num_segments", ctypes.c_int),
+                ("obs_layout", ctypes.c_int)]
 
 
 class FlockTuning(ctypes.Structure):
@@ -60,7 +61,9 @@ PARAM_KEYS = [k for k, _ in FlockParams._fields_]
 
 
 def params_from_dict(p: dict) -> FlockParams:
-    return FlockParams(*(float(p[k]) for k in PARAM_KEYS[:-1]), int(p["num_segments"]))
+    floats = [k for k, t in FlockParams._fields_ if t is ctypes.c_float]
+    return FlockParams(*(float(p[k]) for k in floats), int(p["num_segments"]),
+                       int(p.get("obs_layout", 0)))
 
 
 def params_to_dict(p: FlockParams) -> dict:
@@ -100,6 +103,7 @@ def _load():
         "env_create": [P, T, ctypes.c_int, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
         "env_reset": [vp, vp, vp, vp, vp],
         "env_step": [vp, vp, vp, vp, vp],
+        "env_step_continuous": [vp, vp, vp, vp, vp],
         "env_step_host": [vp, vp, vp, vp, vp],
         "env_step_policy": [vp, vp, vp, vp, vp, vp, vp],
         "env_get_state": [vp, vp],

@@ -31,7 +31,9 @@ __global__ void __launch_bounds__(256) k_apply_bin(const Inst *__restrict__ gI, 
   __syncthreads();
   unsigned err = 0;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < sI.n) phaseA_agent(sI, i, B.actions + sI.agent_base, reset, B.counts, B.cellrank, err);
+  if (i < sI.n)
+    phaseA_agent(sI, i, B.actions + sI.agent_base, B.cactions ? B.cactions + sI.agent_base : nullptr,
+                 reset, B.counts, B.cellrank, err);
   if (err) atomicOr(B.err, err);
 }
 
@@ -80,7 +82,8 @@ __global__ void k_neighbours_direct(const Inst *__restrict__ gI, Bufs B) {
   constexpr int A = 32 / LPA;
   const int gp0 = (blockIdx.x * (blockDim.x >> 5) + warp) * A;
   if (gp0 < sI.n) {
-    const DirectArea W = direct_area(smem + (size_t)warp * direct_warp_bytes(sI.v), sI.v);
+    const DirectArea W =
+        direct_area(smem + (size_t)warp * direct_warp_bytes(sI.v, A), sI.v, A);
     phaseD_direct<H, V, false, true, LPA>(sI, gp0, min(gp0 + A, sI.n), B, W, err);
   }
   if (err) atomicOr(B.err, err);
@@ -232,7 +235,9 @@ int derive(const flock_params &p, int stencil, Inst &I, flock_derived *D) {
   I.ncells = I.nc * I.nc;
   I.halo = stencil;
   I.invw = (float)((double)I.nc / (double)p.side);
-  I.obs_dim = 2 * I.v + 2;
+  if (p.obs_layout != 0 && p.obs_layout != 1) return FLOCK_EINVAL;
+  I.obs_layout = p.obs_layout;
+  I.obs_dim = p.obs_layout == 1 ? I.v + 1 : 2 * I.v + 2;
 
   if (D) {
     memset(D, 0, sizeof *D);
@@ -370,6 +375,7 @@ struct flock_env {
   cudaStream_t cap_stream;
   cudaGraphExec_t graph;
   const void *g_act, *g_obs, *g_rew, *g_coll;
+  int g_cont;  // the cached graph takes continuous actions
   Bufs bufs;
   int n_scan_tiles;
   int scatter_grid;
@@ -395,12 +401,14 @@ extern "C" int flock_default_params(float side, flock_params *out) {
   out->speed_step = 0.25f;
   out->turn_step = (float)(kPi / 8.0);
   out->num_segments = 8;
+  out->obs_layout = 0;
   return FLOCK_OK;
 }
 
 extern "C" int flock_obs_dim(const flock_params *p) {
   if (!p || p->num_segments < 1 || p->num_segments > FLOCK_MAX_SEGMENTS) return FLOCK_EINVAL;
-  return 2 * p->num_segments + 2;
+  if (p->obs_layout != 0 && p->obs_layout != 1) return FLOCK_EINVAL;
+  return p->obs_layout == 1 ? p->num_segments + 1 : 2 * p->num_segments + 2;
 }
 
 static int resolve(const flock_params *p, const flock_tuning *t, int n, Inst &I, flock_tuning &tt,
@@ -478,7 +486,7 @@ extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, v
   e->scatter_grid = g < 1 ? 1 : (g > 4 * sms ? 4 * sms : g);
   e->smemD = e->tuning.mode == 1
                  ? phaseD_smem_bytes(e->inst.cap, e->inst.v, e->tuning.block)
-                 : (size_t)(e->tuning.block / 32) * direct_warp_bytes(e->inst.v);
+                 : (size_t)(e->tuning.block / 32) * direct_warp_bytes(e->inst.v, 32 / e->tuning.lanes);
   int smem_max = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e->smemD + sizeof(Inst) + 1024 > (size_t)smem_max) {
@@ -522,10 +530,12 @@ static cudaError_t launch(bool pdl, void (*k)(KArgs...), int grid, int block, si
   return cudaLaunchKernelEx(&cfg, k, ((KArgs)args)...);
 }
 
-static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, float *obs, float *rew,
-                        int32_t *coll, int reset) {
+// act: discrete actions, or cact (when not null): continuous ones.
+static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const float2 *cact,
+                        float *obs, float *rew, int32_t *coll, int reset) {
   Bufs B = e->bufs;
   B.actions = act;
+  B.cactions = cact;
   B.obs = obs;
   B.reward = rew;
   B.coll = coll;
@@ -608,7 +618,7 @@ extern "C" int env_reset(flock_env *e, const float *state0, float *obs, float *r
   if (e->n > 0)
     CK(cudaMemcpyAsync(e->ws + e->lay.state, state0, (size_t)e->n * 16, cudaMemcpyDeviceToDevice,
                        e->stream));
-  return enqueue_step(e, e->stream, nullptr, obs, rew, coll, 1);
+  return enqueue_step(e, e->stream, nullptr, nullptr, obs, rew, coll, 1);
 }
 
 // Makes `exec` run graph g.  When only kernel arguments differ (new buffer
@@ -630,14 +640,20 @@ static cudaError_t install_graph(cudaGraphExec_t &exec, cudaGraph_t g, cudaStrea
   return e;
 }
 
-extern "C" int env_step(flock_env *e, const int32_t *act, float *obs, float *rew, int32_t *coll) {
-  if (!e || (e->n > 0 && !act)) return FLOCK_EINVAL;
+// One step through the cached graph; act_or_cact is the discrete (cont = 0)
+// or continuous (cont = 1) action buffer.
+static int step_graph(flock_env *e, const void *act_or_cact, int cont, float *obs, float *rew,
+                      int32_t *coll) {
+  if (!e || (e->n > 0 && !act_or_cact)) return FLOCK_EINVAL;
   int rc = check_out(e, obs, rew, coll);
   if (rc) return rc;
-  if (!e->graph || e->g_act != act || e->g_obs != obs || e->g_rew != rew || e->g_coll != coll) {
+  if (!e->graph || e->g_act != act_or_cact || e->g_cont != cont || e->g_obs != obs ||
+      e->g_rew != rew || e->g_coll != coll) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
-    rc = enqueue_step(e, e->cap_stream, act, obs, rew, coll, 0);
+    const int32_t *act = cont ? nullptr : (const int32_t *)act_or_cact;
+    const float2 *cact = cont ? (const float2 *)act_or_cact : nullptr;
+    rc = enqueue_step(e, e->cap_stream, act, cact, obs, rew, coll, 0);
     cudaError_t ce = cudaStreamEndCapture(e->cap_stream, &g);
     if (rc) {
       if (g) cudaGraphDestroy(g);
@@ -650,7 +666,8 @@ extern "C" int env_step(flock_env *e, const int32_t *act, float *obs, float *rew
       e->g_act = nullptr;  // force a rebuild next time
       return cuda_fail(ce, "cudaGraphInstantiate");
     }
-    e->g_act = act;
+    e->g_act = act_or_cact;
+    e->g_cont = cont;
     e->g_obs = obs;
     e->g_rew = rew;
     e->g_coll = coll;
@@ -659,9 +676,19 @@ extern "C" int env_step(flock_env *e, const int32_t *act, float *obs, float *rew
   return FLOCK_OK;
 }
 
+extern "C" int env_step(flock_env *e, const int32_t *act, float *obs, float *rew, int32_t *coll) {
+  return step_graph(e, act, 0, obs, rew, coll);
+}
+
+extern "C" int env_step_continuous(flock_env *e, const float *act2, float *obs, float *rew,
+                                   int32_t *coll) {
+  if (act2 && !aligned(act2, 8)) return FLOCK_EINVAL;
+  return step_graph(e, act2, 1, obs, rew, coll);
+}
+
 extern "C" int env_step_policy(flock_env *e, const uint16_t *weights, int32_t *act, float *rew,
                                int32_t *coll, float *logits, float *obs) {
-  if (!e || e->inst.v != 8) return FLOCK_EINVAL;
+  if (!e || e->inst.v != 8 || e->inst.obs_layout != 0) return FLOCK_EINVAL;
   if (e->n > 0 && (!weights || !act || !rew || !coll || !aligned(weights, 4) ||
                    (obs && !aligned(obs, 8))))
     return FLOCK_EINVAL;

@@ -105,8 +105,8 @@ __global__ void __launch_bounds__(kBatchBlock) k_batch_step(const BatchDev *__re
   for (int f = gtid; f < D.n_total; f += gstride) {
     const int k = find_inst(apre, D.n_inst, f);
     const Inst &I = insts[k];
-    phaseA_agent(I, f - I.agent_base, B.actions + I.agent_base, I.reset, B.counts, B.cellrank,
-                 err);
+    phaseA_agent(I, f - I.agent_base, B.actions + I.agent_base, nullptr, I.reset, B.counts,
+                 B.cellrank, err);
   }
   if (!grid_barrier(ctr, B.err, spin_limit, &flag)) goto done;
 
@@ -326,14 +326,19 @@ extern "C" int env_batch_set(flock_batch *b, int n_inst, const flock_params *par
   std::vector<Inst> ins((size_t)(n_inst > 0 ? n_inst : 1));
   std::vector<int> apre((size_t)n_inst + 1), cpre((size_t)n_inst + 1);
   long long na = 0, ncell = 0, nchunk = 0;
-  int v = 0;
+  int v = 0, layout = 0;
   for (int k = 0; k < n_inst; ++k) {
     Inst &I = ins[k];
     int rc = derive(params[k], b->halo, I, nullptr);
     if (rc) return rc;
     if (n_agents[k] < 0 || (n_agents[k] > 0 && !state[k])) return FLOCK_EINVAL;
-    if (k == 0) v = I.v;
-    if (I.v != v) return FLOCK_EINVAL;  // one sector count per batch
+    if (k == 0) {
+      v = I.v;
+      layout = I.obs_layout;
+    }
+    // one sector count and one observation layout per batch (rows are
+    // flattened with a single row length)
+    if (I.v != v || I.obs_layout != layout) return FLOCK_EINVAL;
     I.n = n_agents[k];
     I.state = reinterpret_cast<float4 *>(state[k]);
     I.agent_base = (int)na;

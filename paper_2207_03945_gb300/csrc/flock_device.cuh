@@ -43,7 +43,7 @@ struct alignas(16) Inst {
   int halo, full, K, reset;
   int obs_dim, cap;  // cap: staged agents that fit in shared memory
   int pieces;        // 32-bit pieces a reward term needs in shared accumulators (2 or 3)
-  int pad1;
+  int obs_layout;    // 0: (distance, count) per sector, speed, heading; 1: distances, speed
   float L, HL, invw, RV, RV2, RC2, INV_SPAN, SMIN, SMAX, TWO_PI, CF, SF, scaleK, inv_scaleK;
   float DT[3], DS[3];
   long long PK, NMAX;
@@ -65,6 +65,7 @@ struct Bufs {
   unsigned *err;       // latched FLOCK_ERR_* bits
   unsigned *bar;       // grid barrier words (count, generation)
   const int32_t *actions;
+  const float2 *cactions;  // continuous actions (acceleration, rotation), or null
   float *obs;
   float *reward;
   int32_t *coll;
@@ -139,18 +140,14 @@ __device__ __forceinline__ bool state_ok(const float4 s, const Inst &I) {
          s.z < I.TWO_PI && s.w >= I.SMIN && s.w <= I.SMAX;
 }
 
-// Section 4.1: accelerate (clamped to [s_min, s_max]), rotate (heading kept in
-// [0, 2pi)), then move one step along the new heading on the torus.
-__device__ __forceinline__ float4 apply_action(float4 st, int a, const Inst &I, unsigned &err) {
-  if ((unsigned)a >= 9u) {
-    a = 4;
-    err |= FLOCK_ERR_ACTION;
-  }
-  const int tu = a / 3, su = a - 3 * tu;
-  float s = fadd(st.w, I.DS[su]);
+// Section 4.1: accelerate by ds (speed clamped to [s_min, s_max]), rotate by
+// dt (heading kept in [0, 2pi); |dt| < pi), then move one step along the new
+// heading on the torus.
+__device__ __forceinline__ float4 move_agent(float4 st, float ds, float dt, const Inst &I) {
+  float s = fadd(st.w, ds);
   if (s < I.SMIN) s = I.SMIN;
   else if (s > I.SMAX) s = I.SMAX;
-  float th = fadd(st.z, I.DT[tu]);
+  float th = fadd(st.z, dt);
   if (th >= I.TWO_PI) th = fsub(th, I.TWO_PI);
   else if (th < 0.0f) th = fadd(th, I.TWO_PI);
   if (th >= I.TWO_PI) th = 0.0f;
@@ -159,6 +156,44 @@ __device__ __forceinline__ float4 apply_action(float4 st, int a, const Inst &I, 
   float x = wrap_coord(fadd(st.x, fmul(s, c)), I.L);
   float y = wrap_coord(fadd(st.y, fmul(s, sn)), I.L);
   return make_float4(x, y, th, s);
+}
+
+// Discrete action a in [0, 9): turn a / 3 and speed change a % 3 index the
+// steps {-Delta, 0, +Delta} and {-a, 0, +a}; other values act as 4 (flagged).
+__device__ __forceinline__ float4 apply_action(float4 st, int a, const Inst &I, unsigned &err) {
+  if ((unsigned)a >= 9u) {
+    a = 4;
+    err |= FLOCK_ERR_ACTION;
+  }
+  const int tu = a / 3, su = a - 3 * tu;
+  return move_agent(st, I.DS[su], I.DT[tu], I);
+}
+
+// Continuous action (acceleration, rotation), Section 4.1: the ranges
+// [-a, a] x [-Delta, Delta] of the discrete steps bound the action (values
+// outside are clamped; a non-finite component counts as 0 and is flagged);
+// then the same speed clamp, heading wrap and move as above.
+__device__ __forceinline__ float4 apply_cont(float4 st, float2 a, const Inst &I, unsigned &err) {
+  float acc = a.x, rot = a.y;
+  if (!isfinite(acc)) {
+    acc = 0.0f;
+    err |= FLOCK_ERR_ACTION;
+  }
+  if (!isfinite(rot)) {
+    rot = 0.0f;
+    err |= FLOCK_ERR_ACTION;
+  }
+  const float amax = I.DS[2], tmax = I.DT[2];
+  acc = acc < -amax ? -amax : (acc > amax ? amax : acc);
+  rot = rot < -tmax ? -tmax : (rot > tmax ? tmax : rot);
+  return move_agent(st, acc, rot, I);
+}
+
+// Element e of an observation row: for e < v the sector's (distance, count),
+// for e == v (speed, heading); layout 1 keeps the distance (or the speed).
+__device__ __forceinline__ void put_obs(const Inst &I, float *row, int e, float2 val) {
+  if (I.obs_layout == 0) *reinterpret_cast<float2 *>(row + 2 * e) = val;
+  else row[e] = val.x;
 }
 
 __device__ __forceinline__ int cell_of(float x, const Inst &I) {
@@ -196,13 +231,16 @@ __device__ __forceinline__ int warp_count(int *counts, int g) {
 // ---------------------------------------------------------------------------
 // Phase A: apply + bin one agent (instance-local index i).
 // ---------------------------------------------------------------------------
+// actions_inst / cactions_inst: the instance's discrete actions, or (when
+// cactions_inst is not null) its continuous ones.
 __device__ __forceinline__ void phaseA_agent(const Inst &I, int i, const int32_t *actions_inst,
-                                             int reset, int *counts, int2 *cellrank,
-                                             unsigned &err) {
+                                             const float2 *cactions_inst, int reset, int *counts,
+                                             int2 *cellrank, unsigned &err) {
   float4 st = I.state[i];
   if (!state_ok(st, I)) err |= FLOCK_ERR_STATE;
   if (!reset) {
-    st = apply_action(st, actions_inst[i], I, err);
+    st = cactions_inst ? apply_cont(st, cactions_inst[i], I, err)
+                       : apply_action(st, actions_inst[i], I, err);
     I.state[i] = st;
   }
   const int g = I.cell_base + cell_of(st.y, I) * I.nc + cell_of(st.x, I);
@@ -408,9 +446,9 @@ __device__ __forceinline__ void write_agent(const Inst &I, const Bufs &B, int i,
   for (int k = 0; k < I.v; ++k) {
     const int ck = cn[k * stride];
     const float dk = ck ? fsqrt(__uint_as_float(md[k * stride])) : I.RV;
-    *reinterpret_cast<float2 *>(o + 2 * k) = make_float2(dk, (float)ck);
+    put_obs(I, o, k, make_float2(dk, (float)ck));
   }
-  *reinterpret_cast<float2 *>(o + 2 * I.v) = make_float2(s, th);
+  put_obs(I, o, I.v, make_float2(s, th));
   const long long total = (long long)acc - (long long)ncoll * I.PK;
   B.reward[I.agent_base + i] = fmul(__ll2float_rn(total), I.inv_scaleK);
   B.coll[I.agent_base + i] = ncoll;
@@ -683,7 +721,7 @@ __device__ void phaseD_tile(const Inst &I, int tx, int ty, const Bufs &B, char *
             } else {
               val = make_float2(sr_, tr);
             }
-            *reinterpret_cast<float2 *>(obs + (long long)ir * I.obs_dim + 2 * e) = val;
+            put_obs(I, obs + (long long)ir * I.obs_dim, e, val);
           }
         }
       }
@@ -764,11 +802,13 @@ struct DirectArea {
   int *cn;
 };
 
-__host__ __device__ inline size_t direct_warp_bytes(int v) {
-  return (size_t)kQueue * 16 + 32 * 8 + 3 * 32 * 4 + 32 + 32 * 4 * 2 + (size_t)32 * v * 8;
+// Bytes of one warp's area for v sectors and A agents per warp (32 / lanes
+// per agent): the per-sector minima and counts take A rows of v.
+__host__ __device__ inline size_t direct_warp_bytes(int v, int A = 32) {
+  return (size_t)kQueue * 16 + 32 * 8 + 3 * 32 * 4 + 32 + 32 * 4 * 2 + (size_t)A * v * 8;
 }
 
-__device__ __forceinline__ DirectArea direct_area(char *base, int v) {
+__device__ __forceinline__ DirectArea direct_area(char *base, int v, int A = 32) {
   DirectArea W;
   W.queue = reinterpret_cast<float4 *>(base);
   W.acc = reinterpret_cast<unsigned long long *>(base + kQueue * 16);
@@ -776,7 +816,7 @@ __device__ __forceinline__ DirectArea direct_area(char *base, int v) {
   W.nin = reinterpret_cast<int *>(base + kQueue * 16 + 32 * 8 + 3 * 32 * 4 + 32);
   W.ncoll = W.nin + 32;
   W.md = reinterpret_cast<unsigned *>(W.ncoll + 32);
-  W.cn = reinterpret_cast<int *>(W.md + 32 * v);
+  W.cn = reinterpret_cast<int *>(W.md + A * v);
   return W;
 }
 
@@ -1144,18 +1184,21 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
     W.accp[32 + lane] = 0u;
     W.accp[64 + lane] = 0u;
   }
+  // per-sector minima and counts of the warp's A agents (A rows of v)
   if (V == 8) {
-    uint4 *m4 = reinterpret_cast<uint4 *>(W.md + lane * 8);
-    int4 *c4 = reinterpret_cast<int4 *>(W.cn + lane * 8);
-    const unsigned inf = 0x7f800000u;
-    m4[0] = make_uint4(inf, inf, inf, inf);
-    m4[1] = make_uint4(inf, inf, inf, inf);
-    c4[0] = make_int4(0, 0, 0, 0);
-    c4[1] = make_int4(0, 0, 0, 0);
+    if (lane < A) {
+      uint4 *m4 = reinterpret_cast<uint4 *>(W.md + lane * 8);
+      int4 *c4 = reinterpret_cast<int4 *>(W.cn + lane * 8);
+      const unsigned inf = 0x7f800000u;
+      m4[0] = make_uint4(inf, inf, inf, inf);
+      m4[1] = make_uint4(inf, inf, inf, inf);
+      c4[0] = make_int4(0, 0, 0, 0);
+      c4[1] = make_int4(0, 0, 0, 0);
+    }
   } else {
-    for (int k = 0; k < v; ++k) {
-      W.md[lane * v + k] = 0x7f800000u;
-      W.cn[lane * v + k] = 0;
+    for (int t = lane; t < A * v; t += 32) {
+      W.md[t] = 0x7f800000u;
+      W.cn[t] = 0;
     }
   }
   int nin = 0, ncoll = 0;
@@ -1247,7 +1290,7 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
         } else {
           val = make_float2(sr_, tr);
         }
-        if (obs) *reinterpret_cast<float2 *>(obs + (long long)ir * I.obs_dim + 2 * e) = val;
+        if (obs) put_obs(I, obs + (long long)ir * I.obs_dim, e, val);
         if (POL)
           *reinterpret_cast<unsigned *>(pc->tile + r * kTileS + 2 * e) = pack_bf16(val.x, val.y);
       }

@@ -100,3 +100,15 @@ def test_cell_geometry():
         assert d["side"] / d["cells_per_side"] >= 5.0
     d2 = F.flock_derive(fi.default_params(fi.side_for(50000)), {"stencil": 2})
     assert d2["cells_per_side"] == 282 and d2["stencil"] == 2
+
+
+def test_obs_layouts():
+    F = _lib()
+    p = fi.default_params(100.0, num_segments=128)
+    assert F.flock_obs_dim(p) == 258
+    p["obs_layout"] = 1
+    assert F.flock_obs_dim(p) == 129
+    assert F.flock_obs_dim(fi.paper_params(16000)) == 129
+    p["obs_layout"] = 2
+    with pytest.raises(F.FlockError):
+        F.flock_obs_dim(p)
