@@ -494,3 +494,34 @@ int oracle_step_cont(const oracle_params *p, int n, float *state, const float *a
   if (flags_out) *flags_out = flags;
   return OR_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* Advantages over a rollout (the trajectory processing of Section 4.3: */
+/* PPO on the n x t trajectories of one training step).                 */
+/* ------------------------------------------------------------------ */
+/* Generalised advantage estimation over T steps of n agents, FP32, one
+ * operation at a time, in this order (the definition written out):
+ *   gl = gamma * lambda
+ *   for t = T-1 down to 0:
+ *     delta_t = (r_t + gamma * v_{t+1}) - v_t
+ *     A_t     = delta_t + gl * A_{t+1}        (A_T = 0)
+ *     R_t     = A_t + v_t                     (the value target)
+ * reward: T x n, value: (T+1) x n (v_T bootstraps the last step: the flock
+ * never terminates), adv and ret: T x n, all row-major by step. */
+int oracle_gae(int T, int n, const float *reward, const float *value, float gamma, float lambda,
+               float *adv, float *ret) {
+  if (T < 0 || n < 0) return OR_EINVAL;
+  if (!(gamma >= 0.0f && gamma <= 1.0f && lambda >= 0.0f && lambda <= 1.0f)) return OR_EINVAL;
+  const float gl = gamma * lambda;
+  for (int i = 0; i < n; ++i) {
+    float a = 0.0f;
+    for (int t = T - 1; t >= 0; --t) {
+      const size_t k = (size_t)t * n + i;
+      const float delta = (reward[k] + gamma * value[k + n]) - value[k];
+      a = delta + gl * a;
+      adv[k] = a;
+      ret[k] = a + value[k];
+    }
+  }
+  return OR_OK;
+}

@@ -80,6 +80,8 @@ def _bind(path):
     lib.oracle_observe_rows.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, fp,
                                         ctypes.c_int, ip, fp, fp, ip, ctypes.c_int]
     lib.oracle_apply.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, fp, ip, up]
+    lib.oracle_gae.argtypes = [ctypes.c_int, ctypes.c_int, fp, fp, ctypes.c_float, ctypes.c_float,
+                               fp, fp]
     lib.oracle_step_cont.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, fp, fp, ctypes.c_int,
                                      fp, fp, ip, up, ctypes.c_int]
     lib.oracle_sincos.argtypes = [ctypes.c_float, fp, fp]
@@ -216,6 +218,23 @@ def step_cont(params: dict, state: np.ndarray, actions: np.ndarray | None = None
     if rc != 0:
         raise ValueError("oracle rejected the call (rc=%d)" % rc)
     return st, obs, rew, coll, int(flags.value)
+
+
+def gae(reward: np.ndarray, value: np.ndarray, gamma: float, lam: float):
+    """Advantages and value targets of a rollout (FP32, the oracle's order):
+    reward (T, n), value (T + 1, n).  Returns (adv, ret), each (T, n)."""
+    lib = _load()
+    r = np.ascontiguousarray(reward, dtype=np.float32)
+    v = np.ascontiguousarray(value, dtype=np.float32)
+    T, n = r.shape
+    assert v.shape == (T + 1, n)
+    adv = np.zeros((T, n), np.float32)
+    ret = np.zeros((T, n), np.float32)
+    rc = lib.oracle_gae(T, n, _f(r), _f(v), ctypes.c_float(gamma), ctypes.c_float(lam), _f(adv),
+                        _f(ret))
+    if rc != 0:
+        raise ValueError("oracle rejected the call (rc=%d)" % rc)
+    return adv, ret
 
 
 def apply(params: dict, state: np.ndarray, actions: np.ndarray):

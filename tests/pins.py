@@ -278,3 +278,61 @@ def check_layout_view_only(seed=43, n=600):
         np.testing.assert_array_equal(x, y)
     # a tenth of the side: about 0.1 pi (L/10)^2 = pi n / 100 neighbours in range
     assert (o0[:, 1:2 * v:2].sum(axis=1) > 0).mean() > 0.9
+
+
+# ---------------------------------------------------------------------------
+# Advantages over a rollout (generalised advantage estimation, FP32)
+# ---------------------------------------------------------------------------
+def _gae64(r, v, gamma, lam):
+    """The recursion in float64 (a second statement, for error bounds)."""
+    T, n = r.shape
+    r = r.astype(np.float64)
+    v = v.astype(np.float64)
+    adv = np.zeros((T, n))
+    a = np.zeros(n)
+    for t in range(T - 1, -1, -1):
+        a = r[t] + gamma * v[t + 1] - v[t] + gamma * lam * a
+        adv[t] = a
+    return adv
+
+
+def check_gae_hand_worked():
+    """Reward 1 every step, values 0, gamma 1/2, lambda 1: the discounted sum
+    of the remaining rewards, 1, 1.5, 1.75, ... exactly."""
+    T, n = 6, 3
+    r = np.ones((T, n), np.float32)
+    v = np.zeros((T + 1, n), np.float32)
+    adv, ret = oracle.gae(r, v, 0.5, 1.0)
+    want = np.array([2.0 - 0.5 ** (T - 1 - t) for t in range(T)], np.float32)
+    np.testing.assert_array_equal(adv, np.repeat(want[:, None], n, axis=1))
+    np.testing.assert_array_equal(ret, adv)
+
+
+def check_gae_special_cases(seed=61, T=64, n=200):
+    """lambda = 0: the one-step TD error r_t + gamma v_{t+1} - v_t; gamma =
+    lambda = 1: the sum of the remaining rewards plus v_T minus v_t
+    (telescoping); both in float64 within the FP32 rounding of the terms."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    r = rng.normal(0.0, 1.0, (T, n)).astype(np.float32)
+    v = rng.normal(0.0, 5.0, (T + 1, n)).astype(np.float32)
+    adv, _ = oracle.gae(r, v, 0.97, 0.0)
+    td = r.astype(np.float64) + 0.97 * v[1:].astype(np.float64) - v[:-1].astype(np.float64)
+    assert np.abs(adv - td).max() <= 1e-5 * (1.0 + np.abs(td).max())
+    adv, ret = oracle.gae(r, v, 1.0, 1.0)
+    tail = np.cumsum(r[::-1].astype(np.float64), axis=0)[::-1]
+    want = tail + v[T].astype(np.float64) - v[:-1].astype(np.float64)
+    assert np.abs(adv - want).max() <= 4 * T * 2.0 ** -24 * (np.abs(r).sum(axis=0).max() + 2 * np.abs(v).max())
+    np.testing.assert_array_equal(ret, (adv + v[:-1]).astype(np.float32))
+
+
+def check_gae_fp64(seed=67, T=128, n=300, gamma=0.99, lam=0.95):
+    """General gamma, lambda: within the FP32 error bound of the float64
+    recursion."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    r = rng.normal(0.3, 1.0, (T, n)).astype(np.float32)
+    v = rng.normal(0.0, 3.0, (T + 1, n)).astype(np.float32)
+    adv, ret = oracle.gae(r, v, gamma, lam)
+    ref = _gae64(r, v, gamma, lam)
+    scale = np.abs(r).max() + 2 * np.abs(v).max()
+    assert np.abs(adv - ref).max() <= 8 * T * 2.0 ** -24 * scale / (1 - gamma * lam) + 1e-7
+    np.testing.assert_array_equal(ret, (adv + v[:-1]).astype(np.float32))

@@ -50,6 +50,12 @@ MUTANTS = {
                                      "o[k] = row[2 * k + 1]; /* distances */"),
     "layout1_heading_for_speed": ("o[v] = row[2 * v];                             /* speed */",
                                   "o[v] = row[2 * v + 1];                             /* speed */"),
+    "gae_bootstrap_from_same_step": ("(reward[k] + gamma * value[k + n]) - value[k]",
+                                     "(reward[k] + gamma * value[k]) - value[k]"),
+    "gae_lambda_dropped": ("const float gl = gamma * lambda;", "const float gl = gamma;"),
+    "gae_target_minus_value": ("ret[k] = a + value[k];", "ret[k] = a - value[k];"),
+    "gae_forward_in_time": ("for (int t = T - 1; t >= 0; --t) {\n      const size_t k",
+                            "for (int t = 0; t < T; ++t) {\n      const size_t k"),
     "move_before_turn": ("  float c, sn;\n  oracle_sincos(th, &c, &sn);\n  float x = st[0] + s * c;",
                          "  float c, sn;\n  oracle_sincos(st[2], &c, &sn);\n  float x = st[0] + s * c;"),
 }
@@ -69,7 +75,10 @@ def _pins_fail():
               ("cont_clamp", pins.check_cont_clamp),
               ("cont_motion", pins.check_cont_motion),
               ("cont_nonfinite", pins.check_cont_nonfinite),
-              ("layout_view_only", pins.check_layout_view_only)]
+              ("layout_view_only", pins.check_layout_view_only),
+              ("gae_hand", pins.check_gae_hand_worked),
+              ("gae_special", pins.check_gae_special_cases),
+              ("gae_fp64", pins.check_gae_fp64)]
     for name, fn in checks:
         try:
             fn()

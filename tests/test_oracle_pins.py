@@ -141,3 +141,15 @@ def test_continuous_nonfinite_action():
 
 def test_view_only_layout():
     pins.check_layout_view_only()
+
+
+def test_gae_hand_worked():
+    pins.check_gae_hand_worked()
+
+
+def test_gae_special_cases():
+    pins.check_gae_special_cases()
+
+
+def test_gae_against_float64():
+    pins.check_gae_fp64()
