@@ -440,6 +440,71 @@ def run_paper_variant(F, torch, dev, stream, steps, warmup, flush, n=16000, seed
                          "traffic": None, "bytes_per_agent": bpa}}
 
 
+def run_rollout(F, torch, dev, stream, reps, flush, n=16000, T=128, seed=0, world=1):
+    """One training step's experience collection of the paper (Section 5:
+    t = 128 environment updates of all agents), as a single graph launch of
+    128 steps of the paper's flock (16,000 agents, continuous actions), then
+    the advantages over the 128 x 16,000 trajectory (generalised advantage
+    estimation, gamma 0.99, lambda 0.95) with seeded values standing in for
+    the critic."""
+    p = fi.paper_params(n)
+    env = F.FlockEnv(p, n, device=dev, stream=stream)
+    acts = torch.from_numpy(fi.random_cont_actions(n, T, seed, p["speed_step"],
+                                                   p["turn_step"])).to(dev)
+    obs = torch.empty((T, n, env.obs_dim), dtype=torch.float32, device=dev)
+    rew = torch.empty((T, n), dtype=torch.float32, device=dev)
+    coll = torch.empty((T, n), dtype=torch.int32, device=dev)
+    val = torch.from_numpy(np.random.Generator(np.random.PCG64(seed + 5)).normal(
+        0.0, 1.0, (T + 1, n)).astype(np.float32)).to(dev)
+    adv = torch.empty((T, n), dtype=torch.float32, device=dev)
+    ret = torch.empty((T, n), dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        env.reset(torch.from_numpy(fi.initial_state(n, p["side"], seed)).to(dev))
+        F.env_rollout(env.env, None, obs, rew, coll, actions2=acts)  # warm-up, graph capture
+        F.flock_gae(rew, val, 0.99, 0.95, adv, ret, stream=stream)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(reps)]
+    for k in range(reps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev[k][0].record(stream)
+            F.env_rollout(env.env, None, obs, rew, coll, actions2=acts)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    # the advantage kernel timed on its own, each run after an L2 flush
+    gae_ms = []
+    for k in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0.record(stream)
+            F.flock_gae(rew, val, 0.99, 0.95, adv, ret, stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        gae_ms.append(e0.elapsed_time(e1))
+    assert env.error() == 0
+    env.close()
+    roll_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(reps)]
+    tot = max_over_ranks(sum(roll_ms), dev)
+    g_ms = float(np.mean(gae_ms))
+    peak, peak_kind = peaks()
+    gae_bytes = 16 * T * n + 4 * n  # reward and value in, advantage and target out
+    return {"value": weak_scaling_value(world, n * T, reps, tot), "unit": UNIT,
+            "agents": n, "steps_per_rollout": T, "ms_per_rollout": tot / reps,
+            "launches_per_rollout": 4 * T,
+            "workload": "rollout of the paper's flock: %d agents x %d steps in one graph "
+                        "launch (continuous actions, 128 sectors, view a tenth of the side), "
+                        "outputs kept for every step" % (n, T),
+            "gae": {"ms": g_ms, "elements": T * n, "gamma": 0.99, "lambda": 0.95,
+                    "roofline": {"bound": "hbm", "kernel": "k_gae",
+                                 "achieved": gae_bytes / (g_ms * 1e-3) / 1e9, "peak": peak,
+                                 "unit": "GB/s",
+                                 "frac": gae_bytes / (g_ms * 1e-3) / 1e9 / peak,
+                                 "peak_source": peak_kind, "traffic": None,
+                                 "bytes_per_element": 16}}}
+
+
 def run_serving(dev, seconds, seed=0, rate=50.0, budget=100 * 10 ** 9, backlog=0):
     """Serving loop with continuous batching: Poisson session arrivals, agent
     counts log-uniform in [500, 50000], episodes of 100..2000 steps, admission
@@ -614,10 +679,11 @@ def main():
     if not args.no_policy:
         policy = run_policy(F, torch, dev, stream, args.steps, args.warmup, flush,
                             seed=rank_seed(rank), world=world)
-    paper = None
+    paper = rollout = None
     if not args.no_paper:
         paper = run_paper_variant(F, torch, dev, stream, min(args.steps, 50), args.warmup, flush,
                                   seed=rank_seed(rank), world=world)
+        rollout = run_rollout(F, torch, dev, stream, 3, flush, seed=rank_seed(rank), world=world)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -652,6 +718,7 @@ def main():
             line["policy"] = policy
         if paper is not None:
             line["paper_variant"] = paper
+            line["rollout"] = rollout
         if serving is not None:
             line["serving"] = serving
 

@@ -169,6 +169,29 @@ int env_step(flock_env *env, const int32_t *actions_dev, float *obs_dev, float *
 int env_step_continuous(flock_env *env, const float *actions2_dev, float *obs_dev,
                         float *reward_dev, int32_t *coll_dev);
 
+/* A rollout: T consecutive steps (env_step or env_step_continuous) as one
+ * launch of a CUDA graph of 4T kernels -- the t = 128 environment updates of
+ * a training step (Section 5).  Exactly one of actions_dev (T x n int32) and
+ * actions2_dev (T x n x 2 float, 8-byte aligned) is given; step t reads row
+ * t and writes rows t of obs_dev (T x n x obs_dim), reward_dev (T x n) and
+ * coll_dev (T x n), so the buffers hold the whole trajectory of every agent.
+ * The graph is kept for the next call with the same T and pointers (and
+ * updated in place when only the pointers change).  T = 0 does nothing. */
+int env_rollout(flock_env *env, int T, const int32_t *actions_dev, const float *actions2_dev,
+                float *obs_dev, float *reward_dev, int32_t *coll_dev);
+
+/* Advantages and value targets over a rollout (the trajectory processing of
+ * PPO, Section 4.3), by generalised advantage estimation in FP32:
+ *   delta_t = (r_t + gamma v_{t+1}) - v_t,  A_t = delta_t + (gamma lambda) A_{t+1},
+ *   A_T = 0,  R_t = A_t + v_t,
+ * evaluated in that order from t = T-1 down, one rounding per operation
+ * (gamma lambda rounded once).  reward_dev: T x n, value_dev: (T+1) x n (row
+ * T bootstraps the last step; the flock never terminates), adv_dev and
+ * ret_dev: T x n, all step-major, device memory, not overlapping.  gamma and
+ * lambda in [0, 1].  Enqueues one kernel on `stream` (a cudaStream_t). */
+int flock_gae(int T, int n, const float *reward_dev, const float *value_dev, float gamma,
+              float lambda, float *adv_dev, float *ret_dev, void *stream);
+
 /* One step whose next actions come from the fused policy: applies
  * actions_inout_dev, observes, and feeds each agent's observation through the
  * shared policy network on chip (the learners' shared MLP of Section 4.3,

@@ -20,7 +20,8 @@ __all__ = [
     "FlockError", "FLOCK_ERR_ACTION", "FLOCK_ERR_STATE", "FLOCK_ERR_TIMEOUT",
     "FLOCK_ERR_OVERFLOW", "flock_default_params", "flock_obs_dim", "flock_workspace_bytes",
     "flock_derive",
-    "env_create", "env_reset", "env_step", "env_step_continuous", "env_step_host", "env_get_state", "env_set_state",
+    "env_create", "env_reset", "env_step", "env_step_continuous", "env_rollout", "flock_gae",
+    "env_step_host", "env_get_state", "env_set_state",
     "env_get_error", "env_get_derived", "env_get_tuning", "env_set_timing",
     "env_get_phase_times", "env_destroy", "FlockEnv", "lib_path", "flock_instance_cells",
     "env_step_policy",
@@ -131,6 +132,35 @@ def env_step(env, actions, obs, reward, coll):
     torch = _torch()
     _abi.check(_abi.lib.env_step(env.handle, _ptr(actions, torch.int32, (env.n,), "actions"),
                                  *_outs(env, obs, reward, coll)))
+
+
+def env_rollout(env, actions, obs, reward, coll, actions2=None):
+    """T steps in one graph launch: actions (T, n) int32, or actions2 (T, n, 2)
+    float32 continuous actions (then actions is None); obs (T, n, obs_dim),
+    reward (T, n) float32 and coll (T, n) int32 receive every step."""
+    torch = _torch()
+    src = actions if actions is not None else actions2
+    if src is None:
+        raise FlockError("give actions or actions2")
+    T = int(src.shape[0])
+    a1 = _ptr(actions, torch.int32, (T, env.n), "actions") if actions is not None else None
+    a2 = _ptr(actions2, torch.float32, (T, env.n, 2), "actions2") if actions2 is not None else None
+    _abi.check(_abi.lib.env_rollout(
+        env.handle, T, a1, a2, _ptr(obs, torch.float32, (T, env.n, env.obs_dim), "obs"),
+        _ptr(reward, torch.float32, (T, env.n), "reward"),
+        _ptr(coll, torch.int32, (T, env.n), "coll")))
+
+
+def flock_gae(reward, value, gamma: float, lam: float, adv, ret, stream=None):
+    """Generalised advantage estimation over a rollout on the GPU: reward
+    (T, n), value (T + 1, n), adv and ret (T, n), float32 CUDA tensors."""
+    torch = _torch()
+    T, n = int(reward.shape[0]), int(reward.shape[1])
+    _abi.check(_abi.lib.flock_gae(
+        T, n, _ptr(reward, torch.float32, (T, n), "reward"),
+        _ptr(value, torch.float32, (T + 1, n), "value"), ctypes.c_float(gamma),
+        ctypes.c_float(lam), _ptr(adv, torch.float32, (T, n), "adv"),
+        _ptr(ret, torch.float32, (T, n), "ret"), _stream(stream)))
 
 
 def env_step_continuous(env, actions2, obs, reward, coll):
@@ -255,6 +285,18 @@ class FlockEnv:
     def step_continuous(self, actions2):
         env_step_continuous(self.env, actions2, self.obs, self.reward, self.coll)
         return self.obs, self.reward, self.coll
+
+    def rollout(self, actions=None, actions2=None):
+        """T steps in one launch; returns new (T, n, obs_dim), (T, n) and (T, n)
+        tensors holding every step's outputs."""
+        torch = _torch()
+        src = actions if actions is not None else actions2
+        T = int(src.shape[0])
+        obs = torch.empty((T, self.n, self.obs_dim), dtype=torch.float32, device=self.device)
+        rew = torch.empty((T, self.n), dtype=torch.float32, device=self.device)
+        coll = torch.empty((T, self.n), dtype=torch.int32, device=self.device)
+        env_rollout(self.env, actions, obs, rew, coll, actions2=actions2)
+        return obs, rew, coll
 
     def state(self):
         torch = _torch()

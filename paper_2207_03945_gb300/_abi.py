@@ -104,6 +104,9 @@ def _load():
         "env_reset": [vp, vp, vp, vp, vp],
         "env_step": [vp, vp, vp, vp, vp],
         "env_step_continuous": [vp, vp, vp, vp, vp],
+        "env_rollout": [vp, ctypes.c_int, vp, vp, vp, vp, vp],
+        "flock_gae": [ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_float, ctypes.c_float, vp, vp,
+                      vp],
         "env_step_host": [vp, vp, vp, vp, vp],
         "env_step_policy": [vp, vp, vp, vp, vp, vp, vp],
         "env_get_state": [vp, vp],

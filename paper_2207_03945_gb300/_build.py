@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libflock.so")
-SOURCES = ["flock.cu", "flock_batch.cu"]
+SOURCES = ["flock.cu", "flock_batch.cu", "flock_rollout.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no FMA contraction anywhere (the model's FP32 formulas are
 # written with explicit round-to-nearest intrinsics as well); IEEE division

@@ -383,6 +383,9 @@ struct flock_env {
   int timing;
   cudaEvent_t ev[5];
   cudaGraphExec_t pgraph;  // step with the fused policy
+  cudaGraphExec_t rgraph;  // a rollout of T steps
+  const void *r_act, *r_obs, *r_rew, *r_coll;
+  int r_T, r_cont;
   const void *p_w, *p_act, *p_rew, *p_coll, *p_log, *p_obs;
 };
 
@@ -686,6 +689,56 @@ extern "C" int env_step_continuous(flock_env *e, const float *act2, float *obs, 
   return step_graph(e, act2, 1, obs, rew, coll);
 }
 
+extern "C" int env_rollout(flock_env *e, int T, const int32_t *act, const float *act2, float *obs,
+                           float *rew, int32_t *coll) {
+  if (!e || T < 0) return FLOCK_EINVAL;
+  if (T == 0) return FLOCK_OK;
+  const int n = e->n;
+  if (n > 0 && ((act == nullptr) == (act2 == nullptr))) return FLOCK_EINVAL;
+  if (act2 && !aligned(act2, 8)) return FLOCK_EINVAL;
+  int rc = check_out(e, obs, rew, coll);
+  if (rc) return rc;
+  const int cont = act2 != nullptr;
+  const void *a = cont ? (const void *)act2 : (const void *)act;
+  if (!e->rgraph || e->r_T != T || e->r_cont != cont || e->r_act != a || e->r_obs != obs ||
+      e->r_rew != rew || e->r_coll != coll) {
+    // T steps in one graph; step t reads actions row t and writes output rows t
+    const int timing = e->timing;
+    e->timing = 0;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const size_t D = (size_t)e->inst.obs_dim;
+    for (int t = 0; t < T && rc == FLOCK_OK; ++t) {
+      const size_t o = (size_t)t * n;
+      rc = enqueue_step(e, e->cap_stream, act ? act + o : nullptr,
+                        act2 ? reinterpret_cast<const float2 *>(act2) + o : nullptr,
+                        obs ? obs + o * D : nullptr, rew ? rew + o : nullptr,
+                        coll ? coll + o : nullptr, 0);
+    }
+    e->timing = timing;
+    cudaError_t ce = cudaStreamEndCapture(e->cap_stream, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+    ce = install_graph(e->rgraph, g, e->stream);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+      e->r_T = 0;  // force a rebuild next time
+      return cuda_fail(ce, "cudaGraphInstantiate");
+    }
+    e->r_T = T;
+    e->r_cont = cont;
+    e->r_act = a;
+    e->r_obs = obs;
+    e->r_rew = rew;
+    e->r_coll = coll;
+  }
+  CK(cudaGraphLaunch(e->rgraph, e->stream));
+  return FLOCK_OK;
+}
+
 extern "C" int env_step_policy(flock_env *e, const uint16_t *weights, int32_t *act, float *rew,
                                int32_t *coll, float *logits, float *obs) {
   if (!e || e->inst.v != 8 || e->inst.obs_layout != 0) return FLOCK_EINVAL;
@@ -813,6 +866,7 @@ extern "C" void env_destroy(flock_env *e) {
     if (e->ev[k]) cudaEventDestroy(e->ev[k]);
   if (e->graph) cudaGraphExecDestroy(e->graph);
   if (e->pgraph) cudaGraphExecDestroy(e->pgraph);
+  if (e->rgraph) cudaGraphExecDestroy(e->rgraph);
   if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
   delete e;
 }
