@@ -106,6 +106,27 @@ def random_cont_actions(n: int, steps: int, seed: int, a_max: float, t_max: floa
     return (u * scale).astype(np.float32)
 
 
+def tag_types(n: int, seed: int, chaser_fraction: float = 0.1) -> np.ndarray:
+    """(n,) uint8 agent types for the tag environment: 1 (chaser) for a
+    random chaser_fraction of the agents (Section 5: a tenth are chasers),
+    0 (runner) for the rest."""
+    rng = np.random.Generator(np.random.PCG64(seed + 32452843))
+    t = np.zeros(n, np.uint8)
+    t[rng.permutation(n)[:int(round(chaser_fraction * n))]] = 1
+    return t
+
+
+def tag_actions(n: int, steps: int, seed: int, s_max: float, t_max: float,
+                over: float = 1.25) -> np.ndarray:
+    """(steps, n, 2) float32 tag actions (speed, rotation), uniform in
+    [-0.25 s_max, over * s_max] x [-over * t_max, over * t_max] (some clamp)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 49979687))
+    u = rng.random((steps, n, 2))
+    spd = -0.25 * s_max + u[..., 0] * (over + 0.25) * s_max
+    rot = (u[..., 1] * 2.0 - 1.0) * over * t_max
+    return np.stack([spd, rot], axis=-1).astype(np.float32)
+
+
 def batch_sizes(n_inst: int = 256, lo: int = 100, hi: int = 20000, seed: int = 0) -> list:
     """Agent counts round(exp(U[ln lo, ln hi])) for a batch of instances."""
     rng = np.random.Generator(np.random.PCG64(seed + 104729))

@@ -525,3 +525,130 @@ int oracle_gae(int T, int n, const float *reward, const float *value, float gamm
   }
   return OR_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* Tag (Section 4.2): runners and chasers.                             */
+/* ------------------------------------------------------------------ */
+/* Agents of type 0 are runners, of type 1 chasers.  Readings (the section
+ * describes the rewards in words only):
+ *   - a runner gets the flock reward from runners (Eq. 1 with f of Fig. 4:
+ *     the linear ramp for 2 d_r <= d < d_v) and -P for every agent it
+ *     touches (d < 2 d_r), runner or chaser ("penalised for touching a
+ *     chaser"; touching a runner is the flock's collision);
+ *   - a chaser gets +P for every runner it touches and nothing else;
+ *   - the view has two colour channels of v sectors: channel 0 holds the
+ *     nearest runner per sector, channel 1 the nearest chaser (d_v when
+ *     empty); the observation is the 2v distances, runners first;
+ *   - the action (speed, rotation) sets the speed, clamped to
+ *     [s_min, s_max], and turns the heading by the rotation clamped to
+ *     [-Delta, Delta]; a non-finite component acts as 0 and is flagged;
+ *   - coll counts every touching pair, whatever the types. */
+static void apply_tag(const oracle_derived *d, float *st, const float *a, uint32_t *flags) {
+  float spd = a[0], rot = a[1];
+  if (!isfinite(spd)) {
+    spd = 0.0f;
+    *flags |= OR_FLAG_ACTION;
+  }
+  if (!isfinite(rot)) {
+    rot = 0.0f;
+    *flags |= OR_FLAG_ACTION;
+  }
+  const float tmax = d->DT[2];
+  if (rot < -tmax) rot = -tmax;
+  else if (rot > tmax) rot = tmax;
+  /* setting the speed is a change of (spd - s); the clamp follows in move_one */
+  if (spd < d->SMIN) spd = d->SMIN;
+  else if (spd > d->SMAX) spd = d->SMAX;
+  st[3] = spd;
+  move_one(d, st, 0.0f, rot);
+}
+
+static void observe_tag(const oracle_derived *d, int n, const float *state, const uint8_t *type,
+                        int i, float *obs_row, float *reward_i, int32_t *coll_i, uint32_t *flags) {
+  const int v = d->v;
+  float mind2[2 * OR_MAXV];
+  for (int k = 0; k < 2 * v; ++k) mind2[k] = INFINITY;
+  const float xi = state[4 * i + 0], yi = state[4 * i + 1];
+  const float thi = state[4 * i + 2];
+  const int ti = type[i] != 0;
+  float c, sn;
+  oracle_sincos(thi, &c, &sn);
+  const float ux = c * d->CF + sn * d->SF;
+  const float uy = sn * d->CF - c * d->SF;
+  const float scaleK = ldexpf(1.0f, d->K);
+  int64_t acc = 0;
+  int64_t nin = 0;
+  int32_t ncoll = 0;
+  for (int j = 0; j < n; ++j) {
+    if (j == i) continue;
+    const int tj = type[j] != 0;
+    float dx = state[4 * j + 0] - xi;
+    if (dx > d->HL) dx = dx - d->L;
+    else if (dx < -d->HL) dx = dx + d->L;
+    float dy = state[4 * j + 1] - yi;
+    if (dy > d->HL) dy = dy - d->L;
+    else if (dy < -d->HL) dy = dy + d->L;
+    float d2 = dx * dx + dy * dy;
+    if (!(d2 < d->RV2)) continue;
+    nin++;
+    const int touch = d2 < d->RC2;
+    if (touch) ncoll++;
+    if (ti == 0) {
+      if (touch) acc -= d->PK;               /* any touch costs a runner P */
+      else if (tj == 0) {                    /* proximity to runners */
+        float t = (d->RV - sqrtf(d2)) * d->INV_SPAN;
+        acc += (int64_t)(t * scaleK);
+      }
+    } else if (touch && tj == 0) {
+      acc += d->PK;                          /* a chaser touching a runner */
+    }
+    float lx = dx * ux + dy * uy;
+    float ly = dy * ux - dx * uy;
+    if (lx == 0.0f && ly == 0.0f) continue;
+    float pa = oracle_diamond(lx, ly);
+    if (pa >= 4.0f) pa = 0.0f;
+    if (!d->full && pa >= d->T[v]) continue;
+    int k = 0;
+    for (int m = 1; m < v; ++m)
+      if (pa >= d->T[m]) k++;
+    k += tj * v; /* colour channel of the neighbour's type */
+    if (d2 < mind2[k]) mind2[k] = d2;
+  }
+  for (int k = 0; k < 2 * v; ++k) obs_row[k] = isinf(mind2[k]) ? d->RV : sqrtf(mind2[k]);
+  *reward_i = (float)acc * ldexpf(1.0f, -d->K);
+  *coll_i = ncoll;
+  if (nin > d->NMAX) *flags |= OR_FLAG_OVERFLOW;
+}
+
+/* One tag update.  type: n bytes (0 runner, 1 chaser); actions: n x 2 floats
+ * (speed, rotation) or NULL for a reset; obs: n x 2v floats. */
+int oracle_step_tag(const oracle_params *p, int n, float *state, const uint8_t *type,
+                    const float *actions, float *obs, float *reward, int32_t *coll,
+                    uint32_t *flags_out, int threads) {
+  oracle_derived d;
+  int rc = oracle_derive(p, &d);
+  if (rc != OR_OK) return rc;
+  if (n < 0) return OR_EINVAL;
+  /* a chaser's reward is +P per touched runner: P * 2^K must fit as well */
+  const size_t D = 2 * (size_t)d.v;
+  uint32_t flags = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!state_ok(&d, state + 4 * i)) flags |= OR_FLAG_STATE;
+    if (actions) apply_tag(&d, state + 4 * i, actions + 2 * i, &flags);
+  }
+  uint32_t oflags = 0;
+#ifdef _OPENMP
+  int nt = threads > 0 ? threads : omp_get_max_threads();
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 16) reduction(| : oflags)
+#else
+  (void)threads;
+#endif
+  for (int i = 0; i < n; ++i) {
+    uint32_t f = 0;
+    observe_tag(&d, n, state, type, i, obs + (size_t)i * D, reward + i, coll + i, &f);
+    oflags |= f;
+  }
+  flags |= oflags;
+  if (flags_out) *flags_out = flags;
+  return OR_OK;
+}

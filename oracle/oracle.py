@@ -80,6 +80,9 @@ def _bind(path):
     lib.oracle_observe_rows.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, fp,
                                         ctypes.c_int, ip, fp, fp, ip, ctypes.c_int]
     lib.oracle_apply.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, fp, ip, up]
+    lib.oracle_step_tag.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, fp,
+                                    ctypes.POINTER(ctypes.c_uint8), fp, fp, fp, ip, up,
+                                    ctypes.c_int]
     lib.oracle_gae.argtypes = [ctypes.c_int, ctypes.c_int, fp, fp, ctypes.c_float, ctypes.c_float,
                                fp, fp]
     lib.oracle_step_cont.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, fp, fp, ctypes.c_int,
@@ -215,6 +218,34 @@ def step_cont(params: dict, state: np.ndarray, actions: np.ndarray | None = None
     rc = lib.oracle_step_cont(ctypes.byref(_params(params)), n, _f(st),
                               _f(act) if act is not None else None, int(layout), _f(obs),
                               _f(rew), _i(coll), ctypes.byref(flags), int(threads))
+    if rc != 0:
+        raise ValueError("oracle rejected the call (rc=%d)" % rc)
+    return st, obs, rew, coll, int(flags.value)
+
+
+def step_tag(params: dict, state: np.ndarray, types: np.ndarray, actions: np.ndarray | None = None,
+             threads: int = 0):
+    """One tag update (Section 4.2): types (N,) uint8 (0 runner, 1 chaser),
+    actions (N, 2) float32 (speed, rotation) or None for a reset.  Returns
+    (new_state, obs (N, 2v), reward, coll, flags)."""
+    lib = _load()
+    st = np.ascontiguousarray(state, dtype=np.float32).copy()
+    n = st.shape[0]
+    ty = np.ascontiguousarray(types, dtype=np.uint8)
+    assert ty.shape == (n,)
+    v = int(params["num_segments"])
+    obs = np.zeros((n, 2 * v), np.float32)
+    rew = np.zeros(n, np.float32)
+    coll = np.zeros(n, np.int32)
+    flags = ctypes.c_uint32(0)
+    act = None
+    if actions is not None:
+        act = np.ascontiguousarray(actions, dtype=np.float32)
+        assert act.shape == (n, 2)
+    rc = lib.oracle_step_tag(ctypes.byref(_params(params)), n, _f(st),
+                             ty.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                             _f(act) if act is not None else None, _f(obs), _f(rew), _i(coll),
+                             ctypes.byref(flags), int(threads))
     if rc != 0:
         raise ValueError("oracle rejected the call (rc=%d)" % rc)
     return st, obs, rew, coll, int(flags.value)

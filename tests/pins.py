@@ -336,3 +336,87 @@ def check_gae_fp64(seed=67, T=128, n=300, gamma=0.99, lam=0.95):
     scale = np.abs(r).max() + 2 * np.abs(v).max()
     assert np.abs(adv - ref).max() <= 8 * T * 2.0 ** -24 * scale / (1 - gamma * lam) + 1e-7
     np.testing.assert_array_equal(ret, (adv + v[:-1]).astype(np.float32))
+
+
+# ---------------------------------------------------------------------------
+# Tag (Section 4.2): runners (type 0) and chasers (type 1)
+# ---------------------------------------------------------------------------
+TAG_CASE = {
+    # hand-derived; full circle of view, 8 sectors, d_v 5, d_r 0.5, P 1, every
+    # agent heading along +x, so a neighbour straight ahead is in sector 4 and
+    # one straight behind in sector 0 (the full-circle sectors start behind)
+    "state": [[50.0, 50.0, 0.0, 0.5],    # A runner
+              [50.5, 50.0, 0.0, 0.5],    # B runner: touches A (0.5)
+              [51.25, 50.0, 0.0, 0.5],   # C chaser: touches B (0.75), A at 1.25
+              [51.75, 50.0, 0.0, 0.5],   # D chaser: touches C (0.5), B at 1.25, A at 1.75
+              [46.0, 50.0, 0.0, 0.5]],   # E runner: A at 4, B at 4.5 (ramp 0.25, 0.125)
+    "types": [0, 0, 1, 1, 0],
+    # runner: -1 per touch, ramp from runners only; chaser: +1 per touched runner
+    "reward": [-1.0 + 0.25, -2.0 + 0.125, 1.0, 0.0, 0.25 + 0.125],
+    "coll": [1, 2, 2, 1, 0],
+    # (agent, channel, sector, distance); every other entry is d_v
+    "view": [(0, 0, 4, 0.5), (0, 1, 4, 1.25), (0, 0, 0, 4.0),
+             (1, 0, 0, 0.5), (1, 1, 4, 0.75),
+             (2, 0, 0, 0.75), (2, 1, 4, 0.5),
+             (3, 0, 0, 1.25), (3, 1, 0, 0.5),
+             (4, 0, 4, 4.0)],
+}
+
+
+def check_tag_hand_worked():
+    p = fi.default_params(100.0, fov=fi.FULL_FOV)
+    st = np.array(TAG_CASE["state"], np.float32)
+    ty = np.array(TAG_CASE["types"], np.uint8)
+    _, obs, rew, coll, flags = oracle.step_tag(p, st, ty, None)
+    assert flags == 0
+    np.testing.assert_array_equal(rew, np.array(TAG_CASE["reward"], np.float32))
+    np.testing.assert_array_equal(coll, np.array(TAG_CASE["coll"], np.int32))
+    want = np.full((5, 16), 5.0, np.float32)
+    for i, ch, k, dist in TAG_CASE["view"]:
+        want[i, 8 * ch + k] = dist
+    np.testing.assert_array_equal(obs, want)
+
+
+def check_tag_all_runners_is_flock(seed=81, n=700):
+    """With no chasers the tag update is the flock update: the runner channel
+    holds the flock's distances, the chaser channel is empty, rewards and
+    collisions are the flock's."""
+    side = fi.side_for(n)
+    p = fi.default_params(side, num_segments=16)
+    st = fi.initial_state(n, side, seed)
+    _, o_t, r_t, c_t, _ = oracle.step_tag(p, st, np.zeros(n, np.uint8), None)
+    _, o_f, r_f, c_f, _ = oracle.step_cont(p, st, None, layout=1)
+    np.testing.assert_array_equal(o_t[:, :16], o_f[:, :16])
+    assert np.all(o_t[:, 16:] == np.float32(p["view_radius"]))
+    np.testing.assert_array_equal(r_t, r_f)
+    np.testing.assert_array_equal(c_t, c_f)
+
+
+def check_tag_channels_swap(seed=83, n=600):
+    """Swapping every type swaps the two colour channels of every view."""
+    side = fi.side_for(n)
+    p = fi.default_params(side, num_segments=8)
+    st = fi.initial_state(n, side, seed)
+    ty = fi.tag_types(n, seed)
+    _, o1, _, c1, _ = oracle.step_tag(p, st, ty, None)
+    _, o2, _, c2, _ = oracle.step_tag(p, st, (1 - ty).astype(np.uint8), None)
+    np.testing.assert_array_equal(o1[:, :8], o2[:, 8:])
+    np.testing.assert_array_equal(o1[:, 8:], o2[:, :8])
+    np.testing.assert_array_equal(c1, c2)
+
+
+def check_tag_motion():
+    """The tag action sets the speed (clamped) and turns the heading:
+    float64 closed form of one move."""
+    p = fi.default_params(100.0)
+    for st0, act in (((50.0, 50.0, 1.0, 0.5), (0.8, 0.2)), ((20.0, 30.0, 3.0, 0.9), (1.7, -0.5))):
+        st = np.array([st0], np.float32)
+        s2, _, _, _, f = oracle.step_tag(p, st, np.zeros(1, np.uint8),
+                                         np.array([act], np.float32))
+        assert f == 0
+        s = min(max(act[0], 0.0), 1.0)
+        rot = max(-float(np.float32(p["turn_step"])), min(float(np.float32(p["turn_step"])), act[1]))
+        th = float(np.float32(np.float32(st0[2]) + np.float32(rot)))
+        assert float(s2[0, 3]) == float(np.float32(s)) and float(s2[0, 2]) == th
+        assert abs(float(s2[0, 0]) - (st0[0] + s * math.cos(th))) < 3e-5
+        assert abs(float(s2[0, 1]) - (st0[1] + s * math.sin(th))) < 3e-5

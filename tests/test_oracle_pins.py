@@ -153,3 +153,19 @@ def test_gae_special_cases():
 
 def test_gae_against_float64():
     pins.check_gae_fp64()
+
+
+def test_tag_hand_worked():
+    pins.check_tag_hand_worked()
+
+
+def test_tag_without_chasers_is_the_flock():
+    pins.check_tag_all_runners_is_flock()
+
+
+def test_tag_type_swap_swaps_channels():
+    pins.check_tag_channels_swap()
+
+
+def test_tag_motion_closed_form():
+    pins.check_tag_motion()
