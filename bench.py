@@ -440,6 +440,47 @@ def run_paper_variant(F, torch, dev, stream, steps, warmup, flush, n=16000, seed
                          "traffic": None, "bytes_per_agent": bpa}}
 
 
+def run_tag(F, torch, dev, stream, steps, warmup, flush, n=17600, seed=0, world=1):
+    """The tag environment at the paper's size (Section 4.2, Section 5: 16,000
+    runners and 1,600 chasers): two colour channels of 64 sectors, view a
+    tenth of the side, (speed, rotation) actions."""
+    p = fi.tag_params(n)
+    env = F.FlockEnv(p, n, device=dev, stream=stream)
+    acts = torch.from_numpy(fi.tag_actions(n, steps + warmup, seed, p["speed_max"],
+                                           p["turn_step"])).to(dev)
+    act_buf = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        env.set_types(torch.from_numpy(fi.tag_types(n, seed)).to(dev))
+        env.reset(torch.from_numpy(fi.initial_state(n, p["side"], seed)).to(dev))
+        for k in range(warmup):
+            act_buf.copy_(acts[k])
+            flush.zero_()
+            env.step_continuous(act_buf)
+    torch.cuda.synchronize()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            act_buf.copy_(acts[warmup + k])
+            flush.zero_()
+            ev0[k].record(stream)
+            env.step_continuous(act_buf)
+            ev1[k].record(stream)
+    torch.cuda.synchronize()
+    assert env.error() == 0
+    tun = env.tuning()
+    env.close()
+    ms = [ev0[k].elapsed_time(ev1[k]) for k in range(steps)]
+    tot = max_over_ranks(sum(ms), dev)
+    return {"value": weak_scaling_value(world, n, steps, tot), "unit": UNIT, "agents": n,
+            "chasers": int(round(0.1 * n)), "ms_per_step": tot / steps,
+            "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+            "tuning": tun,
+            "workload": "tag: %d agents (a tenth chasers), side %.0f, view %.0f, 2 x 64 sectors, "
+                        "fov 250 deg, (speed, rotation) actions" % (n, p["side"],
+                                                                    p["view_radius"])}
+
+
 def run_rollout(F, torch, dev, stream, reps, flush, n=16000, T=128, seed=0, world=1):
     """One training step's experience collection of the paper (Section 5:
     t = 128 environment updates of all agents), as a single graph launch of
@@ -679,11 +720,13 @@ def main():
     if not args.no_policy:
         policy = run_policy(F, torch, dev, stream, args.steps, args.warmup, flush,
                             seed=rank_seed(rank), world=world)
-    paper = rollout = None
+    paper = rollout = tag = None
     if not args.no_paper:
         paper = run_paper_variant(F, torch, dev, stream, min(args.steps, 50), args.warmup, flush,
                                   seed=rank_seed(rank), world=world)
         rollout = run_rollout(F, torch, dev, stream, 3, flush, seed=rank_seed(rank), world=world)
+        tag = run_tag(F, torch, dev, stream, min(args.steps, 50), args.warmup, flush,
+                      seed=rank_seed(rank), world=world)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -719,6 +762,7 @@ def main():
         if paper is not None:
             line["paper_variant"] = paper
             line["rollout"] = rollout
+            line["tag"] = tag
         if serving is not None:
             line["serving"] = serving
 

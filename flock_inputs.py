@@ -47,6 +47,7 @@ def default_params(side: float, **overrides) -> dict:
         "turn_step": float(np.float32(math.pi / 8.0)),
         "num_segments": 8,
         "obs_layout": 0,
+        "kind": 0,
     }
     for k, v in overrides.items():
         if k not in p:
@@ -91,6 +92,18 @@ def paper_params(n_agents: int, **overrides) -> dict:
     side = side_for(n_agents)
     p = default_params(side, view_radius=float(np.float32(side / 10.0)), num_segments=128,
                        obs_layout=1)
+    p.update(overrides)
+    return p
+
+
+def tag_params(n_agents: int, **overrides) -> dict:
+    """The tag environment as the paper runs it (Section 4.2, Section 5): two
+    colour channels of 64 sectors (a 128-value view), view a tenth of the
+    side, field of view 250 degrees, density 0.1; speeds in [0, 1], turns up
+    to pi/8 per step."""
+    side = side_for(n_agents)
+    p = default_params(side, view_radius=float(np.float32(side / 10.0)), num_segments=64,
+                       kind=1)
     p.update(overrides)
     return p
 

@@ -45,6 +45,8 @@
  *                             numbered counter-clockwise from its right edge.
  *   obs, layout 1  n x (v+1) float : the distances of the v sectors, then s
  *                             (the paper's observation: 129 values for v = 128)
+ *   obs, tag       n x 2v float : the v sector distances of the nearest runner,
+ *                             then of the nearest chaser (128 values for v = 64)
  *   reward      n float, coll n int32 (collisions: pairs closer than
  *                             2 * agent_radius)
  * Row i of every output belongs to agent i of the state (never reordered).
@@ -89,6 +91,7 @@ typedef struct flock_params {
   int num_segments;        /* v: sectors of the field of view, 1..128 */
   int obs_layout;          /* 0: (distance, count) per sector, speed, heading (2v + 2
                               values); 1: distance per sector, speed (v + 1 values) */
+  int kind;                /* 0: flock; 1: tag (Section 4.2), see env_set_types */
 } flock_params;
 
 /* Launch shape of the neighbour scan.  Every field may be 0 (library
@@ -160,7 +163,8 @@ int env_step(flock_env *env, const int32_t *actions_dev, float *obs_dev, float *
              int32_t *coll_dev);
 
 /* env_step with the paper's continuous actions (Section 4.1): actions2_dev
- * holds n x 2 floats (acceleration, rotation), 8-byte aligned.  Each is
+ * holds n x 2 floats (acceleration, rotation; for tag (speed, rotation)),
+ * 8-byte aligned.  Each is
  * clamped to [-speed_step, speed_step] and [-turn_step, turn_step]; a
  * component that is not finite acts as 0 and latches FLOCK_ERR_ACTION.  The
  * speed clamp, heading wrap, move and observation are those of env_step.
@@ -211,6 +215,20 @@ int env_step_policy(flock_env *env, const uint16_t *weights_bf16_dev, int32_t *a
  * the host buffers. */
 int env_step_host(flock_env *env, const int32_t *actions_host, float *obs_host,
                   float *reward_host, int32_t *coll_host);
+
+/* Tag (params.kind == 1, Section 4.2): agents of type 0 are runners, of
+ * type 1 (any non-zero byte) chasers.  types_dev: n bytes, copied into the
+ * workspace (all runners after env_create).  A runner's reward is the flock
+ * reward (Eq. 1) over runners, with -collision_penalty for every agent it
+ * touches (closer than 2 agent_radius, either type); a chaser's reward is
+ * +collision_penalty per runner it touches.  The view has two colour
+ * channels (runners, chasers) of num_segments sectors.  With
+ * env_step_continuous the action is (speed, rotation): the speed is set,
+ * clamped to [speed_min, speed_max].  Tag uses the direct neighbour scan
+ * (tuning mode 2) of a single environment; the batch, the fused policy and
+ * flock_step_static take flock instances only.  FLOCK_EINVAL for a flock
+ * environment. */
+int env_set_types(flock_env *env, const uint8_t *types_dev);
 
 /* Copies the current state (n x 4) out of / into the workspace. */
 int env_get_state(flock_env *env, float *state_dev);

@@ -21,6 +21,7 @@ __all__ = [
     "FLOCK_ERR_OVERFLOW", "flock_default_params", "flock_obs_dim", "flock_workspace_bytes",
     "flock_derive",
     "env_create", "env_reset", "env_step", "env_step_continuous", "env_rollout", "flock_gae",
+    "env_set_types",
     "env_step_host", "env_get_state", "env_set_state",
     "env_get_error", "env_get_derived", "env_get_tuning", "env_set_timing",
     "env_get_phase_times", "env_destroy", "FlockEnv", "lib_path", "flock_instance_cells",
@@ -163,6 +164,12 @@ def flock_gae(reward, value, gamma: float, lam: float, adv, ret, stream=None):
         _ptr(ret, torch.float32, (T, n), "ret"), _stream(stream)))
 
 
+def env_set_types(env, types):
+    """Tag: agent types, (n,) uint8 CUDA tensor (0 runner, 1 chaser)."""
+    torch = _torch()
+    _abi.check(_abi.lib.env_set_types(env.handle, _ptr(types, torch.uint8, (env.n,), "types")))
+
+
 def env_step_continuous(env, actions2, obs, reward, coll):
     """Step with continuous actions: actions2 is (n, 2) float32 (acceleration,
     rotation), clamped to [-speed_step, speed_step] x [-turn_step, turn_step]."""
@@ -281,6 +288,9 @@ class FlockEnv:
     def step(self, actions):
         env_step(self.env, actions, self.obs, self.reward, self.coll)
         return self.obs, self.reward, self.coll
+
+    def set_types(self, types):
+        env_set_types(self.env, types)
 
     def step_continuous(self, actions2):
         env_step_continuous(self.env, actions2, self.obs, self.reward, self.coll)

@@ -37,7 +37,7 @@ class FlockParams(ctypes.Structure):
                 ("collision_penalty", ctypes.c_float), ("speed_min", ctypes.c_float),
                 ("speed_max", ctypes.c_float), ("speed_step", ctypes.c_float),
                 ("turn_step", ctypes.c_float), ("num_segments", ctypes.c_int),
-                ("obs_layout", ctypes.c_int)]
+                ("obs_layout", ctypes.c_int), ("kind", ctypes.c_int)]
 
 
 class FlockTuning(ctypes.Structure):
@@ -63,7 +63,7 @@ PARAM_KEYS = [k for k, _ in FlockParams._fields_]
 def params_from_dict(p: dict) -> FlockParams:
     floats = [k for k, t in FlockParams._fields_ if t is ctypes.c_float]
     return FlockParams(*(float(p[k]) for k in floats), int(p["num_segments"]),
-                       int(p.get("obs_layout", 0)))
+                       int(p.get("obs_layout", 0)), int(p.get("kind", 0)))
 
 
 def params_to_dict(p: FlockParams) -> dict:
@@ -111,6 +111,7 @@ def _load():
         "env_step_policy": [vp, vp, vp, vp, vp, vp, vp],
         "env_get_state": [vp, vp],
         "env_set_state": [vp, vp],
+        "env_set_types": [vp, vp],
         "env_get_error": [vp, ctypes.POINTER(ctypes.c_uint32)],
         "env_get_derived": [vp, ctypes.POINTER(FlockDerived)],
         "env_get_tuning": [vp, T],

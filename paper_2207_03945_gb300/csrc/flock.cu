@@ -70,7 +70,8 @@ __global__ void k_neighbours(const Inst *__restrict__ gI, Bufs B) {
 }
 
 // LPA lanes per agent: each warp takes 32 / LPA consecutive sorted agents.
-template <int H, int V, int LPA>
+// TAG: the tag environment (two colour channels of sectors).
+template <int H, int V, int LPA, bool TAG = false>
 __global__ void k_neighbours_direct(const Inst *__restrict__ gI, Bufs B) {
   extern __shared__ __align__(16) char smem[];
   __shared__ Inst sI;
@@ -82,9 +83,9 @@ __global__ void k_neighbours_direct(const Inst *__restrict__ gI, Bufs B) {
   constexpr int A = 32 / LPA;
   const int gp0 = (blockIdx.x * (blockDim.x >> 5) + warp) * A;
   if (gp0 < sI.n) {
-    const DirectArea W =
-        direct_area(smem + (size_t)warp * direct_warp_bytes(sI.v, A), sI.v, A);
-    phaseD_direct<H, V, false, true, LPA>(sI, gp0, min(gp0 + A, sI.n), B, W, err);
+    const int vs = TAG ? 2 * sI.v : sI.v;
+    const DirectArea W = direct_area(smem + (size_t)warp * direct_warp_bytes(vs, A), vs, A);
+    phaseD_direct<H, V, false, true, LPA, TAG>(sI, gp0, min(gp0 + A, sI.n), B, W, err);
   }
   if (err) atomicOr(B.err, err);
 }
@@ -236,8 +237,11 @@ int derive(const flock_params &p, int stencil, Inst &I, flock_derived *D) {
   I.halo = stencil;
   I.invw = (float)((double)I.nc / (double)p.side);
   if (p.obs_layout != 0 && p.obs_layout != 1) return FLOCK_EINVAL;
+  if (p.kind != 0 && p.kind != 1) return FLOCK_EINVAL;
   I.obs_layout = p.obs_layout;
-  I.obs_dim = p.obs_layout == 1 ? I.v + 1 : 2 * I.v + 2;
+  I.kind = p.kind;
+  // tag: the two colour channels of distances; flock: the chosen layout
+  I.obs_dim = p.kind == 1 ? 2 * I.v : (p.obs_layout == 1 ? I.v + 1 : 2 * I.v + 2);
 
   if (D) {
     memset(D, 0, sizeof *D);
@@ -266,6 +270,7 @@ int choose_tuning(const Inst &I, int n, const flock_tuning *req, flock_tuning &t
   t.lanes = r.lanes ? r.lanes : (n <= 32768 ? 4 : (n <= 524288 ? 2 : 1));
   if (t.lanes != 1 && t.lanes != 2 && t.lanes != 4) return FLOCK_EINVAL;
   if (t.mode == 1) t.lanes = 1;
+  if (I.kind == 1 && t.mode != 2) return FLOCK_EINVAL;  // tag: direct form only
   const double w = (double)I.L / I.nc;
   const double per_cell = n > 0 ? (double)n / ((double)I.L * I.L) * w * w : 1.0;
   t.tile_h = r.tile_h ? r.tile_h : 2;
@@ -320,7 +325,13 @@ cudaError_t set_kernel_attrs() {
                          (const void *)k_neighbours_direct<1, 0, 4>,
                          (const void *)k_neighbours_direct<2, 0, 4>,
                          (const void *)k_neighbours_direct<1, 8, 4>,
-                         (const void *)k_neighbours_direct<2, 8, 4>};
+                         (const void *)k_neighbours_direct<2, 8, 4>,
+                         (const void *)k_neighbours_direct<1, 0, 1, true>,
+                         (const void *)k_neighbours_direct<2, 0, 1, true>,
+                         (const void *)k_neighbours_direct<1, 0, 2, true>,
+                         (const void *)k_neighbours_direct<2, 0, 2, true>,
+                         (const void *)k_neighbours_direct<1, 0, 4, true>,
+                         (const void *)k_neighbours_direct<2, 0, 4, true>};
     g_attr_err = cudaSuccess;
     for (const void *f : fns) {
       cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
@@ -335,7 +346,8 @@ cudaError_t set_kernel_attrs() {
 using namespace flock;
 
 struct Layout {
-  size_t state, cellrank, counts, local, cell_start, tile_sum, sxy, sts, sidx, inst, err, h_act, h_obs,
+  size_t state, cellrank, counts, local, cell_start, tile_sum, sxy, sts, sidx, types, stype, inst,
+      err, h_act, h_obs,
       h_rew, h_coll, total;
 };
 
@@ -353,6 +365,8 @@ static Layout make_layout(int n, int C, int D) {
   L.sxy = take((size_t)n * 8);
   L.sts = take((size_t)n * 8);
   L.sidx = take((size_t)n * 4);
+  L.types = take((size_t)n);   // tag: agent types
+  L.stype = take((size_t)n);   // tag: cell-sorted types
   L.inst = take(sizeof(Inst));
   L.err = take(64);
   L.h_act = take((size_t)n * 4);
@@ -405,12 +419,15 @@ extern "C" int flock_default_params(float side, flock_params *out) {
   out->turn_step = (float)(kPi / 8.0);
   out->num_segments = 8;
   out->obs_layout = 0;
+  out->kind = 0;
   return FLOCK_OK;
 }
 
 extern "C" int flock_obs_dim(const flock_params *p) {
   if (!p || p->num_segments < 1 || p->num_segments > FLOCK_MAX_SEGMENTS) return FLOCK_EINVAL;
   if (p->obs_layout != 0 && p->obs_layout != 1) return FLOCK_EINVAL;
+  if (p->kind != 0 && p->kind != 1) return FLOCK_EINVAL;
+  if (p->kind == 1) return 2 * p->num_segments;
   return p->obs_layout == 1 ? p->num_segments + 1 : 2 * p->num_segments + 2;
 }
 
@@ -476,6 +493,10 @@ extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, v
   B.sxy = (float2 *)(e->ws + L.sxy);
   B.sts = (float2 *)(e->ws + L.sts);
   B.sidx = (int *)(e->ws + L.sidx);
+  if (e->inst.kind == 1) {
+    B.types = (const uint8_t *)(e->ws + L.types);
+    B.stype = (uint8_t *)(e->ws + L.stype);
+  }
   B.err = (unsigned *)(e->ws + L.err);
   B.bar = B.err + 4;
   B.n_total = n;
@@ -489,7 +510,9 @@ extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, v
   e->scatter_grid = g < 1 ? 1 : (g > 4 * sms ? 4 * sms : g);
   e->smemD = e->tuning.mode == 1
                  ? phaseD_smem_bytes(e->inst.cap, e->inst.v, e->tuning.block)
-                 : (size_t)(e->tuning.block / 32) * direct_warp_bytes(e->inst.v, 32 / e->tuning.lanes);
+                 : (size_t)(e->tuning.block / 32) *
+                       direct_warp_bytes(e->inst.kind == 1 ? 2 * e->inst.v : e->inst.v,
+                                         32 / e->tuning.lanes);
   int smem_max = 0;
   cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e->smemD + sizeof(Inst) + 1024 > (size_t)smem_max) {
@@ -502,6 +525,7 @@ extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, v
   cudaError_t c1 = cudaMemcpyAsync(e->ws + L.inst, &e->inst, sizeof(Inst), cudaMemcpyHostToDevice, s);
   cudaError_t c2 = cudaMemsetAsync(e->ws + L.counts, 0, (size_t)e->inst.ncells * 4, s);
   cudaError_t c3 = cudaMemsetAsync(e->ws + L.err, 0, 64, s);
+  if (c3 == cudaSuccess && n > 0) c3 = cudaMemsetAsync(e->ws + L.types, 0, (size_t)n, s);  // all runners
   if (c1 != cudaSuccess || c2 != cudaSuccess || c3 != cudaSuccess) {
     cudaStreamDestroy(e->cap_stream);
     delete e;
@@ -572,7 +596,14 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const 
            {k_neighbours_direct<1, 8, 1>, k_neighbours_direct<1, 8, 2>, k_neighbours_direct<1, 8, 4>}},
           {{k_neighbours_direct<2, 0, 1>, k_neighbours_direct<2, 0, 2>, k_neighbours_direct<2, 0, 4>},
            {k_neighbours_direct<2, 8, 1>, k_neighbours_direct<2, 8, 2>, k_neighbours_direct<2, 8, 4>}}};
-      const KD k = kd[e->inst.halo - 1][e->inst.v == 8 ? 1 : 0][lpa == 1 ? 0 : (lpa == 2 ? 1 : 2)];
+      static const KD kt[2][3] = {
+          {k_neighbours_direct<1, 0, 1, true>, k_neighbours_direct<1, 0, 2, true>,
+           k_neighbours_direct<1, 0, 4, true>},
+          {k_neighbours_direct<2, 0, 1, true>, k_neighbours_direct<2, 0, 2, true>,
+           k_neighbours_direct<2, 0, 4, true>}};
+      const int li = lpa == 1 ? 0 : (lpa == 2 ? 1 : 2);
+      const KD k = e->inst.kind == 1 ? kt[e->inst.halo - 1][li]
+                                     : kd[e->inst.halo - 1][e->inst.v == 8 ? 1 : 0][li];
       CK(launch(pdl, k, blocks, blk, sm, s, gI, B));
     }
   }
@@ -741,7 +772,7 @@ extern "C" int env_rollout(flock_env *e, int T, const int32_t *act, const float 
 
 extern "C" int env_step_policy(flock_env *e, const uint16_t *weights, int32_t *act, float *rew,
                                int32_t *coll, float *logits, float *obs) {
-  if (!e || e->inst.v != 8 || e->inst.obs_layout != 0) return FLOCK_EINVAL;
+  if (!e || e->inst.v != 8 || e->inst.obs_layout != 0 || e->inst.kind != 0) return FLOCK_EINVAL;
   if (e->n > 0 && (!weights || !act || !rew || !coll || !aligned(weights, 4) ||
                    (obs && !aligned(obs, 8))))
     return FLOCK_EINVAL;
@@ -805,6 +836,14 @@ extern "C" int env_get_state(flock_env *e, float *state) {
   if (!e || (e->n > 0 && !state)) return FLOCK_EINVAL;
   if (e->n > 0)
     CK(cudaMemcpyAsync(state, e->ws + e->lay.state, (size_t)e->n * 16, cudaMemcpyDeviceToDevice,
+                       e->stream));
+  return FLOCK_OK;
+}
+
+extern "C" int env_set_types(flock_env *e, const uint8_t *types) {
+  if (!e || e->inst.kind != 1 || (e->n > 0 && !types)) return FLOCK_EINVAL;
+  if (e->n > 0)
+    CK(cudaMemcpyAsync(e->ws + e->lay.types, types, (size_t)e->n, cudaMemcpyDeviceToDevice,
                        e->stream));
   return FLOCK_OK;
 }
@@ -946,6 +985,7 @@ extern "C" int flock_step_static(const flock_params *p, int n, float *state_dev,
   int rc = derive(*p, 1, I, nullptr);
   if (rc) return rc;
   if (I.ncells > kStaticMaxCells) return FLOCK_EINVAL;  // cell list larger than the scratch
+  if (I.kind != 0) return FLOCK_EINVAL;                  // flock only
   if (n > 0 && (!state_dev || !obs_dev || !reward_dev || !coll_dev || ((uintptr_t)obs_dev & 7)))
     return FLOCK_EINVAL;
   char *sp = nullptr;

@@ -339,6 +339,7 @@ extern "C" int env_batch_set(flock_batch *b, int n_inst, const flock_params *par
     // one sector count and one observation layout per batch (rows are
     // flattened with a single row length)
     if (I.v != v || I.obs_layout != layout) return FLOCK_EINVAL;
+    if (I.kind != 0) return FLOCK_EINVAL;  // the batch steps flock instances
     I.n = n_agents[k];
     I.state = reinterpret_cast<float4 *>(state[k]);
     I.agent_base = (int)na;

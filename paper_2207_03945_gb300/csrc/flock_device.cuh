@@ -44,6 +44,8 @@ struct alignas(16) Inst {
   int obs_dim, cap;  // cap: staged agents that fit in shared memory
   int pieces;        // 32-bit pieces a reward term needs in shared accumulators (2 or 3)
   int obs_layout;    // 0: (distance, count) per sector, speed, heading; 1: distances, speed
+  int kind;          // 0: flock; 1: tag (runners and chasers, Section 4.2)
+  int pad2, pad3, pad4;
   float L, HL, invw, RV, RV2, RC2, INV_SPAN, SMIN, SMAX, TWO_PI, CF, SF, scaleK, inv_scaleK;
   float DT[3], DS[3];
   long long PK, NMAX;
@@ -66,6 +68,8 @@ struct Bufs {
   unsigned *bar;       // grid barrier words (count, generation)
   const int32_t *actions;
   const float2 *cactions;  // continuous actions (acceleration, rotation), or null
+  const uint8_t *types;    // tag: agent types (0 runner, 1 chaser), agent order; else null
+  uint8_t *stype;          // tag: cell-sorted types; else null
   float *obs;
   float *reward;
   int32_t *coll;
@@ -189,6 +193,26 @@ __device__ __forceinline__ float4 apply_cont(float4 st, float2 a, const Inst &I,
   return move_agent(st, acc, rot, I);
 }
 
+// Tag action (speed, rotation), Section 4.2: sets the speed, clamped to
+// [s_min, s_max], and turns the heading by the rotation clamped to
+// [-Delta, Delta]; a non-finite component counts as 0 and is flagged.
+__device__ __forceinline__ float4 apply_tag(float4 st, float2 a, const Inst &I, unsigned &err) {
+  float spd = a.x, rot = a.y;
+  if (!isfinite(spd)) {
+    spd = 0.0f;
+    err |= FLOCK_ERR_ACTION;
+  }
+  if (!isfinite(rot)) {
+    rot = 0.0f;
+    err |= FLOCK_ERR_ACTION;
+  }
+  const float tmax = I.DT[2];
+  rot = rot < -tmax ? -tmax : (rot > tmax ? tmax : rot);
+  spd = spd < I.SMIN ? I.SMIN : (spd > I.SMAX ? I.SMAX : spd);
+  st.w = spd;
+  return move_agent(st, 0.0f, rot, I);
+}
+
 // Element e of an observation row: for e < v the sector's (distance, count),
 // for e == v (speed, heading); layout 1 keeps the distance (or the speed).
 __device__ __forceinline__ void put_obs(const Inst &I, float *row, int e, float2 val) {
@@ -239,8 +263,9 @@ __device__ __forceinline__ void phaseA_agent(const Inst &I, int i, const int32_t
   float4 st = I.state[i];
   if (!state_ok(st, I)) err |= FLOCK_ERR_STATE;
   if (!reset) {
-    st = cactions_inst ? apply_cont(st, cactions_inst[i], I, err)
-                       : apply_action(st, actions_inst[i], I, err);
+    if (!cactions_inst) st = apply_action(st, actions_inst[i], I, err);
+    else if (I.kind == 1) st = apply_tag(st, cactions_inst[i], I, err);
+    else st = apply_cont(st, cactions_inst[i], I, err);
     I.state[i] = st;
   }
   const int g = I.cell_base + cell_of(st.y, I) * I.nc + cell_of(st.x, I);
@@ -342,6 +367,7 @@ __device__ __forceinline__ void phaseC_agent(int f, const float4 *state_i, const
   B.sxy[pos] = make_float2(st.x, st.y);
   B.sts[pos] = make_float2(st.z, st.w);
   B.sidx[pos] = f;
+  if (B.stype) B.stype[pos] = B.types[f];
 }
 
 __device__ __forceinline__ void phaseC_cell(int c, const Bufs &B, const int *tp) {
@@ -855,22 +881,41 @@ struct Edges {
 // them into the 64-bit sums once per drain (64-bit shared atomics are slow);
 // without it, one 64-bit atomic per term (fewer registers, which the batched
 // kernel needs to keep four blocks per SM).  Both sums are exact integers.
-template <int V, bool PIECES>
+//
+// TAG (Section 4.2): the queue entry's owner word also carries the
+// neighbour's type (bit 8); ti is each lane's own agent type.  A runner's
+// ramp terms come from runners only (its touches cost -P through the
+// collision count, whatever the type); a chaser adds +P per touched runner.
+// The sector accumulators hold two channels of v, the neighbour's type
+// choosing the channel.
+template <int V, bool PIECES, bool TAG = false>
 __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W, int count,
-                                            float ux, float uy, const Edges<V> &E8) {
+                                            float ux, float uy, const Edges<V> &E8, int ti = 0) {
   const int lane = threadIdx.x & 31;
   const int v = V == 8 ? 8 : I.v;
+  const int vs = TAG ? 2 * v : v;  // accumulator row length
   for (int e0 = 0; e0 < count; e0 += 32) {
     const int e = e0 + lane;
     const bool valid = e < count;
     float4 E = valid ? W.queue[e] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int o = valid ? __float_as_int(E.w) : lane;
+    const int w = valid ? __float_as_int(E.w) : lane;
+    const int o = TAG ? (w & 0xff) : w;
+    const int tj = TAG ? (w >> 8) : 0;
     const float uxo = __shfl_sync(kFull, ux, o), uyo = __shfl_sync(kFull, uy, o);
+    const int tio = TAG ? __shfl_sync(kFull, ti, o) : 0;
     if (valid) {
       const float dx = E.x, dy = E.y, d2 = E.z;
-      if (!(d2 < I.RC2)) {
-        const float t = fmul(fsub(I.RV, fsqrt(d2)), I.INV_SPAN);
-        const unsigned long long tv = float_int_u64(fmul(t, I.scaleK));
+      const bool coll = d2 < I.RC2;
+      unsigned long long tv = 0ull;
+      if (!TAG || (tio == 0 && tj == 0)) {
+        if (!coll) {
+          const float t = fmul(fsub(I.RV, fsqrt(d2)), I.INV_SPAN);
+          tv = float_int_u64(fmul(t, I.scaleK));
+        }
+      } else if (tio == 1 && tj == 0 && coll) {
+        tv = (unsigned long long)I.PK;  // a chaser touching a runner
+      }
+      {
         // a drain holds at most kQueue pairs, so each 32-bit piece sum
         // stays below 2^24 * kQueue and exact
         if (PIECES && tv) {
@@ -886,10 +931,11 @@ __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W,
       if (lx != 0.0f || ly != 0.0f) {
         float p = pseudo_angle(lx, ly);
         if (p >= 4.0f) p = 0.0f;
-        const int key = E8.sector(I, p);
+        int key = E8.sector(I, p);
         if (key >= 0) {
-          atomicMin(&W.md[o * v + key], __float_as_uint(d2));
-          atomicAdd(&W.cn[o * v + key], 1);
+          if (TAG) key += tj * v;  // colour channel of the neighbour's type
+          atomicMin(&W.md[o * vs + key], __float_as_uint(d2));
+          atomicAdd(&W.cn[o * vs + key], 1);
         }
       }
     }
@@ -910,11 +956,12 @@ __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W,
 // pairs to the queue (warp-uniform loop), draining when nearly full.
 // With LPA lanes per agent, lane l serves agent slot l % (32 / LPA) and
 // takes every LPA-th candidate of the run, starting at l / (32 / LPA).
-template <bool SHIFT, int V, bool PIECES, int LPA>
+template <bool SHIFT, int V, bool PIECES, int LPA, bool TAG = false>
 __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, const float2 *sxy,
                                            int a, int n, int self, float sx, float sy, float xi,
                                            float yi, float ux, float uy, int &qn, int &nin,
-                                           int &ncoll, const Edges<V> &E8) {
+                                           int &ncoll, const Edges<V> &E8,
+                                           const uint8_t *stype = nullptr, int ti = 0) {
   constexpr int A = 32 / LPA;
   const int lane = threadIdx.x & 31;
   const int slot = lane & (A - 1), sub = lane / A;
@@ -941,11 +988,14 @@ __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, c
       }
     }
     const unsigned m = __ballot_sync(kFull, inr);
-    if (inr) W.queue[qn + __popc(m & lt)] = make_float4(dx, dy, d2, __int_as_float(slot));
+    if (inr) {
+      const int w = TAG ? (slot | ((int)(stype[q] != 0) << 8)) : slot;
+      W.queue[qn + __popc(m & lt)] = make_float4(dx, dy, d2, __int_as_float(w));
+    }
     qn += __popc(m);
     if (qn > kQueue - 32) {
       __syncwarp();
-      drain_direct<V, PIECES>(I, W, qn, ux, uy, E8);
+      drain_direct<V, PIECES, TAG>(I, W, qn, ux, uy, E8, ti);
       qn = 0;
     }
   }
@@ -1147,16 +1197,21 @@ __device__ __forceinline__ void policy_mtile(const PolicyCtx &P, int row0, int &
 
 // A warp takes the 32 / LPA consecutive sorted agents [gp0, gp1); LPA lanes
 // share each agent's candidates (LPA = 1, 2 or 4; the policy form uses 1).
-template <int H, int V, bool POL = false, bool PIECES = true, int LPA = 1>
+// TAG: the tag environment (needs V == 0 and no policy): two colour
+// channels of sectors, type-dependent rewards (see drain_direct), and the
+// observation row is the 2v channel distances.
+template <int H, int V, bool POL = false, bool PIECES = true, int LPA = 1, bool TAG = false>
 __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
                               const DirectArea &W, unsigned &err,
                               const PolicyCtx *pc = nullptr) {
   static_assert(LPA == 1 || LPA == 2 || LPA == 4, "lanes per agent");
   static_assert(!POL || LPA == 1, "the policy tile holds 32 agents");
+  static_assert(!TAG || (V == 0 && !POL), "tag uses the generic sector count");
   constexpr int A = 32 / LPA;
   const int lane = threadIdx.x & 31;
   const int slot = lane & (A - 1);
   const int nc = I.nc, v = V == 8 ? 8 : I.v;
+  const int vs = TAG ? 2 * v : v;  // accumulator row length
   Edges<V> E8;
   E8.load(I);
   const int gp = gp0 + slot;
@@ -1174,6 +1229,7 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
     cx = cell_of(xi, I);
     cy = cell_of(yi, I);
   }
+  const int ti = TAG && have ? (int)(B.stype[gp] != 0) : 0;  // own type
   float c = 1.f, sn = 0.f;
   det_sincos(ts.x, c, sn);
   const float ux = fadd(fmul(c, I.CF), fmul(sn, I.SF));
@@ -1196,7 +1252,7 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
       c4[1] = make_int4(0, 0, 0, 0);
     }
   } else {
-    for (int t = lane; t < A * v; t += 32) {
+    for (int t = lane; t < A * vs; t += 32) {
       W.md[t] = 0x7f800000u;
       W.cn[t] = 0;
     }
@@ -1221,24 +1277,24 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
   if (!wrap_any) {
 #pragma unroll
     for (int r = 0; r < 2 * H + 1; ++r)
-      direct_run<false, V, PIECES, LPA>(I, W, B.sxy, ra[r], rn[r], self, 0.f, 0.f, xi, yi, ux, uy, qn, nin,
-                           ncoll, E8);
+      direct_run<false, V, PIECES, LPA, TAG>(I, W, B.sxy, ra[r], rn[r], self, 0.f, 0.f, xi, yi,
+                                             ux, uy, qn, nin, ncoll, E8, B.stype, ti);
   } else {
 #pragma unroll
     for (int r = 0; r < 2 * H + 1; ++r) {
       const int vr = cy - H + r;
       const float sy = vr < 0 ? -I.L : (vr >= nc ? I.L : 0.0f);
       const int rowg = I.cell_base + wrapi(vr, nc) * nc;
-      direct_run<true, V, PIECES, LPA>(I, W, B.sxy, ra[r], rn[r], self, 0.f, sy, xi, yi, ux, uy, qn, nin,
-                          ncoll, E8);
+      direct_run<true, V, PIECES, LPA, TAG>(I, W, B.sxy, ra[r], rn[r], self, 0.f, sy, xi, yi,
+                                            ux, uy, qn, nin, ncoll, E8, B.stype, ti);
       // cells across the left boundary: virtual columns [vlo, 0) -> [vlo + nc, nc)
       int a = 0, n = 0;
       if (have && lw) {
         a = cst[rowg + vlo + nc];
         n = cst[rowg + nc] - a;
       }
-      direct_run<true, V, PIECES, LPA>(I, W, B.sxy, a, n, self, -I.L, sy, xi, yi, ux, uy, qn, nin, ncoll,
-                          E8);
+      direct_run<true, V, PIECES, LPA, TAG>(I, W, B.sxy, a, n, self, -I.L, sy, xi, yi, ux, uy,
+                                            qn, nin, ncoll, E8, B.stype, ti);
       // cells across the right boundary: virtual columns [nc, vhi) -> [0, vhi - nc)
       a = 0;
       n = 0;
@@ -1246,11 +1302,12 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
         a = cst[rowg];
         n = cst[rowg + vhi - nc] - a;
       }
-      direct_run<true, V, PIECES, LPA>(I, W, B.sxy, a, n, self, I.L, sy, xi, yi, ux, uy, qn, nin, ncoll, E8);
+      direct_run<true, V, PIECES, LPA, TAG>(I, W, B.sxy, a, n, self, I.L, sy, xi, yi, ux, uy,
+                                            qn, nin, ncoll, E8, B.stype, ti);
     }
   }
   __syncwarp();
-  drain_direct<V, PIECES>(I, W, qn, ux, uy, E8);
+  drain_direct<V, PIECES, TAG>(I, W, qn, ux, uy, E8, ti);
   // the lanes of an agent add up their counts
 #pragma unroll
   for (int m = A; m < 32; m <<= 1) {
@@ -1259,14 +1316,16 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
   }
   // reward and collisions
   if (have && lane < A) {
-    const long long total = (long long)W.acc[lane] - (long long)ncoll * I.PK;
+    // a chaser's touches earn through its terms; everyone else's cost P each
+    const long long pen = TAG && ti ? 0ll : (long long)ncoll * I.PK;
+    const long long total = (long long)W.acc[lane] - pen;
     B.reward[I.agent_base + i] = fmul(__ll2float_rn(total), I.inv_scaleK);
     B.coll[I.agent_base + i] = ncoll;
     if ((long long)nin > I.NMAX) err |= FLOCK_ERR_OVERFLOW;
   }
   // observation rows, written whole and contiguous (and, with the policy,
-  // also as BF16 rows of the warp's tile)
-  const int P = v + 1;
+  // also as BF16 rows of the warp's tile); tag rows are the 2v distances
+  const int P = TAG ? 2 * v : v + 1;
   const int rpi = P <= 32 ? 32 / P : 1;
   const int my_r = P <= 32 ? lane / P : 0, my_e = P <= 32 ? lane % P : lane;
   float *obs = B.obs ? B.obs + I.obs_base : nullptr;
@@ -1283,6 +1342,12 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
     const float sr_ = __shfl_sync(kFull, ts.y, r), tr = __shfl_sync(kFull, ts.x, r);
     if (rb + my_r < nb && my_r < rpi) {
       for (int e = my_e; e < P; e += 32) {
+        if (TAG) {
+          const int ck = W.cn[r * vs + e];
+          if (obs)
+            obs[(long long)ir * I.obs_dim + e] = ck ? fsqrt(__uint_as_float(W.md[r * vs + e])) : I.RV;
+          continue;
+        }
         float2 val;
         if (e < v) {
           const int ck = W.cn[r * v + e];
