@@ -212,8 +212,11 @@ int derive(const flock_params &p, int stencil, Inst &I, flock_derived *D) {
   if (nmax < 1.0) return FLOCK_EINVAL;
   I.NMAX = nmax > 9.0e15 ? (long long)9.0e15 : (long long)nmax;
   I.K = K;
-  // a term is below t_max * 2^K; two 24-bit pieces hold it when that is < 2^48
-  I.pieces = ldexp((double)t_max, K) < ldexp(1.0, 48) ? 2 : 3;
+  // a term is at most max(t_max, P) * 2^K (P: a tag chaser's term); two
+  // 24-bit pieces hold it when that is < 2^48
+  const double term_max = (double)t_max > (double)p.collision_penalty ? (double)t_max
+                                                                       : (double)p.collision_penalty;
+  I.pieces = ldexp(term_max, K) < ldexp(1.0, 48) ? 2 : 3;
   I.scaleK = ldexpf(1.0f, K);
   I.inv_scaleK = ldexpf(1.0f, -K);
   const double pk = ldexp((double)p.collision_penalty, K);
@@ -602,8 +605,9 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const 
           {k_neighbours_direct<2, 0, 1, true>, k_neighbours_direct<2, 0, 2, true>,
            k_neighbours_direct<2, 0, 4, true>}};
       const int li = lpa == 1 ? 0 : (lpa == 2 ? 1 : 2);
-      const KD k = e->inst.kind == 1 ? kt[e->inst.halo - 1][li]
-                                     : kd[e->inst.halo - 1][e->inst.v == 8 ? 1 : 0][li];
+      // the V = 8 kernels write observation layout 0 only
+      const int v8 = e->inst.v == 8 && e->inst.obs_layout == 0 ? 1 : 0;
+      const KD k = e->inst.kind == 1 ? kt[e->inst.halo - 1][li] : kd[e->inst.halo - 1][v8][li];
       CK(launch(pdl, k, blocks, blk, sm, s, gI, B));
     }
   }

@@ -193,9 +193,11 @@ static size_t batch_smem(int v) {
 
 using KFn = void (*)(const BatchDev *, Inst *, const int *, const int *, unsigned *, unsigned);
 
-static KFn batch_kernel(int halo, int v) {
-  if (halo == 1) return v == 8 ? k_batch_step<1, 8> : k_batch_step<1, 0>;
-  return v == 8 ? k_batch_step<2, 8> : k_batch_step<2, 0>;
+// The V = 8 kernels write observation layout 0 only.
+static KFn batch_kernel(int halo, int v, int layout) {
+  const bool v8 = v == 8 && layout == 0;
+  if (halo == 1) return v8 ? k_batch_step<1, 8> : k_batch_step<1, 0>;
+  return v8 ? k_batch_step<2, 8> : k_batch_step<2, 0>;
 }
 
 }  // namespace flock
@@ -243,7 +245,7 @@ struct flock_batch {
   char *ws;
   cudaStream_t stream, cap_stream;
   cudaGraphExec_t graph;
-  int grid, v, halo;
+  int grid, v, halo, layout;
   unsigned spin_limit;
   BatchDev dev;  // host copy
   std::vector<Inst> insts;
@@ -300,6 +302,7 @@ extern "C" int env_batch_create(int mi, int ma, int mc, const flock_tuning *t, v
   b->stream = (cudaStream_t)stream;
   b->spin_limit = 1u << 22;
   b->v = 0;
+  b->layout = 0;
   int dev = 0, coop = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
@@ -356,9 +359,9 @@ extern "C" int env_batch_set(flock_batch *b, int n_inst, const flock_params *par
   }
   apre[n_inst] = (int)na;
   cpre[n_inst] = (int)nchunk;
-  if (n_inst > 0 && v != b->v) {
-    // the kernel variant (and its shared memory) depends on v
-    KFn fn = batch_kernel(b->halo, v);
+  if (n_inst > 0 && (v != b->v || layout != b->layout)) {
+    // the kernel variant (and its shared memory) depends on v and the layout
+    KFn fn = batch_kernel(b->halo, v, layout);
     const size_t sm = batch_smem(v);
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
@@ -368,6 +371,7 @@ extern "C" int env_batch_set(flock_batch *b, int n_inst, const flock_params *par
     if (per < 1) return FLOCK_EINVAL;  // too many sectors for one block
     b->grid = per * sms;
     b->v = v;
+    b->layout = layout;
     if (b->graph) {
       BCK(cudaStreamSynchronize(b->stream));
       cudaGraphExecDestroy(b->graph);
@@ -424,7 +428,7 @@ static int batch_enqueue(flock_batch *b, cudaStream_t s) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  KFn fn = batch_kernel(b->halo, b->v);
+  KFn fn = batch_kernel(b->halo, b->v, b->layout);
   BCK(cudaLaunchKernelEx(&cfg, fn, (const BatchDev *)(b->ws + L.dev), (Inst *)(b->ws + L.insts),
                          (const int *)(b->ws + L.apre), (const int *)(b->ws + L.cpre),
                          (unsigned *)(b->ws + L.ctr), b->spin_limit));

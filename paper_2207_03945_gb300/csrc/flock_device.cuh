@@ -874,6 +874,22 @@ struct Edges {
   }
 };
 
+// Adds one reward term (units of 2^-K) to owner o's sum.  PIECES: as 24-bit
+// pieces with 32-bit atomics (a drain holds at most kQueue terms, so each
+// piece sum stays below 2^24 * kQueue and exact); else one 64-bit atomic.
+template <bool PIECES>
+__device__ __forceinline__ void add_term(const Inst &I, const DirectArea &W, int o,
+                                         unsigned long long tv) {
+  if (!tv) return;
+  if (PIECES) {
+    atomicAdd(&W.accp[o], (unsigned)tv & 0xffffffu);
+    atomicAdd(&W.accp[32 + o], (unsigned)(tv >> 24) & 0xffffffu);
+    if (I.pieces > 2) atomicAdd(&W.accp[64 + o], (unsigned)(tv >> 48));
+  } else {
+    atomicAdd(&W.acc[o], tv);
+  }
+}
+
 // Drain for the direct form.  In-range and collision counts are kept by the
 // owner lanes during the candidate scan; here each queued pair adds its ramp
 // term (non-colliding pairs) and its sector minimum and count.
@@ -906,24 +922,17 @@ __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W,
     if (valid) {
       const float dx = E.x, dy = E.y, d2 = E.z;
       const bool coll = d2 < I.RC2;
-      unsigned long long tv = 0ull;
-      if (!TAG || (tio == 0 && tj == 0)) {
+      if constexpr (!TAG) {
         if (!coll) {
           const float t = fmul(fsub(I.RV, fsqrt(d2)), I.INV_SPAN);
-          tv = float_int_u64(fmul(t, I.scaleK));
+          add_term<PIECES>(I, W, o, float_int_u64(fmul(t, I.scaleK)));
         }
-      } else if (tio == 1 && tj == 0 && coll) {
-        tv = (unsigned long long)I.PK;  // a chaser touching a runner
-      }
-      {
-        // a drain holds at most kQueue pairs, so each 32-bit piece sum
-        // stays below 2^24 * kQueue and exact
-        if (PIECES && tv) {
-          atomicAdd(&W.accp[o], (unsigned)tv & 0xffffffu);
-          atomicAdd(&W.accp[32 + o], (unsigned)(tv >> 24) & 0xffffffu);
-          if (I.pieces > 2) atomicAdd(&W.accp[64 + o], (unsigned)(tv >> 48));
-        } else if (tv) {
-          atomicAdd(&W.acc[o], tv);
+      } else {
+        if (tio == 0 && tj == 0 && !coll) {  // a runner near a runner
+          const float t = fmul(fsub(I.RV, fsqrt(d2)), I.INV_SPAN);
+          add_term<PIECES>(I, W, o, float_int_u64(fmul(t, I.scaleK)));
+        } else if (tio == 1 && tj == 0 && coll) {
+          add_term<PIECES>(I, W, o, (unsigned long long)I.PK);  // a chaser touching a runner
         }
       }
       const float lx = fadd(fmul(dx, uxo), fmul(dy, uyo));
@@ -1329,6 +1338,8 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
   const int rpi = P <= 32 ? 32 / P : 1;
   const int my_r = P <= 32 ? lane / P : 0, my_e = P <= 32 ? lane % P : lane;
   float *obs = B.obs ? B.obs + I.obs_base : nullptr;
+  // the V = 8 kernels serve layout 0 only (the host picks V = 0 for layout 1)
+  const bool lay0 = V == 8 || I.obs_layout == 0;
   if (POL) {
     // padding columns 18..31 of every row, and whole rows past the chunk
     unsigned *row = reinterpret_cast<unsigned *>(pc->tile + lane * kTileS);
@@ -1355,7 +1366,11 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
         } else {
           val = make_float2(sr_, tr);
         }
-        if (obs) put_obs(I, obs + (long long)ir * I.obs_dim, e, val);
+        if (obs) {
+          float *row = obs + (long long)ir * I.obs_dim;
+          if (lay0) *reinterpret_cast<float2 *>(row + 2 * e) = val;
+          else row[e] = val.x;  // layout 1: the distance, or the speed
+        }
         if (POL)
           *reinterpret_cast<unsigned *>(pc->tile + r * kTileS + 2 * e) = pack_bf16(val.x, val.y);
       }

@@ -146,3 +146,32 @@ def test_view_only_layout_in_a_batch():
         off += k
     assert b.error() == 0
     b.close()
+
+
+@pytest.mark.parametrize("batch", [False, True])
+def test_view_only_layout_with_eight_sectors(batch):
+    """Layout 1 with v = 8 runs the generic-sector kernels (the eight-sector
+    kernels write layout 0 only): rows equal the oracle's view-only rows."""
+    n = 2500
+    side = fi.side_for(n)
+    p = fi.default_params(side, obs_layout=1)
+    st0 = fi.initial_state(n, side, 57)
+    a = fi.random_actions(n, 1, 57)[0]
+    q0 = dict(p, obs_layout=0)
+    s2, o, r, c, _ = oracle.step(q0, st0, a, threads=0)
+    want = np.concatenate([o[:, 0:16:2], o[:, 16:17]], axis=1)
+    if batch:
+        b = F.FlockBatch(1, n, F.flock_instance_cells(p), 9, device=DEV)
+        b.set([p], [n], [torch.from_numpy(st0).to(DEV)], reset=[0])
+        obs, rew, coll = b.step(torch.from_numpy(a).to(DEV))
+        err = b.error()
+        b.close()
+    else:
+        env = F.FlockEnv(p, n, device=DEV)
+        env.reset(torch.from_numpy(st0).to(DEV))
+        obs, rew, coll = env.step(torch.from_numpy(a).to(DEV))
+        err = env.error()
+        env.close()
+    assert obs.shape == (n, 9)
+    assert np.array_equal(obs.cpu().numpy(), want)
+    assert np.array_equal(rew.cpu().numpy(), r) and err == 0
