@@ -132,9 +132,9 @@ __global__ void __launch_bounds__(kBatchBlock) k_batch_step(const BatchDev *__re
   {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int v = V == 8 ? 8 : insts[0].v;
-    char *wbase = smem + (size_t)warp * (sizeof(Inst) + direct_warp_bytes(v));
+    char *wbase = smem + (size_t)warp * (sizeof(Inst) + direct_warp_bytes(v, 32, kQueue));
     Inst &sI = *reinterpret_cast<Inst *>(wbase);
-    const DirectArea W = direct_area(wbase + sizeof(Inst), v);
+    const DirectArea W = direct_area(wbase + sizeof(Inst), v, 32, kQueue);
     int cur = -1;
     for (;;) {
       int c = 0;
@@ -186,7 +186,7 @@ done:
 static size_t batch_smem(int v) {
   const size_t scan = (size_t)(kScanTile + 34) * 4;
   const size_t prefix = (size_t)(kMaxScanTiles + 1) * 4;
-  const size_t warps = (size_t)(kBatchBlock / 32) * (sizeof(Inst) + direct_warp_bytes(v));
+  const size_t warps = (size_t)(kBatchBlock / 32) * (sizeof(Inst) + direct_warp_bytes(v, 32, kQueue));
   size_t m = scan > prefix ? scan : prefix;
   return m > warps ? m : warps;
 }

@@ -400,7 +400,8 @@ __device__ __forceinline__ void phaseC_cell(int c, const Bufs &B, const int *tp)
 // processed by the direct per-thread path, reading the sorted arrays.
 // ---------------------------------------------------------------------------
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kQueue = 128;  // queued pairs per warp
+constexpr int kQueue = 128;  // queued pairs per warp (tile form; lean direct form)
+constexpr int kQueueWide = 160;  // queued pairs per warp, wide direct form
 
 // x is an integer-valued float in [2^23, 2^62) or 0: its value as an
 // integer, with 32-bit integer operations only (a float -> int64 conversion
@@ -830,16 +831,19 @@ struct DirectArea {
 
 // Bytes of one warp's area for v sectors and A agents per warp (32 / lanes
 // per agent): the per-sector minima and counts take A rows of v.
-__host__ __device__ inline size_t direct_warp_bytes(int v, int A = 32) {
-  return (size_t)kQueue * 16 + 32 * 8 + 3 * 32 * 4 + 32 + 32 * 4 * 2 + (size_t)A * v * 8;
+// q: the queue capacity (kQueueWide for the standalone kernels, kQueue for
+// the batched kernel).
+__host__ __device__ inline size_t direct_warp_bytes(int v, int A = 32, int q = kQueueWide) {
+  return (size_t)q * 16 + 32 * 8 + 3 * 32 * 4 + 32 + 32 * 4 * 2 + (size_t)A * v * 8;
 }
 
-__device__ __forceinline__ DirectArea direct_area(char *base, int v, int A = 32) {
+__device__ __forceinline__ DirectArea direct_area(char *base, int v, int A = 32,
+                                                  int q = kQueueWide) {
   DirectArea W;
   W.queue = reinterpret_cast<float4 *>(base);
-  W.acc = reinterpret_cast<unsigned long long *>(base + kQueue * 16);
-  W.accp = reinterpret_cast<unsigned *>(base + kQueue * 16 + 32 * 8);
-  W.nin = reinterpret_cast<int *>(base + kQueue * 16 + 32 * 8 + 3 * 32 * 4 + 32);
+  W.acc = reinterpret_cast<unsigned long long *>(base + q * 16);
+  W.accp = reinterpret_cast<unsigned *>(base + q * 16 + 32 * 8);
+  W.nin = reinterpret_cast<int *>(base + q * 16 + 32 * 8 + 3 * 32 * 4 + 32);
   W.ncoll = W.nin + 32;
   W.md = reinterpret_cast<unsigned *>(W.ncoll + 32);
   W.cn = reinterpret_cast<int *>(W.md + A * v);
@@ -875,8 +879,8 @@ struct Edges {
 };
 
 // Adds one reward term (units of 2^-K) to owner o's sum.  PIECES: as 24-bit
-// pieces with 32-bit atomics (a drain holds at most kQueue terms, so each
-// piece sum stays below 2^24 * kQueue and exact); else one 64-bit atomic.
+// pieces with 32-bit atomics (a drain holds at most kQueueWide terms, so each
+// piece sum stays below 2^24 * kQueueWide and exact); else one 64-bit atomic.
 template <bool PIECES>
 __device__ __forceinline__ void add_term(const Inst &I, const DirectArea &W, int o,
                                          unsigned long long tv) {
@@ -976,33 +980,87 @@ __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, c
   const int slot = lane & (A - 1), sub = lane / A;
   const unsigned lt = (1u << lane) - 1u;
   const int maxn = __reduce_max_sync(kFull, (unsigned)n);
-  for (int j0 = 0; j0 < maxn; j0 += LPA) {
-    const int j = j0 + sub;
-    const int q = a + j;
-    bool inr = false;
-    float dx = 0.f, dy = 0.f, d2 = 0.f;
-    if (j < n && q != self) {
-      const float2 p = __ldg(sxy + q);
-      dx = fsub(p.x, xi);
-      dy = fsub(p.y, yi);
-      if (SHIFT) {
-        dx = fadd(dx, sx);
-        dy = fadd(dy, sy);
+  if constexpr (!PIECES) {
+    // lean form (the batched kernel, 64 registers): one candidate per lane
+    // and pass, the agent itself skipped
+    for (int j0 = 0; j0 < maxn; j0 += LPA) {
+      const int j = j0 + sub;
+      const int q = a + j;
+      bool inr = false;
+      float dx = 0.f, dy = 0.f, d2 = 0.f;
+      if (j < n && q != self) {
+        const float2 p = __ldg(sxy + q);
+        dx = fsub(p.x, xi);
+        dy = fsub(p.y, yi);
+        if (SHIFT) {
+          dx = fadd(dx, sx);
+          dy = fadd(dy, sy);
+        }
+        d2 = fadd(fmul(dx, dx), fmul(dy, dy));
+        inr = d2 < I.RV2;  // Eq. 1: d_ij < d_v
+        if (inr) {
+          nin++;
+          ncoll += d2 < I.RC2 ? 1 : 0;  // Fig. 4: collision below 2 d_r
+        }
       }
-      d2 = fadd(fmul(dx, dx), fmul(dy, dy));
-      inr = d2 < I.RV2;  // Eq. 1: d_ij < d_v
+      const unsigned m = __ballot_sync(kFull, inr);
       if (inr) {
-        nin++;
-        ncoll += d2 < I.RC2 ? 1 : 0;  // Fig. 4: collision below 2 d_r
+        const int w = TAG ? (slot | ((int)(stype[q] != 0) << 8)) : slot;
+        W.queue[qn + __popc(m & lt)] = make_float4(dx, dy, d2, __int_as_float(w));
+      }
+      qn += __popc(m);
+      if (qn > kQueue - 32) {
+        __syncwarp();
+        drain_direct<V, PIECES, TAG>(I, W, qn, ux, uy, E8, ti);
+        qn = 0;
       }
     }
-    const unsigned m = __ballot_sync(kFull, inr);
-    if (inr) {
-      const int w = TAG ? (slot | ((int)(stype[q] != 0) << 8)) : slot;
-      W.queue[qn + __popc(m & lt)] = make_float4(dx, dy, d2, __int_as_float(w));
+    return;
+  }
+  // wide form: two candidates per lane and pass (their loads in flight
+  // together), one drain test per pass; the agent itself is not skipped here
+  // (its pair, at d^2 = 0, is taken out of the counts and the sum at the end)
+  for (int j0 = 0; j0 < maxn; j0 += 2 * LPA) {
+    const int ja = j0 + sub, jb = ja + LPA;
+    bool ina = false, inb = false;
+    float dxa = 0.f, dya = 0.f, d2a = 0.f, dxb = 0.f, dyb = 0.f, d2b = 0.f;
+    float2 pa = make_float2(0.f, 0.f), pb = make_float2(0.f, 0.f);
+    if (ja < n) pa = __ldg(sxy + a + ja);
+    if (jb < n) pb = __ldg(sxy + a + jb);
+    if (ja < n) {
+      dxa = fsub(pa.x, xi);
+      dya = fsub(pa.y, yi);
+      if (SHIFT) {
+        dxa = fadd(dxa, sx);
+        dya = fadd(dya, sy);
+      }
+      d2a = fadd(fmul(dxa, dxa), fmul(dya, dya));
+      ina = d2a < I.RV2;  // Eq. 1: d_ij < d_v
     }
-    qn += __popc(m);
-    if (qn > kQueue - 32) {
+    if (jb < n) {
+      dxb = fsub(pb.x, xi);
+      dyb = fsub(pb.y, yi);
+      if (SHIFT) {
+        dxb = fadd(dxb, sx);
+        dyb = fadd(dyb, sy);
+      }
+      d2b = fadd(fmul(dxb, dxb), fmul(dyb, dyb));
+      inb = d2b < I.RV2;
+    }
+    nin += (ina ? 1 : 0) + (inb ? 1 : 0);
+    ncoll += (ina && d2a < I.RC2 ? 1 : 0) + (inb && d2b < I.RC2 ? 1 : 0);  // Fig. 4
+    const unsigned ma = __ballot_sync(kFull, ina), mb = __ballot_sync(kFull, inb);
+    if (ina) {
+      const int w = TAG ? (slot | ((int)(stype[a + ja] != 0) << 8)) : slot;
+      W.queue[qn + __popc(ma & lt)] = make_float4(dxa, dya, d2a, __int_as_float(w));
+    }
+    qn += __popc(ma);
+    if (inb) {
+      const int w = TAG ? (slot | ((int)(stype[a + jb] != 0) << 8)) : slot;
+      W.queue[qn + __popc(mb & lt)] = make_float4(dxb, dyb, d2b, __int_as_float(w));
+    }
+    qn += __popc(mb);
+    if (qn > kQueueWide - 64) {
       __syncwarp();
       drain_direct<V, PIECES, TAG>(I, W, qn, ux, uy, E8, ti);
       qn = 0;
@@ -1323,11 +1381,22 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
     nin += __shfl_xor_sync(kFull, nin, m);
     ncoll += __shfl_xor_sync(kFull, ncoll, m);
   }
+  // the agent's own pair (d^2 = 0, met once in its own cell, never under a
+  // periodic shift since L > 2 d_v) was counted in range, as a collision when
+  // 0 < (2 d_r)^2, and otherwise (d_r = 0) added a ramp term unless the agent
+  // is a tag chaser; it has no direction, so no sector
+  long long self_term = 0;
+  if (PIECES && have && lane < A) {  // the wide form only
+    nin -= 1;
+    if (0.0f < I.RC2) ncoll -= 1;
+    else if (!(TAG && ti))
+      self_term = (long long)float_int_u64(fmul(fmul(fsub(I.RV, fsqrt(0.0f)), I.INV_SPAN), I.scaleK));
+  }
   // reward and collisions
   if (have && lane < A) {
     // a chaser's touches earn through its terms; everyone else's cost P each
     const long long pen = TAG && ti ? 0ll : (long long)ncoll * I.PK;
-    const long long total = (long long)W.acc[lane] - pen;
+    const long long total = (long long)W.acc[lane] - self_term - pen;
     B.reward[I.agent_base + i] = fmul(__ll2float_rn(total), I.inv_scaleK);
     B.coll[I.agent_base + i] = ncoll;
     if ((long long)nin > I.NMAX) err |= FLOCK_ERR_OVERFLOW;
