@@ -344,7 +344,7 @@ void env_batch_destroy(flock_batch *batch);
  * ------------------------------------------------------------------------- */
 #define FLOCK_STATIC_MAX_AGENTS 65536
 #define FLOCK_STATIC_MAX_CELLS 32768
-#define FLOCK_STATIC_SCRATCH_BYTES 2229760
+#define FLOCK_STATIC_SCRATCH_BYTES 1705472
 int flock_step_static(const flock_params *params, int n_agents, float *state_dev,
                       const int32_t *actions_dev, float *obs_dev, float *reward_dev,
                       int32_t *coll_dev, void *stream, uint32_t *error_bits_out);

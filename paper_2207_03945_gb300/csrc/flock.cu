@@ -349,7 +349,7 @@ cudaError_t set_kernel_attrs() {
 using namespace flock;
 
 struct Layout {
-  size_t state, cellrank, counts, local, cell_start, tile_sum, sxy, sts, sidx, types, stype, inst,
+  size_t state, cellrank, counts, local, cell_start, tile_sum, sxy, sidx, types, stype, inst,
       err, h_act, h_obs,
       h_rew, h_coll, total;
 };
@@ -366,7 +366,6 @@ static Layout make_layout(int n, int C, int D) {
   L.cell_start = take((size_t)(C + 1) * 4);
   L.tile_sum = take((size_t)(nT + 1) * 4);
   L.sxy = take((size_t)n * 8);
-  L.sts = take((size_t)n * 8);
   L.sidx = take((size_t)n * 4);
   L.types = take((size_t)n);   // tag: agent types
   L.stype = take((size_t)n);   // tag: cell-sorted types
@@ -494,7 +493,6 @@ extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, v
   B.cell_start = (int *)(e->ws + L.cell_start);
   B.tile_sum = (int *)(e->ws + L.tile_sum);
   B.sxy = (float2 *)(e->ws + L.sxy);
-  B.sts = (float2 *)(e->ws + L.sts);
   B.sidx = (int *)(e->ws + L.sidx);
   if (e->inst.kind == 1) {
     B.types = (const uint8_t *)(e->ws + L.types);
@@ -944,8 +942,7 @@ constexpr size_t kSLocal = sa(kSCounts + (size_t)kStaticMaxCells * 4);
 constexpr size_t kSCellStart = sa(kSLocal + (size_t)kStaticMaxCells * 4);
 constexpr size_t kSTileSum = sa(kSCellStart + (size_t)(kStaticMaxCells + 1) * 4);
 constexpr size_t kSSxy = sa(kSTileSum + (size_t)(kStaticScanTiles + 1) * 4);
-constexpr size_t kSSts = sa(kSSxy + (size_t)kStaticMaxAgents * 8);
-constexpr size_t kSSidx = sa(kSSts + (size_t)kStaticMaxAgents * 8);
+constexpr size_t kSSidx = sa(kSSxy + (size_t)kStaticMaxAgents * 8);
 constexpr size_t kSBytes = sa(kSSidx + (size_t)kStaticMaxAgents * 4);
 static_assert(kSBytes == FLOCK_STATIC_SCRATCH_BYTES, "flock.h states the scratch size");
 
@@ -1015,7 +1012,6 @@ extern "C" int flock_step_static(const flock_params *p, int n, float *state_dev,
   B.cell_start = (int *)(sp + kSCellStart);
   B.tile_sum = (int *)(sp + kSTileSum);
   B.sxy = (float2 *)(sp + kSSxy);
-  B.sts = (float2 *)(sp + kSSts);
   B.sidx = (int *)(sp + kSSidx);
   B.err = (unsigned *)(sp + kSErr);
   B.bar = B.err + 4;

@@ -210,7 +210,7 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct BLayout {
   size_t dev, insts, apre, cpre, ctr, err, cellrank, counts, local, cell_start, tile_sum, sxy,
-      sts, sidx, total;
+      sidx, total;
 };
 
 BLayout batch_layout(int mi, int ma, int mc) {
@@ -230,7 +230,6 @@ BLayout batch_layout(int mi, int ma, int mc) {
   L.cell_start = take((size_t)(mc + 1) * 4);
   L.tile_sum = take((size_t)(nT + 1) * 4);
   L.sxy = take((size_t)ma * 8);
-  L.sts = take((size_t)ma * 8);
   L.sidx = take((size_t)ma * 4);
   L.total = o;
   return L;
@@ -392,7 +391,6 @@ extern "C" int env_batch_set(flock_batch *b, int n_inst, const flock_params *par
   B.cell_start = (int *)(b->ws + L.cell_start);
   B.tile_sum = (int *)(b->ws + L.tile_sum);
   B.sxy = (float2 *)(b->ws + L.sxy);
-  B.sts = (float2 *)(b->ws + L.sts);
   B.sidx = (int *)(b->ws + L.sidx);
   B.err = (unsigned *)(b->ws + L.err);
   B.bar = (unsigned *)(b->ws + L.ctr);

@@ -62,7 +62,6 @@ struct Bufs {
   int *cell_start;     // per cell + 1: first sorted position
   int *tile_sum;       // per scan tile: agents in the tile
   float2 *sxy;         // cell-sorted positions (x, y)
-  float2 *sts;         // cell-sorted (theta, s)
   int *sidx;           // cell-sorted flattened agent index
   unsigned *err;       // latched FLOCK_ERR_* bits
   unsigned *bar;       // grid barrier words (count, generation)
@@ -365,7 +364,6 @@ __device__ __forceinline__ void phaseC_agent(int f, const float4 *state_i, const
     return;
   }
   B.sxy[pos] = make_float2(st.x, st.y);
-  B.sts[pos] = make_float2(st.z, st.w);
   B.sidx[pos] = f;
   if (B.stype) B.stype[pos] = B.types[f];
 }
@@ -690,7 +688,8 @@ __device__ void phaseD_tile(const Inst &I, int tx, int ty, const Bufs &B, char *
         self = cs[sr * nsc + H] + al;  // interior run of the row, in sorted order
         const int gp = rs[r] + al;
         i = B.sidx[gp] - I.agent_base;
-        ts = B.sts[gp];
+        const float4 s4 = I.state[i];  // own heading and speed
+        ts = make_float2(s4.z, s4.w);
         const float4 e = stg[self];
         xi = e.x;
         yi = e.y;
@@ -1291,8 +1290,9 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
     const float2 p = B.sxy[gp];
     xi = p.x;
     yi = p.y;
-    ts = B.sts[gp];
     i = B.sidx[gp] - I.agent_base;
+    const float4 s4 = I.state[i];  // own heading and speed (only the owner needs them)
+    ts = make_float2(s4.z, s4.w);
     cx = cell_of(xi, I);
     cy = cell_of(yi, I);
   }

@@ -24,10 +24,10 @@ import numpy as np
 
 # Device bytes a session of n agents and c cells occupies while admitted:
 # resident state (16/agent), the batch's per-agent scratch (cell and rank 8,
-# sorted positions 8, sorted heading and speed 8, sorted index 4), its rows of
-# the flattened actions and outputs (4 + 72 + 4 + 4), per-cell scratch
-# (counts, offsets, starts: 12/cell) and one descriptor.
-BYTES_PER_AGENT = 16 + 8 + 8 + 8 + 4 + 4 + 72 + 4 + 4
+# sorted positions 8, sorted index 4), its rows of the flattened actions and
+# outputs (4 + 72 + 4 + 4), per-cell scratch (counts, offsets, starts:
+# 12/cell) and one descriptor.
+BYTES_PER_AGENT = 16 + 8 + 8 + 4 + 4 + 72 + 4 + 4
 BYTES_PER_CELL = 12
 BYTES_PER_SESSION = 1024
 
