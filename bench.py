@@ -319,7 +319,8 @@ def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256,
     ms = [ev0[k].elapsed_time(ev1[k]) for k in range(steps)]
     tot = max_over_ranks(sum(ms), dev)
     grid, block = F.env_batch_get_launch(b.batch)
-    traffic_key = "batched-%d-%d-s%d" % (n_inst, total, (tuning or {}).get("stencil", 1))
+    bmode = (tuning or {}).get("mode", 2) or 2
+    traffic_key = "batched-%d-%d-s%d-m%d" % (n_inst, total, (tuning or {}).get("stencil", 1), bmode)
     kern_ms = float(np.mean(kern))
     peak, peak_kind = peaks()
     achieved = BYTES_PER_AGENT_STEP * total / (kern_ms * 1e-3) / 1e9
@@ -334,10 +335,13 @@ def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256,
                         "cooperative kernel per step, CUDA graph"
                         % (n_inst, "log-uniform in [100, 20000]" if n_inst > 1 else str(sizes),
                            seed, total),
-            "roofline": {"bound": "hbm", "kernel": "k_batch_step", "achieved": achieved,
+            "roofline": {"bound": "hbm",
+                         "kernel": "k_batch_step" if bmode == 2 else "k_batch_step + k_batch_neigh",
+                         "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_kind,
-                         "traffic": measured_traffic("k_batch_step", traffic_key),
+                         "traffic": measured_traffic("k_batch_step", traffic_key) if bmode == 2
+                         else None,
                          "bytes_per_agent": BYTES_PER_AGENT_STEP}}
 
 

@@ -23,7 +23,9 @@ CANDIDATES = (
      for (w, h) in ((19, 2), (10, 4), (32, 1))] +
     [{"mode": 1, "stencil": 2, "tile_w": 16, "tile_h": 4, "block": 128}])
 
-BATCH_CANDIDATES = ({"stencil": 1}, {"stencil": 2})
+# mode 2: one persistent launch per step; mode 3: persistent binning, then
+# a separate neighbour-scan launch
+BATCH_CANDIDATES = tuple({"stencil": st, "mode": m} for st in (1, 2) for m in (2, 3))
 
 
 def _hold(torch):
@@ -124,8 +126,9 @@ def autotune(params, state0, steps=6, warmup=2, device="cuda", cache=DEFAULT_CAC
 
 def autotune_batch(params_list, sizes, states, steps=4, warmup=2, device="cuda",
                    candidates=BATCH_CANDIDATES):
-    """Best cell size (stencil) for a batch: times one persistent launch per
-    step for each candidate and checks the outputs are identical."""
+    """Best cell size (stencil) and form (one persistent launch, or binning
+    and neighbour scan as two launches) for a batch: times each candidate's
+    steps and checks the outputs are identical."""
     import numpy as np
     import torch
 

@@ -87,7 +87,9 @@ __device__ __forceinline__ int find_inst(const int *pre, int n, int x) {
   return lo;
 }
 
-template <int H, int V>
+// SPLIT: phases A-C only; the neighbour scan runs as the next launch
+// (k_batch_neigh), where it has the registers of a kernel of its own.
+template <int H, int V, bool SPLIT>
 __global__ void __launch_bounds__(kBatchBlock) k_batch_step(const BatchDev *__restrict__ d, Inst *insts,
                                                           const int *__restrict__ apre,
                                                           const int *__restrict__ cpre,
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(kBatchBlock) k_batch_step(const BatchDev *__re
   if (!grid_barrier(ctr, B.err, spin_limit, &flag)) goto done;
 
   // ---- phase D: neighbour scan, one chunk of 32 sorted agents per warp ----
-  {
+  if (!SPLIT) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int v = V == 8 ? 8 : insts[0].v;
     char *wbase = smem + (size_t)warp * (sizeof(Inst) + direct_warp_bytes(v, 32, kQueue));
@@ -183,21 +185,84 @@ done:
   }
 }
 
-static size_t batch_smem(int v) {
+// Phase D of the split form, a launch of its own (so the wide direct scan of
+// the standalone kernels has the registers it wants): every warp takes
+// chunks of 32 cell-sorted agents from the shared ticket (zero when the
+// binning launch ends) and keeps its copy of the instance descriptor while
+// consecutive chunks stay in one instance.  A step whose binning launch gave
+// up at a grid barrier (FLOCK_ERR_TIMEOUT latched) is left unobserved.
+constexpr int kNeighBlock = 128;
+
+template <int H, int V>
+__global__ void __launch_bounds__(kNeighBlock) k_batch_neigh(const BatchDev *__restrict__ d,
+                                                             Inst *insts, const int *cpre,
+                                                             unsigned *ctr) {
+  extern __shared__ __align__(16) char smem[];
+  const BatchDev D = *d;
+  const Bufs &B = D.B;
+  if (ld_acquire(B.err) & FLOCK_ERR_TIMEOUT) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int v = V == 8 ? 8 : insts[0].v;
+  char *wbase = smem + (size_t)warp * (sizeof(Inst) + direct_warp_bytes(v));
+  Inst &sI = *reinterpret_cast<Inst *>(wbase);
+  const DirectArea W = direct_area(wbase + sizeof(Inst), v);
+  unsigned err = 0;
+  int cur = -1;
+  for (;;) {
+    int c = 0;
+    if (lane == 0) c = (int)atomicAdd(&ctr[kCtrTicket], 1u);
+    c = __shfl_sync(kFull, c, 0);
+    if (c >= D.n_chunks) break;
+    const int k = find_inst(cpre, D.n_inst, c);
+    if (k != cur) {
+      const int *src = reinterpret_cast<const int *>(insts + k);
+      int *dst = reinterpret_cast<int *>(&sI);
+      for (int w = lane; w < (int)(sizeof(Inst) / 4); w += 32) dst[w] = src[w];
+      __syncwarp();
+      cur = k;
+    }
+    const int gp0 = sI.agent_base + (c - cpre[k]) * 32;
+    const int gp1 = min(gp0 + 32, sI.agent_base + sI.n);
+    phaseD_direct<H, V, false, true>(sI, gp0, gp1, B, W, err);
+    if (sI.reset && gp0 == sI.agent_base && lane == 0) insts[k].reset = 0;
+  }
+  if (err) atomicOr(B.err, err);
+}
+
+static size_t neigh_smem(int v) {
+  return (size_t)(kNeighBlock / 32) * (sizeof(Inst) + direct_warp_bytes(v));
+}
+
+// Dynamic shared memory of the persistent kernel: the scan tile or the tile
+// prefix, and (fused form) the per-warp areas of phase D.
+static size_t batch_smem(int v, bool split) {
   const size_t scan = (size_t)(kScanTile + 34) * 4;
   const size_t prefix = (size_t)(kMaxScanTiles + 1) * 4;
-  const size_t warps = (size_t)(kBatchBlock / 32) * (sizeof(Inst) + direct_warp_bytes(v, 32, kQueue));
   size_t m = scan > prefix ? scan : prefix;
+  if (split) return m;
+  const size_t warps =
+      (size_t)(kBatchBlock / 32) * (sizeof(Inst) + direct_warp_bytes(v, 32, kQueue));
   return m > warps ? m : warps;
 }
 
 using KFn = void (*)(const BatchDev *, Inst *, const int *, const int *, unsigned *, unsigned);
+using NFn = void (*)(const BatchDev *, Inst *, const int *, unsigned *);
 
 // The V = 8 kernels write observation layout 0 only.
-static KFn batch_kernel(int halo, int v, int layout) {
+static KFn batch_kernel(int halo, int v, int layout, bool split) {
   const bool v8 = v == 8 && layout == 0;
-  if (halo == 1) return v8 ? k_batch_step<1, 8> : k_batch_step<1, 0>;
-  return v8 ? k_batch_step<2, 8> : k_batch_step<2, 0>;
+  if (split) {
+    if (halo == 1) return v8 ? k_batch_step<1, 8, true> : k_batch_step<1, 0, true>;
+    return v8 ? k_batch_step<2, 8, true> : k_batch_step<2, 0, true>;
+  }
+  if (halo == 1) return v8 ? k_batch_step<1, 8, false> : k_batch_step<1, 0, false>;
+  return v8 ? k_batch_step<2, 8, false> : k_batch_step<2, 0, false>;
+}
+
+static NFn neigh_kernel(int halo, int v, int layout) {
+  const bool v8 = v == 8 && layout == 0;
+  if (halo == 1) return v8 ? k_batch_neigh<1, 8> : k_batch_neigh<1, 0>;
+  return v8 ? k_batch_neigh<2, 8> : k_batch_neigh<2, 0>;
 }
 
 }  // namespace flock
@@ -245,6 +310,8 @@ struct flock_batch {
   cudaStream_t stream, cap_stream;
   cudaGraphExec_t graph;
   int grid, v, halo, layout;
+  bool split;
+  int neigh_grid;  // blocks of the split form's neighbour launch (all resident)
   unsigned spin_limit;
   BatchDev dev;  // host copy
   std::vector<Inst> insts;
@@ -293,7 +360,14 @@ extern "C" int env_batch_create(int mi, int ma, int mc, const flock_tuning *t, v
   b->halo = b->tuning.stencil ? b->tuning.stencil : 1;
   if (b->halo != 1 && b->halo != 2) { delete b; return FLOCK_EINVAL; }
   b->tuning.stencil = b->halo;
-  b->tuning.mode = 2;
+  // mode 2: one persistent launch runs every phase; mode 3: the persistent
+  // launch bins (phases A-C) and a second launch runs the neighbour scan
+  b->split = b->tuning.mode == 3;
+  if (b->tuning.mode != 0 && b->tuning.mode != 2 && b->tuning.mode != 3) {
+    delete b;
+    return FLOCK_EINVAL;
+  }
+  b->tuning.mode = b->split ? 3 : 2;
   b->tuning.block = kBatchBlock;
   b->lay = batch_layout(mi, ma, mc);
   if (!ws || ((uintptr_t)ws & 255) || ws_bytes < b->lay.total) { delete b; return FLOCK_ENOSPACE; }
@@ -360,8 +434,8 @@ extern "C" int env_batch_set(flock_batch *b, int n_inst, const flock_params *par
   cpre[n_inst] = (int)nchunk;
   if (n_inst > 0 && (v != b->v || layout != b->layout)) {
     // the kernel variant (and its shared memory) depends on v and the layout
-    KFn fn = batch_kernel(b->halo, v, layout);
-    const size_t sm = batch_smem(v);
+    KFn fn = batch_kernel(b->halo, v, layout, b->split);
+    const size_t sm = batch_smem(v, b->split);
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -369,6 +443,15 @@ extern "C" int env_batch_set(flock_batch *b, int n_inst, const flock_params *par
     BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kBatchBlock, sm));
     if (per < 1) return FLOCK_EINVAL;  // too many sectors for one block
     b->grid = per * sms;
+    if (b->split) {
+      NFn nf = neigh_kernel(b->halo, v, layout);
+      int pn = 0;
+      BCK(cudaFuncSetAttribute(nf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)neigh_smem(v)));
+      BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pn, nf, kNeighBlock, neigh_smem(v)));
+      if (pn < 1) return FLOCK_EINVAL;
+      b->neigh_grid = pn * sms;
+    }
     b->v = v;
     b->layout = layout;
     if (b->graph) {
@@ -419,17 +502,23 @@ static int batch_enqueue(flock_batch *b, cudaStream_t s) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(b->grid);
   cfg.blockDim = dim3(kBatchBlock);
-  cfg.dynamicSmemBytes = batch_smem(b->v);
+  cfg.dynamicSmemBytes = batch_smem(b->v, b->split);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  KFn fn = batch_kernel(b->halo, b->v, b->layout);
+  KFn fn = batch_kernel(b->halo, b->v, b->layout, b->split);
   BCK(cudaLaunchKernelEx(&cfg, fn, (const BatchDev *)(b->ws + L.dev), (Inst *)(b->ws + L.insts),
                          (const int *)(b->ws + L.apre), (const int *)(b->ws + L.cpre),
                          (unsigned *)(b->ws + L.ctr), b->spin_limit));
+  if (b->split) {
+    neigh_kernel(b->halo, b->v, b->layout)<<<b->neigh_grid, kNeighBlock, neigh_smem(b->v), s>>>(
+        (const BatchDev *)(b->ws + L.dev), (Inst *)(b->ws + L.insts),
+        (const int *)(b->ws + L.cpre), (unsigned *)(b->ws + L.ctr));
+    BCK(cudaGetLastError());
+  }
   if (b->timing) BCK(cudaEventRecordWithFlags(b->ev[1], s, cudaEventRecordExternal));
   return FLOCK_OK;
 }
@@ -461,7 +550,16 @@ extern "C" int env_batch_step(flock_batch *b, const int32_t *act, float *obs, fl
       return rc;
     }
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
-    ce = cudaGraphInstantiate(&b->graph, g, 0);
+    if (b->graph) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(b->graph, g, &info) != cudaSuccess) {
+        (void)cudaGetLastError();
+        ce = cudaStreamSynchronize(b->stream);
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+      }
+    }
+    if (!b->graph && ce == cudaSuccess) ce = cudaGraphInstantiate(&b->graph, g, 0);
     cudaGraphDestroy(g);
     if (ce != cudaSuccess) {
       b->graph = nullptr;

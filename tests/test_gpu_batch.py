@@ -3,7 +3,9 @@
 Each instance of a mixed batch must equal the oracle run on that instance
 alone (bit-exact: state, observation, collisions, reward), and equal the
 single-environment path; the active set may change between steps; the
-grid-barrier wait bound turns a stalled barrier into FLOCK_ERR_TIMEOUT."""
+grid-barrier wait bound turns a stalled barrier into FLOCK_ERR_TIMEOUT.
+Mode 2 runs every phase in one persistent launch; mode 3 bins in the
+persistent launch and scans neighbours in a second one."""
 import numpy as np
 import pytest
 
@@ -38,10 +40,14 @@ def batch_for(insts, tuning=None):
                         device=DEV, tuning=tuning)
 
 
-def test_mixed_batch_matches_oracle_per_instance():
+MODES = pytest.mark.parametrize("mode", [2, 3])
+
+
+@MODES
+def test_mixed_batch_matches_oracle_per_instance(mode):
     sizes = [100, 1, 0, 2500, 731, 5000, 64, 33, 12000]
     insts = make_instances(sizes, 100)
-    b = batch_for(insts)
+    b = batch_for(insts, {"mode": mode})
     states = [torch.from_numpy(st).to(DEV) for _, _, st in insts]
     b.set([p for p, _, _ in insts], sizes, states, reset=[1] * len(sizes))
     steps = 4
@@ -89,12 +95,14 @@ def test_batch_equals_single_environment():
     b.close()
 
 
-def test_active_set_changes_between_steps():
-    """Sessions leave and join between steps; the graph is reused."""
+@MODES
+def test_active_set_changes_between_steps(mode):
+    """Sessions leave and join between steps; the graph is reused (mode 3:
+    updated in place for the new chunk count)."""
     sizes = [500, 800, 1200]
     insts = make_instances(sizes, 300)
     extra = make_instances([700], 400)[0]
-    b = F.FlockBatch(4, 4000, 20000, 18, device=DEV)
+    b = F.FlockBatch(4, 4000, 20000, 18, device=DEV, tuning={"mode": mode})
     states = [torch.from_numpy(st).to(DEV) for _, _, st in insts]
     b.set([p for p, _, _ in insts], sizes, states, reset=[1, 1, 1])
     b.step(torch.zeros(sum(sizes), dtype=torch.int32, device=DEV))
@@ -149,13 +157,15 @@ def test_mixed_segment_counts_rejected():
     b.close()
 
 
-def test_barrier_wait_bound_reports_timeout_and_recovers():
+@MODES
+def test_barrier_wait_bound_reports_timeout_and_recovers(mode):
     """With the wait bound at zero every barrier gives up at once: the step
-    returns with FLOCK_ERR_TIMEOUT latched and no hang; after restoring the
-    bound the next steps are correct again."""
+    returns with FLOCK_ERR_TIMEOUT latched and no hang (mode 3: the
+    neighbour launch sees the bit and leaves the step unobserved); after
+    restoring the bound the next steps are correct again."""
     sizes = [3000, 2000]
     insts = make_instances(sizes, 600)
-    b = batch_for(insts)
+    b = batch_for(insts, {"mode": mode})
     states = [torch.from_numpy(st).to(DEV) for _, _, st in insts]
     b.set([p for p, _, _ in insts], sizes, states, reset=[1, 1])
     F.env_batch_set_spin_limit(b.batch, 0)
@@ -179,13 +189,14 @@ def test_barrier_wait_bound_reports_timeout_and_recovers():
     b.close()
 
 
-def test_benchmark_mix_sampled_rows():
+@MODES
+def test_benchmark_mix_sampled_rows(mode):
     """The 256-instance mix of the benchmark (agent counts log-uniform in
     [100, 20000]): every state bit-exact after two steps, and the outputs of
     sampled rows of every instance bit-exact against the oracle."""
     sizes = fi.batch_sizes(256, 100, 20000, 0)
     insts = make_instances(sizes, 1000)
-    b = batch_for(insts)
+    b = batch_for(insts, {"mode": mode})
     states = [torch.from_numpy(st).to(DEV) for _, _, st in insts]
     b.set([p for p, _, _ in insts], sizes, states, reset=[1] * len(sizes))
     b.step(torch.zeros(sum(sizes), dtype=torch.int32, device=DEV))
