@@ -103,7 +103,10 @@ typedef struct flock_tuning {
   int block;   /* threads per block, multiple of 32 in 64..512 */
   int mode;    /* neighbour scan: 1 = tiles of cells staged in shared memory,
                   2 = each warp takes 32 / lanes consecutive cell-sorted agents
-                  and reads their stencil cells through the L1 cache */
+                  and reads their stencil cells through the L1 cache.
+                  Batch: 2 = every phase in one persistent launch; 3 = binning
+                  in the persistent launch, the neighbour scan (direct form)
+                  in a second launch.  Results are identical. */
   int lanes;   /* mode 2: lanes per agent, 1, 2 or 4 (0: 4 up to 32,768 agents,
                   2 up to 524,288, else 1); the lanes of an agent share its
                   candidates.  Mode 1 and the policy step use 1. */
