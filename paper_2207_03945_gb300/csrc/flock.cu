@@ -3,7 +3,7 @@
 //
 // A step is four kernels on the caller's stream, replayed as one CUDA graph:
 //   k_apply_bin   phase A   one thread per agent
-//   k_scan        phase B   one block per scan tile of 2048 cells
+//   k_scan        phase B   one block per scan tile of 1024 cells
 //   k_scatter     phase C   grid-stride over agents and cells
 //   k_neighbours  phase D   one block per tile of cells
 #include <cmath>

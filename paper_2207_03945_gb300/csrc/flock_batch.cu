@@ -4,7 +4,7 @@
 // The kernel runs the four phases of a step over flattened work lists that
 // span all active instances, separated by grid barriers:
 //   A  agents  -> apply actions, bin into the instance's cell list
-//   B  cells   -> exclusive scan, 2048-cell tiles (one global scan: instance
+//   B  cells   -> exclusive scan, 1024-cell tiles (one global scan: instance
 //                 k's cells and agents are contiguous ranges, in the same order)
 //   C  agents  -> counting-sort scatter into cell order
 //   D  chunks  -> 32 consecutive sorted agents of one instance per warp,

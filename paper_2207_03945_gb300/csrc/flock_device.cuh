@@ -26,8 +26,8 @@
 namespace flock {
 
 constexpr int kMaxV = FLOCK_MAX_SEGMENTS;
-constexpr int kScanTile = 2048;        // cells per scan tile (phase B)
-constexpr int kMaxScanTiles = 4096;    // => at most 8M cells
+constexpr int kScanTile = 1024;        // cells per scan tile (phase B)
+constexpr int kMaxScanTiles = 8192;    // => at most 8M cells
 constexpr int kMaxTileW = 64, kMaxTileH = 8;
 constexpr int kMaxStagedCells = (kMaxTileH + 4) * (kMaxTileW + 4);
 
