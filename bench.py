@@ -60,6 +60,16 @@ def sources_digest() -> str:
     return h.hexdigest()
 
 
+def batch_traffic(key: str, mode: int):
+    """DRAM bytes of one batched step from the committed table: the
+    persistent kernel, plus the neighbour launch in the two-launch form."""
+    t = measured_traffic("k_batch_step", key)
+    if mode == 3:
+        t2 = measured_traffic("k_batch_neigh", key)
+        return None if t is None or t2 is None else t + t2
+    return t
+
+
 def tuning_tag(t: dict) -> str:
     """Short name of a launch shape, e.g. m2-s1-b128-l2."""
     tag = "m%d-s%d-b%d" % (t["mode"], t["stencil"], t["block"])
@@ -257,7 +267,7 @@ def run_reference(args):
 
 
 def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256, sizes=None,
-                world=1, tune=True):
+                world=1, tune=True, tuning=None):
     """The batched form: n_inst instances with agent counts log-uniform in
     [100, 20000] (density 0.1 each), all advanced by one persistent kernel
     per step, replayed from a CUDA graph.  With `sizes`, those instances
@@ -274,8 +284,7 @@ def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256,
         arena[off:off + n] = torch.from_numpy(fi.initial_state(n, fi.side_for(n), seed + k))
         states.append(arena[off:off + n])
         off += n
-    tuning = None
-    if tune:
+    if tune and tuning is None:
         from paper_2207_03945_gb300.autotune import autotune_batch
         host_states = [s_.cpu().numpy() for s_ in states]
         tuning, _ = autotune_batch(params, sizes, host_states, device=dev)
@@ -340,8 +349,7 @@ def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256,
                          "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_kind,
-                         "traffic": measured_traffic("k_batch_step", traffic_key) if bmode == 2
-                         else None,
+                         "traffic": batch_traffic(traffic_key, bmode),
                          "bytes_per_agent": BYTES_PER_AGENT_STEP}}
 
 
@@ -591,6 +599,9 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--tuning", default=None,
                     help='launch shape as JSON, e.g. {"mode": 2, "stencil": 1, "block": 128}')
+    ap.add_argument("--batch-tuning", default=None,
+                    help='batched form: launch shape as JSON instead of the autotuner\'s, '
+                         'e.g. {"stencil": 1, "mode": 3}')
     ap.add_argument("--autotune", action="store_true",
                     help="plain step: launch shape from the autotuner instead of the default")
     args = ap.parse_args()
@@ -706,7 +717,8 @@ def main():
     batched = single_fused = None
     if not args.no_batched:
         batched = run_batched(F, torch, dev, stream, args.steps, args.warmup, flush,
-                              seed=rank_seed(rank), world=world)
+                              seed=rank_seed(rank), world=world,
+                              tuning=json.loads(args.batch_tuning) if args.batch_tuning else None)
         # the same 50,000-agent instance as the headline, as a batch of one
         single_fused = run_batched(F, torch, dev, stream, args.steps, args.warmup, flush,
                                    seed=rank_seed(rank), sizes=[n], world=world, tune=False)
