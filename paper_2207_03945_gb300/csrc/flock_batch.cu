@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kNeighBlock) k_batch_neigh(const BatchDev *__r
     }
     const int gp0 = sI.agent_base + (c - cpre[k]) * 32;
     const int gp1 = min(gp0 + 32, sI.agent_base + sI.n);
-    phaseD_direct<H, V, false, true>(sI, gp0, gp1, B, W, err);
+    phaseD_direct<H, V, false, true, 1, false, true>(sI, gp0, gp1, B, W, err);
     if (sI.reset && gp0 == sI.agent_base && lane == 0) insts[k].reset = 0;
   }
   if (err) atomicOr(B.err, err);

@@ -893,6 +893,16 @@ __device__ __forceinline__ void add_term(const Inst &I, const DirectArea &W, int
   }
 }
 
+// x[r] for a run-time r < N, by selects (a dynamic index would put x in
+// local memory).
+template <int N>
+__device__ __forceinline__ int pick(const int (&x)[N], int r) {
+  int v = x[0];
+#pragma unroll
+  for (int k = 1; k < N; ++k) v = r == k ? x[k] : v;
+  return v;
+}
+
 // Drain for the direct form.  In-range and collision counts are kept by the
 // owner lanes during the candidate scan; here each queued pair adds its ramp
 // term (non-colliding pairs) and its sector minimum and count.
@@ -1266,7 +1276,13 @@ __device__ __forceinline__ void policy_mtile(const PolicyCtx &P, int row0, int &
 // TAG: the tag environment (needs V == 0 and no policy): two colour
 // channels of sectors, type-dependent rewards (see drain_direct), and the
 // observation row is the 2v channel distances.
-template <int H, int V, bool POL = false, bool PIECES = true, int LPA = 1, bool TAG = false>
+// COMPACT: the runs of wrapping chunks are walked by a loop that is not
+// unrolled, so that form of the candidate scan appears once in the code (the
+// batched kernels, whose mix of small instances wraps often, run faster with
+// the smaller instruction footprint; a single large instance rarely wraps and
+// runs faster fully unrolled).
+template <int H, int V, bool POL = false, bool PIECES = true, int LPA = 1, bool TAG = false,
+          bool COMPACT = false>
 __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
                               const DirectArea &W, unsigned &err,
                               const PolicyCtx *pc = nullptr) {
@@ -1346,6 +1362,37 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
     for (int r = 0; r < 2 * H + 1; ++r)
       direct_run<false, V, PIECES, LPA, TAG>(I, W, B.sxy, ra[r], rn[r], self, 0.f, 0.f, xi, yi,
                                              ux, uy, qn, nin, ncoll, E8, B.stype, ti);
+  } else if (COMPACT) {
+    // per stencil row three runs: the interior, the cells across the left
+    // boundary (virtual columns [vlo, 0) -> [vlo + nc, nc)) and those across
+    // the right one (virtual columns [nc, vhi) -> [0, vhi - nc))
+#pragma unroll 1
+    for (int t = 0; t < 3 * (2 * H + 1); ++t) {
+      const int r = t / 3, kind = t - 3 * r;
+      const int vr = cy - H + r;
+      const float sy = vr < 0 ? -I.L : (vr >= nc ? I.L : 0.0f);
+      const int rowg = I.cell_base + wrapi(vr, nc) * nc;
+      int a = 0, n = 0;
+      float sx = 0.f;
+      if (kind == 0) {
+        a = pick<2 * H + 1>(ra, r);
+        n = pick<2 * H + 1>(rn, r);
+      } else if (kind == 1) {
+        sx = -I.L;
+        if (have && lw) {
+          a = cst[rowg + vlo + nc];
+          n = cst[rowg + nc] - a;
+        }
+      } else {
+        sx = I.L;
+        if (have && rw) {
+          a = cst[rowg];
+          n = cst[rowg + vhi - nc] - a;
+        }
+      }
+      direct_run<true, V, PIECES, LPA, TAG>(I, W, B.sxy, a, n, self, sx, sy, xi, yi, ux, uy, qn,
+                                            nin, ncoll, E8, B.stype, ti);
+    }
   } else {
 #pragma unroll
     for (int r = 0; r < 2 * H + 1; ++r) {
