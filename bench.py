@@ -398,7 +398,7 @@ def run_policy(F, torch, dev, stream, steps, warmup, flush, n=100000, seed=0, wo
             "roofline": {"bound": "hbm", "kernel": "whole step (4 kernels)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,
-                         "traffic": measured_traffic("k_neighbours_policy", "policy-%d" % n),
+                         "traffic": None,  # a whole-step figure; see profiles/ for the kernel
                          "bytes_per_agent": POLICY_BYTES_PER_AGENT}}
 
 
