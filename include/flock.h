@@ -161,7 +161,8 @@ int env_reset(flock_env *env, const float *state0_dev, float *obs_dev, float *re
 
 /* One step (the hot path): applies actions_dev, then observes.  Enqueues a
  * CUDA graph of the binning and neighbour-scan kernels (captured on the
- * first call and again whenever an output pointer changes). */
+ * first call; when a buffer pointer changes, the graph is updated in place
+ * and launches already enqueued keep their pointers). */
 int env_step(flock_env *env, const int32_t *actions_dev, float *obs_dev, float *reward_dev,
              int32_t *coll_dev);
 
@@ -290,8 +291,9 @@ int env_batch_create(int max_instances, int max_agents, int max_cells,
  * (or reset == NULL for none) makes the next step observe instance k without
  * applying its actions (its initial observation).  The descriptors are
  * copied to the device in stream order; no kernel is re-captured.
- * Returns FLOCK_EINVAL if a parameter set is invalid, if num_segments
- * differs between instances, or if a total exceeds the batch's maxima. */
+ * Returns FLOCK_EINVAL if a parameter set is invalid, if num_segments or
+ * obs_layout differs between instances, if an instance is a tag instance,
+ * or if a total exceeds the batch's maxima. */
 int env_batch_set(flock_batch *batch, int n_inst, const flock_params *params,
                   const int *n_agents, float *const *state_dev, const int *reset);
 

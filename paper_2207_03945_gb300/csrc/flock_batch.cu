@@ -1,5 +1,7 @@
 // Batched flock step: many independent instances of the environment of arXiv
-// 2207.03945 (Section 4.1) advanced by one persistent cooperative kernel.
+// 2207.03945 (Section 4.1) advanced by one persistent cooperative kernel (or,
+// mode 3, that kernel for the binning and a second persistent launch for the
+// neighbour scan).
 //
 // The kernel runs the four phases of a step over flattened work lists that
 // span all active instances, separated by grid barriers:
