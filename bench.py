@@ -47,16 +47,26 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
 CSRC = os.path.join(ROOT, "paper_2207_03945_gb300", "csrc")
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without comments and blank lines (comment edits do not
+    change a kernel)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip())
+
+
 def sources_digest() -> str:
-    """SHA-256 over the kernel sources and the public header."""
+    """SHA-256 over the code (comments removed) of the kernel sources and the
+    public header."""
     import hashlib
     h = hashlib.sha256()
     files = sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h")))
-    for f in files:
-        with open(os.path.join(CSRC, f), "rb") as fh:
-            h.update(f.encode() + b"\0" + fh.read())
-    with open(os.path.join(ROOT, "include", "flock.h"), "rb") as fh:
-        h.update(b"flock.h\0" + fh.read())
+    paths = [(f, os.path.join(CSRC, f)) for f in files]
+    paths.append(("flock.h", os.path.join(ROOT, "include", "flock.h")))
+    for name, path in paths:
+        with open(path, encoding="utf-8") as fh:
+            h.update(name.encode() + b"\0" + _code_only(fh.read()).encode())
     return h.hexdigest()
 
 
