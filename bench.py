@@ -722,7 +722,8 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e = {"value": world * n * e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": n * 4, "d2h_bytes_per_step": n * (env.obs_dim + 2) * 4,
-           "call": "env_step_host (pinned host buffers, synchronous)"}
+           "call": "env_step_host (pinned host buffers: the actions read in place over "
+                   "NVLink-C2C, the outputs copied out; synchronous)"}
 
     batched = single_fused = None
     if not args.no_batched:

@@ -214,9 +214,12 @@ int flock_gae(int T, int n, const float *reward_dev, const float *value_dev, flo
 int env_step_policy(flock_env *env, const uint16_t *weights_bf16_dev, int32_t *actions_inout_dev,
                     float *reward_dev, int32_t *coll_dev, float *logits_dev, float *obs_dev);
 
-/* env_step from and to host memory: copies the actions in, steps, copies the
- * outputs out, and waits for the stream.  Returns after the outputs are in
- * the host buffers. */
+/* env_step from and to host memory, waiting for the stream: returns after
+ * the outputs are in the host buffers.  Page-locked, mapped actions
+ * (cudaHostAlloc / pinned tensors; the GPU reaches them coherently over
+ * NVLink-C2C on Grace-Blackwell) are read by the step's first kernel in
+ * place, others are copied in; the outputs are copied out of the
+ * workspace. */
 int env_step_host(flock_env *env, const int32_t *actions_host, float *obs_host,
                   float *reward_host, int32_t *coll_host);
 

@@ -818,11 +818,21 @@ extern "C" int env_step_host(flock_env *e, const int32_t *act_h, float *obs_h, f
   const size_t n = (size_t)e->n;
   if (n > 0 && (!act_h || !obs_h || !rew_h || !coll_h)) return FLOCK_EINVAL;
   const Layout &L = e->lay;
-  int32_t *act = (int32_t *)(e->ws + L.h_act);
+  const int32_t *act = (const int32_t *)(e->ws + L.h_act);
   float *obs = (float *)(e->ws + L.h_obs);
   float *rew = (float *)(e->ws + L.h_rew);
   int32_t *coll = (int32_t *)(e->ws + L.h_coll);
-  if (n > 0) CK(cudaMemcpyAsync(act, act_h, n * 4, cudaMemcpyHostToDevice, e->stream));
+  // Page-locked, mapped actions (Grace-Blackwell reaches host memory
+  // coherently over NVLink-C2C) are read by the binning kernel in place; the
+  // outputs go through the workspace and one copy each (written in place,
+  // their scattered rows crossed the link more slowly than one bulk copy).
+  void *da = nullptr;
+  if (n > 0 && cudaHostGetDevicePointer(&da, (void *)act_h, 0) == cudaSuccess) {
+    act = (const int32_t *)da;
+  } else {
+    (void)cudaGetLastError();
+    if (n > 0) CK(cudaMemcpyAsync((void *)act, act_h, n * 4, cudaMemcpyHostToDevice, e->stream));
+  }
   int rc = env_step(e, act, obs, rew, coll);
   if (rc) return rc;
   if (n > 0) {

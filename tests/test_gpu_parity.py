@@ -281,23 +281,39 @@ def test_checkpoint_resume_is_identical():
     env2.close()
 
 
-def test_host_buffer_step_matches_device_step():
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_step_matches_device_step(pinned):
+    """Host buffers: page-locked actions are read by the kernels in place
+    (mapped host memory), pageable ones are copied in; the two host steps,
+    then a device step, all match the oracle."""
     n = 5000
     side = fi.side_for(n)
     p = fi.default_params(side)
     st0 = fi.initial_state(n, side, 12)
-    acts = fi.random_actions(n, 2, 12)
+    acts = fi.random_actions(n, 3, 12)
     env = F.FlockEnv(p, n, device=DEV)
     env.reset(torch.from_numpy(st0).to(DEV))
-    obs_h = torch.empty((n, 18), dtype=torch.float32).pin_memory()
-    rew_h = torch.empty(n, dtype=torch.float32).pin_memory()
-    coll_h = torch.empty(n, dtype=torch.int32).pin_memory()
-    act_h = torch.from_numpy(acts[0]).pin_memory()
-    F.env_step_host(env.env, act_h, obs_h, rew_h, coll_h)
-    o, _ = oracle_run(p, st0, acts[:1])
-    assert np.array_equal(obs_h.numpy(), o[1][1])
-    assert np.array_equal(rew_h.numpy(), o[1][2])
-    assert np.array_equal(coll_h.numpy(), o[1][3])
+    o, _ = oracle_run(p, st0, acts)
+    for t in range(2):
+        if pinned:
+            obs_h = torch.empty((n, 18), dtype=torch.float32).pin_memory()
+            rew_h = torch.empty(n, dtype=torch.float32).pin_memory()
+            coll_h = torch.empty(n, dtype=torch.int32).pin_memory()
+            act_h = torch.from_numpy(acts[t]).pin_memory()
+            F.env_step_host(env.env, act_h, obs_h, rew_h, coll_h)
+            got = (obs_h.numpy(), rew_h.numpy(), coll_h.numpy())
+        else:
+            obs_n = np.zeros((n, 18), np.float32)
+            rew_n = np.zeros(n, np.float32)
+            coll_n = np.zeros(n, np.int32)
+            F.env_step_host(env.env, np.ascontiguousarray(acts[t]), obs_n, rew_n, coll_n)
+            got = (obs_n, rew_n, coll_n)
+        assert np.array_equal(got[0], o[t + 1][1]), t
+        assert np.array_equal(got[1], o[t + 1][2]), t
+        assert np.array_equal(got[2], o[t + 1][3]), t
+    obs, rew, coll = env.step(torch.from_numpy(acts[2]).to(DEV))
+    assert np.array_equal(obs.cpu().numpy(), o[3][1])
+    assert env.error() == 0
     env.close()
 
 
