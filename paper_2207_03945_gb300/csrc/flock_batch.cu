@@ -92,7 +92,7 @@ __device__ __forceinline__ int find_inst(const int *pre, int n, int x) {
 // SPLIT: phases A-C only; the neighbour scan runs as the next launch
 // (k_batch_neigh), where it has the registers of a kernel of its own.
 template <int H, int V, bool SPLIT>
-__global__ void __launch_bounds__(kBatchBlock) k_batch_step(const BatchDev *__restrict__ d, Inst *insts,
+__global__ void __launch_bounds__(kBatchBlock, SPLIT ? 6 : 1) k_batch_step(const BatchDev *__restrict__ d, Inst *insts,
                                                           const int *__restrict__ apre,
                                                           const int *__restrict__ cpre,
                                                           unsigned *ctr, unsigned spin_limit) {
@@ -235,11 +235,13 @@ static size_t neigh_smem(int v) {
   return (size_t)(kNeighBlock / 32) * (sizeof(Inst) + direct_warp_bytes(v));
 }
 
-// Dynamic shared memory of the persistent kernel: the scan tile or the tile
-// prefix, and (fused form) the per-warp areas of phase D.
-static size_t batch_smem(int v, bool split) {
+// Dynamic shared memory of the persistent kernel: the scan tile or the prefix
+// of max_tiles scan tiles, and (fused form) the per-warp areas of phase D.
+// Sized by the batch's cell capacity, so that the binning-only kernel of the
+// two-launch form fits six blocks per SM.
+static size_t batch_smem(int v, bool split, int max_tiles) {
   const size_t scan = (size_t)(kScanTile + 34) * 4;
-  const size_t prefix = (size_t)(kMaxScanTiles + 1) * 4;
+  const size_t prefix = (size_t)(max_tiles + 1) * 4;
   size_t m = scan > prefix ? scan : prefix;
   if (split) return m;
   const size_t warps =
@@ -437,7 +439,7 @@ extern "C" int env_batch_set(flock_batch *b, int n_inst, const flock_params *par
   if (n_inst > 0 && (v != b->v || layout != b->layout)) {
     // the kernel variant (and its shared memory) depends on v and the layout
     KFn fn = batch_kernel(b->halo, v, layout, b->split);
-    const size_t sm = batch_smem(v, b->split);
+    const size_t sm = batch_smem(v, b->split, (b->max_cells + kScanTile - 1) / kScanTile);
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -504,7 +506,7 @@ static int batch_enqueue(flock_batch *b, cudaStream_t s) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(b->grid);
   cfg.blockDim = dim3(kBatchBlock);
-  cfg.dynamicSmemBytes = batch_smem(b->v, b->split);
+  cfg.dynamicSmemBytes = batch_smem(b->v, b->split, (b->max_cells + kScanTile - 1) / kScanTile);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
