@@ -723,7 +723,7 @@ def main():
     e2e = {"value": world * n * e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": n * 4, "d2h_bytes_per_step": n * (env.obs_dim + 2) * 4,
            "call": "env_step_host (pinned host buffers: the actions read in place over "
-                   "NVLink-C2C, the outputs copied out; synchronous)"}
+                   "NVLink-C2C, the outputs copied out by one kernel; synchronous)"}
 
     batched = single_fused = None
     if not args.no_batched:

@@ -218,8 +218,9 @@ int env_step_policy(flock_env *env, const uint16_t *weights_bf16_dev, int32_t *a
  * the outputs are in the host buffers.  Page-locked, mapped actions
  * (cudaHostAlloc / pinned tensors; the GPU reaches them coherently over
  * NVLink-C2C on Grace-Blackwell) are read by the step's first kernel in
- * place, others are copied in; the outputs are copied out of the
- * workspace. */
+ * place, others are copied in.  The outputs are written to the workspace,
+ * then copied out: to page-locked, mapped output buffers by one copy kernel,
+ * to others by one copy per buffer. */
 int env_step_host(flock_env *env, const int32_t *actions_host, float *obs_host,
                   float *reward_host, int32_t *coll_host);
 

@@ -6,6 +6,7 @@
 //   k_scan        phase B   one block per scan tile of 1024 cells
 //   k_scatter     phase C   grid-stride over agents and cells
 //   k_neighbours  phase D   one block per tile of cells
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -115,6 +116,39 @@ __global__ void k_neighbours_policy(const Inst *__restrict__ gI, Bufs B,
     phaseD_direct<H, 8, true>(sI, gp0, min(gp0 + 32, sI.n), B, W, err, &pc);
   }
   if (err) atomicOr(B.err, err);
+}
+
+// Copies a step's outputs (observations, rewards, collision counts) from the
+// workspace to page-locked, mapped host buffers: one kernel instead of one
+// copy per buffer, 16 bytes per store where both ends are 16-byte aligned
+// (else 4).  Every size is a multiple of 4 bytes and every pointer 4-byte
+// aligned (checked by the host).
+struct CopyOut {
+  const char *src[3];
+  char *dst[3];
+  size_t bytes[3];
+};
+
+__global__ void __launch_bounds__(256) k_copy_out(CopyOut J) {
+  pdl_wait();
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const char *src = J.src[k];
+    char *dst = J.dst[k];
+    const size_t nb = J.bytes[k];
+    size_t done = 0;
+    if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0) {
+      const size_t n16 = nb / 16;
+      const int4 *s4 = reinterpret_cast<const int4 *>(src);
+      int4 *d4 = reinterpret_cast<int4 *>(dst);
+      for (size_t t = tid; t < n16; t += stride) d4[t] = s4[t];
+      done = n16 * 16;
+    }
+    for (size_t t = done + tid * 4; t < nb; t += stride * 4)
+      *reinterpret_cast<int *>(dst + t) = *reinterpret_cast<const int *>(src + t);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -395,6 +429,7 @@ struct flock_env {
   Bufs bufs;
   int n_scan_tiles;
   int scatter_grid;
+  int copy_grid;  // k_copy_out (host-buffer step)
   size_t smemD;
   int timing;
   cudaEvent_t ev[5];
@@ -509,6 +544,9 @@ extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, v
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int g = (n + 255) / 256;
   e->scatter_grid = g < 1 ? 1 : (g > 4 * sms ? 4 * sms : g);
+  // 16-byte units of the outputs, one per thread, at most 8 blocks per SM
+  const size_t units = ((size_t)n * e->inst.obs_dim * 4 + (size_t)n * 8) / 16;
+  e->copy_grid = (int)std::max<size_t>(1, std::min<size_t>((units + 255) / 256, (size_t)sms * 8));
   e->smemD = e->tuning.mode == 1
                  ? phaseD_smem_bytes(e->inst.cap, e->inst.v, e->tuning.block)
                  : (size_t)(e->tuning.block / 32) *
@@ -823,9 +861,10 @@ extern "C" int env_step_host(flock_env *e, const int32_t *act_h, float *obs_h, f
   float *rew = (float *)(e->ws + L.h_rew);
   int32_t *coll = (int32_t *)(e->ws + L.h_coll);
   // Page-locked, mapped actions (Grace-Blackwell reaches host memory
-  // coherently over NVLink-C2C) are read by the binning kernel in place; the
-  // outputs go through the workspace and one copy each (written in place,
-  // their scattered rows crossed the link more slowly than one bulk copy).
+  // coherently over NVLink-C2C) are read by the binning kernel in place.  The
+  // outputs go through the workspace (written in place, their scattered rows
+  // crossed the link more slowly than a bulk copy), then to mapped host
+  // buffers by one copy kernel, else by one copy each.
   void *da = nullptr;
   if (n > 0 && cudaHostGetDevicePointer(&da, (void *)act_h, 0) == cudaSuccess) {
     act = (const int32_t *)da;
@@ -836,9 +875,32 @@ extern "C" int env_step_host(flock_env *e, const int32_t *act_h, float *obs_h, f
   int rc = env_step(e, act, obs, rew, coll);
   if (rc) return rc;
   if (n > 0) {
-    CK(cudaMemcpyAsync(obs_h, obs, n * e->inst.obs_dim * 4, cudaMemcpyDeviceToHost, e->stream));
-    CK(cudaMemcpyAsync(rew_h, rew, n * 4, cudaMemcpyDeviceToHost, e->stream));
-    CK(cudaMemcpyAsync(coll_h, coll, n * 4, cudaMemcpyDeviceToHost, e->stream));
+    const size_t ob = n * e->inst.obs_dim * 4;
+    void *dobs = nullptr, *drew = nullptr, *dcoll = nullptr;
+    const bool mapped =
+        cudaHostGetDevicePointer(&dobs, obs_h, 0) == cudaSuccess &&
+        cudaHostGetDevicePointer(&drew, rew_h, 0) == cudaSuccess &&
+        cudaHostGetDevicePointer(&dcoll, coll_h, 0) == cudaSuccess &&
+        ((reinterpret_cast<uintptr_t>(dobs) | reinterpret_cast<uintptr_t>(drew) |
+          reinterpret_cast<uintptr_t>(dcoll)) & 3) == 0;
+    if (mapped) {
+      CopyOut J;
+      J.src[0] = (const char *)obs;
+      J.src[1] = (const char *)rew;
+      J.src[2] = (const char *)coll;
+      J.dst[0] = (char *)dobs;
+      J.dst[1] = (char *)drew;
+      J.dst[2] = (char *)dcoll;
+      J.bytes[0] = ob;
+      J.bytes[1] = n * 4;
+      J.bytes[2] = n * 4;
+      CK(launch(true, k_copy_out, e->copy_grid, 256, 0, e->stream, J));
+    } else {
+      (void)cudaGetLastError();
+      CK(cudaMemcpyAsync(obs_h, obs, ob, cudaMemcpyDeviceToHost, e->stream));
+      CK(cudaMemcpyAsync(rew_h, rew, n * 4, cudaMemcpyDeviceToHost, e->stream));
+      CK(cudaMemcpyAsync(coll_h, coll, n * 4, cudaMemcpyDeviceToHost, e->stream));
+    }
   }
   CK(cudaStreamSynchronize(e->stream));
   return FLOCK_OK;

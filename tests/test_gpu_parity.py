@@ -281,12 +281,15 @@ def test_checkpoint_resume_is_identical():
     env2.close()
 
 
-@pytest.mark.parametrize("pinned", [True, False])
-def test_host_buffer_step_matches_device_step(pinned):
+@pytest.mark.parametrize("buffers", ["pinned", "pinned_offset", "pageable"])
+def test_host_buffer_step_matches_device_step(buffers):
     """Host buffers: page-locked actions are read by the kernels in place
-    (mapped host memory), pageable ones are copied in; the two host steps,
-    then a device step, all match the oracle."""
-    n = 5000
+    (mapped host memory) and page-locked outputs written by the copy kernel
+    (16-byte stores; 4-byte ones for buffers one element off a 16-byte
+    boundary), pageable ones are copied in and out; the two host steps, then
+    a device step, all match the oracle.  4,999 agents: no buffer is a whole
+    number of 16-byte units."""
+    n = 4999
     side = fi.side_for(n)
     p = fi.default_params(side)
     st0 = fi.initial_state(n, side, 12)
@@ -294,11 +297,12 @@ def test_host_buffer_step_matches_device_step(pinned):
     env = F.FlockEnv(p, n, device=DEV)
     env.reset(torch.from_numpy(st0).to(DEV))
     o, _ = oracle_run(p, st0, acts)
+    k = 1 if buffers == "pinned_offset" else 0
     for t in range(2):
-        if pinned:
-            obs_h = torch.empty((n, 18), dtype=torch.float32).pin_memory()
-            rew_h = torch.empty(n, dtype=torch.float32).pin_memory()
-            coll_h = torch.empty(n, dtype=torch.int32).pin_memory()
+        if buffers != "pageable":
+            obs_h = torch.empty(n * 18 + k, dtype=torch.float32).pin_memory()[k:].view(n, 18)
+            rew_h = torch.empty(n + k, dtype=torch.float32).pin_memory()[k:]
+            coll_h = torch.empty(n + k, dtype=torch.int32).pin_memory()[k:]
             act_h = torch.from_numpy(acts[t]).pin_memory()
             F.env_step_host(env.env, act_h, obs_h, rew_h, coll_h)
             got = (obs_h.numpy(), rew_h.numpy(), coll_h.numpy())
