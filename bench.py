@@ -282,7 +282,8 @@ def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256,
     [100, 20000] (density 0.1 each), all advanced by one persistent kernel
     per step, replayed from a CUDA graph.  With `sizes`, those instances
     instead.  Returns a dict for the JSON line."""
-    if sizes is None:
+    mix = sizes is None
+    if mix:
         sizes = fi.batch_sizes(n_inst, 100, 20000, seed)
     n_inst = len(sizes)
     params = [fi.default_params(fi.side_for(n)) for n in sizes]
@@ -352,7 +353,8 @@ def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256,
             "workload": "batched: %d flock instances, agent counts %s (seed %d, %d agents), "
                         "density 0.1, view radius 5, 8 sectors, fov 250 deg, one persistent "
                         "cooperative kernel per step, CUDA graph"
-                        % (n_inst, "log-uniform in [100, 20000]" if n_inst > 1 else str(sizes),
+                        % (n_inst, "log-uniform in [100, 20000]" if mix else
+                           "%d x %d" % (n_inst, sizes[0]) if len(set(sizes)) == 1 else str(sizes),
                            seed, total),
             "roofline": {"bound": "hbm",
                          "kernel": "k_batch_step" if bmode == 2 else "k_batch_step + k_batch_neigh",
@@ -733,6 +735,10 @@ def main():
         # the same 50,000-agent instance as the headline, as a batch of one
         single_fused = run_batched(F, torch, dev, stream, args.steps, args.warmup, flush,
                                    seed=rank_seed(rank), sizes=[n], world=world, tune=False)
+        # like for like with the headline: its agents as ten 5,000-agent instances
+        ten = run_batched(F, torch, dev, stream, args.steps, args.warmup, flush,
+                          seed=rank_seed(rank), sizes=[n // 10] * 10, world=world, tune=False,
+                          tuning=batched["tuning"])
     serving = None
     if args.serve_seconds > 0:
         serving = {
@@ -784,6 +790,7 @@ def main():
         if batched is not None:
             line["batched"] = batched
             line["single_instance_persistent"] = single_fused
+            line["batched_10_instances"] = ten
         if policy is not None:
             line["policy"] = policy
         if paper is not None:

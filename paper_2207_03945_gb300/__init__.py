@@ -394,6 +394,39 @@ def env_batch_set(batch, params_list, n_agents, states, reset=None):
     batch.states = list(states)  # keep the tensors alive while active
 
 
+def env_batch_set_rows(batch, params_c, n_agents, arena, rows, reset=None):
+    """Active set whose states are row ranges of one arena ((R, 4) float32 on
+    the device): instance k's state is arena[rows[k] : rows[k] + n_agents[k]].
+    params_c: FlockParams structs (from params_from_dict, built once per
+    instance).  For callers that change the set often, such as the serving
+    loop: one check of the arena and of the row ranges, no per-instance tensor
+    checks or dict conversions."""
+    import numpy as np
+    torch = _torch()
+    if not isinstance(arena, torch.Tensor) or arena.dim() != 2 or arena.shape[1] != 4:
+        raise FlockError("arena must be an (R, 4) tensor")
+    k = len(params_c)
+    n = np.asarray(n_agents, dtype=np.int64).reshape(-1)
+    r = np.asarray(rows, dtype=np.int64).reshape(-1)
+    if len(n) != k or len(r) != k:
+        raise FlockError("params, agent counts and rows differ in length")
+    if k and (n.min() < 0 or r.min() < 0 or int((r + n).max()) > arena.shape[0]):
+        raise FlockError("row range outside the arena")
+    if any(not isinstance(q, _abi.FlockParams) for q in params_c):
+        raise FlockError("params_c must be FlockParams structs")
+    base = _ptr(arena, torch.float32, name="arena").value
+    P = (_abi.FlockParams * max(k, 1))(*params_c)
+    N = np.ascontiguousarray(n, dtype=np.int32) if k else np.zeros(1, np.int32)
+    S = (base + 16 * r).astype(np.uint64) if k else np.zeros(1, np.uint64)
+    R = (np.asarray([bool(x) for x in reset], dtype=np.int32) if reset is not None and k
+         else np.zeros(max(k, 1), np.int32))
+    _abi.check(_abi.lib.env_batch_set(batch.handle, k, P,
+                                      N.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                      S.ctypes.data_as(ctypes.POINTER(ctypes.c_void_p)),
+                                      R.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+    batch.states = [arena]  # keep the arena alive while active
+
+
 def env_batch_step(batch, actions, obs, reward, coll):
     torch = _torch()
     _abi.check(_abi.lib.env_batch_step(batch.handle, _ptr(actions, torch.int32, name="actions"),
@@ -457,6 +490,14 @@ class FlockBatch:
 
     def set(self, params_list, n_agents, states, reset=None):
         env_batch_set(self.batch, params_list, n_agents, states, reset)
+        self._offsets(n_agents)
+
+    def set_rows(self, params_c, n_agents, arena, rows, reset=None):
+        """The active set as row ranges of one arena (env_batch_set_rows)."""
+        env_batch_set_rows(self.batch, params_c, n_agents, arena, rows, reset)
+        self._offsets(n_agents)
+
+    def _offsets(self, n_agents):
         self.offsets = []
         off = 0
         for n in n_agents:

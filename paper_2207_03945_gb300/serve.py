@@ -45,6 +45,7 @@ class Session:
     seed: int
     t_arrival: float
     params: dict = None
+    params_c: object = None   # the same as the library's struct, built once
     offset: int = -1          # first agent row of its state in the arena
     steps_done: int = 0
     t_admit: float = None
@@ -167,8 +168,9 @@ class FlockServer:
 
         import torch
 
-        from . import FlockBatch, flock_default_params, flock_instance_cells
+        from . import FlockBatch, _abi, flock_default_params, flock_instance_cells
         self.torch = torch
+        self._params_c = _abi.params_from_dict
         self.dev = torch.device(device)
         self.stream = stream
         self.tuning = tuning
@@ -195,18 +197,17 @@ class FlockServer:
     def submit(self, n, steps, seed, t_arrival=None):
         p = self.params_fn(n)
         s = Session(self.next_sid, int(n), self.cells_fn(p), int(steps), int(seed),
-                    time.perf_counter() if t_arrival is None else t_arrival, params=p)
+                    time.perf_counter() if t_arrival is None else t_arrival, params=p,
+                    params_c=self._params_c(p))
         self.next_sid += 1
         return s if self.sched.submit(s) else None
 
     def _sync_set(self):
         ids = [s.sid for s in self.sched.active]
         if ids != self._active_ids or any(s.reset for s in self.sched.active):
-            torch = self.torch
             act = self.sched.active
-            self.batch.set([s.params for s in act], [s.n for s in act],
-                           [self.arena[s.offset:s.offset + s.n] for s in act],
-                           reset=[s.reset for s in act])
+            self.batch.set_rows([s.params_c for s in act], [s.n for s in act], self.arena,
+                                [s.offset for s in act], reset=[s.reset for s in act])
             self._active_ids = ids
             self.set_changes += 1
 
@@ -228,16 +229,13 @@ class FlockServer:
             return 0
         t0 = time.perf_counter()
         self._sync_set()
-        off = 0
-        if True:
-            for s in act:
-                view = self.actions[off:off + s.n]
-                if self.action_fn is not None:
-                    self.action_fn(s, s.steps_done, view)
-                off += s.n
-            if self.action_fn is None:
-                self.actions[:off].random_(0, 9, generator=self.gen)
-            obs, rew, coll = self.batch.step(self.actions[:off])
+        off = self.batch.n_total
+        if self.action_fn is not None:
+            for s, o in zip(act, self.batch.offsets):
+                self.action_fn(s, s.steps_done, self.actions[o:o + s.n])
+        else:
+            self.actions[:off].random_(0, 9, generator=self.gen)
+        obs, rew, coll = self.batch.step(self.actions[:off])
         if self.stream is not None:
             self.stream.synchronize()
         else:

@@ -112,3 +112,24 @@ def test_obs_layouts():
     p["obs_layout"] = 2
     with pytest.raises(F.FlockError):
         F.flock_obs_dim(p)
+
+
+def test_set_rows_argument_checks():
+    """The row-range form of the batch set rejects, before any call into the
+    library, ranges outside the arena, mismatched lengths, dicts in place of
+    parameter structs and a host arena."""
+    F = _lib()
+    torch = pytest.importorskip("torch")
+    from paper_2207_03945_gb300 import _abi
+    p = _abi.params_from_dict(fi.default_params(100.0))
+    arena = torch.zeros((100, 4))
+    with pytest.raises(F.FlockError):  # rows 90..109 of 100
+        F.env_batch_set_rows(None, [p], [20], arena, [90])
+    with pytest.raises(F.FlockError):
+        F.env_batch_set_rows(None, [p, p], [20], arena, [0])
+    with pytest.raises(F.FlockError):
+        F.env_batch_set_rows(None, [fi.default_params(100.0)], [20], arena, [0])
+    with pytest.raises(F.FlockError):
+        F.env_batch_set_rows(None, [p], [20], torch.zeros((100, 3)), [0])
+    with pytest.raises(F.FlockError):  # a host tensor is not device memory
+        F.env_batch_set_rows(None, [p], [20], arena, [0])

@@ -95,6 +95,34 @@ def test_batch_equals_single_environment():
     b.close()
 
 
+def test_set_rows_equals_set():
+    """The active set given as row ranges of one arena (the serving loop's
+    form, instances in an order and at rows unlike their flattened order)
+    steps exactly like the same set given as one tensor per instance."""
+    sizes = [3000, 150, 7000]
+    insts = make_instances(sizes, 210)
+    rows = [9000, 0, 1000]  # arena rows of each instance
+    arena = torch.zeros((16000, 4), dtype=torch.float32, device=DEV)
+    for (p, n, st), r in zip(insts, rows):
+        arena[r:r + n] = torch.from_numpy(st).to(DEV)
+    b1, b2 = batch_for(insts), batch_for(insts)
+    b1.set([p for p, _, _ in insts], sizes, [torch.from_numpy(st).to(DEV) for _, _, st in insts],
+           reset=[1, 1, 1])
+    from paper_2207_03945_gb300 import _abi
+    b2.set_rows([_abi.params_from_dict(p) for p, _, _ in insts], sizes, arena, rows,
+                reset=[1, 1, 1])
+    assert b1.offsets == b2.offsets and b1.n_total == b2.n_total
+    acts = fi.random_actions(sum(sizes), 3, 21)
+    for t in range(3):
+        a = torch.from_numpy(acts[t]).to(DEV)
+        o1, r1, c1 = (x.cpu().numpy().copy() for x in b1.step(a))
+        o2, r2, c2 = (x.cpu().numpy().copy() for x in b2.step(a))
+        assert np.array_equal(o1, o2) and np.array_equal(r1, r2) and np.array_equal(c1, c2), t
+    assert b1.error() == 0 and b2.error() == 0
+    b1.close()
+    b2.close()
+
+
 @MODES
 def test_active_set_changes_between_steps(mode):
     """Sessions leave and join between steps; the graph is reused (mode 3:
