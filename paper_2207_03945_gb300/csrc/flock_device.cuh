@@ -824,7 +824,7 @@ struct DirectArea {
   unsigned long long *acc;  // [32]: each owner lane's reward sum (units of 2^-K)
   unsigned *accp;           // [3][32]: pieces of the current drain (bits 0-23, 24-47, 48-)
   int *nin, *ncoll;
-  unsigned *md;
+  unsigned *md;  // per-sector minimum distance (bits of a non-negative float)
   int *cn;
 };
 
@@ -935,14 +935,18 @@ __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W,
     if (valid) {
       const float dx = E.x, dy = E.y, d2 = E.z;
       const bool coll = d2 < I.RC2;
+      // the distance: the ramp term's, and the sector minimum's (sqrt is
+      // monotone, so the minimum of the rounded roots is the rounded root of
+      // the minimum d^2)
+      const float dist = fsqrt(d2);
       if constexpr (!TAG) {
         if (!coll) {
-          const float t = fmul(fsub(I.RV, fsqrt(d2)), I.INV_SPAN);
+          const float t = fmul(fsub(I.RV, dist), I.INV_SPAN);
           add_term<PIECES>(I, W, o, float_int_u64(fmul(t, I.scaleK)));
         }
       } else {
         if (tio == 0 && tj == 0 && !coll) {  // a runner near a runner
-          const float t = fmul(fsub(I.RV, fsqrt(d2)), I.INV_SPAN);
+          const float t = fmul(fsub(I.RV, dist), I.INV_SPAN);
           add_term<PIECES>(I, W, o, float_int_u64(fmul(t, I.scaleK)));
         } else if (tio == 1 && tj == 0 && coll) {
           add_term<PIECES>(I, W, o, (unsigned long long)I.PK);  // a chaser touching a runner
@@ -956,7 +960,7 @@ __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W,
         int key = E8.sector(I, p);
         if (key >= 0) {
           if (TAG) key += tj * v;  // colour channel of the neighbour's type
-          atomicMin(&W.md[o * vs + key], __float_as_uint(d2));
+          atomicMin(&W.md[o * vs + key], __float_as_uint(dist));
           atomicAdd(&W.cn[o * vs + key], 1);
         }
       }
@@ -1448,9 +1452,12 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
     B.coll[I.agent_base + i] = ncoll;
     if ((long long)nin > I.NMAX) err |= FLOCK_ERR_OVERFLOW;
   }
-  // observation rows, written whole and contiguous (and, with the policy,
-  // also as BF16 rows of the warp's tile); tag rows are the 2v distances
-  const int P = TAG ? 2 * v : v + 1;
+  // observation rows (and, with the policy, also BF16 rows of the warp's
+  // tile).  The last entry of a flock row, (speed, heading) (layout 1: the
+  // speed), comes from the agent's own lane; the v sector entries of several
+  // rows at a time from all lanes, each row's contiguous.  Tag rows are the
+  // 2v distances.
+  const int P = TAG ? 2 * v : v;  // entries per row from the sector arrays
   const int rpi = P <= 32 ? 32 / P : 1;
   const int my_r = P <= 32 ? lane / P : 0, my_e = P <= 32 ? lane % P : lane;
   float *obs = B.obs ? B.obs + I.obs_base : nullptr;
@@ -1463,29 +1470,32 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
     for (int w2 = 0; w2 < kTileS / 2; ++w2)
       if (w2 >= 9 || lane >= nb) row[w2] = 0u;
   }
+  if (!TAG && have && lane < A) {
+    const float2 val = make_float2(ts.y, ts.x);
+    if (obs) {
+      float *row = obs + (long long)i * I.obs_dim;
+      if (lay0) *reinterpret_cast<float2 *>(row + 2 * v) = val;
+      else row[v] = val.x;
+    }
+    if (POL) *reinterpret_cast<unsigned *>(pc->tile + lane * kTileS + 2 * v) = pack_bf16(val.x, val.y);
+  }
   for (int rb = 0; rb < nb; rb += rpi) {
     const int r = min(rb + my_r, 31);
     const int ir = __shfl_sync(kFull, i, r);
-    const float sr_ = __shfl_sync(kFull, ts.y, r), tr = __shfl_sync(kFull, ts.x, r);
     if (rb + my_r < nb && my_r < rpi) {
       for (int e = my_e; e < P; e += 32) {
         if (TAG) {
           const int ck = W.cn[r * vs + e];
           if (obs)
-            obs[(long long)ir * I.obs_dim + e] = ck ? fsqrt(__uint_as_float(W.md[r * vs + e])) : I.RV;
+            obs[(long long)ir * I.obs_dim + e] = ck ? __uint_as_float(W.md[r * vs + e]) : I.RV;
           continue;
         }
-        float2 val;
-        if (e < v) {
-          const int ck = W.cn[r * v + e];
-          val = make_float2(ck ? fsqrt(__uint_as_float(W.md[r * v + e])) : I.RV, (float)ck);
-        } else {
-          val = make_float2(sr_, tr);
-        }
+        const int ck = W.cn[r * v + e];
+        const float2 val = make_float2(ck ? __uint_as_float(W.md[r * v + e]) : I.RV, (float)ck);
         if (obs) {
           float *row = obs + (long long)ir * I.obs_dim;
           if (lay0) *reinterpret_cast<float2 *>(row + 2 * e) = val;
-          else row[e] = val.x;  // layout 1: the distance, or the speed
+          else row[e] = val.x;  // layout 1: the distance only
         }
         if (POL)
           *reinterpret_cast<unsigned *>(pc->tile + r * kTileS + 2 * e) = pack_bf16(val.x, val.y);
