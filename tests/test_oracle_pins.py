@@ -169,3 +169,19 @@ def test_tag_type_swap_swaps_channels():
 
 def test_tag_motion_closed_form():
     pins.check_tag_motion()
+
+
+def test_rounded_sqrt_is_monotone():
+    """The identity the neighbour kernels rely on when they keep each sector's
+    minimum as a distance: correctly rounded float32 sqrt is monotone, so the
+    minimum of the rounded roots is the rounded root of the minimum d^2 (the
+    observation's nearest distance).  Checked on every 61st float32 bit
+    pattern in [0, 26) and on random sets of squared distances."""
+    bits = np.arange(0, np.float32(26.0).view(np.uint32), 61, dtype=np.uint32)
+    x = bits.view(np.float32)
+    r = np.sqrt(x)
+    assert r.dtype == np.float32 and np.all(np.diff(r) >= 0)
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        d2 = (rng.random(rng.integers(1, 40)) * 25.0).astype(np.float32)
+        assert np.sqrt(d2).min().view(np.uint32) == np.sqrt(d2.min()).view(np.uint32)
