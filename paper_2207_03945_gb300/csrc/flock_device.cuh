@@ -1317,6 +1317,21 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
     cy = cell_of(yi, I);
   }
   const int ti = TAG && have ? (int)(B.stype[gp] != 0) : 0;  // own type
+  // the cell starts of the stencil rows are read before anything waits on
+  // the agent's own state row, so that the two reads are in flight together
+  // stencil columns [cx - H, cx + H] split into runs that do not wrap
+  const int vlo = cx - H, vhi = cx + H + 1;
+  const int ma = max(vlo, 0), mb = min(vhi, nc);  // interior run
+  const bool lw = vlo < 0, rw = vhi > nc;         // left / right boundary runs
+  const bool wrap_any = __any_sync(kFull, have && (lw || rw || cy - H < 0 || cy + H >= nc));
+  const int *cst = B.cell_start;
+  int ra[2 * H + 1], rn[2 * H + 1];
+#pragma unroll
+  for (int r = 0; r < 2 * H + 1; ++r) {
+    const int rowg = I.cell_base + wrapi(cy - H + r, nc) * nc;
+    ra[r] = have ? cst[rowg + ma] : 0;
+    rn[r] = have ? cst[rowg + mb] - ra[r] : 0;
+  }
   float c = 1.f, sn = 0.f;
   det_sincos(ts.x, c, sn);
   const float ux = fadd(fmul(c, I.CF), fmul(sn, I.SF));
@@ -1345,19 +1360,6 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
     }
   }
   int nin = 0, ncoll = 0;
-  // stencil columns [cx - H, cx + H] split into runs that do not wrap
-  const int vlo = cx - H, vhi = cx + H + 1;
-  const int ma = max(vlo, 0), mb = min(vhi, nc);  // interior run
-  const bool lw = vlo < 0, rw = vhi > nc;         // left / right boundary runs
-  const bool wrap_any = __any_sync(kFull, have && (lw || rw || cy - H < 0 || cy + H >= nc));
-  const int *cst = B.cell_start;
-  int ra[2 * H + 1], rn[2 * H + 1];
-#pragma unroll
-  for (int r = 0; r < 2 * H + 1; ++r) {
-    const int rowg = I.cell_base + wrapi(cy - H + r, nc) * nc;
-    ra[r] = have ? cst[rowg + ma] : 0;
-    rn[r] = have ? cst[rowg + mb] - ra[r] : 0;
-  }
   __syncwarp();
   int qn = 0;
   const int self = have ? gp : -1;
