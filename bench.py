@@ -745,10 +745,11 @@ def main():
             "as_specified": run_serving(dev, args.serve_seconds, seed=rank_seed(rank)),
             "saturated_small_budget": run_serving(dev, max(5.0, args.serve_seconds / 2),
                                                   seed=rank_seed(rank) + 1, budget=10 ** 8,
-                                                  backlog=200),
+                                                  backlog=5000),
             "workload": "serving: Poisson arrivals 50/s, agents log-uniform in [500, 50000], "
                         "episodes uniform in [100, 2000] steps, 100 GB budget, random actions; "
-                        "plus a saturated run (200 sessions queued at t=0, 100 MB budget)"}
+                        "plus a saturated run (5,000 sessions queued at t=0, more than the run "
+                        "serves, 100 MB budget so that admission binds)"}
     policy = None
     if not args.no_policy:
         policy = run_policy(F, torch, dev, stream, args.steps, args.warmup, flush,

@@ -80,6 +80,7 @@ class SessionScheduler:
         self.admitted = 0
         self.rejected = 0
         self.finished = []
+        self.version = 0  # bumped whenever the active set changes
 
     # -- arena ranges: first fit, coalescing on free --
     def _alloc(self, n):
@@ -135,12 +136,15 @@ class SessionScheduler:
             self.active.append(s)
             self.admitted += 1
             out.append(s)
+        if out:
+            self.version += 1
         return out
 
     def retire(self, now):
         """Remove sessions whose episode is complete; returns them."""
         done = [s for s in self.active if s.steps_done >= s.steps]
         if done:
+            self.version += 1
             self.active = [s for s in self.active if s.steps_done < s.steps]
             for s in done:
                 s.t_done = now
@@ -191,7 +195,8 @@ class FlockServer:
         self.iterations = 0
         self.agent_steps = 0
         self.set_changes = 0
-        self._active_ids = None
+        self._version = None      # scheduler version of the uploaded set
+        self._pending_reset = False
         self.on_step = None  # optional callback(session, obs, reward, coll) after each step
 
     def submit(self, n, steps, seed, t_arrival=None):
@@ -203,12 +208,15 @@ class FlockServer:
         return s if self.sched.submit(s) else None
 
     def _sync_set(self):
-        ids = [s.sid for s in self.sched.active]
-        if ids != self._active_ids or any(s.reset for s in self.sched.active):
+        # re-upload the descriptors when the set changed, and once more after
+        # a step that reset newly admitted sessions (to clear their flags)
+        if self.sched.version != self._version or self._pending_reset:
             act = self.sched.active
+            reset = [s.reset for s in act]
             self.batch.set_rows([s.params_c for s in act], [s.n for s in act], self.arena,
-                                [s.offset for s in act], reset=[s.reset for s in act])
-            self._active_ids = ids
+                                [s.offset for s in act], reset=reset)
+            self._version = self.sched.version
+            self._pending_reset = any(reset)
             self.set_changes += 1
 
     def iteration(self):
@@ -292,6 +300,7 @@ class FlockServer:
             "queue_wait_p50_ms": 1e3 * float(np.percentile(waits, 50)) if waits else None,
             "queue_wait_p99_ms": 1e3 * float(np.percentile(waits, 99)) if waits else None,
             "agent_steps_per_s": self.agent_steps / wall if wall else None,
+            "agents_per_iteration": self.agent_steps / self.iterations if self.iterations else 0,
             "wall_s": wall,
         }
 

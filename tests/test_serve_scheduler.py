@@ -97,3 +97,23 @@ def test_random_workload_keeps_invariants():
         assert sc.used_cells <= sc.max_cells
         free = sum(l for _, l in sc.free) + sum(s.n for s in sc.active)
         assert free == sc.arena_agents
+
+
+def test_version_changes_with_the_active_set_only():
+    """The server re-uploads instance descriptors only when the scheduler's
+    version moved: admissions and retirements bump it, idle calls do not."""
+    sc = serve.SessionScheduler(budget_bytes=10 ** 12, max_slots=4, arena_agents=10 ** 6,
+                                max_cells=10 ** 6)
+    v0 = sc.version
+    assert sc.admit(0.0) == [] and sc.retire(0.0) == [] and sc.version == v0
+    sc.submit(sess(0, 100, steps=2))
+    sc.submit(sess(1, 100, steps=5))
+    sc.admit(0.0)
+    v1 = sc.version
+    assert v1 != v0
+    for s in sc.active:
+        s.steps_done += 1
+    assert sc.retire(0.1) == [] and sc.admit(0.1) == [] and sc.version == v1
+    for s in sc.active:
+        s.steps_done += 1
+    assert [s.sid for s in sc.retire(0.2)] == [0] and sc.version != v1
