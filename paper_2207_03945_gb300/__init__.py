@@ -10,7 +10,6 @@ if the library has not been built (``__graft_entry__.build()``).
 from __future__ import annotations
 
 import ctypes
-import os
 
 from . import _abi
 from ._abi import (FLOCK_ERR_ACTION, FLOCK_ERR_OVERFLOW, FLOCK_ERR_STATE, FLOCK_ERR_TIMEOUT,
@@ -27,7 +26,7 @@ __all__ = [
     "env_get_phase_times", "env_destroy", "FlockEnv", "lib_path", "flock_instance_cells",
     "env_step_policy",
     "flock_batch_workspace_bytes", "env_batch_create", "env_batch_set", "env_batch_step",
-    "env_batch_get_error", "env_batch_set_spin_limit", "env_batch_get_launch",
+    "env_batch_set_rows", "env_batch_get_error", "env_batch_set_spin_limit", "env_batch_get_launch",
     "env_batch_set_timing", "env_batch_get_time", "env_batch_destroy", "FlockBatch",
     "flock_step_static",
 ]
