@@ -230,8 +230,9 @@ class FlockServer:
         now = time.perf_counter()
         self.sched.retire(now)
         for s in self.sched.admit(now):
+            # the client's initial state, copied straight into its arena rows
             st = torch.from_numpy(np.ascontiguousarray(self.state_fn(s), dtype=np.float32))
-            self.arena[s.offset:s.offset + s.n].copy_(st.to(self.dev, non_blocking=False))
+            self.arena[s.offset:s.offset + s.n].copy_(st)
         act = self.sched.active
         if not act:
             return 0
