@@ -133,3 +133,37 @@ def test_set_rows_argument_checks():
         F.env_batch_set_rows(None, [p], [20], torch.zeros((100, 3)), [0])
     with pytest.raises(F.FlockError):  # a host tensor is not device memory
         F.env_batch_set_rows(None, [p], [20], arena, [0])
+
+
+def test_binding_refuses_host_memory_and_bad_shapes():
+    """No CPU fallback: every device entry point of the binding rejects host
+    tensors (and wrong dtypes or shapes) with FlockError before it reaches
+    the library; the host-buffer step rejects arrays of the wrong shape."""
+    import types
+    F = _lib()
+    torch = pytest.importorskip("torch")
+    env = types.SimpleNamespace(handle=None, n=10, obs_dim=18)
+    a = torch.zeros(10, dtype=torch.int32)
+    o = torch.zeros((10, 18))
+    r = torch.zeros(10)
+    c = torch.zeros(10, dtype=torch.int32)
+    calls = [
+        lambda: F.env_step(env, a, o, r, c),
+        lambda: F.env_step_continuous(env, torch.zeros((10, 2)), o, r, c),
+        lambda: F.env_rollout(env, torch.zeros((4, 10), dtype=torch.int32),
+                              torch.zeros((4, 10, 18)), torch.zeros((4, 10)),
+                              torch.zeros((4, 10), dtype=torch.int32)),
+        lambda: F.env_rollout(env, None, o, r, c),
+        lambda: F.flock_gae(torch.zeros((4, 10)), torch.zeros((5, 10)), 0.99, 0.95,
+                            torch.zeros((4, 10)), torch.zeros((4, 10))),
+        lambda: F.env_set_types(env, torch.zeros(10, dtype=torch.uint8)),
+        lambda: F.env_get_state(env, torch.zeros((10, 4))),
+        lambda: F.env_step_host(env, np.zeros(9, np.int32), np.zeros((10, 18), np.float32),
+                                np.zeros(10, np.float32), np.zeros(10, np.int32)),
+        lambda: F.env_step_host(env, np.zeros(10, np.int32), np.zeros((10, 17), np.float32),
+                                np.zeros(10, np.float32), np.zeros(10, np.int32)),
+        lambda: F.env_step_host(env, torch.zeros(10, dtype=torch.int64), o, r, c),
+    ]
+    for k, call in enumerate(calls):
+        with pytest.raises(F.FlockError):
+            call()
