@@ -21,7 +21,7 @@ __all__ = [
     "flock_derive",
     "env_create", "env_reset", "env_step", "env_step_continuous", "env_rollout", "flock_gae",
     "env_set_types",
-    "env_step_host", "env_get_state", "env_set_state",
+    "env_step_host", "env_step_host_bind", "env_get_state", "env_set_state",
     "env_get_error", "env_get_derived", "env_get_tuning", "env_set_timing",
     "env_get_phase_times", "env_destroy", "FlockEnv", "lib_path", "flock_instance_cells",
     "env_step_policy",
@@ -194,26 +194,51 @@ def env_step_policy(env, weights_bf16, actions, reward, coll, logits=None, obs=N
         _ptr(obs, torch.float32, (env.n, env.obs_dim), "obs") if obs is not None else None))
 
 
-def env_step_host(env, actions, obs, reward, coll):
-    """Host-memory step: numpy arrays or pinned CPU tensors; waits for completion."""
+def _host_ptrs(env, actions, obs, reward, coll):
+    """Host pointers of the four buffers of a host-memory step, checked."""
     import numpy as np
+    torch = _torch()
+    n, d = env.n, env.obs_dim
+    np_types = {torch.int32: np.int32, torch.float32: np.float32}
 
     def hp(a, dtype, shape, name):
-        torch = _torch()
         if isinstance(a, torch.Tensor):
             if a.is_cuda or a.dtype != dtype or not a.is_contiguous() or tuple(a.shape) != shape:
                 raise FlockError("%s: bad host tensor" % name)
             return ctypes.c_void_p(a.data_ptr())
-        if not isinstance(a, np.ndarray) or not a.flags.c_contiguous or a.shape != shape:
+        if (not isinstance(a, np.ndarray) or not a.flags.c_contiguous or a.shape != shape
+                or a.dtype != np_types[dtype]):
             raise FlockError("%s: bad host array" % name)
         return ctypes.c_void_p(a.ctypes.data)
 
-    torch = _torch()
-    n, d = env.n, env.obs_dim
-    _abi.check(_abi.lib.env_step_host(env.handle, hp(actions, torch.int32, (n,), "actions"),
-                                      hp(obs, torch.float32, (n, d), "obs"),
-                                      hp(reward, torch.float32, (n,), "reward"),
-                                      hp(coll, torch.int32, (n,), "coll")))
+    return (hp(actions, torch.int32, (n,), "actions"), hp(obs, torch.float32, (n, d), "obs"),
+            hp(reward, torch.float32, (n,), "reward"), hp(coll, torch.int32, (n,), "coll"))
+
+
+def env_step_host(env, actions, obs, reward, coll):
+    """Host-memory step: numpy arrays or pinned CPU tensors; waits for completion."""
+    _abi.check(_abi.lib.env_step_host(env.handle, *_host_ptrs(env, actions, obs, reward, coll)))
+
+
+def env_step_host_bind(env, actions, obs, reward, coll):
+    """Checks the four host buffers of env_step_host once and returns a
+    callable that runs env_step_host on them: the same C call, without
+    re-checking the buffers on every step.  For loops that step many times
+    through the same pinned buffers (refilling the actions and reading the
+    outputs in place).  The buffers stay referenced by the callable; it
+    raises once the environment is closed."""
+    ptrs = _host_ptrs(env, actions, obs, reward, coll)
+    keep = (actions, obs, reward, coll)
+    lib_step, check = _abi.lib.env_step_host, _abi.check
+
+    def step():
+        h = env.handle
+        if not h:
+            raise FlockError("environment closed")
+        check(lib_step(h, *ptrs))
+
+    step.buffers = keep
+    return step
 
 
 def env_get_state(env, state):

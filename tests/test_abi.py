@@ -167,3 +167,33 @@ def test_binding_refuses_host_memory_and_bad_shapes():
     for k, call in enumerate(calls):
         with pytest.raises(F.FlockError):
             call()
+
+
+def test_bound_host_step_makes_the_same_call(monkeypatch):
+    """env_step_host_bind checks the buffers once and then issues exactly the
+    env_step_host call (same handle, same four host pointers) per step; it
+    refuses to run once the environment is closed."""
+    import types
+    F = _lib()
+    torch = pytest.importorskip("torch")
+    from paper_2207_03945_gb300 import _abi
+    calls = []
+    fake = types.SimpleNamespace(env_step_host=lambda *a: calls.append(a) or 0)
+    monkeypatch.setattr(_abi, "lib", fake)
+    env = types.SimpleNamespace(handle=12345, n=10, obs_dim=18)
+    bufs = (np.zeros(10, np.int32), np.zeros((10, 18), np.float32), np.zeros(10, np.float32),
+            torch.zeros(10, dtype=torch.int32))
+    F.env_step_host(env, *bufs)
+    step = F.env_step_host_bind(env, *bufs)
+    step()
+    step()
+    assert len(calls) == 3
+    ref = [calls[0][0]] + [p.value for p in calls[0][1:]]
+    for c in calls[1:]:
+        assert [c[0]] + [p.value for p in c[1:]] == ref
+    assert ref[1] == bufs[0].ctypes.data and ref[4] == bufs[3].data_ptr()
+    env.handle = None
+    with pytest.raises(F.FlockError):
+        step()
+    with pytest.raises(F.FlockError):  # float64 observations are refused
+        F.env_step_host_bind(env, bufs[0], np.zeros((10, 18)), bufs[2], bufs[3])

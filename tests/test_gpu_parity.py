@@ -304,7 +304,10 @@ def test_host_buffer_step_matches_device_step(buffers):
             rew_h = torch.empty(n + k, dtype=torch.float32).pin_memory()[k:]
             coll_h = torch.empty(n + k, dtype=torch.int32).pin_memory()[k:]
             act_h = torch.from_numpy(acts[t]).pin_memory()
-            F.env_step_host(env.env, act_h, obs_h, rew_h, coll_h)
+            if t == 0:
+                F.env_step_host(env.env, act_h, obs_h, rew_h, coll_h)
+            else:  # the same call through buffers bound once
+                F.env_step_host_bind(env.env, act_h, obs_h, rew_h, coll_h)()
             got = (obs_h.numpy(), rew_h.numpy(), coll_h.numpy())
         else:
             obs_n = np.zeros((n, 18), np.float32)
