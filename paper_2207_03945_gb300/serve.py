@@ -18,7 +18,7 @@ from __future__ import annotations
 
 import collections
 import time
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 
@@ -50,7 +50,7 @@ class Session:
     steps_done: int = 0
     t_admit: float = None
     t_done: float = None
-    latencies: list = field(default_factory=list)
+    it0: int = -1             # the server's first iteration that stepped it
     reset: bool = True        # next step observes without moving
 
     @property
@@ -197,6 +197,11 @@ class FlockServer:
         self.set_changes = 0
         self._version = None      # scheduler version of the uploaded set
         self._pending_reset = False
+        # per iteration: latency and sessions stepped (a session's step
+        # latencies are those of the iterations from its it0 on)
+        self.iter_lat = []
+        self.iter_sessions = []
+        self._fresh = []          # admitted, first step not yet taken
         self.on_step = None  # optional callback(session, obs, reward, coll) after each step
 
     def submit(self, n, steps, seed, t_arrival=None):
@@ -233,6 +238,8 @@ class FlockServer:
             # the client's initial state, copied straight into its arena rows
             st = torch.from_numpy(np.ascontiguousarray(self.state_fn(s), dtype=np.float32))
             self.arena[s.offset:s.offset + s.n].copy_(st)
+            s.it0 = self.iterations
+            self._fresh.append(s)
         act = self.sched.active
         if not act:
             return 0
@@ -250,17 +257,26 @@ class FlockServer:
         else:
             torch.cuda.synchronize()
         t1 = time.perf_counter()
-        off = 0
+        if self.on_step is not None:
+            for s, o in zip(act, self.batch.offsets):
+                self.on_step(s, obs[o:o + s.n], rew[o:o + s.n], coll[o:o + s.n])
+        # per-session work kept to the step count (the latency is recorded
+        # once for the iteration)
         for s in act:
-            if self.on_step is not None:
-                self.on_step(s, obs[off:off + s.n], rew[off:off + s.n], coll[off:off + s.n])
-            s.latencies.append(t1 - t0)
             s.steps_done += 1
+        for s in self._fresh:
             s.reset = False
-            off += s.n
+        self._fresh = []
+        self.iter_lat.append(t1 - t0)
+        self.iter_sessions.append(len(act))
         self.iterations += 1
         self.agent_steps += off
         return len(act)
+
+    def session_latencies(self, s):
+        """Step latencies (seconds) of session s: those of the iterations it
+        was stepped in, which are consecutive from its first."""
+        return self.iter_lat[s.it0:s.it0 + s.steps_done] if s.it0 >= 0 else []
 
     def run(self, arrivals, duration=None, drain=True):
         """Replay `arrivals` = [(t, n, steps, seed), ...] in real time (t in
@@ -287,7 +303,8 @@ class FlockServer:
         return self.stats()
 
     def stats(self):
-        lat = [x for s in self.sched.finished + self.sched.active for x in s.latencies]
+        # every session stepped in an iteration saw that iteration's latency
+        lat = np.repeat(np.asarray(self.iter_lat), np.asarray(self.iter_sessions, dtype=np.int64))
         waits = [s.t_admit - s.t_arrival for s in self.sched.finished + self.sched.active
                  if s.t_admit is not None]
         wall = getattr(self, "wall", None)
@@ -296,8 +313,8 @@ class FlockServer:
             "sessions_finished": len(self.sched.finished),
             "sessions_waiting": len(self.sched.queue), "iterations": self.iterations,
             "agent_steps": self.agent_steps, "set_changes": self.set_changes,
-            "step_latency_p50_ms": 1e3 * float(np.percentile(lat, 50)) if lat else None,
-            "step_latency_p99_ms": 1e3 * float(np.percentile(lat, 99)) if lat else None,
+            "step_latency_p50_ms": 1e3 * float(np.percentile(lat, 50)) if lat.size else None,
+            "step_latency_p99_ms": 1e3 * float(np.percentile(lat, 99)) if lat.size else None,
             "queue_wait_p50_ms": 1e3 * float(np.percentile(waits, 50)) if waits else None,
             "queue_wait_p99_ms": 1e3 * float(np.percentile(waits, 99)) if waits else None,
             "agent_steps_per_s": self.agent_steps / wall if wall else None,

@@ -65,7 +65,10 @@ def test_every_session_steps_its_episode_once_per_iteration(monkeypatch):
     # five stepping iterations, then one that only retires b
     assert n_iter == 6 and srv.iterations == 5
     assert a.steps_done == 3 and b.steps_done == 5
-    assert len(a.latencies) == 3 and len(b.latencies) == 5
+    la, lb = srv.session_latencies(a), srv.session_latencies(b)
+    assert len(la) == 3 and len(lb) == 5 and la == lb[:3] and all(x >= 0 for x in lb)
+    st = srv.stats()
+    assert st["step_latency_p50_ms"] is not None and st["agents_per_iteration"] == 3400 / 5
     assert srv.agent_steps == 3 * 300 + 5 * 500
     assert srv.batch.steps == [800, 800, 800, 500, 500]
     assert sorted(set(seen)) == [(a.sid, 300), (b.sid, 500)]
