@@ -52,6 +52,7 @@ class Session:
     t_done: float = None
     it0: int = -1             # the server's first iteration that stepped it
     reset: bool = True        # next step observes without moving
+    cancelled: bool = False   # left before its episode ended
 
     @property
     def bytes(self):
@@ -80,6 +81,7 @@ class SessionScheduler:
         self.admitted = 0
         self.rejected = 0
         self.finished = []
+        self.cancelled = []
         self.version = 0  # bumped whenever the active set changes
 
     # -- arena ranges: first fit, coalescing on free --
@@ -139,6 +141,25 @@ class SessionScheduler:
         if out:
             self.version += 1
         return out
+
+    def cancel(self, sess: Session, now) -> bool:
+        """Removes a session whose client left: from the queue, or from the
+        running set, freeing its slot, memory and arena rows at once (call it
+        between steps).  False if the session is neither waiting nor running."""
+        if any(q is sess for q in self.queue):
+            self.queue = collections.deque(q for q in self.queue if q is not sess)
+        elif any(a is sess for a in self.active):
+            self.active = [s for s in self.active if s is not sess]
+            self._release(sess.offset, sess.n)
+            self.used_bytes -= sess.bytes
+            self.used_cells -= sess.cells
+            self.version += 1
+        else:
+            return False
+        sess.cancelled = True
+        sess.t_done = now
+        self.cancelled.append(sess)
+        return True
 
     def retire(self, now):
         """Remove sessions whose episode is complete; returns them."""
@@ -202,6 +223,7 @@ class FlockServer:
         self.iter_lat = []
         self.iter_sessions = []
         self._fresh = []          # admitted, first step not yet taken
+        self._cancel = []         # cancellations taken at the next iteration
         self.on_step = None  # optional callback(session, obs, reward, coll) after each step
 
     def submit(self, n, steps, seed, t_arrival=None):
@@ -230,9 +252,18 @@ class FlockServer:
         with self.torch.cuda.stream(self.stream) if self.stream is not None else _null():
             return self._iteration()
 
+    def cancel(self, sess):
+        """A client left: its session stops before the next iteration (safe
+        to call from on_step or between iterations)."""
+        self._cancel.append(sess)
+
     def _iteration(self):
         torch = self.torch
         now = time.perf_counter()
+        if self._cancel:
+            for s in self._cancel:
+                self.sched.cancel(s, now)
+            self._cancel = []
         self.sched.retire(now)
         for s in self.sched.admit(now):
             # the client's initial state, copied straight into its arena rows
@@ -305,12 +336,14 @@ class FlockServer:
     def stats(self):
         # every session stepped in an iteration saw that iteration's latency
         lat = np.repeat(np.asarray(self.iter_lat), np.asarray(self.iter_sessions, dtype=np.int64))
-        waits = [s.t_admit - s.t_arrival for s in self.sched.finished + self.sched.active
+        waits = [s.t_admit - s.t_arrival
+                 for s in self.sched.finished + self.sched.active + self.sched.cancelled
                  if s.t_admit is not None]
         wall = getattr(self, "wall", None)
         return {
             "sessions_admitted": self.sched.admitted, "sessions_rejected": self.sched.rejected,
             "sessions_finished": len(self.sched.finished),
+            "sessions_cancelled": len(self.sched.cancelled),
             "sessions_waiting": len(self.sched.queue), "iterations": self.iterations,
             "agent_steps": self.agent_steps, "set_changes": self.set_changes,
             "step_latency_p50_ms": 1e3 * float(np.percentile(lat, 50)) if lat.size else None,

@@ -103,3 +103,29 @@ def test_admission_waits_for_the_budget(monkeypatch):
     srv.iteration()            # x retired, y admitted in its arena rows
     assert [s.sid for s in srv.sched.active] == [y.sid] and y.offset == x.offset
     assert y.steps_done == 1
+
+
+def test_client_leaving_mid_episode(monkeypatch):
+    """A client that disconnects during a step (from on_step): its session is
+    not stepped again, its rows go to the next waiting session, the others
+    run on; the descriptors are re-uploaded without it."""
+    nbytes = serve.session_bytes(1000, 1000)
+    srv = make_server(monkeypatch, budget=int(2.5 * nbytes))
+    x = srv.submit(1000, steps=10, seed=1)
+    y = srv.submit(1000, steps=3, seed=2)
+    z = srv.submit(1000, steps=2, seed=3)     # waits for memory
+
+    def on_step(s, obs, rew, coll):
+        if s is x and s.steps_done == 1:      # x's client leaves after its second step
+            srv.cancel(s)
+    srv.on_step = on_step
+    while srv.sched.active or srv.sched.queue:
+        srv.iteration()
+        assert srv.iterations < 20
+    assert x.cancelled and x.steps_done == 2 and not y.cancelled and y.steps_done == 3
+    assert z.steps_done == 2 and z.offset == x.offset   # admitted into x's rows
+    st = srv.stats()
+    assert st["sessions_cancelled"] == 1 and st["sessions_finished"] == 2
+    assert all(x_ is not x for x_ in srv.sched.active)
+    # the upload after the cancellation: y, then z in x's former rows, z resetting
+    assert ([1000, 1000], [y.offset, z.offset], [False, True]) in srv.batch.sets

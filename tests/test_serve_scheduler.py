@@ -117,3 +117,24 @@ def test_version_changes_with_the_active_set_only():
     for s in sc.active:
         s.steps_done += 1
     assert [s.sid for s in sc.retire(0.2)] == [0] and sc.version != v1
+
+
+def test_cancel_waiting_and_running_sessions():
+    """A client that leaves: a waiting session leaves the queue; a running
+    one frees its slot, memory and arena rows at once, so the next waiting
+    session is admitted into them; unknown or finished sessions are refused."""
+    b = serve.session_bytes(1000, 500)
+    sc = serve.SessionScheduler(budget_bytes=b + 10, max_slots=4, arena_agents=10000,
+                                max_cells=100000)
+    ss = [sess(k, 1000, steps=5) for k in range(3)]
+    for s in ss:
+        assert sc.submit(s)
+    assert [s.sid for s in sc.admit(0.0)] == [0]  # the budget holds one
+    assert sc.cancel(ss[2], 0.1) and [s.sid for s in sc.queue] == [1]
+    v = sc.version
+    assert sc.cancel(ss[0], 0.2)
+    assert sc.version != v and sc.active == [] and sc.used_bytes == 0 and sc.used_cells == 0
+    assert [s.sid for s in sc.admit(0.3)] == [1] and ss[1].offset == ss[0].offset
+    assert not sc.cancel(ss[0], 0.4) and not sc.cancel(sess(9, 10), 0.4)
+    assert [s.sid for s in sc.cancelled] == [2, 0] and all(s.cancelled for s in sc.cancelled)
+    assert sc.finished == []
