@@ -134,7 +134,8 @@ typedef struct flock_batch flock_batch;
  * v = 8, fov = 250 degrees.  Returns FLOCK_EINVAL for a NULL out. */
 int flock_default_params(float side, flock_params *out);
 
-/* 2v + 2 for valid params, else FLOCK_EINVAL. */
+/* Values per observation row for valid params: 2v + 2 (obs_layout 0),
+ * v + 1 (obs_layout 1), 2v (tag); else FLOCK_EINVAL. */
 int flock_obs_dim(const flock_params *params);
 
 /* Device workspace (bytes) that env_create needs for n_agents agents. */
@@ -337,7 +338,13 @@ void env_batch_destroy(flock_batch *batch);
  *   actions_dev  n int32, or NULL to observe the state without moving it;
  *   obs_dev, reward_dev, coll_dev  the outputs, as for env_step.
  * The call enqueues on `stream` and returns; with error_bits_out non-NULL it
- * waits for the stream and stores the FLOCK_ERR_* bits of this call.
+ * waits for the stream and stores the FLOCK_ERR_* bits of this call.  Any
+ * observation layout is accepted; obs_dev holds flock_obs_dim(params) values
+ * per row, 8-byte aligned.  `stream` must belong to the current device, and
+ * must not be in stream capture: each call copies its parameter descriptor
+ * from pageable host memory (and may wait for the stream), so a call made
+ * while `stream` is being captured, or with a stream of another device,
+ * returns FLOCK_EINVAL and enqueues nothing.
  *
  * Limits: at most FLOCK_STATIC_MAX_AGENTS agents and a cell list of at most
  * FLOCK_STATIC_MAX_CELLS cells (cells_per_side^2 of flock_derive with the

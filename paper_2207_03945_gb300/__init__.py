@@ -560,7 +560,7 @@ def flock_step_static(params: dict, state, actions, obs, reward, coll, stream=No
     returns the step's FLOCK_ERR_* bits after the stream has finished."""
     torch = _torch()
     n = int(state.shape[0])
-    d = 2 * int(params["num_segments"]) + 2
+    d = flock_obs_dim(params)
     bits = ctypes.c_uint32(0)
     _abi.check(_abi.lib.flock_step_static(
         ctypes.byref(_abi.params_from_dict(params)), n,

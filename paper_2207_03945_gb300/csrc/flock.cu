@@ -1061,6 +1061,20 @@ extern "C" int flock_step_static(const flock_params *p, int n, float *state_dev,
   if (I.kind != 0) return FLOCK_EINVAL;                  // flock only
   if (n > 0 && (!state_dev || !obs_dev || !reward_dev || !coll_dev || ((uintptr_t)obs_dev & 7)))
     return FLOCK_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  // The call copies its descriptor from pageable host memory and, with
+  // error_bits_out, waits for the stream: neither is allowed while the
+  // stream is being captured, so such a call is refused before it enqueues
+  // anything.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return FLOCK_EINVAL;
+  // The scratch address and the grid size below are those of the current
+  // device: a stream of another device is refused.
+  int cur_dev = 0, stream_dev = 0;
+  CK(cudaGetDevice(&cur_dev));
+  CK(cudaStreamGetDevice(s, &stream_dev));
+  if (stream_dev != cur_dev) return FLOCK_EINVAL;
   char *sp = nullptr;
   rc = static_scratch(&sp);
   if (rc) return rc;
@@ -1076,7 +1090,6 @@ extern "C" int flock_step_static(const flock_params *p, int n, float *state_dev,
   I.cell_base = 0;
   I.obs_base = 0;
   set_tiles(I, n, t);
-  cudaStream_t s = (cudaStream_t)stream;
   Bufs B{};
   B.cellrank = (int2 *)(sp + kSCellrank);
   B.counts = (int *)(sp + kSCounts);
@@ -1107,9 +1120,8 @@ extern "C" int flock_step_static(const flock_params *p, int n, float *state_dev,
   }
   k_scan<<<B.n_scan_tiles, 256, 0, s>>>(B);
   CK(cudaGetLastError());
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cur_dev));
   int g = (n + 255) / 256;
   g = g < 1 ? 1 : (g > 4 * sms ? 4 * sms : g);
   k_scatter<<<g, 256, 0, s>>>(gI, B);
@@ -1117,7 +1129,9 @@ extern "C" int flock_step_static(const flock_params *p, int n, float *state_dev,
   if (n > 0) {
     const size_t smem = (size_t)(t.block / 32) * direct_warp_bytes(I.v);
     const int blocks = (n + t.block - 1) / t.block;
-    if (I.v == 8) k_neighbours_direct<1, 8, 1><<<blocks, t.block, smem, s>>>(gI, B);
+    // the V = 8 kernel writes observation layout 0 only (float2 entries of
+    // 2v + 2 value rows); every other layout takes the generic kernel
+    if (I.v == 8 && I.obs_layout == 0) k_neighbours_direct<1, 8, 1><<<blocks, t.block, smem, s>>>(gI, B);
     else k_neighbours_direct<1, 0, 1><<<blocks, t.block, smem, s>>>(gI, B);
     CK(cudaGetLastError());
   }
