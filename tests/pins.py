@@ -420,3 +420,139 @@ def check_tag_motion():
         assert float(s2[0, 3]) == float(np.float32(s)) and float(s2[0, 2]) == th
         assert abs(float(s2[0, 0]) - (st0[0] + s * math.cos(th))) < 3e-5
         assert abs(float(s2[0, 1]) - (st0[1] + s * math.sin(th))) < 3e-5
+
+
+def fraction_to_f32(q):
+    """The float32 nearest to the rational q (ties to even), by integer
+    arithmetic on the exact value: no intermediate float64 rounding."""
+    from fractions import Fraction
+    q = Fraction(q)
+    if q == 0:
+        return np.float32(0.0)
+    sign = -1.0 if q < 0 else 1.0
+    a = abs(q)
+    # e with 2^e <= a < 2^(e+1)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    e = max(e, -126)  # subnormal range keeps the exponent of the smallest normal
+    scaled = a * Fraction(2) ** (23 - e)  # the 24-bit significand, as a rational
+    m = scaled.numerator // scaled.denominator
+    rem = scaled - m
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and m % 2 == 1):
+        m += 1
+    return np.float32(sign * math.ldexp(m, e - 23))  # exact: m <= 2^24
+
+
+def exact_rewards(p, st):
+    """Rewards of Eq. 1 (Fig. 4 shape, reading 2) for the agents of state st,
+    summed exactly: each pair's FP32 term computed with numpy float32 (one
+    rounding per operation, the specified formulas), then the terms of an
+    agent added as exact rationals (fractions.Fraction) and the sum rounded
+    once to float32.  Independent of the oracle's fixed-point accumulator."""
+    from fractions import Fraction
+    f = np.float32
+    L = f(p["side"])
+    HL = f(f(0.5) * L)
+    rv = f(p["view_radius"])
+    dr = f(p["agent_radius"])
+    RV2 = f(rv * rv)
+    two_dr = f(f(2.0) * dr)
+    RC2 = f(two_dr * two_dr)
+    inv_span = f(1.0 / (float(rv) - 2.0 * float(dr)))
+    P = f(p["collision_penalty"])
+    x = st[:, 0].astype(np.float32)
+    y = st[:, 1].astype(np.float32)
+    n = st.shape[0]
+    out = np.zeros(n, np.float32)
+    for i in range(n):
+        dx = (x - x[i]).astype(np.float32)
+        dy = (y - y[i]).astype(np.float32)
+        dx = np.where(dx > HL, dx - L, np.where(dx < -HL, dx + L, dx)).astype(np.float32)
+        dy = np.where(dy > HL, dy - L, np.where(dy < -HL, dy + L, dy)).astype(np.float32)
+        d2 = (dx * dx + dy * dy).astype(np.float32)
+        inr = d2 < RV2
+        inr[i] = False
+        coll = inr & (d2 < RC2)
+        ramp = inr & ~coll
+        t = ((rv - np.sqrt(d2[ramp])).astype(np.float32) * inv_span).astype(np.float32)
+        s = sum((Fraction(float(v)) for v in t), Fraction(0))
+        s -= int(coll.sum()) * Fraction(float(P))
+        out[i] = fraction_to_f32(s)
+    return out
+
+
+def check_exact_reward_sum(over, n=360, side=40.0, seed=91):
+    """The oracle's rewards equal the exact sums of exact_rewards bit for bit
+    (reading 15: the exact sum of the FP32 terms, rounded once).  A
+    fixed-point resolution 2^-K too coarse for some term, a truncated term or
+    a penalty off the grid breaks the equality.  Returns the oracle's K."""
+    p = fi.default_params(side, **over)
+    st = fi.initial_state(n, side, seed)
+    st2, obs, rew, coll, flags = oracle.step(p, st, None)
+    assert flags == 0
+    ref = exact_rewards(p, st2)
+    bad = np.flatnonzero(rew.view(np.uint32) != ref.view(np.uint32))
+    assert bad.size == 0, (over, bad[:5], rew[bad[:5]], ref[bad[:5]])
+    # the case has terms of both kinds and cancellations near zero
+    assert (coll > 0).any() or float(p["agent_radius"]) == 0.0
+    return oracle.derive(p)["K"]
+
+
+def edge_pairs_state(p, pairs=24):
+    """Isolated pairs of agents whose distance is just below the view radius:
+    pair j has one agent at x = 0 and the other at x = d_j = d_v - (j + 1)
+    ulp(d_v) (a float32, so the offset is exactly d_j), in a row of its own,
+    rows 3 d_v apart.  Each agent's reward is then one of the smallest ramp
+    terms, those whose last bits set the fixed-point resolution."""
+    f = np.float32
+    rv = f(p["view_radius"])
+    L = float(f(p["side"]))
+    gap = 3.0 * float(rv)
+    assert pairs * gap < L
+    st = []
+    d = rv
+    for j in range(pairs):
+        d = np.nextafter(d, f(0.0))
+        y0 = f(gap * j + 0.5)
+        st.append([0.0, y0, 0.0, 0.5])
+        st.append([d, y0, 0.0, 0.5])
+    return np.array(st, np.float32)
+
+
+def smallest_term(p):
+    """The ramp term of a neighbour at the largest float32 distance below d_v
+    (FP32, the specified formula): the smallest term the sum can receive."""
+    f = np.float32
+    rv = f(p["view_radius"])
+    dr = f(p["agent_radius"])
+    inv_span = f(1.0 / (float(rv) - 2.0 * float(dr)))
+    return f(f(rv - np.nextafter(rv, f(0.0))) * inv_span)
+
+
+def odd_smallest_term_radius(lo=2.0, hi=9.0, step=0.1):
+    """The first view radius in [lo, hi) (agent radius 0.5) whose smallest
+    ramp term has an odd 24-bit significand: for it the resolution must be
+    exactly fine enough for that last bit."""
+    for k in range(int(round((hi - lo) / step))):
+        rv = round(lo + k * step, 6)
+        t = smallest_term({"view_radius": rv, "agent_radius": 0.5})
+        if t.view(np.uint32) & 1:
+            return rv
+    raise AssertionError("no radius with an odd smallest term")
+
+
+def check_exact_reward_edge_pairs(over, side=None):
+    """The smallest ramp terms (pairs just inside the view radius) summed by
+    the oracle equal their exact values: each agent's reward is its pair's
+    term, bit for bit (a fixed-point resolution one bit too coarse truncates
+    them).  Checked against exact_rewards."""
+    rv = float(over.get("view_radius", 5.0))
+    p = fi.default_params(side or max(200.0, 80.0 * rv), **over)
+    st = edge_pairs_state(p)
+    st2, obs, rew, coll, flags = oracle.step(p, st, None)
+    assert flags == 0
+    ref = exact_rewards(p, st2)
+    # float32 positions round some offsets onto the range edge (no term)
+    assert (ref > 0).mean() >= 0.5 and np.all(coll == 0)
+    np.testing.assert_array_equal(rew.view(np.uint32), ref.view(np.uint32), err_msg=str(over))

@@ -65,6 +65,8 @@ MUTANTS = {
     "tag_channels_swapped": ("k += tj * v; /* colour channel of the neighbour's type */",
                              "k += (1 - tj) * v; /* colour channel of the neighbour's type */"),
     "tag_speed_added": ("  st[3] = spd;\n  move_one(d, st, 0.0f, rot);", "  move_one(d, st, spd, rot);"),
+    "exact_sum_resolution_one_short": ("int K = 24 - e;", "int K = 23 - e;"),
+    "exact_sum_resolution_two_short": ("int K = 24 - e;", "int K = 22 - e;"),
     "move_before_turn": ("  float c, sn;\n  oracle_sincos(th, &c, &sn);\n  float x = st[0] + s * c;",
                          "  float c, sn;\n  oracle_sincos(st[2], &c, &sn);\n  float x = st[0] + s * c;"),
 }
@@ -91,7 +93,12 @@ def _pins_fail():
               ("tag_hand", pins.check_tag_hand_worked),
               ("tag_flock", pins.check_tag_all_runners_is_flock),
               ("tag_swap", pins.check_tag_channels_swap),
-              ("tag_motion", pins.check_tag_motion)]
+              ("tag_motion", pins.check_tag_motion),
+              ("exact_sum", lambda: [pins.check_exact_reward_sum(o, n=200, side=30.0) for o in
+                                     ({}, {"view_radius": 7.3}, {"agent_radius": 0.0})]),
+              ("exact_sum_edge", lambda: [pins.check_exact_reward_edge_pairs(o) for o in
+                                          ({}, {"view_radius": 7.3},
+                                           {"view_radius": pins.odd_smallest_term_radius()})])]
     for name, fn in checks:
         try:
             fn()

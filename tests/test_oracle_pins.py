@@ -185,3 +185,51 @@ def test_rounded_sqrt_is_monotone():
     for _ in range(200):
         d2 = (rng.random(rng.integers(1, 40)) * 25.0).astype(np.float32)
         assert np.sqrt(d2).min().view(np.uint32) == np.sqrt(d2.min()).view(np.uint32)
+
+
+def test_fraction_rounding_helper():
+    """fraction_to_f32 agrees with numpy's correctly rounded conversion where
+    float64 holds the value exactly, and rounds ties to even."""
+    from fractions import Fraction
+    rng = np.random.default_rng(7)
+    for v in rng.standard_normal(2000) * 10.0 ** rng.integers(-8, 8, 2000):
+        assert pins.fraction_to_f32(Fraction(float(v))) == np.float32(v)
+    one = Fraction(1)
+    ulp = Fraction(1, 2 ** 23)
+    assert pins.fraction_to_f32(one + ulp / 2) == np.float32(1.0)  # tie to even (down)
+    assert pins.fraction_to_f32(one + 3 * ulp / 2) == np.float32(1.0 + 2 * 2.0 ** -23)  # up
+    assert pins.fraction_to_f32(one + ulp / 2 + Fraction(1, 2 ** 60)) == np.float32(1.0 + 2.0 ** -23)
+
+
+def test_reward_is_the_exact_sum_for_several_resolutions():
+    """Reading 15 against an independent exact sum (rationals, one rounding),
+    on parameter sets whose fixed-point resolutions 2^-K differ: the
+    defaults (K = 46), a view radius of 7.3 (47), a penalty of 0.375, agents
+    of radius 0 (no collisions; ramp terms up to 1), a penalty of 3 * 2^-30
+    (K set by the penalty, 52) and a view radius of 0.3 on a square of side 4
+    (45)."""
+    ks = set()
+    for over, side in (({}, 40.0), ({"view_radius": 7.3}, 40.0),
+                       ({"collision_penalty": 0.375}, 40.0), ({"agent_radius": 0.0}, 40.0),
+                       ({"collision_penalty": 3.0 * 2.0 ** -30}, 40.0),
+                       ({"view_radius": 0.3, "agent_radius": 0.1}, 4.0)):
+        ks.add(pins.check_exact_reward_sum(over, side=side))
+    assert len(ks) >= 4, ks
+
+
+@pytest.mark.parametrize("over", [{}, {"view_radius": 7.3}, {"view_radius": 3.1},
+                                  {"view_radius": 7.3, "agent_radius": 0.0}, "odd"])
+def test_smallest_ramp_terms_are_exact(over):
+    """Pairs just inside the view radius: each reward is the pair's own
+    (smallest possible) ramp term, exactly.  "odd": a radius whose smallest
+    term has an odd significand, where the resolution 2^-K must be exactly
+    as fine as that term's last bit (and is: K is the least that holds it)."""
+    if over == "odd":
+        rv = pins.odd_smallest_term_radius()
+        over = {"view_radius": rv}
+        p = fi.default_params(200.0, **over)
+        t = pins.smallest_term(p)
+        K = oracle.derive(p)["K"]
+        scaled = float(t) * 2.0 ** K
+        assert scaled == int(scaled) and int(scaled) % 2 == 1, (rv, K)
+    pins.check_exact_reward_edge_pairs(over)
