@@ -365,6 +365,47 @@ def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256,
                          "bytes_per_agent": BYTES_PER_AGENT_STEP}}
 
 
+def run_plain(F, torch, dev, stream, n, steps, warmup, flush, seed=0, world=1, what=""):
+    """The plain single-instance step at n agents (density 0.1, side
+    sqrt(n / 0.1), the defaults): `steps` consecutive steps of uniform random
+    actions, each timed with CUDA events on the library's stream, L2 flushed
+    between steps.  Returns agent-steps/s and p50/p99 step latency."""
+    side = fi.side_for(n)
+    p = fi.default_params(side)
+    env = F.FlockEnv(p, n, device=dev, stream=stream)
+    acts = torch.from_numpy(fi.random_actions(n, steps + warmup, seed)).to(dev)
+    act_buf = torch.empty(n, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        env.reset(torch.from_numpy(fi.initial_state(n, side, seed)).to(dev))
+        for k in range(warmup):
+            act_buf.copy_(acts[k])
+            flush.zero_()
+            env.step(act_buf)
+    torch.cuda.synchronize()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            act_buf.copy_(acts[warmup + k])
+            flush.zero_()
+            ev0[k].record(stream)
+            env.step(act_buf)
+            ev1[k].record(stream)
+    torch.cuda.synchronize()
+    assert env.error() == 0
+    tun = env.tuning()
+    env.close()
+    ms = [ev0[k].elapsed_time(ev1[k]) for k in range(steps)]
+    tot = max_over_ranks(sum(ms), dev)
+    return {"value": weak_scaling_value(world, n, steps, tot), "unit": UNIT, "agents": n,
+            "steps": steps, "ms_per_step": tot / steps, "p50_ms": float(np.percentile(ms, 50)),
+            "p99_ms": float(np.percentile(ms, 99)), "tuning": tun,
+            "workload": "plain flock step%s: %d agents, side %.1f, density 0.1, view radius 5, "
+                        "8 sectors, fov 250 deg, uniform random actions, seed %d, %d steps, "
+                        "L2 flushed between steps" % (what, n, side, seed, steps)}
+
+
 POLICY_BYTES_PER_AGENT = 48  # state 16 in + 16 out, action 4 in + 4 out, reward 4, coll 4
 
 
@@ -753,10 +794,22 @@ def main():
                         "episodes uniform in [100, 2000] steps, 100 GB budget, random actions; "
                         "plus a saturated run (5,000 sessions queued at t=0, more than the run "
                         "serves, 100 MB budget so that admission binds)"}
-    policy = None
+    # the other plain-step configurations: 1,000 agents for 100 steps, 5,000
+    # agents (the same density) for 1,000 steps
+    small = {"n1000_100_steps": run_plain(F, torch, dev, stream, 1000, 100, args.warmup, flush,
+                                          seed=rank_seed(rank), world=world),
+             "n5000_1000_steps": run_plain(F, torch, dev, stream, 5000, 1000, args.warmup, flush,
+                                           seed=rank_seed(rank), world=world)}
+    policy = plain100k = None
     if not args.no_policy:
         policy = run_policy(F, torch, dev, stream, args.steps, args.warmup, flush,
                             seed=rank_seed(rank), world=world)
+        # the plain step on the policy's 100,000 agents, like for like
+        plain100k = run_plain(F, torch, dev, stream, 100000, args.steps, args.warmup, flush,
+                              seed=rank_seed(rank), world=world,
+                              what=" (the fused policy's agent count, observations written)")
+        policy["plain_step_same_agents"] = {k: plain100k[k] for k in
+                                            ("value", "ms_per_step", "p50_ms", "p99_ms")}
     paper = rollout = tag = None
     if not args.no_paper:
         paper = run_paper_variant(F, torch, dev, stream, min(args.steps, 50), args.warmup, flush,
@@ -795,6 +848,7 @@ def main():
             line["batched"] = batched
             line["single_instance_persistent"] = single_fused
             line["batched_10_instances"] = ten
+        line["plain_small"] = small
         if policy is not None:
             line["policy"] = policy
         if paper is not None:

@@ -494,10 +494,12 @@ def env_batch_destroy(batch):
 
 class FlockBatch:
     """Convenience owner of a batch: allocates the workspace and the
-    flattened output tensors with torch and calls the C ABI."""
+    flattened output tensors with torch and calls the C ABI.  With
+    out_buffers=2 it keeps two sets of outputs, so that a step may write one
+    set while the caller still reads the other (step(..., buf=k))."""
 
     def __init__(self, max_instances: int, max_agents: int, max_cells: int, obs_dim: int,
-                 device="cuda", stream=None, tuning: dict | None = None):
+                 device="cuda", stream=None, tuning: dict | None = None, out_buffers: int = 1):
         torch = _torch()
         self.device = torch.device(device)
         self.obs_dim = int(obs_dim)
@@ -505,10 +507,12 @@ class FlockBatch:
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.batch = env_batch_create(max_instances, max_agents, max_cells, self.workspace,
                                       stream, tuning)
-        self.obs = torch.empty((max(max_agents, 1), self.obs_dim), dtype=torch.float32,
-                               device=self.device)
-        self.reward = torch.empty(max(max_agents, 1), dtype=torch.float32, device=self.device)
-        self.coll = torch.empty(max(max_agents, 1), dtype=torch.int32, device=self.device)
+        m = max(max_agents, 1)
+        self.outs = [(torch.empty((m, self.obs_dim), dtype=torch.float32, device=self.device),
+                      torch.empty(m, dtype=torch.float32, device=self.device),
+                      torch.empty(m, dtype=torch.int32, device=self.device))
+                     for _ in range(max(1, int(out_buffers)))]
+        self.obs, self.reward, self.coll = self.outs[0]
         self.n_total = 0
         self.offsets = []
 
@@ -529,10 +533,11 @@ class FlockBatch:
             off += int(n)
         self.n_total = off
 
-    def step(self, actions):
-        env_batch_step(self.batch, actions, self.obs, self.reward, self.coll)
+    def step(self, actions, buf: int = 0):
+        obs, reward, coll = self.outs[buf]
+        env_batch_step(self.batch, actions, obs, reward, coll)
         n = self.n_total
-        return self.obs[:n], self.reward[:n], self.coll[:n]
+        return obs[:n], reward[:n], coll[:n]
 
     def error(self) -> int:
         return env_batch_get_error(self.batch)

@@ -47,7 +47,8 @@ class Session:
     params: dict = None
     params_c: object = None   # the same as the library's struct, built once
     offset: int = -1          # first agent row of its state in the arena
-    steps_done: int = 0
+    steps_done: int = 0       # steps whose results were delivered
+    steps_issued: int = 0     # steps launched (one ahead of delivery when pipelined)
     t_admit: float = None
     t_done: float = None
     it0: int = -1             # the server's first iteration that stepped it
@@ -162,11 +163,13 @@ class SessionScheduler:
         return True
 
     def retire(self, now):
-        """Remove sessions whose episode is complete; returns them."""
-        done = [s for s in self.active if s.steps_done >= s.steps]
+        """Remove sessions whose episode's steps have all been issued (their
+        rows may be reused: later uploads follow those steps in stream
+        order); returns them."""
+        done = [s for s in self.active if s.steps_issued >= s.steps]
         if done:
             self.version += 1
-            self.active = [s for s in self.active if s.steps_done < s.steps]
+            self.active = [s for s in self.active if s.steps_issued < s.steps]
             for s in done:
                 s.t_done = now
                 self._release(s.offset, s.n)
@@ -184,11 +187,24 @@ class FlockServer:
     n agents (default: the library defaults on a square of side
     sqrt(n / 0.1), i.e. density 0.1); action_fn(session, step, out) fills the
     session's int32 actions for one step into the device tensor `out`
-    (default: uniform random actions drawn on the device)."""
+    (default: uniform random actions drawn on the device).
+
+    pipeline=True overlaps the host's work for iteration i (retiring,
+    admitting, uploading states and descriptors, drawing actions, launching)
+    with the GPU's execution of iteration i - 1: the host waits on an event
+    of the previous iteration instead of synchronising after each one, and
+    the outputs alternate between two buffers so that a step never
+    overwrites results not yet delivered.  Results (on_step) then arrive one
+    iteration after their step was issued, and action_fn must be stream
+    ordered (device work on the server's stream, as the default is): actions
+    for step k + 1 are drawn before step k's results reach the host.  A
+    session cancelled from on_step may have had one more step issued, whose
+    results are dropped.  pipeline=False delivers every step before the next
+    is issued."""
 
     def __init__(self, budget_bytes, state_fn, max_slots=256, arena_agents=2_000_000,
                  max_cells=1_000_000, device="cuda", stream=None, params_fn=None,
-                 action_fn=None, queue_limit=100000, tuning=None):
+                 action_fn=None, queue_limit=100000, tuning=None, pipeline=True):
         import math
 
         import torch
@@ -199,6 +215,7 @@ class FlockServer:
         self.dev = torch.device(device)
         self.stream = stream
         self.tuning = tuning
+        self.pipeline = bool(pipeline)
         self.params_fn = params_fn or (
             lambda n: flock_default_params(max(math.sqrt(max(n, 1) / 0.1), 12.0)))
         self.state_fn = state_fn
@@ -208,21 +225,30 @@ class FlockServer:
                                       queue_limit)
         self.arena = torch.empty((arena_agents, 4), dtype=torch.float32, device=self.dev)
         self.batch = FlockBatch(max_slots, arena_agents, max_cells, 18, device=self.dev,
-                                stream=stream, tuning=tuning)
+                                stream=stream, tuning=tuning,
+                                out_buffers=2 if self.pipeline else 1)
         self.actions = torch.empty(arena_agents, dtype=torch.int32, device=self.dev)
         self.gen = torch.Generator(device=self.dev)
         self.gen.manual_seed(12345)
+        cuda = self.dev.type == "cuda"
+        # page-locked staging of admitted sessions' initial states: a mirror
+        # of the arena rows, so uploads of different sessions never share rows
+        self._stage = torch.empty((arena_agents, 4), dtype=torch.float32,
+                                  pin_memory=cuda)
+        self._upload_ev = torch.cuda.Event() if cuda else None
+        self._upload_pending = False
+        self._events = [torch.cuda.Event() if cuda else None for _ in range(2)]
         self.next_sid = 0
         self.iterations = 0
         self.agent_steps = 0
         self.set_changes = 0
         self._version = None      # scheduler version of the uploaded set
-        self._pending_reset = False
-        # per iteration: latency and sessions stepped (a session's step
-        # latencies are those of the iterations from its it0 on)
+        # per delivered iteration: latency (issue to results) and sessions
+        # stepped (a session's step latencies are those of the iterations from
+        # its it0 on)
         self.iter_lat = []
         self.iter_sessions = []
-        self._fresh = []          # admitted, first step not yet taken
+        self._inflight = None     # the issued iteration whose results are pending
         self._cancel = []         # cancellations taken at the next iteration
         self.on_step = None  # optional callback(session, obs, reward, coll) after each step
 
@@ -235,20 +261,20 @@ class FlockServer:
         return s if self.sched.submit(s) else None
 
     def _sync_set(self):
-        # re-upload the descriptors when the set changed, and once more after
-        # a step that reset newly admitted sessions (to clear their flags)
-        if self.sched.version != self._version or self._pending_reset:
+        # re-upload the descriptors when the set changed; a session's reset
+        # flag is cleared on the device by the step that observes it, and on
+        # the host when that step is issued, so it needs no second upload
+        if self.sched.version != self._version:
             act = self.sched.active
-            reset = [s.reset for s in act]
             self.batch.set_rows([s.params_c for s in act], [s.n for s in act], self.arena,
-                                [s.offset for s in act], reset=reset)
+                                [s.offset for s in act], reset=[s.reset for s in act])
             self._version = self.sched.version
-            self._pending_reset = any(reset)
             self.set_changes += 1
 
     def iteration(self):
-        """Retire, admit, step every admitted session once.  Returns the
-        number of sessions stepped."""
+        """Deliver cancellations, retire, admit, issue one step of every
+        admitted session, and deliver the results of the previous iteration
+        (pipeline) or of this one.  Returns the number of sessions stepped."""
         with self.torch.cuda.stream(self.stream) if self.stream is not None else _null():
             return self._iteration()
 
@@ -256,6 +282,22 @@ class FlockServer:
         """A client left: its session stops before the next iteration (safe
         to call from on_step or between iterations)."""
         self._cancel.append(sess)
+
+    def _upload_states(self, admitted):
+        torch = self.torch
+        if not admitted:
+            return
+        # staging rows may still feed the previous iteration's upload
+        if self._upload_pending and self._upload_ev is not None:
+            self._upload_ev.synchronize()
+        for s in admitted:
+            st = np.ascontiguousarray(self.state_fn(s), dtype=np.float32)
+            self._stage[s.offset:s.offset + s.n].numpy()[...] = st
+            self.arena[s.offset:s.offset + s.n].copy_(self._stage[s.offset:s.offset + s.n],
+                                                      non_blocking=True)
+        if self._upload_ev is not None:
+            self._upload_ev.record()
+            self._upload_pending = True
 
     def _iteration(self):
         torch = self.torch
@@ -265,44 +307,67 @@ class FlockServer:
                 self.sched.cancel(s, now)
             self._cancel = []
         self.sched.retire(now)
-        for s in self.sched.admit(now):
-            # the client's initial state, copied straight into its arena rows
-            st = torch.from_numpy(np.ascontiguousarray(self.state_fn(s), dtype=np.float32))
-            self.arena[s.offset:s.offset + s.n].copy_(st)
+        admitted = self.sched.admit(now)
+        for s in admitted:
             s.it0 = self.iterations
-            self._fresh.append(s)
+        self._upload_states(admitted)
         act = self.sched.active
         if not act:
+            self._deliver_inflight()
             return 0
         t0 = time.perf_counter()
         self._sync_set()
         off = self.batch.n_total
+        offsets = list(self.batch.offsets)
         if self.action_fn is not None:
-            for s, o in zip(act, self.batch.offsets):
-                self.action_fn(s, s.steps_done, self.actions[o:o + s.n])
+            for s, o in zip(act, offsets):
+                self.action_fn(s, s.steps_issued, self.actions[o:o + s.n])
         else:
             self.actions[:off].random_(0, 9, generator=self.gen)
-        obs, rew, coll = self.batch.step(self.actions[:off])
-        if self.stream is not None:
-            self.stream.synchronize()
-        else:
-            torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        if self.on_step is not None:
-            for s, o in zip(act, self.batch.offsets):
-                self.on_step(s, obs[o:o + s.n], rew[o:o + s.n], coll[o:o + s.n])
-        # per-session work kept to the step count (the latency is recorded
-        # once for the iteration)
+        k = self.iterations % 2 if self.pipeline else 0
+        obs, rew, coll = self.batch.step(self.actions[:off], buf=k)
+        ev = self._events[k]
+        if ev is not None:
+            ev.record()
         for s in act:
-            s.steps_done += 1
-        for s in self._fresh:
-            s.reset = False
-        self._fresh = []
-        self.iter_lat.append(t1 - t0)
-        self.iter_sessions.append(len(act))
+            s.steps_issued += 1
+            s.reset = False  # the device clears its copy in this step
+        entry = (list(zip(act, offsets)), obs, rew, coll, ev, t0)
         self.iterations += 1
         self.agent_steps += off
+        if self.pipeline:
+            prev, self._inflight = self._inflight, entry
+            if prev is not None:
+                self._deliver(prev)
+        else:
+            self._deliver(entry)
         return len(act)
+
+    def _deliver_inflight(self):
+        if self._inflight is not None:
+            prev, self._inflight = self._inflight, None
+            self._deliver(prev)
+
+    def _deliver(self, entry):
+        members, obs, rew, coll, ev, t0 = entry
+        if ev is not None:
+            ev.synchronize()
+        elif self.stream is not None:
+            self.stream.synchronize()
+        t1 = time.perf_counter()
+        self.iter_lat.append(t1 - t0)
+        self.iter_sessions.append(len(members))
+        for s, o in members:
+            if s.cancelled:
+                continue  # issued before its client left: results dropped
+            if self.on_step is not None:
+                self.on_step(s, obs[o:o + s.n], rew[o:o + s.n], coll[o:o + s.n])
+            s.steps_done += 1
+
+    def drain(self):
+        """Deliver the results of the last issued iteration."""
+        with self.torch.cuda.stream(self.stream) if self.stream is not None else _null():
+            self._deliver_inflight()
 
     def session_latencies(self, s):
         """Step latencies (seconds) of session s: those of the iterations it
@@ -323,13 +388,13 @@ class FlockServer:
             if duration is not None and now >= duration:
                 break
             if not self.sched.active and not self.sched.queue:
+                self.drain()
                 if not pending:
-                    if drain:
-                        break
                     break
                 time.sleep(min(0.001, max(0.0, pending[0][0] - now)))
                 continue
             self.iteration()
+        self.drain()
         self.wall = time.perf_counter() - t_start
         return self.stats()
 
@@ -346,6 +411,7 @@ class FlockServer:
             "sessions_cancelled": len(self.sched.cancelled),
             "sessions_waiting": len(self.sched.queue), "iterations": self.iterations,
             "agent_steps": self.agent_steps, "set_changes": self.set_changes,
+            "pipeline": self.pipeline,
             "step_latency_p50_ms": 1e3 * float(np.percentile(lat, 50)) if lat.size else None,
             "step_latency_p99_ms": 1e3 * float(np.percentile(lat, 99)) if lat.size else None,
             "queue_wait_p50_ms": 1e3 * float(np.percentile(waits, 50)) if waits else None,
@@ -356,6 +422,7 @@ class FlockServer:
         }
 
     def close(self):
+        self.drain()
         self.batch.close()
 
 

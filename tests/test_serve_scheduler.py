@@ -28,7 +28,7 @@ def test_budget_and_slots_bind_and_order_is_fifo():
     assert sc.used_bytes == 2 * b
     # nothing more until one leaves
     assert sc.admit(0.1) == []
-    sc.active[0].steps_done = 3
+    sc.active[0].steps_issued = 3
     assert [s.sid for s in sc.retire(0.2)] == [0]
     assert [s.sid for s in sc.admit(0.3)] == [2]
     assert sc.admitted == 3 and sc.rejected == 0 and len(sc.queue) == 1
@@ -63,7 +63,7 @@ def test_arena_ranges_are_disjoint_and_reused():
     assert ranges[-1][1] <= 1000
     # the middle one leaves; a session of 250 does not fit in the 200 hole
     # nor the 100 tail, one of 150 fits into the hole
-    sc.active[1].steps_done = 99
+    sc.active[1].steps_issued = 99
     sc.retire(1.0)
     sc.submit(sess(9, 250))
     assert sc.admit(1.1) == []
@@ -73,7 +73,7 @@ def test_arena_ranges_are_disjoint_and_reused():
     assert got and got[0].offset == 300
     # everything leaves: the arena is one free range again
     for s in sc.active:
-        s.steps_done = 99
+        s.steps_issued = 99
     sc.retire(2.0)
     assert sc.free == [(0, 1000)] and sc.used_bytes == 0 and sc.used_cells == 0
 
@@ -89,7 +89,7 @@ def test_random_workload_keeps_invariants():
                            cells=rnd.randint(1, 1500)))
         sc.admit(it)
         for s in sc.active:
-            s.steps_done += 1
+            s.steps_issued += 1
         sc.retire(it)
         ranges = sorted((s.offset, s.offset + s.n) for s in sc.active)
         assert all(a[1] <= b[0] for a, b in zip(ranges, ranges[1:]))
@@ -112,10 +112,10 @@ def test_version_changes_with_the_active_set_only():
     v1 = sc.version
     assert v1 != v0
     for s in sc.active:
-        s.steps_done += 1
+        s.steps_issued += 1
     assert sc.retire(0.1) == [] and sc.admit(0.1) == [] and sc.version == v1
     for s in sc.active:
-        s.steps_done += 1
+        s.steps_issued += 1
     assert [s.sid for s in sc.retire(0.2)] == [0] and sc.version != v1
 
 
