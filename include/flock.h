@@ -74,6 +74,8 @@ extern "C" {
 #define FLOCK_ERR_TIMEOUT 4u  /* a grid barrier of the batched kernel gave up waiting */
 #define FLOCK_ERR_OVERFLOW 8u /* an agent had more in-range neighbours than the exact
                                  reward sum holds (see flock_derived.nmax) */
+#define FLOCK_ERR_BOUNDS 16u  /* debug build (FLOCK_DEBUG, libflock_debug.so) only: an
+                                 index check failed; the access was skipped */
 
 #define FLOCK_MAX_SEGMENTS 128
 
@@ -107,9 +109,11 @@ typedef struct flock_tuning {
                   Batch: 2 = every phase in one persistent launch; 3 = binning
                   in the persistent launch, the neighbour scan (direct form)
                   in a second launch.  Results are identical. */
-  int lanes;   /* mode 2: lanes per agent, 1, 2 or 4 (0: 4 up to 32,768 agents,
-                  2 up to 524,288, else 1); the lanes of an agent share its
-                  candidates.  Mode 1 and the policy step use 1. */
+  int lanes;   /* mode 2: lanes per agent, 1, 2, 4 or 32 (0: 32 when an agent
+                  has 256 or more candidates in its stencil cells on average,
+                  else 4 up to 32,768 agents, 2 up to 524,288, else 1); the
+                  lanes of an agent share its candidates.  Mode 1 and the
+                  policy step use 1. */
 } flock_tuning;
 
 /* Constants the library derives from flock_params (host, double precision

@@ -12,12 +12,13 @@ from __future__ import annotations
 import ctypes
 
 from . import _abi
-from ._abi import (FLOCK_ERR_ACTION, FLOCK_ERR_OVERFLOW, FLOCK_ERR_STATE, FLOCK_ERR_TIMEOUT,
-                   FlockError)
+from ._abi import (FLOCK_ERR_ACTION, FLOCK_ERR_BOUNDS, FLOCK_ERR_OVERFLOW, FLOCK_ERR_STATE,
+                   FLOCK_ERR_TIMEOUT, FlockError)
 
 __all__ = [
     "FlockError", "FLOCK_ERR_ACTION", "FLOCK_ERR_STATE", "FLOCK_ERR_TIMEOUT",
-    "FLOCK_ERR_OVERFLOW", "flock_default_params", "flock_obs_dim", "flock_workspace_bytes",
+    "FLOCK_ERR_OVERFLOW", "FLOCK_ERR_BOUNDS", "flock_default_params", "flock_obs_dim",
+    "flock_workspace_bytes",
     "flock_derive",
     "env_create", "env_reset", "env_step", "env_step_continuous", "env_rollout", "flock_gae",
     "env_set_types",

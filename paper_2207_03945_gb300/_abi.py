@@ -17,6 +17,7 @@ FLOCK_ERR_ACTION = 1
 FLOCK_ERR_STATE = 2
 FLOCK_ERR_TIMEOUT = 4
 FLOCK_ERR_OVERFLOW = 8
+FLOCK_ERR_BOUNDS = 16
 MAX_SEGMENTS = 128
 STATIC_MAX_AGENTS = 65536
 STATIC_MAX_CELLS = 32768
@@ -87,11 +88,11 @@ def derived_to_dict(d: FlockDerived) -> dict:
     return out
 
 
-def _load():
-    if not os.path.exists(LIB_PATH):
-        raise ImportError("libflock.so is not built (%s); run __graft_entry__.build() "
-                          "-- there is no CPU fallback" % LIB_PATH)
-    lib = ctypes.CDLL(LIB_PATH)
+def _load(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError("%s is not built; run __graft_entry__.build() "
+                          "-- there is no CPU fallback" % path)
+    lib = ctypes.CDLL(path)
     vp = ctypes.c_void_p
     P = ctypes.POINTER(FlockParams)
     T = ctypes.POINTER(FlockTuning)
@@ -147,6 +148,24 @@ def _load():
 
 
 lib = _load()
+DEBUG_LIB_PATH = os.path.join(HERE, "libflock_debug.so")
+
+
+def use_library(path):
+    """Makes the binding call the library at `path` (for example the
+    FLOCK_DEBUG build, libflock_debug.so, whose index checks latch
+    FLOCK_ERR_BOUNDS); returns the previous library handle, which
+    restore_library puts back.  Handles created by one library must be used
+    and destroyed with that library."""
+    global lib
+    prev = lib
+    lib = _load(path)
+    return prev
+
+
+def restore_library(handle):
+    global lib
+    lib = handle
 
 
 def check(rc):

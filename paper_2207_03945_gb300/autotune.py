@@ -3,7 +3,7 @@
 For a workload (parameters and agent count) it times every candidate launch
 shape -- neighbour-scan form (warp chunks through L1, or shared-memory tiles
 of several sizes), cell size (3 x 3 stencil of cells >= d_v, or 5 x 5 of
-cells >= d_v / 2), lanes per agent (1, 2 or 4) and block size -- checks that each candidate gives the
+cells >= d_v / 2), lanes per agent (1, 2, 4 or 32) and block size -- checks that each candidate gives the
 same bits as the library's default (every shape must), and keeps the
 fastest.  Results are cached in a JSON file keyed by GPU name, agent-count
 bucket (power of two) and sector count.
@@ -19,6 +19,7 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "flock_gb300_tun
 CANDIDATES = (
     [{"mode": 2, "stencil": s, "block": b, "lanes": l}
      for s in (1, 2) for b in (64, 128, 256) for l in (1, 2, 4)] +
+    [{"mode": 2, "stencil": s, "block": 128, "lanes": 32} for s in (1, 2)] +
     [{"mode": 1, "stencil": 1, "tile_w": w, "tile_h": h, "block": 128}
      for (w, h) in ((19, 2), (10, 4), (32, 1))] +
     [{"mode": 1, "stencil": 2, "tile_w": 16, "tile_h": 4, "block": 128}])

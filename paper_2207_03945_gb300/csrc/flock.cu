@@ -303,9 +303,16 @@ int choose_tuning(const Inst &I, int n, const flock_tuning *req, flock_tuning &t
   t.block = r.block ? r.block : 128;
   if (t.block < 64 || t.block > 512 || t.block % 32) return FLOCK_EINVAL;
   // lanes per agent: more lanes keep more warps in flight when there are
-  // few agents; with many, one lane per agent has the least overhead
-  t.lanes = r.lanes ? r.lanes : (n <= 32768 ? 4 : (n <= 524288 ? 2 : 1));
-  if (t.lanes != 1 && t.lanes != 2 && t.lanes != 4) return FLOCK_EINVAL;
+  // few agents; with many, one lane per agent has the least overhead.  An
+  // agent with hundreds of candidates (a view much wider than the spacing of
+  // the agents) gets a whole warp.
+  const double wc = (double)I.L / I.nc;
+  const double cand = n > 0 ? (double)n / ((double)I.L * I.L) * (2.0 * I.halo + 1.0) *
+                                  (2.0 * I.halo + 1.0) * wc * wc
+                            : 0.0;
+  t.lanes = r.lanes ? r.lanes
+                    : (cand >= 256.0 ? 32 : (n <= 32768 ? 4 : (n <= 524288 ? 2 : 1)));
+  if (t.lanes != 1 && t.lanes != 2 && t.lanes != 4 && t.lanes != 32) return FLOCK_EINVAL;
   if (t.mode == 1) t.lanes = 1;
   if (I.kind == 1 && t.mode != 2) return FLOCK_EINVAL;  // tag: direct form only
   const double w = (double)I.L / I.nc;
@@ -368,7 +375,11 @@ cudaError_t set_kernel_attrs() {
                          (const void *)k_neighbours_direct<1, 0, 2, true>,
                          (const void *)k_neighbours_direct<2, 0, 2, true>,
                          (const void *)k_neighbours_direct<1, 0, 4, true>,
-                         (const void *)k_neighbours_direct<2, 0, 4, true>};
+                         (const void *)k_neighbours_direct<2, 0, 4, true>,
+                         (const void *)k_neighbours_direct<1, 0, 32>,
+                         (const void *)k_neighbours_direct<2, 0, 32>,
+                         (const void *)k_neighbours_direct<1, 0, 32, true>,
+                         (const void *)k_neighbours_direct<2, 0, 32, true>};
     g_attr_err = cudaSuccess;
     for (const void *f : fns) {
       cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
@@ -500,6 +511,7 @@ extern "C" int flock_derive(const flock_params *p, const flock_tuning *t, flock_
 
 extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, void *ws,
                           size_t ws_bytes, void *stream, flock_env **out) {
+  NvtxRange nvtx_range("flock:env_create");
   if (!out) return FLOCK_EINVAL;
   *out = nullptr;
   flock_env *e = new (std::nothrow) flock_env();
@@ -611,13 +623,23 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const 
   // with timing events between the kernels, plain stream order
   const bool pdl = !tm;
   if (tm) CK(cudaEventRecordWithFlags(e->ev[0], s, cudaEventRecordExternal));
-  if (n > 0) CK(launch(false, k_apply_bin, (n + 255) / 256, 256, 0, s, gI, B, reset));
+  {
+    NvtxRange r("flock:apply_bin");
+    if (n > 0) CK(launch(false, k_apply_bin, (n + 255) / 256, 256, 0, s, gI, B, reset));
+  }
   if (tm) CK(cudaEventRecordWithFlags(e->ev[1], s, cudaEventRecordExternal));
-  // k_scan follows k_apply_bin only when there was one
-  CK(launch(pdl && n > 0, k_scan, e->n_scan_tiles, 256, 0, s, B));
+  {
+    NvtxRange r("flock:scan");
+    // k_scan follows k_apply_bin only when there was one
+    CK(launch(pdl && n > 0, k_scan, e->n_scan_tiles, 256, 0, s, B));
+  }
   if (tm) CK(cudaEventRecordWithFlags(e->ev[2], s, cudaEventRecordExternal));
-  CK(launch(pdl, k_scatter, e->scatter_grid, 256, 0, s, gI, B));
+  {
+    NvtxRange r("flock:scatter");
+    CK(launch(pdl, k_scatter, e->scatter_grid, 256, 0, s, gI, B));
+  }
   if (tm) CK(cudaEventRecordWithFlags(e->ev[3], s, cudaEventRecordExternal));
+  NvtxRange r_neigh("flock:neighbours");
   if (n > 0) {
     const int blk = e->tuning.block;
     const size_t sm = e->smemD;
@@ -630,17 +652,22 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const 
       const int per_block = blk / lpa;  // agents per block
       const int blocks = (n + per_block - 1) / per_block;
       using KD = void (*)(const Inst *, Bufs);
-      static const KD kd[2][2][3] = {
-          {{k_neighbours_direct<1, 0, 1>, k_neighbours_direct<1, 0, 2>, k_neighbours_direct<1, 0, 4>},
-           {k_neighbours_direct<1, 8, 1>, k_neighbours_direct<1, 8, 2>, k_neighbours_direct<1, 8, 4>}},
-          {{k_neighbours_direct<2, 0, 1>, k_neighbours_direct<2, 0, 2>, k_neighbours_direct<2, 0, 4>},
-           {k_neighbours_direct<2, 8, 1>, k_neighbours_direct<2, 8, 2>, k_neighbours_direct<2, 8, 4>}}};
-      static const KD kt[2][3] = {
+      // one agent per warp (32 lanes) has the generic-sector kernel only
+      static const KD kd[2][2][4] = {
+          {{k_neighbours_direct<1, 0, 1>, k_neighbours_direct<1, 0, 2>, k_neighbours_direct<1, 0, 4>,
+            k_neighbours_direct<1, 0, 32>},
+           {k_neighbours_direct<1, 8, 1>, k_neighbours_direct<1, 8, 2>, k_neighbours_direct<1, 8, 4>,
+            k_neighbours_direct<1, 0, 32>}},
+          {{k_neighbours_direct<2, 0, 1>, k_neighbours_direct<2, 0, 2>, k_neighbours_direct<2, 0, 4>,
+            k_neighbours_direct<2, 0, 32>},
+           {k_neighbours_direct<2, 8, 1>, k_neighbours_direct<2, 8, 2>, k_neighbours_direct<2, 8, 4>,
+            k_neighbours_direct<2, 0, 32>}}};
+      static const KD kt[2][4] = {
           {k_neighbours_direct<1, 0, 1, true>, k_neighbours_direct<1, 0, 2, true>,
-           k_neighbours_direct<1, 0, 4, true>},
+           k_neighbours_direct<1, 0, 4, true>, k_neighbours_direct<1, 0, 32, true>},
           {k_neighbours_direct<2, 0, 1, true>, k_neighbours_direct<2, 0, 2, true>,
-           k_neighbours_direct<2, 0, 4, true>}};
-      const int li = lpa == 1 ? 0 : (lpa == 2 ? 1 : 2);
+           k_neighbours_direct<2, 0, 4, true>, k_neighbours_direct<2, 0, 32, true>}};
+      const int li = lpa == 1 ? 0 : (lpa == 2 ? 1 : (lpa == 4 ? 2 : 3));
       // the V = 8 kernels write observation layout 0 only
       const int v8 = e->inst.v == 8 && e->inst.obs_layout == 0 ? 1 : 0;
       const KD k = e->inst.kind == 1 ? kt[e->inst.halo - 1][li] : kd[e->inst.halo - 1][v8][li];
@@ -686,6 +713,7 @@ static int check_out(const flock_env *e, const float *obs, const float *rew, con
 }
 
 extern "C" int env_reset(flock_env *e, const float *state0, float *obs, float *rew, int32_t *coll) {
+  NvtxRange nvtx_range("flock:env_reset");
   if (!e || (e->n > 0 && !state0)) return FLOCK_EINVAL;
   int rc = check_out(e, obs, rew, coll);
   if (rc) return rc;
@@ -751,17 +779,20 @@ static int step_graph(flock_env *e, const void *act_or_cact, int cont, float *ob
 }
 
 extern "C" int env_step(flock_env *e, const int32_t *act, float *obs, float *rew, int32_t *coll) {
+  NvtxRange nvtx_range("flock:env_step");
   return step_graph(e, act, 0, obs, rew, coll);
 }
 
 extern "C" int env_step_continuous(flock_env *e, const float *act2, float *obs, float *rew,
                                    int32_t *coll) {
+  NvtxRange nvtx_range("flock:env_step_continuous");
   if (act2 && !aligned(act2, 8)) return FLOCK_EINVAL;
   return step_graph(e, act2, 1, obs, rew, coll);
 }
 
 extern "C" int env_rollout(flock_env *e, int T, const int32_t *act, const float *act2, float *obs,
                            float *rew, int32_t *coll) {
+  NvtxRange nvtx_range("flock:env_rollout");
   if (!e || T < 0) return FLOCK_EINVAL;
   if (T == 0) return FLOCK_OK;
   const int n = e->n;
@@ -812,6 +843,7 @@ extern "C" int env_rollout(flock_env *e, int T, const int32_t *act, const float 
 
 extern "C" int env_step_policy(flock_env *e, const uint16_t *weights, int32_t *act, float *rew,
                                int32_t *coll, float *logits, float *obs) {
+  NvtxRange nvtx_range("flock:env_step_policy");
   if (!e || e->inst.v != 8 || e->inst.obs_layout != 0 || e->inst.kind != 0) return FLOCK_EINVAL;
   if (e->n > 0 && (!weights || !act || !rew || !coll || !aligned(weights, 4) ||
                    (obs && !aligned(obs, 8))))
@@ -852,6 +884,7 @@ extern "C" int env_step_policy(flock_env *e, const uint16_t *weights, int32_t *a
 
 extern "C" int env_step_host(flock_env *e, const int32_t *act_h, float *obs_h, float *rew_h,
                              int32_t *coll_h) {
+  NvtxRange nvtx_range("flock:env_step_host");
   if (!e) return FLOCK_EINVAL;
   const size_t n = (size_t)e->n;
   if (n > 0 && (!act_h || !obs_h || !rew_h || !coll_h)) return FLOCK_EINVAL;
@@ -931,6 +964,7 @@ extern "C" int env_set_state(flock_env *e, const float *state) {
 }
 
 extern "C" int env_get_error(flock_env *e, uint32_t *bits) {
+  NvtxRange nvtx_range("flock:env_get_error");
   if (!e || !bits) return FLOCK_EINVAL;
   uint32_t w = 0;
   CK(cudaMemcpyAsync(&w, e->ws + e->lay.err, 4, cudaMemcpyDeviceToHost, e->stream));
@@ -1052,6 +1086,7 @@ int static_scratch(char **out) {
 extern "C" int flock_step_static(const flock_params *p, int n, float *state_dev,
                                  const int32_t *actions_dev, float *obs_dev, float *reward_dev,
                                  int32_t *coll_dev, void *stream, uint32_t *error_bits_out) {
+  NvtxRange nvtx_range("flock:flock_step_static");
   if (!p || n < 0) return FLOCK_EINVAL;
   if (n > kStaticMaxAgents) return FLOCK_EINVAL;  // more agents than the fixed scratch holds
   Inst I;

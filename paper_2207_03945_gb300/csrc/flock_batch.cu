@@ -351,6 +351,7 @@ extern "C" int flock_batch_workspace_bytes(int mi, int ma, int mc, const flock_t
 
 extern "C" int env_batch_create(int mi, int ma, int mc, const flock_tuning *t, void *ws,
                                 size_t ws_bytes, void *stream, flock_batch **out) {
+  NvtxRange nvtx_range("flock:env_batch_create");
   if (!out) return FLOCK_EINVAL;
   *out = nullptr;
   if (mi < 1 || ma < 0 || mc < 1 || mc > kMaxScanTiles * kScanTile) return FLOCK_EINVAL;
@@ -401,6 +402,7 @@ extern "C" int env_batch_create(int mi, int ma, int mc, const flock_tuning *t, v
 
 extern "C" int env_batch_set(flock_batch *b, int n_inst, const flock_params *params,
                              const int *n_agents, float *const *state, const int *reset) {
+  NvtxRange nvtx_range("flock:env_batch_set");
   if (!b || n_inst < 0 || n_inst > b->max_inst || (n_inst > 0 && (!params || !n_agents || !state)))
     return FLOCK_EINVAL;
   std::vector<Inst> ins((size_t)(n_inst > 0 ? n_inst : 1));
@@ -514,6 +516,7 @@ static int batch_enqueue(flock_batch *b, cudaStream_t s) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   KFn fn = batch_kernel(b->halo, b->v, b->layout, b->split);
+  NvtxRange r("flock:batch_launches");
   BCK(cudaLaunchKernelEx(&cfg, fn, (const BatchDev *)(b->ws + L.dev), (Inst *)(b->ws + L.insts),
                          (const int *)(b->ws + L.apre), (const int *)(b->ws + L.cpre),
                          (unsigned *)(b->ws + L.ctr), b->spin_limit));
@@ -529,6 +532,7 @@ static int batch_enqueue(flock_batch *b, cudaStream_t s) {
 
 extern "C" int env_batch_step(flock_batch *b, const int32_t *act, float *obs, float *rew,
                               int32_t *coll) {
+  NvtxRange nvtx_range("flock:env_batch_step");
   if (!b || !b->configured) return FLOCK_EINVAL;
   if (b->dev.n_total == 0) return FLOCK_OK;
   if (!act || !obs || !rew || !coll || ((uintptr_t)obs & 7)) return FLOCK_EINVAL;
@@ -575,6 +579,7 @@ extern "C" int env_batch_step(flock_batch *b, const int32_t *act, float *obs, fl
 }
 
 extern "C" int env_batch_get_error(flock_batch *b, uint32_t *bits) {
+  NvtxRange nvtx_range("flock:env_batch_get_error");
   if (!b || !bits) return FLOCK_EINVAL;
   uint32_t w = 0;
   BCK(cudaMemcpyAsync(&w, b->ws + b->lay.err, 4, cudaMemcpyDeviceToHost, b->stream));

@@ -917,9 +917,15 @@ __device__ __forceinline__ int pick(const int (&x)[N], int r) {
 // collision count, whatever the type); a chaser adds +P per touched runner.
 // The sector accumulators hold two channels of v, the neighbour's type
 // choosing the channel.
-template <int V, bool PIECES, bool TAG = false>
+//
+// ONE (one agent per warp, 32 lanes per agent): every queued pair belongs to
+// that agent, so each lane adds its terms to its own register sum `racc`
+// (added up over the warp at the end) instead of shared-memory atomics that
+// would all hit one word, and the agent's frame needs no shuffle.
+template <int V, bool PIECES, bool TAG = false, bool ONE = false>
 __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W, int count,
-                                            float ux, float uy, const Edges<V> &E8, int ti = 0) {
+                                            float ux, float uy, const Edges<V> &E8, int ti,
+                                            unsigned long long &racc) {
   const int lane = threadIdx.x & 31;
   const int v = V == 8 ? 8 : I.v;
   const int vs = TAG ? 2 * v : v;  // accumulator row length
@@ -928,10 +934,11 @@ __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W,
     const bool valid = e < count;
     float4 E = valid ? W.queue[e] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int w = valid ? __float_as_int(E.w) : lane;
-    const int o = TAG ? (w & 0xff) : w;
+    const int o = ONE ? 0 : (TAG ? (w & 0xff) : w);
     const int tj = TAG ? (w >> 8) : 0;
-    const float uxo = __shfl_sync(kFull, ux, o), uyo = __shfl_sync(kFull, uy, o);
-    const int tio = TAG ? __shfl_sync(kFull, ti, o) : 0;
+    const float uxo = ONE ? ux : __shfl_sync(kFull, ux, o);
+    const float uyo = ONE ? uy : __shfl_sync(kFull, uy, o);
+    const int tio = TAG ? (ONE ? ti : __shfl_sync(kFull, ti, o)) : 0;
     if (valid) {
       const float dx = E.x, dy = E.y, d2 = E.z;
       const bool coll = d2 < I.RC2;
@@ -942,14 +949,20 @@ __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W,
       if constexpr (!TAG) {
         if (!coll) {
           const float t = fmul(fsub(I.RV, dist), I.INV_SPAN);
-          add_term<PIECES>(I, W, o, float_int_u64(fmul(t, I.scaleK)));
+          const unsigned long long tv = float_int_u64(fmul(t, I.scaleK));
+          if (ONE) racc += tv;
+          else add_term<PIECES>(I, W, o, tv);
         }
       } else {
         if (tio == 0 && tj == 0 && !coll) {  // a runner near a runner
           const float t = fmul(fsub(I.RV, dist), I.INV_SPAN);
-          add_term<PIECES>(I, W, o, float_int_u64(fmul(t, I.scaleK)));
+          const unsigned long long tv = float_int_u64(fmul(t, I.scaleK));
+          if (ONE) racc += tv;
+          else add_term<PIECES>(I, W, o, tv);
         } else if (tio == 1 && tj == 0 && coll) {
-          add_term<PIECES>(I, W, o, (unsigned long long)I.PK);  // a chaser touching a runner
+          // a chaser touching a runner
+          if (ONE) racc += (unsigned long long)I.PK;
+          else add_term<PIECES>(I, W, o, (unsigned long long)I.PK);
         }
       }
       const float lx = fadd(fmul(dx, uxo), fmul(dy, uyo));
@@ -967,7 +980,7 @@ __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W,
     }
   }
   __syncwarp();
-  if (!PIECES) return;
+  if (!PIECES || ONE) return;
   // each lane folds its own pieces into its 64-bit sum
   W.acc[lane] += (unsigned long long)W.accp[lane] +
                  ((unsigned long long)W.accp[32 + lane] << 24) +
@@ -987,8 +1000,10 @@ __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, c
                                            int a, int n, int self, float sx, float sy, float xi,
                                            float yi, float ux, float uy, int &qn, int &nin,
                                            int &ncoll, const Edges<V> &E8,
-                                           const uint8_t *stype = nullptr, int ti = 0) {
+                                           const uint8_t *stype, int ti,
+                                           unsigned long long &racc) {
   constexpr int A = 32 / LPA;
+  constexpr bool ONE = A == 1;
   const int lane = threadIdx.x & 31;
   const int slot = lane & (A - 1), sub = lane / A;
   const unsigned lt = (1u << lane) - 1u;
@@ -1024,7 +1039,7 @@ __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, c
       qn += __popc(m);
       if (qn > kQueue - 32) {
         __syncwarp();
-        drain_direct<V, PIECES, TAG>(I, W, qn, ux, uy, E8, ti);
+        drain_direct<V, PIECES, TAG, ONE>(I, W, qn, ux, uy, E8, ti, racc);
         qn = 0;
       }
     }
@@ -1075,7 +1090,7 @@ __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, c
     qn += __popc(mb);
     if (qn > kQueueWide - 64) {
       __syncwarp();
-      drain_direct<V, PIECES, TAG>(I, W, qn, ux, uy, E8, ti);
+      drain_direct<V, PIECES, TAG, ONE>(I, W, qn, ux, uy, E8, ti, racc);
       qn = 0;
     }
   }
@@ -1276,7 +1291,10 @@ __device__ __forceinline__ void policy_mtile(const PolicyCtx &P, int row0, int &
 }
 
 // A warp takes the 32 / LPA consecutive sorted agents [gp0, gp1); LPA lanes
-// share each agent's candidates (LPA = 1, 2 or 4; the policy form uses 1).
+// share each agent's candidates (LPA = 1, 2, 4 or 32; the policy form uses
+// 1).  LPA = 32 gives a whole warp to one agent: the form for agents with
+// hundreds of candidates (a wide view), whose few agents would otherwise
+// leave most of the GPU idle.
 // TAG: the tag environment (needs V == 0 and no policy): two colour
 // channels of sectors, type-dependent rewards (see drain_direct), and the
 // observation row is the 2v channel distances.
@@ -1290,7 +1308,7 @@ template <int H, int V, bool POL = false, bool PIECES = true, int LPA = 1, bool 
 __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
                               const DirectArea &W, unsigned &err,
                               const PolicyCtx *pc = nullptr) {
-  static_assert(LPA == 1 || LPA == 2 || LPA == 4, "lanes per agent");
+  static_assert(LPA == 1 || LPA == 2 || LPA == 4 || LPA == 32, "lanes per agent");
   static_assert(!POL || LPA == 1, "the policy tile holds 32 agents");
   static_assert(!TAG || (V == 0 && !POL), "tag uses the generic sector count");
   constexpr int A = 32 / LPA;
@@ -1360,6 +1378,7 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
     }
   }
   int nin = 0, ncoll = 0;
+  unsigned long long racc = 0;  // one agent per warp: this lane's share of its reward sum
   __syncwarp();
   int qn = 0;
   const int self = have ? gp : -1;
@@ -1367,7 +1386,7 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
 #pragma unroll
     for (int r = 0; r < 2 * H + 1; ++r)
       direct_run<false, V, PIECES, LPA, TAG>(I, W, B.sxy, ra[r], rn[r], self, 0.f, 0.f, xi, yi,
-                                             ux, uy, qn, nin, ncoll, E8, B.stype, ti);
+                                             ux, uy, qn, nin, ncoll, E8, B.stype, ti, racc);
   } else if (COMPACT) {
     // per stencil row three runs: the interior, the cells across the left
     // boundary (virtual columns [vlo, 0) -> [vlo + nc, nc)) and those across
@@ -1397,7 +1416,7 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
         }
       }
       direct_run<true, V, PIECES, LPA, TAG>(I, W, B.sxy, a, n, self, sx, sy, xi, yi, ux, uy, qn,
-                                            nin, ncoll, E8, B.stype, ti);
+                                            nin, ncoll, E8, B.stype, ti, racc);
     }
   } else {
 #pragma unroll
@@ -1406,7 +1425,7 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
       const float sy = vr < 0 ? -I.L : (vr >= nc ? I.L : 0.0f);
       const int rowg = I.cell_base + wrapi(vr, nc) * nc;
       direct_run<true, V, PIECES, LPA, TAG>(I, W, B.sxy, ra[r], rn[r], self, 0.f, sy, xi, yi,
-                                            ux, uy, qn, nin, ncoll, E8, B.stype, ti);
+                                            ux, uy, qn, nin, ncoll, E8, B.stype, ti, racc);
       // cells across the left boundary: virtual columns [vlo, 0) -> [vlo + nc, nc)
       int a = 0, n = 0;
       if (have && lw) {
@@ -1414,7 +1433,7 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
         n = cst[rowg + nc] - a;
       }
       direct_run<true, V, PIECES, LPA, TAG>(I, W, B.sxy, a, n, self, -I.L, sy, xi, yi, ux, uy,
-                                            qn, nin, ncoll, E8, B.stype, ti);
+                                            qn, nin, ncoll, E8, B.stype, ti, racc);
       // cells across the right boundary: virtual columns [nc, vhi) -> [0, vhi - nc)
       a = 0;
       n = 0;
@@ -1423,11 +1442,18 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
         n = cst[rowg + vhi - nc] - a;
       }
       direct_run<true, V, PIECES, LPA, TAG>(I, W, B.sxy, a, n, self, I.L, sy, xi, yi, ux, uy,
-                                            qn, nin, ncoll, E8, B.stype, ti);
+                                            qn, nin, ncoll, E8, B.stype, ti, racc);
     }
   }
   __syncwarp();
-  drain_direct<V, PIECES, TAG>(I, W, qn, ux, uy, E8, ti);
+  drain_direct<V, PIECES, TAG, A == 1>(I, W, qn, ux, uy, E8, ti, racc);
+  if (A == 1) {
+    // one agent per warp: the lanes' register sums make its reward sum
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) racc += __shfl_xor_sync(kFull, racc, m);
+    if (lane == 0) W.acc[0] = racc;
+    __syncwarp();
+  }
   // the lanes of an agent add up their counts
 #pragma unroll
   for (int m = A; m < 32; m <<= 1) {

@@ -5,7 +5,23 @@
 
 #include "flock.h"
 
+// NVTX push/pop, defined in flock_nvtx.cu: the NVTX header includes the
+// system's fcntl.h, whose `struct flock` would clash with namespace flock.
+extern "C" __attribute__((visibility("hidden"))) void flock_nvtx_push(const char *name);
+extern "C" __attribute__((visibility("hidden"))) void flock_nvtx_pop(void);
+
 namespace flock {
+
+// NVTX range over a scope (header-only NVTX 3: without a profiler attached a
+// range costs a few nanoseconds and needs no library).  Entry points and
+// the launches of each phase are named "flock:<what>", so a timeline shows
+// where a step's host time goes and which call enqueued which kernels.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { flock_nvtx_push(name); }
+  ~NvtxRange() { flock_nvtx_pop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct Inst;
 

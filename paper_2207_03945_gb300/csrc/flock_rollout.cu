@@ -76,6 +76,7 @@ using namespace flock;
 
 extern "C" int flock_gae(int T, int n, const float *reward, const float *value, float gamma,
                          float lambda, float *adv, float *ret, void *stream) {
+  flock::NvtxRange nvtx_range("flock:gae");
   if (T < 0 || n < 0) return FLOCK_EINVAL;
   if (!(gamma >= 0.0f && gamma <= 1.0f && lambda >= 0.0f && lambda <= 1.0f)) return FLOCK_EINVAL;
   if (T == 0 || n == 0) return FLOCK_OK;

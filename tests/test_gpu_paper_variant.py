@@ -53,6 +53,8 @@ def same(g, o, tag):
 
 
 @pytest.mark.parametrize("tuning", [None, {"mode": 2, "lanes": 1}, {"mode": 2, "lanes": 4},
+                                    {"mode": 2, "lanes": 32},
+                                    {"mode": 2, "stencil": 2, "lanes": 32},
                                     {"mode": 2, "stencil": 2}, {"mode": 1}],
                          ids=lambda d: "default" if d is None else "-".join(
                              "%s%s" % kv for kv in d.items()))
@@ -80,6 +82,19 @@ def test_paper_variant_full_size():
     o, _ = oracle_cont(p, st0, acts, 1)
     same(g, o, "16k")
     assert err == 0
+
+
+def test_wide_view_gets_a_warp_per_agent():
+    """The library's default launch shape for the paper's flock (about 1,800
+    candidates per agent) gives each agent a whole warp."""
+    p = fi.paper_params(16000)
+    env = F.FlockEnv(p, 16000, device=DEV)
+    assert env.tuning()["lanes"] == 32
+    env.close()
+    p = fi.default_params(fi.side_for(50000))
+    env = F.FlockEnv(p, 50000, device=DEV)
+    assert env.tuning()["lanes"] in (1, 2, 4)
+    env.close()
 
 
 def test_continuous_with_discrete_values_equals_discrete_step():

@@ -159,6 +159,8 @@ def test_parameter_variants(over):
     {"mode": 2, "stencil": 1, "tile_w": 0, "tile_h": 0, "block": 512, "lanes": 4},
     {"mode": 2, "stencil": 2, "tile_w": 0, "tile_h": 0, "block": 128, "lanes": 4},
     {"mode": 2, "stencil": 2, "tile_w": 0, "tile_h": 0, "block": 256, "lanes": 2},
+    {"mode": 2, "stencil": 1, "tile_w": 0, "tile_h": 0, "block": 128, "lanes": 32},
+    {"mode": 2, "stencil": 2, "tile_w": 0, "tile_h": 0, "block": 64, "lanes": 32},
 ], ids=lambda d: "m%d-s%d-%dx%d-b%d-l%d" % (d["mode"], d["stencil"], d["tile_w"], d["tile_h"],
                                              d["block"], d.get("lanes", 1)))
 def test_launch_shapes_are_bit_identical(tuning):
@@ -176,10 +178,10 @@ def test_launch_shapes_are_bit_identical(tuning):
     assert_same(g, o, str(tuning))
 
 
-@pytest.mark.parametrize("mode", [1, 2, 4])
+@pytest.mark.parametrize("mode", [1, 2, 4, 32])
 @pytest.mark.parametrize("side,stencil", [(11.0, 1), (10.5, 1), (10.5, 2), (16.0, 1), (26.0, 2)])
 def test_small_square_wraps_everywhere(side, stencil, mode):
-    """mode 4 here: the direct form (mode 2) with 4 lanes per agent."""
+    """mode 4 (32) here: the direct form (mode 2) with 4 (32) lanes per agent."""
     # squares only just wider than 2 d_v: one to five cells per axis, every
     # stencil wraps and some visit a cell twice under different shifts
     n, steps = 60, 10
@@ -187,13 +189,13 @@ def test_small_square_wraps_everywhere(side, stencil, mode):
     st0 = fi.initial_state(n, side, 5)
     acts = fi.random_actions(n, steps, 5)
     tun = {"stencil": stencil, "mode": mode} if mode < 4 else {"stencil": stencil, "mode": 2,
-                                                                 "lanes": 4}
+                                                                 "lanes": mode}
     g, _, _ = gpu_run(p, st0, acts, tun)
     o, _ = oracle_run(p, st0, acts)
     assert_same(g, o, "side %g" % side)
 
 
-@pytest.mark.parametrize("mode", [1, 2, 4])
+@pytest.mark.parametrize("mode", [1, 2, 4, 32])
 def test_dense_cluster_exceeds_shared_memory(mode):
     """6,000 agents packed into a 20 x 20 patch: in mode 1 tiles overflow the
     shared staging buffer and take the per-thread path; in mode 2 warps see
@@ -205,7 +207,7 @@ def test_dense_cluster_exceeds_shared_memory(mode):
     st0[:, 1] = (40.0 + 20.0 * rng.random(n)).astype(np.float32)
     p = fi.default_params(100.0)
     acts = fi.random_actions(n, 2, 6)
-    g, err, _ = gpu_run(p, st0, acts, {"mode": mode} if mode < 4 else {"mode": 2, "lanes": 4})
+    g, err, _ = gpu_run(p, st0, acts, {"mode": mode} if mode < 4 else {"mode": 2, "lanes": mode})
     o, flags = oracle_run(p, st0, acts)
     assert_same(g, o, "cluster")
     assert err == flags == 0

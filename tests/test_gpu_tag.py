@@ -40,7 +40,8 @@ def test_hand_worked_case_on_gpu():
 
 
 @pytest.mark.parametrize("tuning", [None, {"mode": 2, "lanes": 1}, {"mode": 2, "lanes": 2},
-                                    {"mode": 2, "stencil": 2, "lanes": 4}],
+                                    {"mode": 2, "stencil": 2, "lanes": 4},
+                                    {"mode": 2, "lanes": 32}, {"mode": 2, "stencil": 2, "lanes": 32}],
                          ids=lambda d: "default" if d is None else "-".join(
                              "%s%s" % kv for kv in d.items()))
 def test_tag_trajectory(tuning):
