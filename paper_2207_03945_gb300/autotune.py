@@ -25,8 +25,12 @@ CANDIDATES = (
     [{"mode": 1, "stencil": 2, "tile_w": 16, "tile_h": 4, "block": 128}])
 
 # mode 2: one persistent launch per step; mode 3: persistent binning, then
-# a separate neighbour-scan launch
-BATCH_CANDIDATES = tuple({"stencil": st, "mode": m} for st in (1, 2) for m in (2, 3))
+# a separate neighbour-scan launch with `block` threads per block; mode 4:
+# binning by three kernels, then the neighbour launch
+BATCH_CANDIDATES = tuple(
+    [{"stencil": st, "mode": 2} for st in (1, 2)] +
+    [{"stencil": st, "mode": m, "block": blk} for st in (1, 2) for m in (3, 4)
+     for blk in (64, 128, 256)])
 
 
 def _hold(torch):

@@ -18,14 +18,6 @@
 
 namespace flock {
 
-// Programmatic dependent launch: a kernel launched with the programmatic
-// serialization attribute is set up while the kernel before it drains; it
-// waits here until that kernel has finished and its writes are visible.
-// (No early trigger: blocks of the next kernel held resident while this one
-// still runs made the step slower.)  Launched without the attribute, the
-// wait returns at once.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
 __global__ void __launch_bounds__(256) k_apply_bin(const Inst *__restrict__ gI, Bufs B, int reset) {
   __shared__ Inst sI;
   load_inst(sI, gI);
@@ -314,7 +306,7 @@ int choose_tuning(const Inst &I, int n, const flock_tuning *req, flock_tuning &t
                     : (cand >= 256.0 ? 32 : (n <= 32768 ? 4 : (n <= 524288 ? 2 : 1)));
   if (t.lanes != 1 && t.lanes != 2 && t.lanes != 4 && t.lanes != 32) return FLOCK_EINVAL;
   if (t.mode == 1) t.lanes = 1;
-  if (I.kind == 1 && t.mode != 2) return FLOCK_EINVAL;  // tag: direct form only
+  if (I.kind == 1 && t.mode == 1) return FLOCK_EINVAL;  // tag: direct forms only
   const double w = (double)I.L / I.nc;
   const double per_cell = n > 0 ? (double)n / ((double)I.L * I.L) * w * w : 1.0;
   t.tile_h = r.tile_h ? r.tile_h : 2;
@@ -380,11 +372,11 @@ cudaError_t set_kernel_attrs() {
                          (const void *)k_neighbours_direct<2, 0, 32>,
                          (const void *)k_neighbours_direct<1, 0, 32, true>,
                          (const void *)k_neighbours_direct<2, 0, 32, true>};
-    g_attr_err = cudaSuccess;
-    for (const void *f : fns) {
-      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
-      if (e != cudaSuccess && g_attr_err == cudaSuccess) g_attr_err = e;
-    }
+    for (const void *f : fns)
+      if (g_attr_err == cudaSuccess) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+        if (e != cudaSuccess) g_attr_err = e;
+      }
   });
   return g_attr_err;
 }
@@ -588,26 +580,6 @@ extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, v
   return FLOCK_OK;
 }
 
-// Launch with programmatic stream serialization (pdl = true): the kernel's
-// blocks may be scheduled while the previous kernel in the stream finishes,
-// hiding the launch gap; every kernel launched this way waits in pdl_wait()
-// before it reads what the previous one wrote.
-template <typename... KArgs, typename... Args>
-static cudaError_t launch(bool pdl, void (*k)(KArgs...), int grid, int block, size_t smem,
-                         cudaStream_t s, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3((unsigned)block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = pdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, k, ((KArgs)args)...);
-}
-
 // act: discrete actions, or cact (when not null): continuous ones.
 static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const float2 *cact,
                         float *obs, float *rew, int32_t *coll, int reset) {
@@ -670,7 +642,8 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const 
       const int li = lpa == 1 ? 0 : (lpa == 2 ? 1 : (lpa == 4 ? 2 : 3));
       // the V = 8 kernels write observation layout 0 only
       const int v8 = e->inst.v == 8 && e->inst.obs_layout == 0 ? 1 : 0;
-      const KD k = e->inst.kind == 1 ? kt[e->inst.halo - 1][li] : kd[e->inst.halo - 1][v8][li];
+      const int h = e->inst.halo - 1;
+      const KD k = e->inst.kind == 1 ? kt[h][li] : kd[h][v8][li];
       CK(launch(pdl, k, blocks, blk, sm, s, gI, B));
     }
   }
@@ -963,6 +936,22 @@ extern "C" int env_set_state(flock_env *e, const float *state) {
   return FLOCK_OK;
 }
 
+#ifdef FLOCK_DEBUG
+// Debug build: takes (reads and clears) this translation unit's latched
+// FLOCK_ERR_BOUNDS word; waits for the stream.
+static unsigned dbg_take(cudaStream_t s) {
+  unsigned w = 0;
+  const unsigned z = 0;
+  if (cudaMemcpyFromSymbolAsync(&w, flock::g_flock_dbg_bits, 4, 0, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaMemcpyToSymbolAsync(flock::g_flock_dbg_bits, &z, 4, 0, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return FLOCK_ERR_BOUNDS;  // could not read it: report the check as failed
+  return w;
+}
+#endif
+
 extern "C" int env_get_error(flock_env *e, uint32_t *bits) {
   NvtxRange nvtx_range("flock:env_get_error");
   if (!e || !bits) return FLOCK_EINVAL;
@@ -970,6 +959,9 @@ extern "C" int env_get_error(flock_env *e, uint32_t *bits) {
   CK(cudaMemcpyAsync(&w, e->ws + e->lay.err, 4, cudaMemcpyDeviceToHost, e->stream));
   CK(cudaMemsetAsync(e->ws + e->lay.err, 0, 4, e->stream));
   CK(cudaStreamSynchronize(e->stream));
+#ifdef FLOCK_DEBUG
+  w |= dbg_take(e->stream);
+#endif
   *bits = w;
   return FLOCK_OK;
 }
@@ -1174,6 +1166,9 @@ extern "C" int flock_step_static(const flock_params *p, int n, float *state_dev,
     uint32_t w = 0;
     CK(cudaMemcpyAsync(&w, sp + kSErr, 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+#ifdef FLOCK_DEBUG
+    w |= dbg_take(s);
+#endif
     *error_bits_out = w;
   }
   return FLOCK_OK;

@@ -187,19 +187,70 @@ done:
   }
 }
 
-// Phase D of the split form, a launch of its own (so the wide direct scan of
+// ---------------------------------------------------------------------------
+// Binning as three kernels (mode 4), the single environment's form over the
+// flattened agents and cells of all active instances: each kernel walks its
+// work list with a grid-stride loop (a fixed grid serves every active set);
+// the scan and scatter start under programmatic dependent launch.  No grid
+// barrier: the kernel boundaries order the phases.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_bbin_apply(const BatchDev *__restrict__ d,
+                                                    const Inst *__restrict__ insts,
+                                                    const int *__restrict__ apre, unsigned *ctr) {
+  const BatchDev D = *d;
+  const Bufs &B = D.B;
+  // the chunk ticket of this step's neighbour launch (the previous step's
+  // launch has finished: this kernel starts after it in stream order)
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctr[kCtrTicket] = 0;
+  unsigned err = 0;
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < D.n_total; f += gridDim.x * blockDim.x) {
+    const int k = find_inst(apre, D.n_inst, f);
+    const Inst &I = insts[k];
+    phaseA_agent(I, f - I.agent_base, B.actions + I.agent_base, nullptr, I.reset, B.counts,
+                 B.cellrank, err);
+  }
+  if (err) atomicOr(B.err, err);
+}
+
+__global__ void __launch_bounds__(256) k_bbin_scan(const BatchDev *__restrict__ d) {
+  __shared__ int sm[kScanTile + 34];
+  pdl_wait();
+  const BatchDev D = *d;
+  for (int t = blockIdx.x; t < D.n_scan_tiles; t += gridDim.x) phaseB_tile(t, D.B, sm);
+}
+
+// dynamic shared memory: (scan tiles + 1) ints of tile prefix
+__global__ void __launch_bounds__(256) k_bbin_scatter(const BatchDev *__restrict__ d,
+                                                      const Inst *__restrict__ insts,
+                                                      const int *__restrict__ apre) {
+  extern __shared__ int tp[];
+  __shared__ int wsum[33];
+  pdl_wait();
+  const BatchDev D = *d;
+  const Bufs &B = D.B;
+  tile_prefix(B, tp, wsum);
+  const int stride = gridDim.x * blockDim.x;
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < D.n_total; f += stride) {
+    const int k = find_inst(apre, D.n_inst, f);
+    const Inst &I = insts[k];
+    phaseC_agent(f, I.state + (f - I.agent_base), B, tp);
+  }
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= D.c_total; c += stride)
+    phaseC_cell(c, B, tp);
+}
+
+// Phase D of the split forms, a launch of its own (so the wide direct scan of
 // the standalone kernels has the registers it wants): every warp takes
 // chunks of 32 cell-sorted agents from the shared ticket (zero when the
-// binning launch ends) and keeps its copy of the instance descriptor while
+// binning ends) and keeps its copy of the instance descriptor while
 // consecutive chunks stay in one instance.  A step whose binning launch gave
 // up at a grid barrier (FLOCK_ERR_TIMEOUT latched) is left unobserved.
-constexpr int kNeighBlock = 128;
-
 template <int H, int V>
-__global__ void __launch_bounds__(kNeighBlock) k_batch_neigh(const BatchDev *__restrict__ d,
-                                                             Inst *insts, const int *cpre,
-                                                             unsigned *ctr) {
+__global__ void __launch_bounds__(256) k_batch_neigh(const BatchDev *__restrict__ d,
+                                                     Inst *insts, const int *cpre,
+                                                     unsigned *ctr) {
   extern __shared__ __align__(16) char smem[];
+  pdl_wait();
   const BatchDev D = *d;
   const Bufs &B = D.B;
   if (ld_acquire(B.err) & FLOCK_ERR_TIMEOUT) return;
@@ -231,8 +282,8 @@ __global__ void __launch_bounds__(kNeighBlock) k_batch_neigh(const BatchDev *__r
   if (err) atomicOr(B.err, err);
 }
 
-static size_t neigh_smem(int v) {
-  return (size_t)(kNeighBlock / 32) * (sizeof(Inst) + direct_warp_bytes(v));
+static size_t neigh_smem(int v, int block) {
+  return (size_t)(block / 32) * (sizeof(Inst) + direct_warp_bytes(v));
 }
 
 // Dynamic shared memory of the persistent kernel: the scan tile or the prefix
@@ -314,8 +365,13 @@ struct flock_batch {
   cudaStream_t stream, cap_stream;
   cudaGraphExec_t graph;
   int grid, v, halo, layout;
-  bool split;
+  int mode;        // 2: fused persistent; 3: persistent binning + neighbour launch;
+                   // 4: binning kernels + neighbour launch
+  bool split;      // the neighbour scan is a launch of its own (modes 3, 4)
+  bool kbin;       // binning by three kernels (mode 4)
+  int nblock;      // threads per block of the neighbour launch
   int neigh_grid;  // blocks of the split form's neighbour launch (all resident)
+  int bin_grid, scan_grid, scatter_grid;  // mode 4 binning kernels (grid-stride)
   unsigned spin_limit;
   BatchDev dev;  // host copy
   std::vector<Inst> insts;
@@ -366,14 +422,23 @@ extern "C" int env_batch_create(int mi, int ma, int mc, const flock_tuning *t, v
   if (b->halo != 1 && b->halo != 2) { delete b; return FLOCK_EINVAL; }
   b->tuning.stencil = b->halo;
   // mode 2: one persistent launch runs every phase; mode 3: the persistent
-  // launch bins (phases A-C) and a second launch runs the neighbour scan
-  b->split = b->tuning.mode == 3;
-  if (b->tuning.mode != 0 && b->tuning.mode != 2 && b->tuning.mode != 3) {
+  // launch bins (phases A-C) and a second launch runs the neighbour scan;
+  // mode 4: three binning kernels, then the neighbour launch
+  b->mode = b->tuning.mode ? b->tuning.mode : 2;
+  if (b->mode < 2 || b->mode > 4) {
     delete b;
     return FLOCK_EINVAL;
   }
-  b->tuning.mode = b->split ? 3 : 2;
-  b->tuning.block = kBatchBlock;
+  b->split = b->mode != 2;
+  b->kbin = b->mode == 4;
+  // tuning.block: the neighbour launch's block in the split forms
+  b->nblock = b->split ? (b->tuning.block ? b->tuning.block : 128) : kBatchBlock;
+  if (b->nblock < 64 || b->nblock > 256 || b->nblock % 32) {
+    delete b;
+    return FLOCK_EINVAL;
+  }
+  b->tuning.mode = b->mode;
+  b->tuning.block = b->nblock;
   b->lay = batch_layout(mi, ma, mc);
   if (!ws || ((uintptr_t)ws & 255) || ws_bytes < b->lay.total) { delete b; return FLOCK_ENOSPACE; }
   b->ws = (char *)ws;
@@ -381,10 +446,16 @@ extern "C" int env_batch_create(int mi, int ma, int mc, const flock_tuning *t, v
   b->spin_limit = 1u << 22;
   b->v = 0;
   b->layout = 0;
-  int dev = 0, coop = 0;
+  int dev = 0, coop = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  if (!coop) { delete b; return FLOCK_EINVAL; }
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (!coop && !b->kbin) { delete b; return FLOCK_EINVAL; }
+  // grid-stride binning kernels: a few resident blocks per SM
+  b->bin_grid = 8 * sms;
+  b->scatter_grid = 4 * sms;
+  const int max_tiles = (mc + kScanTile - 1) / kScanTile;
+  b->scan_grid = max_tiles < 4 * sms ? max_tiles : 4 * sms;
   cudaError_t ce = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
   if (ce != cudaSuccess) { delete b; return cuda_fail(ce, "cudaStreamCreate"); }
   const BLayout &L = b->lay;
@@ -440,21 +511,25 @@ extern "C" int env_batch_set(flock_batch *b, int n_inst, const flock_params *par
   cpre[n_inst] = (int)nchunk;
   if (n_inst > 0 && (v != b->v || layout != b->layout)) {
     // the kernel variant (and its shared memory) depends on v and the layout
-    KFn fn = batch_kernel(b->halo, v, layout, b->split);
-    const size_t sm = batch_smem(v, b->split, (b->max_cells + kScanTile - 1) / kScanTile);
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    BCK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kBatchBlock, sm));
-    if (per < 1) return FLOCK_EINVAL;  // too many sectors for one block
-    b->grid = per * sms;
+    if (!b->kbin) {
+      KFn fn = batch_kernel(b->halo, v, layout, b->split);
+      const size_t sm = batch_smem(v, b->split, (b->max_cells + kScanTile - 1) / kScanTile);
+      BCK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kBatchBlock, sm));
+      if (per < 1) return FLOCK_EINVAL;  // too many sectors for one block
+      b->grid = per * sms;
+    } else {
+      b->grid = b->bin_grid;
+    }
     if (b->split) {
       NFn nf = neigh_kernel(b->halo, v, layout);
+      const size_t nsm = neigh_smem(v, b->nblock);
       int pn = 0;
-      BCK(cudaFuncSetAttribute(nf, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)neigh_smem(v)));
-      BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pn, nf, kNeighBlock, neigh_smem(v)));
+      BCK(cudaFuncSetAttribute(nf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsm));
+      BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pn, nf, b->nblock, nsm));
       if (pn < 1) return FLOCK_EINVAL;
       b->neigh_grid = pn * sms;
     }
@@ -502,9 +577,38 @@ extern "C" int env_batch_set(flock_batch *b, int n_inst, const flock_params *par
   return FLOCK_OK;
 }
 
+static int batch_enqueue_persistent(flock_batch *b, cudaStream_t s);
+
 static int batch_enqueue(flock_batch *b, cudaStream_t s) {
   const BLayout &L = b->lay;
   if (b->timing) BCK(cudaEventRecordWithFlags(b->ev[0], s, cudaEventRecordExternal));
+  const BatchDev *dv = (const BatchDev *)(b->ws + L.dev);
+  Inst *ins = (Inst *)(b->ws + L.insts);
+  const int *apre = (const int *)(b->ws + L.apre);
+  const int *cpre = (const int *)(b->ws + L.cpre);
+  unsigned *ctr = (unsigned *)(b->ws + L.ctr);
+  if (b->kbin) {
+    NvtxRange r("flock:batch_binning");
+    const int max_tiles = (b->max_cells + kScanTile - 1) / kScanTile;
+    BCK(launch(false, k_bbin_apply, b->bin_grid, 256, 0, s, dv, (const Inst *)ins, apre, ctr));
+    BCK(launch(true, k_bbin_scan, b->scan_grid, 256, 0, s, dv));
+    BCK(launch(true, k_bbin_scatter, b->scatter_grid, 256, (size_t)(max_tiles + 1) * 4, s, dv,
+               (const Inst *)ins, apre));
+  } else {
+    const int rc = batch_enqueue_persistent(b, s);
+    if (rc) return rc;
+  }
+  if (b->split) {
+    NvtxRange r("flock:batch_neighbours");
+    BCK(launch(b->kbin, neigh_kernel(b->halo, b->v, b->layout), b->neigh_grid,
+               b->nblock, neigh_smem(b->v, b->nblock), s, dv, ins, cpre, ctr));
+  }
+  if (b->timing) BCK(cudaEventRecordWithFlags(b->ev[1], s, cudaEventRecordExternal));
+  return FLOCK_OK;
+}
+
+static int batch_enqueue_persistent(flock_batch *b, cudaStream_t s) {
+  const BLayout &L = b->lay;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(b->grid);
   cfg.blockDim = dim3(kBatchBlock);
@@ -516,17 +620,10 @@ static int batch_enqueue(flock_batch *b, cudaStream_t s) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   KFn fn = batch_kernel(b->halo, b->v, b->layout, b->split);
-  NvtxRange r("flock:batch_launches");
+  NvtxRange r("flock:batch_persistent");
   BCK(cudaLaunchKernelEx(&cfg, fn, (const BatchDev *)(b->ws + L.dev), (Inst *)(b->ws + L.insts),
                          (const int *)(b->ws + L.apre), (const int *)(b->ws + L.cpre),
                          (unsigned *)(b->ws + L.ctr), b->spin_limit));
-  if (b->split) {
-    neigh_kernel(b->halo, b->v, b->layout)<<<b->neigh_grid, kNeighBlock, neigh_smem(b->v), s>>>(
-        (const BatchDev *)(b->ws + L.dev), (Inst *)(b->ws + L.insts),
-        (const int *)(b->ws + L.cpre), (unsigned *)(b->ws + L.ctr));
-    BCK(cudaGetLastError());
-  }
-  if (b->timing) BCK(cudaEventRecordWithFlags(b->ev[1], s, cudaEventRecordExternal));
   return FLOCK_OK;
 }
 
@@ -578,6 +675,22 @@ extern "C" int env_batch_step(flock_batch *b, const int32_t *act, float *obs, fl
   return FLOCK_OK;
 }
 
+#ifdef FLOCK_DEBUG
+// Debug build: takes (reads and clears) this translation unit's latched
+// FLOCK_ERR_BOUNDS word; waits for the stream.
+static unsigned dbg_take(cudaStream_t s) {
+  unsigned w = 0;
+  const unsigned z = 0;
+  if (cudaMemcpyFromSymbolAsync(&w, flock::g_flock_dbg_bits, 4, 0, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaMemcpyToSymbolAsync(flock::g_flock_dbg_bits, &z, 4, 0, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return FLOCK_ERR_BOUNDS;  // could not read it: report the check as failed
+  return w;
+}
+#endif
+
 extern "C" int env_batch_get_error(flock_batch *b, uint32_t *bits) {
   NvtxRange nvtx_range("flock:env_batch_get_error");
   if (!b || !bits) return FLOCK_EINVAL;
@@ -592,6 +705,9 @@ extern "C" int env_batch_get_error(flock_batch *b, uint32_t *bits) {
     BCK(cudaMemsetAsync(b->ws + b->lay.counts, 0, (size_t)b->max_cells * 4, b->stream));
     BCK(cudaStreamSynchronize(b->stream));
   }
+#ifdef FLOCK_DEBUG
+  w |= dbg_take(b->stream);
+#endif
   *bits = w;
   return FLOCK_OK;
 }

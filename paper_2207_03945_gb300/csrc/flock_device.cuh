@@ -75,6 +75,66 @@ struct Bufs {
   int n_total, c_total, n_scan_tiles, pad;
 };
 
+// Debug build (FLOCK_DEBUG, libflock_debug.so): index checks on the step's
+// scratch and output accesses.  A failed check latches FLOCK_ERR_BOUNDS in
+// this translation unit's word (read and cleared with the error bits) and
+// the access is skipped; nothing traps.  In the release build every check
+// is the constant true and compiles away.
+#ifdef FLOCK_DEBUG
+static __device__ unsigned g_flock_dbg_bits;
+__device__ __forceinline__ bool dbg_ok(bool cond) {
+  if (!cond) atomicOr(&g_flock_dbg_bits, FLOCK_ERR_BOUNDS);
+  return cond;
+}
+#else
+__device__ __forceinline__ constexpr bool dbg_ok(bool) { return true; }
+#endif
+
+// Shared-memory accesses of the neighbour scan's per-warp areas, issued as
+// shared-space instructions on 32-bit shared addresses.  The areas are
+// carved from dynamic shared memory and reached through pointers whose
+// address space the compiler does not always see; generic-address atomics
+// cost several times a shared one.  `red` updates return nothing.
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void sred_add_u32(unsigned a, unsigned v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void sred_min_u32(unsigned a, unsigned v) {
+  asm volatile("red.shared.min.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void sred_add_u64(unsigned a, unsigned long long v) {
+  asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+__device__ __forceinline__ void sst_f4(unsigned a, float4 v) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ float4 sld_f4(unsigned a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(a)
+               : "memory");
+  return v;
+}
+
+// A candidate run [a, a + n) of the sorted arrays (n_total entries); in the
+// debug build a run outside them is checked, latched and emptied.
+__device__ __forceinline__ void dbg_run(int a, int &n, int n_total) {
+  if (!dbg_ok(n <= 0 || (a >= 0 && a + n <= n_total))) n = 0;
+}
+
+// Programmatic dependent launch: a kernel launched with the programmatic
+// serialization attribute is set up while the kernel before it drains; it
+// waits here until that kernel has finished and its writes are visible.
+// (No early trigger: blocks of the next kernel held resident while this one
+// still runs made the step slower.)  Launched without the attribute, the
+// wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // Exactly-rounded FP32 arithmetic.
 // ---------------------------------------------------------------------------
@@ -268,6 +328,7 @@ __device__ __forceinline__ void phaseA_agent(const Inst &I, int i, const int32_t
     I.state[i] = st;
   }
   const int g = I.cell_base + cell_of(st.y, I) * I.nc + cell_of(st.x, I);
+  if (!dbg_ok(g >= I.cell_base && g < I.cell_base + I.ncells)) return;
   cellrank[I.agent_base + i] = make_int2(g, warp_count(counts, g));
 }
 
@@ -357,6 +418,7 @@ __device__ __forceinline__ void tile_prefix(const Bufs &B, int *tp, int *wsum) {
 __device__ __forceinline__ void phaseC_agent(int f, const float4 *state_i, const Bufs &B,
                                              const int *tp) {
   const int2 cr = B.cellrank[f];
+  if (!dbg_ok(cr.x >= 0 && cr.x < B.c_total && cr.y >= 0)) return;
   const float4 st = *state_i;
   const int pos = tp[cr.x / kScanTile] + B.local[cr.x] + cr.y;
   if ((unsigned)pos >= (unsigned)B.n_total) {  // inconsistent counts: never write out of range
@@ -527,9 +589,9 @@ __device__ __forceinline__ void drain(const Inst &I, const WarpArea &W, int coun
       if (!coll) {
         const float t = fmul(fsub(I.RV, fsqrt(d2)), I.INV_SPAN);
         const unsigned long long tv = float_int_u64(fmul(t, I.scaleK));
-        if (tv) atomicAdd(&W.acc[o], tv);
+        if (tv) sred_add_u64(smem_u32(W.acc) + 8u * (unsigned)o, tv);
       }
-      atomicAdd(reinterpret_cast<unsigned *>(&W.ncoll[o]), coll ? 0x10001u : 1u);
+      sred_add_u32(smem_u32(W.ncoll) + 4u * (unsigned)o, coll ? 0x10001u : 1u);
       const float lx = fadd(fmul(dx, uxo), fmul(dy, uyo));
       const float ly = fsub(fmul(dy, uxo), fmul(dx, uyo));
       if (lx != 0.0f || ly != 0.0f) {
@@ -537,8 +599,9 @@ __device__ __forceinline__ void drain(const Inst &I, const WarpArea &W, int coun
         if (p >= 4.0f) p = 0.0f;
         if (I.full || p < I.T[v]) {
           const int key = sector_of(p, I.T, v);
-          atomicMin(&W.md[o * v + key], __float_as_uint(d2));
-          atomicAdd(&W.cn[o * v + key], 1);
+          const unsigned off = 4u * (unsigned)(o * v + key);
+          sred_min_u32(smem_u32(W.md) + off, __float_as_uint(d2));
+          sred_add_u32(smem_u32(W.cn) + off, 1u);
         }
       }
     }
@@ -885,11 +948,12 @@ __device__ __forceinline__ void add_term(const Inst &I, const DirectArea &W, int
                                          unsigned long long tv) {
   if (!tv) return;
   if (PIECES) {
-    atomicAdd(&W.accp[o], (unsigned)tv & 0xffffffu);
-    atomicAdd(&W.accp[32 + o], (unsigned)(tv >> 24) & 0xffffffu);
-    if (I.pieces > 2) atomicAdd(&W.accp[64 + o], (unsigned)(tv >> 48));
+    const unsigned a = smem_u32(W.accp) + 4u * (unsigned)o;
+    sred_add_u32(a, (unsigned)tv & 0xffffffu);
+    sred_add_u32(a + 128u, (unsigned)(tv >> 24) & 0xffffffu);
+    if (I.pieces > 2) sred_add_u32(a + 256u, (unsigned)(tv >> 48));
   } else {
-    atomicAdd(&W.acc[o], tv);
+    sred_add_u64(smem_u32(W.acc) + 8u * (unsigned)o, tv);
   }
 }
 
@@ -929,10 +993,11 @@ __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W,
   const int lane = threadIdx.x & 31;
   const int v = V == 8 ? 8 : I.v;
   const int vs = TAG ? 2 * v : v;  // accumulator row length
+  const unsigned q_s = smem_u32(W.queue), md_s = smem_u32(W.md), cn_s = smem_u32(W.cn);
   for (int e0 = 0; e0 < count; e0 += 32) {
     const int e = e0 + lane;
     const bool valid = e < count;
-    float4 E = valid ? W.queue[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 E = valid ? sld_f4(q_s + 16u * (unsigned)e) : make_float4(0.f, 0.f, 0.f, 0.f);
     const int w = valid ? __float_as_int(E.w) : lane;
     const int o = ONE ? 0 : (TAG ? (w & 0xff) : w);
     const int tj = TAG ? (w >> 8) : 0;
@@ -971,10 +1036,11 @@ __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W,
         float p = pseudo_angle(lx, ly);
         if (p >= 4.0f) p = 0.0f;
         int key = E8.sector(I, p);
-        if (key >= 0) {
+        if (key >= 0 && dbg_ok(key < v && o < 32)) {
           if (TAG) key += tj * v;  // colour channel of the neighbour's type
-          atomicMin(&W.md[o * vs + key], __float_as_uint(dist));
-          atomicAdd(&W.cn[o * vs + key], 1);
+          const unsigned off = 4u * (unsigned)(o * vs + key);
+          sred_min_u32(md_s + off, __float_as_uint(dist));
+          sred_add_u32(cn_s + off, 1u);
         }
       }
     }
@@ -1034,7 +1100,8 @@ __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, c
       const unsigned m = __ballot_sync(kFull, inr);
       if (inr) {
         const int w = TAG ? (slot | ((int)(stype[q] != 0) << 8)) : slot;
-        W.queue[qn + __popc(m & lt)] = make_float4(dx, dy, d2, __int_as_float(w));
+        sst_f4(smem_u32(W.queue) + 16u * (unsigned)(qn + __popc(m & lt)),
+               make_float4(dx, dy, d2, __int_as_float(w)));
       }
       qn += __popc(m);
       if (qn > kQueue - 32) {
@@ -1046,8 +1113,7 @@ __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, c
     return;
   }
   // wide form: two candidates per lane and pass (their loads in flight
-  // together), one drain test per pass; the agent itself is not skipped here
-  // (its pair, at d^2 = 0, is taken out of the counts and the sum at the end)
+  // together), one drain test per pass
   for (int j0 = 0; j0 < maxn; j0 += 2 * LPA) {
     const int ja = j0 + sub, jb = ja + LPA;
     bool ina = false, inb = false;
@@ -1063,7 +1129,7 @@ __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, c
         dya = fadd(dya, sy);
       }
       d2a = fadd(fmul(dxa, dxa), fmul(dya, dya));
-      ina = d2a < I.RV2;  // Eq. 1: d_ij < d_v
+      ina = d2a < I.RV2 && a + ja != self;  // Eq. 1: d_ij < d_v, j != i
     }
     if (jb < n) {
       dxb = fsub(pb.x, xi);
@@ -1073,19 +1139,22 @@ __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, c
         dyb = fadd(dyb, sy);
       }
       d2b = fadd(fmul(dxb, dxb), fmul(dyb, dyb));
-      inb = d2b < I.RV2;
+      inb = d2b < I.RV2 && a + jb != self;
     }
     nin += (ina ? 1 : 0) + (inb ? 1 : 0);
     ncoll += (ina && d2a < I.RC2 ? 1 : 0) + (inb && d2b < I.RC2 ? 1 : 0);  // Fig. 4
     const unsigned ma = __ballot_sync(kFull, ina), mb = __ballot_sync(kFull, inb);
+    const unsigned q_s = smem_u32(W.queue);
     if (ina) {
       const int w = TAG ? (slot | ((int)(stype[a + ja] != 0) << 8)) : slot;
-      W.queue[qn + __popc(ma & lt)] = make_float4(dxa, dya, d2a, __int_as_float(w));
+      sst_f4(q_s + 16u * (unsigned)(qn + __popc(ma & lt)),
+             make_float4(dxa, dya, d2a, __int_as_float(w)));
     }
     qn += __popc(ma);
     if (inb) {
       const int w = TAG ? (slot | ((int)(stype[a + jb] != 0) << 8)) : slot;
-      W.queue[qn + __popc(mb & lt)] = make_float4(dxb, dyb, d2b, __int_as_float(w));
+      sst_f4(q_s + 16u * (unsigned)(qn + __popc(mb & lt)),
+             make_float4(dxb, dyb, d2b, __int_as_float(w)));
     }
     qn += __popc(mb);
     if (qn > kQueueWide - 64) {
@@ -1305,7 +1374,7 @@ __device__ __forceinline__ void policy_mtile(const PolicyCtx &P, int row0, int &
 // runs faster fully unrolled).
 template <int H, int V, bool POL = false, bool PIECES = true, int LPA = 1, bool TAG = false,
           bool COMPACT = false>
-__device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
+__device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
                               const DirectArea &W, unsigned &err,
                               const PolicyCtx *pc = nullptr) {
   static_assert(LPA == 1 || LPA == 2 || LPA == 4 || LPA == 32, "lanes per agent");
@@ -1324,17 +1393,18 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
   float xi = 0.f, yi = 0.f;
   float2 ts = make_float2(0.f, 0.f);
   int i = 0, cx = 0, cy = 0;
-  if (have) {
+  if (have && dbg_ok(gp >= 0 && gp < B.n_total)) {
     const float2 p = B.sxy[gp];
     xi = p.x;
     yi = p.y;
     i = B.sidx[gp] - I.agent_base;
+    if (!dbg_ok(i >= 0 && i < I.n)) i = 0;
     const float4 s4 = I.state[i];  // own heading and speed (only the owner needs them)
     ts = make_float2(s4.z, s4.w);
     cx = cell_of(xi, I);
     cy = cell_of(yi, I);
   }
-  const int ti = TAG && have ? (int)(B.stype[gp] != 0) : 0;  // own type
+  const int ti = TAG && have ? (int)(B.stype[gp] != 0) : 0;  // own type (tag)
   // the cell starts of the stencil rows are read before anything waits on
   // the agent's own state row, so that the two reads are in flight together
   // stencil columns [cx - H, cx + H] split into runs that do not wrap
@@ -1349,6 +1419,7 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
     const int rowg = I.cell_base + wrapi(cy - H + r, nc) * nc;
     ra[r] = have ? cst[rowg + ma] : 0;
     rn[r] = have ? cst[rowg + mb] - ra[r] : 0;
+    dbg_run(ra[r], rn[r], B.n_total);
   }
   float c = 1.f, sn = 0.f;
   det_sincos(ts.x, c, sn);
@@ -1381,6 +1452,7 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
   unsigned long long racc = 0;  // one agent per warp: this lane's share of its reward sum
   __syncwarp();
   int qn = 0;
+  // the agent's own sorted position: its candidate scan skips it
   const int self = have ? gp : -1;
   if (!wrap_any) {
 #pragma unroll
@@ -1415,6 +1487,7 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
           n = cst[rowg + vhi - nc] - a;
         }
       }
+      dbg_run(a, n, B.n_total);
       direct_run<true, V, PIECES, LPA, TAG>(I, W, B.sxy, a, n, self, sx, sy, xi, yi, ux, uy, qn,
                                             nin, ncoll, E8, B.stype, ti, racc);
     }
@@ -1432,6 +1505,7 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
         a = cst[rowg + vlo + nc];
         n = cst[rowg + nc] - a;
       }
+      dbg_run(a, n, B.n_total);
       direct_run<true, V, PIECES, LPA, TAG>(I, W, B.sxy, a, n, self, -I.L, sy, xi, yi, ux, uy,
                                             qn, nin, ncoll, E8, B.stype, ti, racc);
       // cells across the right boundary: virtual columns [nc, vhi) -> [0, vhi - nc)
@@ -1441,6 +1515,7 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
         a = cst[rowg];
         n = cst[rowg + vhi - nc] - a;
       }
+      dbg_run(a, n, B.n_total);
       direct_run<true, V, PIECES, LPA, TAG>(I, W, B.sxy, a, n, self, I.L, sy, xi, yi, ux, uy,
                                             qn, nin, ncoll, E8, B.stype, ti, racc);
     }
@@ -1460,22 +1535,11 @@ __device__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
     nin += __shfl_xor_sync(kFull, nin, m);
     ncoll += __shfl_xor_sync(kFull, ncoll, m);
   }
-  // the agent's own pair (d^2 = 0, met once in its own cell, never under a
-  // periodic shift since L > 2 d_v) was counted in range, as a collision when
-  // 0 < (2 d_r)^2, and otherwise (d_r = 0) added a ramp term unless the agent
-  // is a tag chaser; it has no direction, so no sector
-  long long self_term = 0;
-  if (PIECES && have && lane < A) {  // the wide form only
-    nin -= 1;
-    if (0.0f < I.RC2) ncoll -= 1;
-    else if (!(TAG && ti))
-      self_term = (long long)float_int_u64(fmul(fmul(fsub(I.RV, fsqrt(0.0f)), I.INV_SPAN), I.scaleK));
-  }
   // reward and collisions
   if (have && lane < A) {
     // a chaser's touches earn through its terms; everyone else's cost P each
     const long long pen = TAG && ti ? 0ll : (long long)ncoll * I.PK;
-    const long long total = (long long)W.acc[lane] - self_term - pen;
+    const long long total = (long long)W.acc[lane] - pen;
     B.reward[I.agent_base + i] = fmul(__ll2float_rn(total), I.inv_scaleK);
     B.coll[I.agent_base + i] = ncoll;
     if ((long long)nin > I.NMAX) err |= FLOCK_ERR_OVERFLOW;

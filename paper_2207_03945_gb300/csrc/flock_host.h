@@ -37,4 +37,24 @@ int cuda_fail(cudaError_t e, const char *what);
 // Raises the dynamic shared-memory limit of the neighbour kernels (once).
 cudaError_t set_kernel_attrs();
 
+// Launch with programmatic stream serialization (pdl = true): the kernel's
+// blocks may be scheduled while the previous kernel in the stream finishes,
+// hiding the launch gap; every kernel launched this way waits in pdl_wait()
+// before it reads what the previous one wrote.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch(bool pdl, void (*k)(KArgs...), int grid, int block, size_t smem,
+                          cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, ((KArgs)args)...);
+}
+
 }  // namespace flock

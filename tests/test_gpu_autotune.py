@@ -32,5 +32,7 @@ def test_batch_stencil_choice():
     params = [fi.default_params(fi.side_for(n)) for n in sizes]
     states = [fi.initial_state(n, fi.side_for(n), k) for k, n in enumerate(sizes)]
     tuning, report = at.autotune_batch(params, sizes, states, steps=2, warmup=2)
-    assert len(report) == 4 and all(same for _, _, same in report)
-    assert tuning["stencil"] in (1, 2)
+    assert len(report) == len(at.BATCH_CANDIDATES) and all(same for _, _, same in report)
+    assert tuning["stencil"] in (1, 2) and tuning["mode"] in (2, 3, 4)
+    # the separate neighbour launch's block size is part of the search
+    assert {c.get("block") for c, _, _ in report} >= {64, 128, 256}

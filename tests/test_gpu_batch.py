@@ -5,7 +5,9 @@ alone (bit-exact: state, observation, collisions, reward), and equal the
 single-environment path; the active set may change between steps; the
 grid-barrier wait bound turns a stalled barrier into FLOCK_ERR_TIMEOUT.
 Mode 2 runs every phase in one persistent launch; mode 3 bins in the
-persistent launch and scans neighbours in a second one."""
+persistent launch and scans neighbours in a second one; mode 4 bins with
+three kernels (apply and count, scan, scatter) over all instances, then
+scans neighbours in a fourth launch."""
 import numpy as np
 import pytest
 
@@ -40,7 +42,8 @@ def batch_for(insts, tuning=None):
                         device=DEV, tuning=tuning)
 
 
-MODES = pytest.mark.parametrize("mode", [2, 3])
+MODES = pytest.mark.parametrize("mode", [2, 3, 4])
+BARRIER_MODES = pytest.mark.parametrize("mode", [2, 3])  # the forms with grid barriers
 
 
 @MODES
@@ -185,7 +188,7 @@ def test_mixed_segment_counts_rejected():
     b.close()
 
 
-@MODES
+@BARRIER_MODES
 def test_barrier_wait_bound_reports_timeout_and_recovers(mode):
     """With the wait bound at zero every barrier gives up at once: the step
     returns with FLOCK_ERR_TIMEOUT latched and no hang (mode 3: the
@@ -242,5 +245,36 @@ def test_benchmark_mix_sampled_rows(mode):
         assert np.array_equal(o_all[off + rows], o), k
         assert np.array_equal(r_all[off + rows], r), k
         assert np.array_equal(c_all[off + rows], c), k
+    assert b.error() == 0
+    b.close()
+
+
+@pytest.mark.parametrize("tuning", [{"mode": 3, "block": 64}, {"mode": 3, "block": 256},
+                                    {"mode": 4, "block": 64}, {"mode": 4, "block": 256},
+                                    {"mode": 4, "stencil": 2, "block": 128}],
+                         ids=lambda d: "-".join("%s%s" % kv for kv in d.items()))
+def test_neighbour_launch_block_sizes(tuning):
+    """Every block size of the separate neighbour launch (the autotuner's
+    choices) gives the oracle's bits, on a mix with empty and one-agent
+    instances."""
+    sizes = [900, 0, 1, 4100, 37, 2600]
+    insts = make_instances(sizes, 700)
+    b = batch_for(insts, tuning)
+    assert F.env_batch_get_launch(b.batch)[0] > 0
+    states = [torch.from_numpy(st).to(DEV) for _, _, st in insts]
+    b.set([p for p, _, _ in insts], sizes, states, reset=[1] * len(sizes))
+    b.step(torch.zeros(sum(sizes), dtype=torch.int32, device=DEV))
+    a = fi.random_actions(sum(sizes), 2, 7)
+    ref = [st.copy() for _, _, st in insts]
+    for t in range(2):
+        obs, rew, coll = b.step(torch.from_numpy(a[t]).to(DEV))
+        torch.cuda.synchronize()
+        for k, (p, n, _) in enumerate(insts):
+            off = b.offsets[k]
+            ref[k], o, r, c, _ = oracle.step(p, ref[k], a[t][off:off + n])
+            assert np.array_equal(obs[off:off + n].cpu().numpy(), o), (t, k)
+            assert np.array_equal(rew[off:off + n].cpu().numpy(), r), (t, k)
+            assert np.array_equal(coll[off:off + n].cpu().numpy(), c), (t, k)
+            assert np.array_equal(states[k].cpu().numpy(), ref[k]), (t, k)
     assert b.error() == 0
     b.close()

@@ -188,8 +188,8 @@ def test_small_square_wraps_everywhere(side, stencil, mode):
     p = fi.default_params(side)
     st0 = fi.initial_state(n, side, 5)
     acts = fi.random_actions(n, steps, 5)
-    tun = {"stencil": stencil, "mode": mode} if mode < 4 else {"stencil": stencil, "mode": 2,
-                                                                 "lanes": mode}
+    tun = ({"stencil": stencil, "mode": mode} if mode < 4 else
+           {"stencil": stencil, "mode": 2, "lanes": mode})
     g, _, _ = gpu_run(p, st0, acts, tun)
     o, _ = oracle_run(p, st0, acts)
     assert_same(g, o, "side %g" % side)
@@ -207,7 +207,8 @@ def test_dense_cluster_exceeds_shared_memory(mode):
     st0[:, 1] = (40.0 + 20.0 * rng.random(n)).astype(np.float32)
     p = fi.default_params(100.0)
     acts = fi.random_actions(n, 2, 6)
-    g, err, _ = gpu_run(p, st0, acts, {"mode": mode} if mode < 4 else {"mode": 2, "lanes": mode})
+    tun = {"mode": mode} if mode < 4 else {"mode": 2, "lanes": mode}
+    g, err, _ = gpu_run(p, st0, acts, tun)
     o, flags = oracle_run(p, st0, acts)
     assert_same(g, o, "cluster")
     assert err == flags == 0

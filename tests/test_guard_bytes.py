@@ -2,7 +2,7 @@
 outputs and (for a batch) the instance states live inside larger device
 allocations whose margins hold a fixed byte pattern.  After resets and steps
 of single environments (discrete and continuous actions, a ragged agent
-count) and of batches in both launch forms, every margin is unchanged: no
+count) and of batches in all three launch forms, every margin is unchanged: no
 write lands outside the buffers handed over through the C ABI.  (An
 out-of-bounds check that needs no sanitizer; nothing here can fault.)"""
 import numpy as np
@@ -71,7 +71,7 @@ def test_single_environment_writes_stay_inside_its_buffers(case):
         assert g.intact()
 
 
-@pytest.mark.parametrize("mode", [2, 3])
+@pytest.mark.parametrize("mode", [2, 3, 4])
 def test_batch_writes_stay_inside_its_buffers(mode):
     sizes = [1500, 99, 4001]
     tuning = {"stencil": 1, "mode": mode}
