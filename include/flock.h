@@ -208,17 +208,20 @@ int env_rollout(flock_env *env, int T, const int32_t *actions_dev, const float *
 int flock_gae(int T, int n, const float *reward_dev, const float *value_dev, float gamma,
               float lambda, float *adv_dev, float *ret_dev, void *stream);
 
-/* One step whose next actions come from the fused policy: applies
+/* One step whose next actions come from the policy: applies
  * actions_inout_dev, observes, and feeds each agent's observation through the
- * shared policy network on chip (the learners' shared MLP of Section 4.3,
- * here 18 -> 64 -> 64 -> 9 with tanh, as the 18-value observation needs;
- * needs num_segments == 8 and obs_layout 0), then overwrites actions_inout_dev with the greedy
- * actions (largest logit, lowest index on ties) for the next step.
+ * shared policy network (the learners' shared MLP of Section 4.3, here
+ * 18 -> 64 -> 64 -> 9 with tanh, as the 18-value observation needs; needs
+ * num_segments == 8 and obs_layout 0), then overwrites actions_inout_dev with
+ * the greedy actions (largest logit, lowest index on ties) for the next step.
+ * The neighbour scan hands the observations to the network as BF16 rows in
+ * the workspace (48 bytes per agent, which stay in L2 at these sizes); the
+ * network runs in the step's fifth kernel.
  * weights_bf16_dev: 5,961 bfloat16 values, W1[64][18] b1[64] W2[64][64]
  * b2[64] W3[9][64] b3[9], each W row-major [out][in].  Operands are BF16 on
  * the tensor cores, accumulation FP32, tanh the hardware approximation.
- * logits_dev (n x 9 floats) and obs_dev (n x 18) may be NULL; with NULL obs
- * the observations never reach device memory. */
+ * logits_dev (n x 9 floats) and obs_dev (n x 18) may be NULL (with NULL obs
+ * no FP32 observation is written). */
 int env_step_policy(flock_env *env, const uint16_t *weights_bf16_dev, int32_t *actions_inout_dev,
                     float *reward_dev, int32_t *coll_dev, float *logits_dev, float *obs_dev);
 
@@ -241,7 +244,7 @@ int env_step_host(flock_env *env, const int32_t *actions_host, float *obs_host,
  * channels (runners, chasers) of num_segments sectors.  With
  * env_step_continuous the action is (speed, rotation): the speed is set,
  * clamped to [speed_min, speed_max].  Tag uses the direct neighbour scan
- * (tuning mode 2) of a single environment; the batch, the fused policy and
+ * (tuning mode 2) of a single environment; the batch, the policy step and
  * flock_step_static take flock instances only.  FLOCK_EINVAL for a flock
  * environment. */
 int env_set_types(flock_env *env, const uint8_t *types_dev);

@@ -78,36 +78,77 @@ __global__ void k_neighbours_direct(const Inst *__restrict__ gI, Bufs B) {
   if (gp0 < sI.n) {
     const int vs = TAG ? 2 * sI.v : sI.v;
     const DirectArea W = direct_area(smem + (size_t)warp * direct_warp_bytes(vs, A), vs, A);
-    phaseD_direct<H, V, false, true, LPA, TAG>(sI, gp0, min(gp0 + A, sI.n), B, W, err);
+    phaseD_direct<H, V, true, LPA, TAG>(sI, gp0, min(gp0 + A, sI.n), B, W, err);
   }
   if (err) atomicOr(B.err, err);
 }
 
-// Neighbour scan with the fused policy (v = 8): observations go through the
-// MLP on chip; greedy actions (and optionally logits and observations) out.
-template <int H>
-__global__ void k_neighbours_policy(const Inst *__restrict__ gI, Bufs B,
-                                    const unsigned short *__restrict__ wblob, int32_t *actions,
-                                    float *logits) {
+// The shared policy network (Section 4.3; 18 -> 64 -> 64 -> 9 with tanh) on
+// the step's observations: the neighbour scan leaves each agent's
+// observation as a BF16 row in the workspace (48 bytes, resident in L2), and
+// this kernel runs the network on the tensor cores (mma.sync m16n8k16, FP32
+// accumulate), 32 agents per warp, and writes the greedy actions (largest
+// logit, lowest index on ties) and optionally the logits.  The weights are
+// staged in shared memory once per block; blocks walk the agents with a
+// grid-stride loop.  (A fused form that ran the network in the neighbour
+// scan's epilogue held 94 registers and 46 KB of shared memory per block,
+// and took 1.67 times the plain step at 100,000 agents.)
+constexpr int kMlpBlock = 128;
+
+__global__ void __launch_bounds__(kMlpBlock) k_policy_mlp(const unsigned *__restrict__ pobs, int n,
+                                                          const unsigned short *__restrict__ wblob,
+                                                          int32_t *actions, float *logits) {
   extern __shared__ __align__(16) char smem[];
-  __shared__ Inst sI;
-  load_inst(sI, gI);
-  load_policy(wblob, smem);
+  load_policy(wblob, smem);  // the weights do not depend on the previous kernel
   pdl_wait();
   __syncthreads();
-  unsigned err = 0;
-  const int warp = threadIdx.x >> 5;
-  const int gp0 = (blockIdx.x * (blockDim.x >> 5) + warp) * 32;
-  if (gp0 < sI.n) {
-    char *wp = smem + kPolicyBytes + (size_t)warp * (direct_warp_bytes(8) + kTileBytes);
-    const DirectArea W = direct_area(wp, 8);
-    PolicyCtx pc = policy_ctx(smem);
-    pc.tile = reinterpret_cast<unsigned short *>(wp + direct_warp_bytes(8));
-    pc.actions = actions;
-    pc.logits = logits;
-    phaseD_direct<H, 8, true>(sI, gp0, min(gp0 + 32, sI.n), B, W, err, &pc);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  PolicyCtx pc = policy_ctx(smem);
+  pc.tile = reinterpret_cast<unsigned short *>(smem + kPolicyBytes + (size_t)warp * kTileBytes);
+  pc.actions = actions;
+  pc.logits = logits;
+  unsigned *row = reinterpret_cast<unsigned *>(pc.tile + lane * kTileS);
+  const int stride = gridDim.x * (kMlpBlock / 32) * 32;
+  for (int base = (blockIdx.x * (kMlpBlock / 32) + warp) * 32; base < n; base += stride) {
+    const int nb = min(32, n - base);
+    // this lane's row: 9 words of values, the rest of the tile row zero
+    uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a, c = a;
+    if (lane < nb) {
+      const uint4 *src = reinterpret_cast<const uint4 *>(pobs + (long long)(base + lane) * kPobsWords);
+      a = src[0];
+      b = src[1];
+      c = src[2];
+    }
+    row[0] = a.x; row[1] = a.y; row[2] = a.z; row[3] = a.w;
+    row[4] = b.x; row[5] = b.y; row[6] = b.z; row[7] = b.w;
+    row[8] = c.x;
+#pragma unroll
+    for (int w2 = 9; w2 < kTileS / 2; ++w2) row[w2] = 0u;
+    __syncwarp();
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      int alo = 0, ahi = 0;
+      float lg[2][4];
+      policy_mtile(pc, 16 * mt, alo, ahi, lg);
+      const int rlo = 16 * mt + g, rhi = rlo + 8;
+      if (t == 0) {
+        if (rlo < nb) actions[base + rlo] = alo;
+        if (rhi < nb) actions[base + rhi] = ahi;
+      }
+      if (logits) {
+        const int c4[4] = {2 * t, 2 * t + 1, 8 + 2 * t, 9 + 2 * t};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (c4[j] < 9) {
+            if (rlo < nb) logits[(long long)(base + rlo) * 9 + c4[j]] = lg[0][j];
+            if (rhi < nb) logits[(long long)(base + rhi) * 9 + c4[j]] = lg[1][j];
+          }
+        }
+      }
+    }
+    __syncwarp();
   }
-  if (err) atomicOr(B.err, err);
 }
 
 // Copies a step's outputs (observations, rewards, collision counts) from the
@@ -347,8 +388,7 @@ cudaError_t set_kernel_attrs() {
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int want = maxsm - (int)sizeof(Inst) - 1024;
-    const void *fns[] = {(const void *)k_neighbours_policy<1>,
-                         (const void *)k_neighbours_policy<2>,
+    const void *fns[] = {(const void *)k_policy_mlp,
                          (const void *)k_neighbours<1>, (const void *)k_neighbours<2>,
                          (const void *)k_neighbours_direct<1, 0, 1>,
                          (const void *)k_neighbours_direct<2, 0, 1>,
@@ -387,8 +427,7 @@ using namespace flock;
 
 struct Layout {
   size_t state, cellrank, counts, local, cell_start, tile_sum, sxy, sidx, types, stype, inst,
-      err, h_act, h_obs,
-      h_rew, h_coll, total;
+      err, h_act, h_obs, h_rew, h_coll, pobs, total;
 };
 
 static Layout make_layout(int n, int C, int D) {
@@ -412,6 +451,7 @@ static Layout make_layout(int n, int C, int D) {
   L.h_obs = take((size_t)n * D * 4);
   L.h_rew = take((size_t)n * 4);
   L.h_coll = take((size_t)n * 4);
+  L.pobs = take((size_t)n * kPobsWords * 4);  // policy step: BF16 observation rows
   L.total = o;
   return L;
 }
@@ -433,10 +473,11 @@ struct flock_env {
   int n_scan_tiles;
   int scatter_grid;
   int copy_grid;  // k_copy_out (host-buffer step)
+  int mlp_grid;   // k_policy_mlp: blocks at most (grid-stride over the agents)
   size_t smemD;
   int timing;
   cudaEvent_t ev[5];
-  cudaGraphExec_t pgraph;  // step with the fused policy
+  cudaGraphExec_t pgraph;  // step with the policy
   cudaGraphExec_t rgraph;  // a rollout of T steps
   const void *r_act, *r_obs, *r_rew, *r_coll;
   int r_T, r_cont;
@@ -551,6 +592,7 @@ extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, v
   // 16-byte units of the outputs, one per thread, at most 8 blocks per SM
   const size_t units = ((size_t)n * e->inst.obs_dim * 4 + (size_t)n * 8) / 16;
   e->copy_grid = (int)std::max<size_t>(1, std::min<size_t>((units + 255) / 256, (size_t)sms * 8));
+  e->mlp_grid = sms * 8;
   e->smemD = e->tuning.mode == 1
                  ? phaseD_smem_bytes(e->inst.cap, e->inst.v, e->tuning.block)
                  : (size_t)(e->tuning.block / 32) *
@@ -581,14 +623,18 @@ extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, v
 }
 
 // act: discrete actions, or cact (when not null): continuous ones.
+// pobs (policy step): the neighbour scan also writes BF16 observation rows
+// there; it then runs in the direct form whatever the tuning's mode.
 static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const float2 *cact,
-                        float *obs, float *rew, int32_t *coll, int reset) {
+                        float *obs, float *rew, int32_t *coll, int reset,
+                        unsigned *pobs = nullptr) {
   Bufs B = e->bufs;
   B.actions = act;
   B.cactions = cact;
   B.obs = obs;
   B.reward = rew;
   B.coll = coll;
+  B.pobs = pobs;
   const Inst *gI = (const Inst *)(e->ws + e->lay.inst);
   const int n = e->n;
   const bool tm = e->timing != 0;
@@ -615,7 +661,7 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const 
   if (n > 0) {
     const int blk = e->tuning.block;
     const size_t sm = e->smemD;
-    if (e->tuning.mode == 1) {
+    if (e->tuning.mode == 1 && !pobs) {
       const int tiles = e->inst.tiles_x * e->inst.tiles_y;
       if (e->inst.halo == 1) CK(launch(pdl, k_neighbours<1>, tiles, blk, sm, s, gI, B));
       else CK(launch(pdl, k_neighbours<2>, tiles, blk, sm, s, gI, B));
@@ -651,27 +697,22 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const 
   return FLOCK_OK;
 }
 
+// The policy step: the step's four kernels, the neighbour scan also writing
+// BF16 observation rows into the workspace, then the network.
 static int enqueue_policy_step(flock_env *e, cudaStream_t s, const unsigned short *w,
                                int32_t *act, float *rew, int32_t *coll, float *logits,
                                float *obs) {
-  Bufs B = e->bufs;
-  B.actions = act;
-  B.obs = obs;
-  B.reward = rew;
-  B.coll = coll;
-  const Inst *gI = (const Inst *)(e->ws + e->lay.inst);
+  unsigned *pobs = (unsigned *)(e->ws + e->lay.pobs);
+  int rc = enqueue_step(e, s, act, nullptr, obs, rew, coll, 0, pobs);
+  if (rc) return rc;
   const int n = e->n;
-  if (n > 0) CK(launch(false, k_apply_bin, (n + 255) / 256, 256, 0, s, gI, B, 0));
-  CK(launch(n > 0, k_scan, e->n_scan_tiles, 256, 0, s, B));
-  CK(launch(true, k_scatter, e->scatter_grid, 256, 0, s, gI, B));
   if (n > 0) {
-    const int block = e->tuning.block;
-    const size_t smem = kPolicyBytes + (size_t)(block / 32) * (direct_warp_bytes(8) + kTileBytes);
-    const int blocks = (n + block - 1) / block;
-    if (e->inst.halo == 1)
-      CK(launch(true, k_neighbours_policy<1>, blocks, block, smem, s, gI, B, w, act, logits));
-    else
-      CK(launch(true, k_neighbours_policy<2>, blocks, block, smem, s, gI, B, w, act, logits));
+    NvtxRange r("flock:policy_mlp");
+    const size_t smem = kPolicyBytes + (size_t)(kMlpBlock / 32) * kTileBytes;
+    int blocks = (n + kMlpBlock - 1) / kMlpBlock;
+    blocks = blocks < e->mlp_grid ? blocks : e->mlp_grid;
+    CK(launch(true, k_policy_mlp, blocks, kMlpBlock, smem, s, (const unsigned *)pobs, n, w, act,
+              logits));
   }
   return FLOCK_OK;
 }
@@ -821,11 +862,6 @@ extern "C" int env_step_policy(flock_env *e, const uint16_t *weights, int32_t *a
   if (e->n > 0 && (!weights || !act || !rew || !coll || !aligned(weights, 4) ||
                    (obs && !aligned(obs, 8))))
     return FLOCK_EINVAL;
-  const size_t smem = kPolicyBytes + (size_t)(e->tuning.block / 32) * (direct_warp_bytes(8) + kTileBytes);
-  int dev = 0, smem_max = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (smem + sizeof(Inst) + 1024 > (size_t)smem_max) return FLOCK_EINVAL;
   if (!e->pgraph || e->p_w != weights || e->p_act != act || e->p_rew != rew ||
       e->p_coll != coll || e->p_log != logits || e->p_obs != obs) {
     cudaGraph_t g = nullptr;

@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kBatchBlock, SPLIT ? 6 : 1) k_batch_step(const
       }
       const int gp0 = sI.agent_base + (c - __ldg(cpre + k)) * 32;
       const int gp1 = min(gp0 + 32, sI.agent_base + sI.n);
-      phaseD_direct<H, V, false, false>(sI, gp0, gp1, B, W, err);
+      phaseD_direct<H, V, false>(sI, gp0, gp1, B, W, err);
       // an instance observed without actions goes back to normal stepping
       if (sI.reset && gp0 == sI.agent_base && lane == 0) insts[k].reset = 0;
     }
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(256) k_batch_neigh(const BatchDev *__restrict_
     }
     const int gp0 = sI.agent_base + (c - cpre[k]) * 32;
     const int gp1 = min(gp0 + 32, sI.agent_base + sI.n);
-    phaseD_direct<H, V, false, true, 1, false, true>(sI, gp0, gp1, B, W, err);
+    phaseD_direct<H, V, true, 1, false, true>(sI, gp0, gp1, B, W, err);
     if (sI.reset && gp0 == sI.agent_base && lane == 0) insts[k].reset = 0;
   }
   if (err) atomicOr(B.err, err);

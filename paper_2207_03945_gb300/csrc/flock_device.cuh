@@ -72,8 +72,14 @@ struct Bufs {
   float *obs;
   float *reward;
   int32_t *coll;
+  unsigned *pobs;  // policy step: BF16 observation rows (kPobsWords per agent, agent order), or null
   int n_total, c_total, n_scan_tiles, pad;
 };
+
+// Row of a BF16 observation for the policy network: 18 values (8 sectors x
+// (distance, count), speed, heading) as 9 packed pairs, padded to 12 words
+// (48 bytes, so rows start on 16-byte boundaries).
+constexpr int kPobsWords = 12;
 
 // Debug build (FLOCK_DEBUG, libflock_debug.so): index checks on the step's
 // scratch and output accesses.  A failed check latches FLOCK_ERR_BOUNDS in
@@ -119,6 +125,35 @@ __device__ __forceinline__ float4 sld_f4(unsigned a) {
                : "r"(a)
                : "memory");
   return v;
+}
+
+// Predicated forms: the predicate is evaluated inside the instruction
+// sequence, so a conditional update costs no branch (a branch around a
+// side effect in the neighbour scan's pair loop costs the warp far more
+// than the update: divergence and reconvergence bookkeeping).
+__device__ __forceinline__ void sred_add_u32_if(bool p, unsigned a, unsigned v) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q red.shared.add.u32 [%0], %1;\n\t}"
+      ::"r"(a), "r"(v), "r"((unsigned)p)
+      : "memory");
+}
+__device__ __forceinline__ void sred_min_u32_if(bool p, unsigned a, unsigned v) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q red.shared.min.u32 [%0], %1;\n\t}"
+      ::"r"(a), "r"(v), "r"((unsigned)p)
+      : "memory");
+}
+__device__ __forceinline__ void sred_add_u64_if(bool p, unsigned a, unsigned long long v) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q red.shared.add.u64 [%0], %1;\n\t}"
+      ::"r"(a), "l"(v), "r"((unsigned)p)
+      : "memory");
+}
+__device__ __forceinline__ void sst_f4_if(bool p, unsigned a, float4 v) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t@q st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n\t}"
+      ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"((unsigned)p)
+      : "memory");
 }
 
 // A candidate run [a, a + n) of the sorted arrays (n_total entries); in the
@@ -926,13 +961,14 @@ struct Edges {
   // returns the sector, or -1 when outside the field of view
   __device__ __forceinline__ int sector(const Inst &I, float p) const {
     if (V == 8) {
-      if (!I.full && p >= t[7]) return -1;
+      const bool out = !I.full && p >= t[7];
       const bool b2 = p >= t[3];
       const float t1 = b2 ? t[5] : t[1];
       const bool b1 = p >= t1;
       const float t0 = b2 ? (b1 ? t[6] : t[4]) : (b1 ? t[2] : t[0]);
       const bool b0 = p >= t0;
-      return (b2 ? 4 : 0) + (b1 ? 2 : 0) + (b0 ? 1 : 0);
+      const int k = (b2 ? 4 : 0) + (b1 ? 2 : 0) + (b0 ? 1 : 0);
+      return out ? -1 : k;
     } else {
       if (!I.full && p >= I.T[I.v]) return -1;
       return sector_of(p, I.T, I.v);
@@ -987,66 +1023,84 @@ __device__ __forceinline__ int pick(const int (&x)[N], int r) {
 // (added up over the warp at the end) instead of shared-memory atomics that
 // would all hit one word, and the agent's frame needs no shuffle.
 template <int V, bool PIECES, bool TAG = false, bool ONE = false>
-__device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W, int count,
-                                            float ux, float uy, const Edges<V> &E8, int ti,
-                                            unsigned long long &racc) {
+__device__ __forceinline__ int drain_direct(const Inst &I, const DirectArea &W, int count,
+                                           float ux, float uy, const Edges<V> &E8, int ti,
+                                           unsigned long long &racc, bool all = true) {
   const int lane = threadIdx.x & 31;
   const int v = V == 8 ? 8 : I.v;
   const int vs = TAG ? 2 * v : v;  // accumulator row length
   const unsigned q_s = smem_u32(W.queue), md_s = smem_u32(W.md), cn_s = smem_u32(W.cn);
-  for (int e0 = 0; e0 < count; e0 += 32) {
+  const unsigned ap_s = smem_u32(W.accp), a64_s = smem_u32(W.acc);
+  // mid-scan, only whole rounds of 32 pairs are taken; the rest stays queued
+  const int take = all ? count : (count & ~31);
+  // Branch-free pair body: every lane computes every quantity (an idle lane
+  // on a harmless stand-in pair) and the shared-memory updates carry their
+  // condition as a predicate.
+  for (int e0 = 0; e0 < take; e0 += 32) {
     const int e = e0 + lane;
-    const bool valid = e < count;
-    float4 E = valid ? sld_f4(q_s + 16u * (unsigned)e) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int w = valid ? __float_as_int(E.w) : lane;
+    const bool valid = e < take;
+    const float4 E = sld_f4(q_s + 16u * (unsigned)(valid ? e : 0));
+    const int w = valid ? __float_as_int(E.w) : 0;
     const int o = ONE ? 0 : (TAG ? (w & 0xff) : w);
     const int tj = TAG ? (w >> 8) : 0;
     const float uxo = ONE ? ux : __shfl_sync(kFull, ux, o);
     const float uyo = ONE ? uy : __shfl_sync(kFull, uy, o);
     const int tio = TAG ? (ONE ? ti : __shfl_sync(kFull, ti, o)) : 0;
-    if (valid) {
-      const float dx = E.x, dy = E.y, d2 = E.z;
-      const bool coll = d2 < I.RC2;
-      // the distance: the ramp term's, and the sector minimum's (sqrt is
-      // monotone, so the minimum of the rounded roots is the rounded root of
-      // the minimum d^2)
-      const float dist = fsqrt(d2);
-      if constexpr (!TAG) {
-        if (!coll) {
-          const float t = fmul(fsub(I.RV, dist), I.INV_SPAN);
-          const unsigned long long tv = float_int_u64(fmul(t, I.scaleK));
-          if (ONE) racc += tv;
-          else add_term<PIECES>(I, W, o, tv);
-        }
-      } else {
-        if (tio == 0 && tj == 0 && !coll) {  // a runner near a runner
-          const float t = fmul(fsub(I.RV, dist), I.INV_SPAN);
-          const unsigned long long tv = float_int_u64(fmul(t, I.scaleK));
-          if (ONE) racc += tv;
-          else add_term<PIECES>(I, W, o, tv);
-        } else if (tio == 1 && tj == 0 && coll) {
-          // a chaser touching a runner
-          if (ONE) racc += (unsigned long long)I.PK;
-          else add_term<PIECES>(I, W, o, (unsigned long long)I.PK);
-        }
-      }
-      const float lx = fadd(fmul(dx, uxo), fmul(dy, uyo));
-      const float ly = fsub(fmul(dy, uxo), fmul(dx, uyo));
-      if (lx != 0.0f || ly != 0.0f) {
-        float p = pseudo_angle(lx, ly);
-        if (p >= 4.0f) p = 0.0f;
-        int key = E8.sector(I, p);
-        if (key >= 0 && dbg_ok(key < v && o < 32)) {
-          if (TAG) key += tj * v;  // colour channel of the neighbour's type
-          const unsigned off = 4u * (unsigned)(o * vs + key);
-          sred_min_u32(md_s + off, __float_as_uint(dist));
-          sred_add_u32(cn_s + off, 1u);
-        }
-      }
+    const float dx = valid ? E.x : 1.0f, dy = valid ? E.y : 0.0f;
+    const float d2 = valid ? E.z : 1.0f;
+    const bool coll = d2 < I.RC2;
+    // the distance: the ramp term's, and the sector minimum's (sqrt is
+    // monotone, so the minimum of the rounded roots is the rounded root of
+    // the minimum d^2)
+    const float dist = fsqrt(d2);
+    // reward term of this pair for its owner (units of 2^-K): the ramp of
+    // Fig. 4 for a non-colliding pair; for tag a runner's ramp counts runners
+    // only, and a chaser earns P per runner it touches
+    bool ramp, touch = false;
+    if constexpr (!TAG) {
+      ramp = valid && !coll;
+    } else {
+      ramp = valid && tio == 0 && tj == 0 && !coll;
+      touch = valid && tio == 1 && tj == 0 && coll;
     }
+    const float t = fmul(fsub(I.RV, dist), I.INV_SPAN);
+    unsigned long long tv = float_int_u64(fmul(ramp ? t : 0.0f, I.scaleK));
+    if (TAG) tv = touch ? (unsigned long long)I.PK : tv;
+    if (ONE) {
+      racc += tv;
+    } else if (PIECES) {
+      const unsigned pa = ap_s + 4u * (unsigned)o;
+      const bool nz = tv != 0ull;
+      sred_add_u32_if(nz, pa, (unsigned)tv & 0xffffffu);
+      sred_add_u32_if(nz, pa + 128u, (unsigned)(tv >> 24) & 0xffffffu);
+      sred_add_u32_if(nz && I.pieces > 2, pa + 256u, (unsigned)(tv >> 48));
+    } else {
+      sred_add_u64_if(tv != 0ull, a64_s + 8u * (unsigned)o, tv);
+    }
+    // direction in the owner's field-of-view frame, pseudo-angle, sector
+    const float lx = fadd(fmul(dx, uxo), fmul(dy, uyo));
+    const float ly = fsub(fmul(dy, uxo), fmul(dx, uyo));
+    const bool dir = lx != 0.0f || ly != 0.0f;  // coincident agents have none
+    float p = pseudo_angle(dir ? lx : 1.0f, ly);
+    if (p >= 4.0f) p = 0.0f;
+    int key = E8.sector(I, p);
+    const bool seen = valid && dir && key >= 0 && dbg_ok(key < v && o < 32);
+    if (TAG) key += tj * v;  // colour channel of the neighbour's type
+    const unsigned off = 4u * (unsigned)(o * vs + (seen ? key : 0));
+    sred_min_u32_if(seen, md_s + off, __float_as_uint(dist));
+    sred_add_u32_if(seen, cn_s + off, 1u);
   }
   __syncwarp();
-  if (!PIECES || ONE) return;
+  // the pairs not taken move to the front of the queue
+  const int rest = count - take;
+  if (rest > 0) {
+    const bool mv = lane < rest;
+    const float4 E = sld_f4(q_s + 16u * (unsigned)(take + (mv ? lane : 0)));
+    __syncwarp();
+    sst_f4_if(mv, q_s + 16u * (unsigned)lane, E);
+    __syncwarp();
+  }
+  if (!PIECES || ONE) return rest;
   // each lane folds its own pieces into its 64-bit sum
   W.acc[lane] += (unsigned long long)W.accp[lane] +
                  ((unsigned long long)W.accp[32 + lane] << 24) +
@@ -1055,6 +1109,7 @@ __device__ __forceinline__ void drain_direct(const Inst &I, const DirectArea &W,
   W.accp[32 + lane] = 0u;
   W.accp[64 + lane] = 0u;
   __syncwarp();
+  return rest;
 }
 
 // One run of candidates [a, a + n) with shifts (sx, sy); appends in-range
@@ -1098,16 +1153,13 @@ __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, c
         }
       }
       const unsigned m = __ballot_sync(kFull, inr);
-      if (inr) {
-        const int w = TAG ? (slot | ((int)(stype[q] != 0) << 8)) : slot;
-        sst_f4(smem_u32(W.queue) + 16u * (unsigned)(qn + __popc(m & lt)),
-               make_float4(dx, dy, d2, __int_as_float(w)));
-      }
+      const int w = TAG ? (slot | ((int)(inr && stype[q] != 0) << 8)) : slot;
+      sst_f4_if(inr, smem_u32(W.queue) + 16u * (unsigned)(qn + __popc(m & lt)),
+                make_float4(dx, dy, d2, __int_as_float(w)));
       qn += __popc(m);
       if (qn > kQueue - 32) {
         __syncwarp();
-        drain_direct<V, PIECES, TAG, ONE>(I, W, qn, ux, uy, E8, ti, racc);
-        qn = 0;
+        qn = drain_direct<V, PIECES, TAG, ONE>(I, W, qn, ux, uy, E8, ti, racc, false);
       }
     }
     return;
@@ -1145,35 +1197,35 @@ __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, c
     ncoll += (ina && d2a < I.RC2 ? 1 : 0) + (inb && d2b < I.RC2 ? 1 : 0);  // Fig. 4
     const unsigned ma = __ballot_sync(kFull, ina), mb = __ballot_sync(kFull, inb);
     const unsigned q_s = smem_u32(W.queue);
-    if (ina) {
-      const int w = TAG ? (slot | ((int)(stype[a + ja] != 0) << 8)) : slot;
-      sst_f4(q_s + 16u * (unsigned)(qn + __popc(ma & lt)),
-             make_float4(dxa, dya, d2a, __int_as_float(w)));
+    {
+      const int w = TAG ? (slot | ((int)(ina && stype[a + ja] != 0) << 8)) : slot;
+      sst_f4_if(ina, q_s + 16u * (unsigned)(qn + __popc(ma & lt)),
+                make_float4(dxa, dya, d2a, __int_as_float(w)));
     }
     qn += __popc(ma);
-    if (inb) {
-      const int w = TAG ? (slot | ((int)(stype[a + jb] != 0) << 8)) : slot;
-      sst_f4(q_s + 16u * (unsigned)(qn + __popc(mb & lt)),
-             make_float4(dxb, dyb, d2b, __int_as_float(w)));
+    {
+      const int w = TAG ? (slot | ((int)(inb && stype[a + jb] != 0) << 8)) : slot;
+      sst_f4_if(inb, q_s + 16u * (unsigned)(qn + __popc(mb & lt)),
+                make_float4(dxb, dyb, d2b, __int_as_float(w)));
     }
     qn += __popc(mb);
     if (qn > kQueueWide - 64) {
       __syncwarp();
-      drain_direct<V, PIECES, TAG, ONE>(I, W, qn, ux, uy, E8, ti, racc);
-      qn = 0;
+      qn = drain_direct<V, PIECES, TAG, ONE>(I, W, qn, ux, uy, E8, ti, racc, false);
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// Fused policy: the shared MLP of the learners (Section 4.3; two hidden
+// Policy network: the shared MLP of the learners (Section 4.3; two hidden
 // layers of 64 with tanh, here 18 -> 64 -> 64 -> 9 on the 18-value
-// observation) applied to the observations while they are still on chip.
-// BF16 operands on the tensor cores (mma.sync m16n8k16), FP32 accumulate;
-// the greedy action (largest logit, lowest index on ties) is written back.
-// A warp holds its 32 agents' observations as a BF16 tile [32][kTileS];
-// each layer's accumulators, passed through tanh and rounded to BF16, are
-// the next layer's A fragments without leaving the registers.
+// observation), run by k_policy_mlp on the BF16 observation rows the
+// neighbour scan leaves in the workspace.  BF16 operands on the tensor cores
+// (mma.sync m16n8k16), FP32 accumulate; the greedy action (largest logit,
+// lowest index on ties) is written back.  A warp holds its 32 agents'
+// observations as a BF16 tile [32][kTileS]; each layer's accumulators,
+// passed through tanh and rounded to BF16, are the next layer's A fragments
+// without leaving the registers.
 // ---------------------------------------------------------------------------
 constexpr int kW1S = 40, kW2S = 72, kW3S = 72, kTileS = 40;  // padded row strides (bf16)
 constexpr size_t kPolicyBytes = (size_t)(64 * kW1S + 64 * kW2S + 16 * kW3S) * 2 + (64 + 64 + 16) * 4;
@@ -1360,8 +1412,7 @@ __device__ __forceinline__ void policy_mtile(const PolicyCtx &P, int row0, int &
 }
 
 // A warp takes the 32 / LPA consecutive sorted agents [gp0, gp1); LPA lanes
-// share each agent's candidates (LPA = 1, 2, 4 or 32; the policy form uses
-// 1).  LPA = 32 gives a whole warp to one agent: the form for agents with
+// share each agent's candidates (LPA = 1, 2, 4 or 32).  LPA = 32 gives a whole warp to one agent: the form for agents with
 // hundreds of candidates (a wide view), whose few agents would otherwise
 // leave most of the GPU idle.
 // TAG: the tag environment (needs V == 0 and no policy): two colour
@@ -1372,14 +1423,11 @@ __device__ __forceinline__ void policy_mtile(const PolicyCtx &P, int row0, int &
 // batched kernels, whose mix of small instances wraps often, run faster with
 // the smaller instruction footprint; a single large instance rarely wraps and
 // runs faster fully unrolled).
-template <int H, int V, bool POL = false, bool PIECES = true, int LPA = 1, bool TAG = false,
-          bool COMPACT = false>
+template <int H, int V, bool PIECES = true, int LPA = 1, bool TAG = false, bool COMPACT = false>
 __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
-                              const DirectArea &W, unsigned &err,
-                              const PolicyCtx *pc = nullptr) {
+                              const DirectArea &W, unsigned &err) {
   static_assert(LPA == 1 || LPA == 2 || LPA == 4 || LPA == 32, "lanes per agent");
-  static_assert(!POL || LPA == 1, "the policy tile holds 32 agents");
-  static_assert(!TAG || (V == 0 && !POL), "tag uses the generic sector count");
+  static_assert(!TAG || V == 0, "tag uses the generic sector count");
   constexpr int A = 32 / LPA;
   const int lane = threadIdx.x & 31;
   const int slot = lane & (A - 1);
@@ -1521,7 +1569,7 @@ __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, c
     }
   }
   __syncwarp();
-  drain_direct<V, PIECES, TAG, A == 1>(I, W, qn, ux, uy, E8, ti, racc);
+  drain_direct<V, PIECES, TAG, A == 1>(I, W, qn, ux, uy, E8, ti, racc, true);
   if (A == 1) {
     // one agent per warp: the lanes' register sums make its reward sum
 #pragma unroll
@@ -1555,13 +1603,6 @@ __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, c
   float *obs = B.obs ? B.obs + I.obs_base : nullptr;
   // the V = 8 kernels serve layout 0 only (the host picks V = 0 for layout 1)
   const bool lay0 = V == 8 || I.obs_layout == 0;
-  if (POL) {
-    // padding columns 18..31 of every row, and whole rows past the chunk
-    unsigned *row = reinterpret_cast<unsigned *>(pc->tile + lane * kTileS);
-#pragma unroll
-    for (int w2 = 0; w2 < kTileS / 2; ++w2)
-      if (w2 >= 9 || lane >= nb) row[w2] = 0u;
-  }
   if (!TAG && have && lane < A) {
     const float2 val = make_float2(ts.y, ts.x);
     if (obs) {
@@ -1569,7 +1610,8 @@ __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, c
       if (lay0) *reinterpret_cast<float2 *>(row + 2 * v) = val;
       else row[v] = val.x;
     }
-    if (POL) *reinterpret_cast<unsigned *>(pc->tile + lane * kTileS + 2 * v) = pack_bf16(val.x, val.y);
+    if (V == 8 && B.pobs)
+      B.pobs[(long long)(I.agent_base + i) * kPobsWords + v] = pack_bf16(val.x, val.y);
   }
   for (int rb = 0; rb < nb; rb += rpi) {
     const int r = min(rb + my_r, 31);
@@ -1589,38 +1631,12 @@ __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, c
           if (lay0) *reinterpret_cast<float2 *>(row + 2 * e) = val;
           else row[e] = val.x;  // layout 1: the distance only
         }
-        if (POL)
-          *reinterpret_cast<unsigned *>(pc->tile + r * kTileS + 2 * e) = pack_bf16(val.x, val.y);
+        if (V == 8 && B.pobs)
+          B.pobs[(long long)(I.agent_base + ir) * kPobsWords + e] = pack_bf16(val.x, val.y);
       }
     }
   }
   __syncwarp();
-  if (POL) {
-    const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      int alo = 0, ahi = 0;
-      float lg[2][4];
-      policy_mtile(*pc, 16 * mt, alo, ahi, lg);
-      const int rlo = 16 * mt + g, rhi = rlo + 8;
-      const int ilo = __shfl_sync(kFull, i, rlo), ihi = __shfl_sync(kFull, i, rhi);
-      if (t == 0) {
-        if (rlo < nb) pc->actions[I.agent_base + ilo] = alo;
-        if (rhi < nb) pc->actions[I.agent_base + ihi] = ahi;
-      }
-      if (pc->logits) {
-        const int c4[4] = {2 * t, 2 * t + 1, 8 + 2 * t, 9 + 2 * t};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (c4[j] < 9) {
-            if (rlo < nb) pc->logits[(long long)(I.agent_base + ilo) * 9 + c4[j]] = lg[0][j];
-            if (rhi < nb) pc->logits[(long long)(I.agent_base + ihi) * 9 + c4[j]] = lg[1][j];
-          }
-        }
-      }
-    }
-    __syncwarp();
-  }
 }
 
 }  // namespace flock

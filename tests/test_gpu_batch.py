@@ -260,9 +260,9 @@ def test_neighbour_launch_block_sizes(tuning):
     sizes = [900, 0, 1, 4100, 37, 2600]
     insts = make_instances(sizes, 700)
     b = batch_for(insts, tuning)
-    assert F.env_batch_get_launch(b.batch)[0] > 0
     states = [torch.from_numpy(st).to(DEV) for _, _, st in insts]
     b.set([p for p, _, _ in insts], sizes, states, reset=[1] * len(sizes))
+    assert F.env_batch_get_launch(b.batch)[0] > 0
     b.step(torch.zeros(sum(sizes), dtype=torch.int32, device=DEV))
     a = fi.random_actions(sum(sizes), 2, 7)
     ref = [st.copy() for _, _, st in insts]
