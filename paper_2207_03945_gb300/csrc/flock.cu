@@ -592,7 +592,7 @@ extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, v
   // 16-byte units of the outputs, one per thread, at most 8 blocks per SM
   const size_t units = ((size_t)n * e->inst.obs_dim * 4 + (size_t)n * 8) / 16;
   e->copy_grid = (int)std::max<size_t>(1, std::min<size_t>((units + 255) / 256, (size_t)sms * 8));
-  e->mlp_grid = sms * 8;
+  e->mlp_grid = sms * 2;  // each block stages the weights once, then walks many agents
   e->smemD = e->tuning.mode == 1
                  ? phaseD_smem_bytes(e->inst.cap, e->inst.v, e->tuning.block)
                  : (size_t)(e->tuning.block / 32) *

@@ -16,6 +16,8 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "flock_device.cuh"
@@ -338,7 +340,7 @@ BLayout batch_layout(int mi, int ma, int mc) {
   size_t o = 0;
   auto take = [&](size_t b) { size_t at = o; o = a256(o + b); return at; };
   const int nT = (mc + kScanTile - 1) / kScanTile;
-  L.dev = take(sizeof(BatchDev));
+  L.dev = take(2 * sizeof(BatchDev));  // two slots (see env_batch_step)
   L.insts = take((size_t)mi * sizeof(Inst));
   L.apre = take((size_t)(mi + 1) * 4);
   L.cpre = take((size_t)(mi + 1) * 4);
@@ -376,7 +378,19 @@ struct flock_batch {
   BatchDev dev;  // host copy
   std::vector<Inst> insts;
   std::vector<int> apre, cpre;
-  const void *g_act, *g_obs, *g_rew, *g_coll;
+  // Two descriptor slots in device memory, each with the output pointers of
+  // the steps that use it and a graph reading it: a caller alternating two
+  // sets of outputs re-uploads nothing per step.
+  struct Slot {
+    const void *act, *obs, *rew, *coll;
+    cudaGraphExec_t graph;
+    bool dirty;  // the device copy is older than the host's
+  } slot[2];
+  int last;  // slot of the last step
+  // Derived descriptors of parameter sets seen before, keyed by the
+  // parameter bytes: a serving session's set is derived once, not at every
+  // change of the active set.  Cleared when it outgrows 4 x max_inst.
+  std::unordered_map<std::string, Inst> derived;
   int timing;
   cudaEvent_t ev[2];
   bool configured;
@@ -471,6 +485,20 @@ extern "C" int env_batch_create(int mi, int ma, int mc, const flock_tuning *t, v
   return FLOCK_OK;
 }
 
+// Destroys the slots' graphs (re-captured at the next step), after the
+// stream has finished with them.
+static cudaError_t drop_graphs(flock_batch *b) {
+  if (!b->slot[0].graph && !b->slot[1].graph) return cudaSuccess;
+  const cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < 2; ++k)
+    if (b->slot[k].graph) {
+      cudaGraphExecDestroy(b->slot[k].graph);
+      b->slot[k].graph = nullptr;
+    }
+  return cudaSuccess;
+}
+
 extern "C" int env_batch_set(flock_batch *b, int n_inst, const flock_params *params,
                              const int *n_agents, float *const *state, const int *reset) {
   NvtxRange nvtx_range("flock:env_batch_set");
@@ -482,8 +510,16 @@ extern "C" int env_batch_set(flock_batch *b, int n_inst, const flock_params *par
   int v = 0, layout = 0;
   for (int k = 0; k < n_inst; ++k) {
     Inst &I = ins[k];
-    int rc = derive(params[k], b->halo, I, nullptr);
-    if (rc) return rc;
+    const std::string key(reinterpret_cast<const char *>(&params[k]), sizeof(flock_params));
+    auto hit = b->derived.find(key);
+    if (hit != b->derived.end()) {
+      I = hit->second;
+    } else {
+      int rc = derive(params[k], b->halo, I, nullptr);
+      if (rc) return rc;
+      if (b->derived.size() >= (size_t)4 * b->max_inst) b->derived.clear();
+      b->derived.emplace(key, I);
+    }
     if (n_agents[k] < 0 || (n_agents[k] > 0 && !state[k])) return FLOCK_EINVAL;
     if (k == 0) {
       v = I.v;
@@ -535,11 +571,7 @@ extern "C" int env_batch_set(flock_batch *b, int n_inst, const flock_params *par
     }
     b->v = v;
     b->layout = layout;
-    if (b->graph) {
-      BCK(cudaStreamSynchronize(b->stream));
-      cudaGraphExecDestroy(b->graph);
-      b->graph = nullptr;
-    }
+    BCK(drop_graphs(b));
   }
   const BLayout &L = b->lay;
   BatchDev &D = b->dev;
@@ -572,17 +604,17 @@ extern "C" int env_batch_set(flock_batch *b, int n_inst, const flock_params *par
     BCK(cudaMemcpyAsync(b->ws + L.cpre, b->cpre.data(), (size_t)(n_inst + 1) * 4,
                         cudaMemcpyHostToDevice, b->stream));
   }
-  b->g_act = b->g_obs = b->g_rew = b->g_coll = nullptr;  // outputs re-uploaded at next step
+  b->slot[0].dirty = b->slot[1].dirty = true;  // both descriptors re-uploaded when next used
   b->configured = true;
   return FLOCK_OK;
 }
 
-static int batch_enqueue_persistent(flock_batch *b, cudaStream_t s);
+static int batch_enqueue_persistent(flock_batch *b, cudaStream_t s, const BatchDev *dv);
 
-static int batch_enqueue(flock_batch *b, cudaStream_t s) {
+static int batch_enqueue(flock_batch *b, cudaStream_t s, int k) {
   const BLayout &L = b->lay;
   if (b->timing) BCK(cudaEventRecordWithFlags(b->ev[0], s, cudaEventRecordExternal));
-  const BatchDev *dv = (const BatchDev *)(b->ws + L.dev);
+  const BatchDev *dv = (const BatchDev *)(b->ws + L.dev) + k;
   Inst *ins = (Inst *)(b->ws + L.insts);
   const int *apre = (const int *)(b->ws + L.apre);
   const int *cpre = (const int *)(b->ws + L.cpre);
@@ -595,7 +627,7 @@ static int batch_enqueue(flock_batch *b, cudaStream_t s) {
     BCK(launch(true, k_bbin_scatter, b->scatter_grid, 256, (size_t)(max_tiles + 1) * 4, s, dv,
                (const Inst *)ins, apre));
   } else {
-    const int rc = batch_enqueue_persistent(b, s);
+    const int rc = batch_enqueue_persistent(b, s, dv);
     if (rc) return rc;
   }
   if (b->split) {
@@ -607,7 +639,7 @@ static int batch_enqueue(flock_batch *b, cudaStream_t s) {
   return FLOCK_OK;
 }
 
-static int batch_enqueue_persistent(flock_batch *b, cudaStream_t s) {
+static int batch_enqueue_persistent(flock_batch *b, cudaStream_t s, const BatchDev *dv) {
   const BLayout &L = b->lay;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(b->grid);
@@ -621,7 +653,7 @@ static int batch_enqueue_persistent(flock_batch *b, cudaStream_t s) {
   cfg.numAttrs = 1;
   KFn fn = batch_kernel(b->halo, b->v, b->layout, b->split);
   NvtxRange r("flock:batch_persistent");
-  BCK(cudaLaunchKernelEx(&cfg, fn, (const BatchDev *)(b->ws + L.dev), (Inst *)(b->ws + L.insts),
+  BCK(cudaLaunchKernelEx(&cfg, fn, dv, (Inst *)(b->ws + L.insts),
                          (const int *)(b->ws + L.apre), (const int *)(b->ws + L.cpre),
                          (unsigned *)(b->ws + L.ctr), b->spin_limit));
   return FLOCK_OK;
@@ -633,45 +665,50 @@ extern "C" int env_batch_step(flock_batch *b, const int32_t *act, float *obs, fl
   if (!b || !b->configured) return FLOCK_EINVAL;
   if (b->dev.n_total == 0) return FLOCK_OK;
   if (!act || !obs || !rew || !coll || ((uintptr_t)obs & 7)) return FLOCK_EINVAL;
-  if (act != b->g_act || obs != b->g_obs || rew != b->g_rew || coll != b->g_coll) {
+  // the slot holding these pointers, else the one not used last
+  int k = -1;
+  for (int j = 0; j < 2; ++j) {
+    const flock_batch::Slot &q = b->slot[j];
+    if (q.act == act && q.obs == obs && q.rew == rew && q.coll == coll) k = j;
+  }
+  if (k < 0) {
+    k = b->last ^ 1;
+    flock_batch::Slot &q = b->slot[k];
+    q.act = act;
+    q.obs = obs;
+    q.rew = rew;
+    q.coll = coll;
+    q.dirty = true;  // the graph reads the slot's descriptor: no re-capture needed
+  }
+  flock_batch::Slot &q = b->slot[k];
+  if (q.dirty) {
     b->dev.B.actions = act;
     b->dev.B.obs = obs;
     b->dev.B.reward = rew;
     b->dev.B.coll = coll;
-    BCK(cudaMemcpyAsync(b->ws + b->lay.dev, &b->dev, sizeof(BatchDev), cudaMemcpyHostToDevice,
-                        b->stream));
-    b->g_act = act;
-    b->g_obs = obs;
-    b->g_rew = rew;
-    b->g_coll = coll;
+    BCK(cudaMemcpyAsync((BatchDev *)(b->ws + b->lay.dev) + k, &b->dev, sizeof(BatchDev),
+                        cudaMemcpyHostToDevice, b->stream));
+    q.dirty = false;
   }
-  if (!b->graph) {
+  if (!q.graph) {
     cudaGraph_t g = nullptr;
     BCK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-    int rc = batch_enqueue(b, b->cap_stream);
+    int rc = batch_enqueue(b, b->cap_stream, k);
     cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &g);
     if (rc) {
       if (g) cudaGraphDestroy(g);
       return rc;
     }
     if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
-    if (b->graph) {
-      cudaGraphExecUpdateResultInfo info;
-      if (cudaGraphExecUpdate(b->graph, g, &info) != cudaSuccess) {
-        (void)cudaGetLastError();
-        ce = cudaStreamSynchronize(b->stream);
-        cudaGraphExecDestroy(b->graph);
-        b->graph = nullptr;
-      }
-    }
-    if (!b->graph && ce == cudaSuccess) ce = cudaGraphInstantiate(&b->graph, g, 0);
+    ce = cudaGraphInstantiate(&q.graph, g, 0);
     cudaGraphDestroy(g);
     if (ce != cudaSuccess) {
-      b->graph = nullptr;
+      q.graph = nullptr;
       return cuda_fail(ce, "cudaGraphInstantiate");
     }
   }
-  BCK(cudaGraphLaunch(b->graph, b->stream));
+  b->last = k;
+  BCK(cudaGraphLaunch(q.graph, b->stream));
   return FLOCK_OK;
 }
 
@@ -714,11 +751,7 @@ extern "C" int env_batch_get_error(flock_batch *b, uint32_t *bits) {
 
 extern "C" int env_batch_set_spin_limit(flock_batch *b, unsigned limit) {
   if (!b) return FLOCK_EINVAL;
-  if (b->graph) {
-    BCK(cudaStreamSynchronize(b->stream));
-    cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
-  }
+  BCK(drop_graphs(b));
   b->spin_limit = limit;
   return FLOCK_OK;
 }
@@ -734,11 +767,7 @@ extern "C" int env_batch_set_timing(flock_batch *b, int enable) {
   if (!b) return FLOCK_EINVAL;
   if (enable && !b->ev[0])
     for (int k = 0; k < 2; ++k) BCK(cudaEventCreate(&b->ev[k]));
-  if ((enable != 0) != (b->timing != 0) && b->graph) {
-    BCK(cudaStreamSynchronize(b->stream));
-    cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
-  }
+  if ((enable != 0) != (b->timing != 0)) BCK(drop_graphs(b));
   b->timing = enable != 0;
   return FLOCK_OK;
 }
@@ -755,7 +784,8 @@ extern "C" void env_batch_destroy(flock_batch *b) {
   cudaStreamSynchronize(b->stream);
   for (int k = 0; k < 2; ++k)
     if (b->ev[k]) cudaEventDestroy(b->ev[k]);
-  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (int k = 0; k < 2; ++k)
+    if (b->slot[k].graph) cudaGraphExecDestroy(b->slot[k].graph);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   delete b;
 }

@@ -1248,32 +1248,37 @@ __device__ __forceinline__ float bf16_bits_to_float(unsigned short b) {
 }
 
 // Block-cooperative load of the blob into the padded shared layout (call,
-// then __syncthreads).  Padding columns and rows are zero.
+// then __syncthreads).  Padding columns and rows are zero.  Every matrix of
+// the blob starts at an even BF16 offset and has an even row length (18 or
+// 64), so the copy moves BF16 pairs (the blob is 4-byte aligned).
 __device__ __forceinline__ void load_policy(const unsigned short *__restrict__ blob, char *base) {
-  unsigned short *W1 = reinterpret_cast<unsigned short *>(base);
-  unsigned short *W2 = W1 + 64 * kW1S;
-  unsigned short *W3 = W2 + 64 * kW2S;
-  float *b1 = reinterpret_cast<float *>(W3 + 16 * kW3S);
+  const unsigned *bw = reinterpret_cast<const unsigned *>(blob);
+  unsigned *W1 = reinterpret_cast<unsigned *>(base);  // [64][kW1S / 2]
+  unsigned *W2 = W1 + 64 * (kW1S / 2);                 // [64][kW2S / 2]
+  unsigned *W3 = W2 + 64 * (kW2S / 2);                 // [16][kW3S / 2]
+  float *b1 = reinterpret_cast<float *>(W3 + 16 * (kW3S / 2));
   float *b2 = b1 + 64, *b3 = b2 + 64;
-  for (int e = threadIdx.x; e < 64 * kW1S; e += blockDim.x) {
-    const int n = e / kW1S, k = e - n * kW1S;
-    W1[e] = k < 18 ? blob[n * 18 + k] : (unsigned short)0;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < 64 * (kW1S / 2); e += nt) {
+    const int n = e / (kW1S / 2), k2 = e - n * (kW1S / 2);
+    W1[e] = k2 < 9 ? __ldg(bw + n * 9 + k2) : 0u;
   }
-  for (int e = threadIdx.x; e < 64 * kW2S; e += blockDim.x) {
-    const int n = e / kW2S, k = e - n * kW2S;
-    W2[e] = k < 64 ? blob[kOffW2 + n * 64 + k] : (unsigned short)0;
+  for (int e = tid; e < 64 * (kW2S / 2); e += nt) {
+    const int n = e / (kW2S / 2), k2 = e - n * (kW2S / 2);
+    W2[e] = k2 < 32 ? __ldg(bw + kOffW2 / 2 + n * 32 + k2) : 0u;
   }
-  for (int e = threadIdx.x; e < 16 * kW3S; e += blockDim.x) {
-    const int n = e / kW3S, k = e - n * kW3S;
-    W3[e] = (n < 9 && k < 64) ? blob[kOffW3 + n * 64 + k] : (unsigned short)0;
+  for (int e = tid; e < 16 * (kW3S / 2); e += nt) {
+    const int n = e / (kW3S / 2), k2 = e - n * (kW3S / 2);
+    W3[e] = (n < 9 && k2 < 32) ? __ldg(bw + kOffW3 / 2 + n * 32 + k2) : 0u;
   }
-  for (int e = threadIdx.x; e < 64; e += blockDim.x) {
+  for (int e = tid; e < 64; e += nt) {
     b1[e] = bf16_bits_to_float(blob[kOffB1 + e]);
     b2[e] = bf16_bits_to_float(blob[kOffB2 + e]);
   }
-  for (int e = threadIdx.x; e < 16; e += blockDim.x)
-    b3[e] = e < 9 ? bf16_bits_to_float(blob[kOffB3 + e]) : 0.0f;
+  for (int e = tid; e < 16; e += nt) b3[e] = e < 9 ? bf16_bits_to_float(blob[kOffB3 + e]) : 0.0f;
 }
+
+static_assert(kOffW2 % 2 == 0 && kOffW3 % 2 == 0, "policy matrices start on BF16 pairs");
 
 __device__ __forceinline__ PolicyCtx policy_ctx(char *base) {
   PolicyCtx P;
