@@ -109,9 +109,10 @@ typedef struct flock_tuning {
                   and reads their stencil cells through the L1 cache.
                   Batch: 2 = every phase in one persistent launch; 3 = binning
                   in the persistent launch, the neighbour scan (direct form)
-                  in a second launch; 4 = binning by three kernels (apply and
-                  count, scan, scatter) over all instances, then the
-                  neighbour launch.  Results are identical. */
+                  in a second launch; 4 (0: the default) = binning by three
+                  kernels (apply and count, scan, scatter) over all
+                  instances, then the neighbour launch.  Results are
+                  identical. */
   int lanes;   /* mode 2: lanes per agent, 1, 2, 4 or 32 (0: 32 when an agent
                   has 256 or more candidates in its stencil cells on average,
                   else 4 up to 32,768 agents, 2 up to 524,288, else 1); the
@@ -333,6 +334,56 @@ int env_batch_set_timing(flock_batch *batch, int enable);
 int env_batch_get_time(flock_batch *batch, float *ms_out);
 
 void env_batch_destroy(flock_batch *batch);
+
+/* ---------------------------------------------------------------------------
+ * Slabs: one square decomposed over several devices (a square too large for
+ * one GPU's memory).  Band b of R owns the rows [r_b, r_{b+1}) of the
+ * square's cell grid (flock_derive: cells_per_side rows of width side /
+ * cells_per_side).  A slab environment holds the cell list of its band plus
+ * H rows on each side (H = the stencil's halo, 1 for the 3 x 3 stencil):
+ * rows [row0, row0 + nrows) modulo cells_per_side, row0 = r_b - H, nrows =
+ * r_{b+1} - r_b + 2H.  Each step (Section 4.1: all agents act, then all
+ * observe the new positions):
+ *   1. env_slab_apply: the band's own agents take their actions;
+ *   2. the caller moves agents that left the band to the band that now owns
+ *      them, and copies every own agent in the H rows next to a band edge to
+ *      the band across that edge (a ghost; coordinates on the square, never
+ *      shifted, so offsets across the square's edge are formed as on the
+ *      undivided square);
+ *   3. env_slab_observe: own agents observe own and ghost agents.
+ * The outputs equal those of the undivided square, bit for bit (same
+ * pairs, same FP32 operations, exact reward sums).  Agents must not move
+ * more than one band per step (speed_max below the band height).  The
+ * decomposition itself (which agents move, which are ghosts, the exchange)
+ * is in the Python package (slab.py); these calls compute on one device.
+ * ------------------------------------------------------------------------- */
+
+/* Workspace of a slab environment of at most n_max agents (own + ghosts)
+ * and rows [row0, row0 + nrows) (0 <= row0 < cells_per_side, 2H + 1 <=
+ * nrows <= cells_per_side).  The tuning must use the direct neighbour scan
+ * (mode 0 or 2). */
+int flock_slab_workspace_bytes(const flock_params *params, const flock_tuning *tuning_or_null,
+                               int n_max, int row0, int nrows, size_t *bytes_out);
+
+/* Creates a slab environment (the ownership and stream rules of env_create).
+ * Use env_slab_apply / env_slab_observe (and env_get_error, env_destroy) with
+ * it, not env_reset / env_step. */
+int env_slab_create(const flock_params *params, const flock_tuning *tuning_or_null, int n_max,
+                    int row0, int nrows, void *workspace_dev, size_t workspace_bytes,
+                    void *stream, flock_env **out);
+
+/* Applies actions_dev (n int32, the discrete actions of env_step) to the n
+ * agents of state_dev (n x 4 floats, 16-byte aligned) in place.  Invalid
+ * actions and states latch FLOCK_ERR_ACTION / FLOCK_ERR_STATE. */
+int env_slab_apply(flock_env *env, int n, float *state_dev, const int32_t *actions_dev);
+
+/* Observes the first n_own agents of state_dev ((n_own + n_ghost) x 4
+ * floats: the band's own agents, then its ghosts, all already moved) over
+ * all of them: obs_dev (n_own x obs_dim), reward_dev and coll_dev (n_own)
+ * as for env_step.  n_own + n_ghost <= n_max.  Every agent must lie in the
+ * slab's rows. */
+int env_slab_observe(flock_env *env, int n_own, int n_ghost, const float *state_dev,
+                     float *obs_dev, float *reward_dev, int32_t *coll_dev);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free step.  (The paper has no counterpart: this entry point exists

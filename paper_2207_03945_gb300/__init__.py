@@ -28,6 +28,7 @@ __all__ = [
     "env_step_policy",
     "flock_batch_workspace_bytes", "env_batch_create", "env_batch_set", "env_batch_step",
     "env_batch_set_rows", "env_batch_get_error", "env_batch_set_spin_limit", "env_batch_get_launch",
+    "FlockSlab",
     "env_batch_set_timing", "env_batch_get_time", "env_batch_destroy", "FlockBatch",
     "flock_step_static",
 ]
@@ -576,3 +577,68 @@ def flock_step_static(params: dict, state, actions, obs, reward, coll, stream=No
         _ptr(coll, torch.int32, (n,), "coll"), _stream(stream),
         ctypes.byref(bits) if wait else None))
     return int(bits.value) if wait else None
+
+
+# ---------------------------------------------------------------------------
+# Slabs (one square decomposed over several devices; see slab.py)
+# ---------------------------------------------------------------------------
+class FlockSlab:
+    """A slab environment: the cell list of rows [row0, row0 + nrows) of a
+    square's grid (modulo its cells per side), for at most n_max own and
+    ghost agents.  apply() moves own agents; observe() observes the own
+    agents over own and ghost agents (env_slab_apply / env_slab_observe)."""
+
+    def __init__(self, params: dict, n_max: int, row0: int, nrows: int, device="cuda",
+                 stream=None, tuning: dict | None = None):
+        torch = _torch()
+        self.params = dict(params)
+        self.n_max = int(n_max)
+        self.device = torch.device(device)
+        self.obs_dim = flock_obs_dim(params)
+        t = _abi.tuning_from_dict(tuning)
+        pc = _abi.params_from_dict(params)
+        nbytes = ctypes.c_size_t(0)
+        _abi.check(_abi.lib.flock_slab_workspace_bytes(
+            ctypes.byref(pc), ctypes.byref(t) if t is not None else None, self.n_max, int(row0),
+            int(nrows), ctypes.byref(nbytes)))
+        self.workspace = torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8,
+                                     device=self.device)
+        h = ctypes.c_void_p()
+        _abi.check(_abi.lib.env_slab_create(
+            ctypes.byref(pc), ctypes.byref(t) if t is not None else None, self.n_max, int(row0),
+            int(nrows), _ptr(self.workspace, torch.uint8, name="workspace"),
+            ctypes.c_size_t(self.workspace.numel()), _stream(stream), ctypes.byref(h)))
+        self.env = _Env(h, self.n_max, self.obs_dim, self.workspace)
+
+    def apply(self, state, actions):
+        """Actions (n int32) of the n agents of state (n x 4 float32), in place."""
+        torch = _torch()
+        n = int(state.shape[0])
+        _abi.check(_abi.lib.env_slab_apply(
+            self.env.handle, n, _ptr(state, torch.float32, (n, 4), "state"),
+            _ptr(actions, torch.int32, (n,), "actions")))
+
+    def observe(self, state, n_own: int, obs, reward, coll):
+        """Observation, reward and collisions of the first n_own agents of
+        state (own agents, then ghosts) over all of them."""
+        torch = _torch()
+        n = int(state.shape[0])
+        _abi.check(_abi.lib.env_slab_observe(
+            self.env.handle, int(n_own), n - int(n_own), _ptr(state, torch.float32, (n, 4), "state"),
+            _ptr(obs, torch.float32, (int(n_own), self.obs_dim), "obs"),
+            _ptr(reward, torch.float32, (int(n_own),), "reward"),
+            _ptr(coll, torch.int32, (int(n_own),), "coll")))
+
+    def error(self) -> int:
+        return env_get_error(self.env)
+
+    def close(self):
+        if self.env is not None:
+            env_destroy(self.env)
+            self.env = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -133,6 +133,12 @@ def _load(path=LIB_PATH):
         "env_batch_get_time": [vp, ctypes.POINTER(ctypes.c_float)],
         "flock_step_static": [P, ctypes.c_int, vp, vp, vp, vp, vp, vp,
                               ctypes.POINTER(ctypes.c_uint32)],
+        "flock_slab_workspace_bytes": [P, T, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_size_t)],
+        "env_slab_create": [P, T, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t,
+                            vp, ctypes.POINTER(vp)],
+        "env_slab_apply": [vp, ctypes.c_int, vp, vp],
+        "env_slab_observe": [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)

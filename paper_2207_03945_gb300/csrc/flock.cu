@@ -93,7 +93,7 @@ __global__ void k_neighbours_direct(const Inst *__restrict__ gI, Bufs B) {
 // grid-stride loop.  (A fused form that ran the network in the neighbour
 // scan's epilogue held 94 registers and 46 KB of shared memory per block,
 // and took 1.67 times the plain step at 100,000 agents.)
-constexpr int kMlpBlock = 128;
+constexpr int kMlpBlock = 256;
 
 __global__ void __launch_bounds__(kMlpBlock) k_policy_mlp(const unsigned *__restrict__ pobs, int n,
                                                           const unsigned short *__restrict__ wblob,
@@ -304,6 +304,8 @@ int derive(const flock_params &p, int stencil, Inst &I, flock_derived *D) {
   if (ncd < stencil || ncd * ncd > (double)kMaxScanTiles * kScanTile) return FLOCK_EINVAL;
   I.nc = (int)ncd;
   I.ncells = I.nc * I.nc;
+  I.row0 = 0;  // a whole square: every row, every agent observed
+  I.nrows = I.nc;
   I.halo = stencil;
   I.invw = (float)((double)I.nc / (double)p.side);
   if (p.obs_layout != 0 && p.obs_layout != 1) return FLOCK_EINVAL;
@@ -521,6 +523,7 @@ static int resolve(const flock_params *p, const flock_tuning *t, int n, Inst &I,
   rc = choose_tuning(I, n, t, tt);
   if (rc) return rc;
   I.n = n;
+  I.n_own = n;
   set_tiles(I, n, tt);
   return FLOCK_OK;
 }
@@ -542,14 +545,26 @@ extern "C" int flock_derive(const flock_params *p, const flock_tuning *t, flock_
   return derive(*p, (t && t->stencil) ? t->stencil : 1, I, out);
 }
 
-extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, void *ws,
-                          size_t ws_bytes, void *stream, flock_env **out) {
-  NvtxRange nvtx_range("flock:env_create");
+// Geometry of a slab (rows [row0, row0 + nrows) of the square's cell grid,
+// modulo nc; nrows = 0: the whole square) applied to a resolved descriptor.
+static int set_slab(Inst &I, const flock_tuning &t, int row0, int nrows) {
+  if (nrows == 0 && row0 == 0) return FLOCK_OK;
+  if (t.mode != 2) return FLOCK_EINVAL;  // slabs use the direct neighbour scan
+  if (row0 < 0 || row0 >= I.nc || nrows < 2 * I.halo + 1 || nrows > I.nc) return FLOCK_EINVAL;
+  I.row0 = row0;
+  I.nrows = nrows;
+  I.ncells = nrows * I.nc;
+  return FLOCK_OK;
+}
+
+static int create_env(const flock_params *p, const flock_tuning *t, int n, int row0, int nrows,
+                      void *ws, size_t ws_bytes, void *stream, flock_env **out) {
   if (!out) return FLOCK_EINVAL;
   *out = nullptr;
   flock_env *e = new (std::nothrow) flock_env();
   if (!e) return FLOCK_EINVAL;
   int rc = resolve(p, t, n, e->inst, e->tuning, &e->derived);
+  if (!rc) rc = set_slab(e->inst, e->tuning, row0, nrows);
   if (rc) { delete e; return rc; }
   e->params = *p;
   e->n = n;
@@ -622,12 +637,20 @@ extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, v
   return FLOCK_OK;
 }
 
+extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, void *ws,
+                          size_t ws_bytes, void *stream, flock_env **out) {
+  NvtxRange nvtx_range("flock:env_create");
+  return create_env(p, t, n, 0, 0, ws, ws_bytes, stream, out);
+}
+
 // act: discrete actions, or cact (when not null): continuous ones.
 // pobs (policy step): the neighbour scan also writes BF16 observation rows
 // there; it then runs in the direct form whatever the tuning's mode.
+// n_run >= 0 (a slab's observation): that many agents this time (at most the
+// environment's n); the descriptor in the workspace must say the same.
 static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const float2 *cact,
                         float *obs, float *rew, int32_t *coll, int reset,
-                        unsigned *pobs = nullptr) {
+                        unsigned *pobs = nullptr, int n_run = -1) {
   Bufs B = e->bufs;
   B.actions = act;
   B.cactions = cact;
@@ -636,7 +659,8 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const 
   B.coll = coll;
   B.pobs = pobs;
   const Inst *gI = (const Inst *)(e->ws + e->lay.inst);
-  const int n = e->n;
+  const int n = n_run >= 0 ? n_run : e->n;
+  B.n_total = n;
   const bool tm = e->timing != 0;
   // with timing events between the kernels, plain stream order
   const bool pdl = !tm;
@@ -1048,6 +1072,80 @@ extern "C" void env_destroy(flock_env *e) {
 
 
 // ---------------------------------------------------------------------------
+// Slabs: one square decomposed over several devices.  A slab environment's
+// cell list holds a band of rows of the square's grid; each step the caller
+// (the decomposition in slab.py) applies the actions of the agents it owns
+// (env_slab_apply), moves the agents that crossed into another band to its
+// owner and copies the agents near each band edge to the neighbouring band
+// as ghosts, then observes its own agents over its own and the ghost agents
+// (env_slab_observe).  Positions keep their coordinates on the square, so
+// the minimum-image offsets are those of the undivided square.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_apply(const Inst *__restrict__ gI, float4 *state,
+                                               const int32_t *__restrict__ actions, int n,
+                                               unsigned *errw) {
+  const Inst &I = *gI;
+  unsigned err = 0;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    float4 st = state[i];
+    if (!state_ok(st, I)) err |= FLOCK_ERR_STATE;
+    state[i] = apply_action(st, actions[i], I, err);
+  }
+  if (err) atomicOr(errw, err);
+}
+
+extern "C" int flock_slab_workspace_bytes(const flock_params *p, const flock_tuning *t, int n_max,
+                                          int row0, int nrows, size_t *bytes) {
+  if (!bytes || nrows <= 0) return FLOCK_EINVAL;
+  Inst I;
+  flock_tuning tt;
+  int rc = resolve(p, t, n_max, I, tt, nullptr);
+  if (!rc) rc = set_slab(I, tt, row0, nrows);
+  if (rc) return rc;
+  *bytes = make_layout(n_max, I.ncells, I.obs_dim).total;
+  return FLOCK_OK;
+}
+
+extern "C" int env_slab_create(const flock_params *p, const flock_tuning *t, int n_max, int row0,
+                               int nrows, void *ws, size_t ws_bytes, void *stream,
+                               flock_env **out) {
+  NvtxRange nvtx_range("flock:env_slab_create");
+  if (nrows <= 0) return FLOCK_EINVAL;
+  return create_env(p, t, n_max, row0, nrows, ws, ws_bytes, stream, out);
+}
+
+extern "C" int env_slab_apply(flock_env *e, int n, float *state_dev, const int32_t *actions_dev) {
+  NvtxRange nvtx_range("flock:env_slab_apply");
+  if (!e || n < 0 || n > e->n) return FLOCK_EINVAL;
+  if (n == 0) return FLOCK_OK;
+  if (!state_dev || !actions_dev || !aligned(state_dev, 16) || !aligned(actions_dev, 4))
+    return FLOCK_EINVAL;
+  CK(launch(false, k_apply, (n + 255) / 256, 256, 0, e->stream,
+            (const Inst *)(e->ws + e->lay.inst), reinterpret_cast<float4 *>(state_dev),
+            actions_dev, n, e->bufs.err));
+  return FLOCK_OK;
+}
+
+extern "C" int env_slab_observe(flock_env *e, int n_own, int n_ghost, const float *state_dev,
+                                float *obs, float *rew, int32_t *coll) {
+  NvtxRange nvtx_range("flock:env_slab_observe");
+  if (!e || n_own < 0 || n_ghost < 0 || n_own + n_ghost > e->n) return FLOCK_EINVAL;
+  const int n = n_own + n_ghost;
+  if (n > 0 && (!state_dev || !aligned(state_dev, 16))) return FLOCK_EINVAL;
+  if (n_own > 0 && (!obs || !rew || !coll || !aligned(obs, 8))) return FLOCK_EINVAL;
+  Inst I = e->inst;
+  I.n = n;
+  I.n_own = n_own;
+  // the host copy is staged by the time the call returns (pageable memory)
+  CK(cudaMemcpyAsync(e->ws + e->lay.inst, &I, sizeof(Inst), cudaMemcpyHostToDevice, e->stream));
+  if (n > 0)
+    CK(cudaMemcpyAsync(e->ws + e->lay.state, state_dev, (size_t)n * 16, cudaMemcpyDeviceToDevice,
+                       e->stream));
+  return enqueue_step(e, e->stream, nullptr, nullptr, obs, rew, coll, 1, nullptr, n);
+}
+
+// ---------------------------------------------------------------------------
 // Allocation-free step.
 //
 // Some callers cannot allocate device memory at all: code that runs inside a
@@ -1148,6 +1246,7 @@ extern "C" int flock_step_static(const flock_params *p, int n, float *state_dev,
   t.mode = 2;
   t.block = 128;
   I.n = n;
+  I.n_own = n;
   I.state = reinterpret_cast<float4 *>(state_dev);
   I.agent_base = 0;
   I.cell_base = 0;

@@ -45,7 +45,12 @@ struct alignas(16) Inst {
   int pieces;        // 32-bit pieces a reward term needs in shared accumulators (2 or 3)
   int obs_layout;    // 0: (distance, count) per sector, speed, heading; 1: distances, speed
   int kind;          // 0: flock; 1: tag (runners and chasers, Section 4.2)
-  int pad2, pad3, pad4;
+  // a slab of a larger square (decomposition over devices): its cell list
+  // holds the rows [row0, row0 + nrows) of the square's grid (modulo nc),
+  // and only its first n_own agents are observed (the rest are ghosts,
+  // copies of a neighbouring slab's agents).  A whole square: row0 = 0,
+  // nrows = nc, n_own = n.
+  int row0, nrows, n_own;
   float L, HL, invw, RV, RV2, RC2, INV_SPAN, SMIN, SMAX, TWO_PI, CF, SF, scaleK, inv_scaleK;
   float DT[3], DS[3];
   long long PK, NMAX;
@@ -314,6 +319,13 @@ __device__ __forceinline__ void put_obs(const Inst &I, float *row, int e, float2
   else row[e] = val.x;
 }
 
+// Row of the instance's cell list that holds row gr of the square's grid
+// (gr - row0 modulo nc; the identity for a whole square).
+__device__ __forceinline__ int lrow(const Inst &I, int gr) {
+  const int r = gr - I.row0;
+  return r < 0 ? r + I.nc : r;
+}
+
 __device__ __forceinline__ int cell_of(float x, const Inst &I) {
   int c = __float2int_rz(fmul(x, I.invw));
   c = c < 0 ? 0 : c;
@@ -362,7 +374,7 @@ __device__ __forceinline__ void phaseA_agent(const Inst &I, int i, const int32_t
     else st = apply_cont(st, cactions_inst[i], I, err);
     I.state[i] = st;
   }
-  const int g = I.cell_base + cell_of(st.y, I) * I.nc + cell_of(st.x, I);
+  const int g = I.cell_base + lrow(I, cell_of(st.y, I)) * I.nc + cell_of(st.x, I);
   if (!dbg_ok(g >= I.cell_base && g < I.cell_base + I.ncells)) return;
   cellrank[I.agent_base + i] = make_int2(g, warp_count(counts, g));
 }
@@ -1441,7 +1453,7 @@ __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, c
   Edges<V> E8;
   E8.load(I);
   const int gp = gp0 + slot;
-  const bool have = gp < gp1;
+  bool have = gp < gp1;
   const int nb = gp1 - gp0;
   float xi = 0.f, yi = 0.f;
   float2 ts = make_float2(0.f, 0.f);
@@ -1457,6 +1469,8 @@ __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, c
     cx = cell_of(xi, I);
     cy = cell_of(yi, I);
   }
+  // a slab's ghosts (agents past its first n_own) are candidates only
+  if (i >= I.n_own) have = false;
   const int ti = TAG && have ? (int)(B.stype[gp] != 0) : 0;  // own type (tag)
   // the cell starts of the stencil rows are read before anything waits on
   // the agent's own state row, so that the two reads are in flight together
@@ -1469,7 +1483,7 @@ __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, c
   int ra[2 * H + 1], rn[2 * H + 1];
 #pragma unroll
   for (int r = 0; r < 2 * H + 1; ++r) {
-    const int rowg = I.cell_base + wrapi(cy - H + r, nc) * nc;
+    const int rowg = I.cell_base + lrow(I, wrapi(cy - H + r, nc)) * nc;
     ra[r] = have ? cst[rowg + ma] : 0;
     rn[r] = have ? cst[rowg + mb] - ra[r] : 0;
     dbg_run(ra[r], rn[r], B.n_total);
@@ -1521,7 +1535,7 @@ __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, c
       const int r = t / 3, kind = t - 3 * r;
       const int vr = cy - H + r;
       const float sy = vr < 0 ? -I.L : (vr >= nc ? I.L : 0.0f);
-      const int rowg = I.cell_base + wrapi(vr, nc) * nc;
+      const int rowg = I.cell_base + lrow(I, wrapi(vr, nc)) * nc;
       int a = 0, n = 0;
       float sx = 0.f;
       if (kind == 0) {
@@ -1549,7 +1563,7 @@ __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, c
     for (int r = 0; r < 2 * H + 1; ++r) {
       const int vr = cy - H + r;
       const float sy = vr < 0 ? -I.L : (vr >= nc ? I.L : 0.0f);
-      const int rowg = I.cell_base + wrapi(vr, nc) * nc;
+      const int rowg = I.cell_base + lrow(I, wrapi(vr, nc)) * nc;
       direct_run<true, V, PIECES, LPA, TAG>(I, W, B.sxy, ra[r], rn[r], self, 0.f, sy, xi, yi,
                                             ux, uy, qn, nin, ncoll, E8, B.stype, ti, racc);
       // cells across the left boundary: virtual columns [vlo, 0) -> [vlo + nc, nc)
@@ -1621,7 +1635,8 @@ __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, c
   for (int rb = 0; rb < nb; rb += rpi) {
     const int r = min(rb + my_r, 31);
     const int ir = __shfl_sync(kFull, i, r);
-    if (rb + my_r < nb && my_r < rpi) {
+    const bool hr = __shfl_sync(kFull, have, r);  // a ghost's row gets no output
+    if (rb + my_r < nb && my_r < rpi && hr) {
       for (int e = my_e; e < P; e += 32) {
         if (TAG) {
           const int ck = W.cn[r * vs + e];
