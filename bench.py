@@ -71,13 +71,36 @@ def sources_digest() -> str:
 
 
 def batch_traffic(key: str, mode: int):
-    """DRAM bytes of one batched step from the committed table: the
-    persistent kernel, plus the neighbour launch in the two-launch form."""
-    t = measured_traffic("k_batch_step", key)
-    if mode == 3:
-        t2 = measured_traffic("k_batch_neigh", key)
-        return None if t is None or t2 is None else t + t2
-    return t
+    """DRAM bytes of one batched step from the committed table: the sum over
+    the step's kernels in that form (None unless all are in the table)."""
+    kernels = {2: ["k_batch_step"], 3: ["k_batch_step", "k_batch_neigh"],
+               4: ["k_bbin_apply", "k_bbin_scan", "k_bbin_scatter", "k_batch_neigh"]}
+    vals = [measured_traffic(k, key) for k in kernels.get(mode, [])]
+    return None if not vals or any(v is None for v in vals) else sum(vals)
+
+
+def pair_counts(params: dict, state, stencil: int = 1):
+    """(candidate tests, in-range pairs) of one step of the square at these
+    positions: candidates are the other agents in each agent's stencil cells
+    (the library's cell list), pairs the ordered pairs closer than the view
+    radius (counted in float64: a throughput figure, not a parity check)."""
+    from scipy.spatial import cKDTree
+    import paper_2207_03945_gb300 as F
+    d = F.flock_derive(params, {"stencil": stencil})
+    nc, h, invw = int(d["cells_per_side"]), int(d["stencil"]), np.float32(d["inv_cell_width"])
+    xy = np.asarray(state, dtype=np.float32)[:, :2]
+    cells = np.clip((xy * invw).astype(np.int64), 0, nc - 1)
+    grid = np.zeros((nc, nc), np.int64)
+    np.add.at(grid, (cells[:, 1], cells[:, 0]), 1)
+    box = np.zeros_like(grid)
+    for dy in range(-h, h + 1):
+        for dx in range(-h, h + 1):
+            box += np.roll(np.roll(grid, dy, axis=0), dx, axis=1)
+    cand = int(box[cells[:, 1], cells[:, 0]].sum()) - len(xy)
+    L = float(params["side"])
+    tree = cKDTree(np.mod(xy.astype(np.float64), L), boxsize=L)
+    pairs = int(tree.count_neighbors(tree, float(params["view_radius"]))) - len(xy)
+    return cand, pairs
 
 
 def tuning_tag(t: dict) -> str:
@@ -276,6 +299,14 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+BATCH_FORMS = {2: "every phase in one persistent cooperative kernel",
+               3: "binning in a persistent cooperative kernel, then the neighbour launch",
+               4: "binning by three kernels (apply and count, scan, scatter), then the "
+                  "neighbour launch"}
+BATCH_KERNELS = {2: "k_batch_step", 3: "k_batch_step + k_batch_neigh",
+                 4: "k_bbin_apply + k_bbin_scan + k_bbin_scatter + k_batch_neigh"}
+
+
 def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256, sizes=None,
                 world=1, tune=True, tuning=None):
     """The batched form: n_inst instances with agent counts log-uniform in
@@ -339,7 +370,7 @@ def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256,
     ms = [ev0[k].elapsed_time(ev1[k]) for k in range(steps)]
     tot = max_over_ranks(sum(ms), dev)
     grid, block = F.env_batch_get_launch(b.batch)
-    bmode = (tuning or {}).get("mode", 2) or 2
+    bmode = (tuning or {}).get("mode", 4) or 4  # the library's default form is 4
     traffic_key = "batched-%d-%d-s%d-m%d" % (n_inst, total, (tuning or {}).get("stencil", 1), bmode)
     kern_ms = float(np.mean(kern))
     peak, peak_kind = peaks()
@@ -351,13 +382,13 @@ def run_batched(F, torch, dev, stream, steps, warmup, flush, seed=0, n_inst=256,
             "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
             "grid": grid, "block": block,
             "workload": "batched: %d flock instances, agent counts %s (seed %d, %d agents), "
-                        "density 0.1, view radius 5, 8 sectors, fov 250 deg, one persistent "
-                        "cooperative kernel per step, CUDA graph"
+                        "density 0.1, view radius 5, 8 sectors, fov 250 deg, %s, one CUDA "
+                        "graph per step"
                         % (n_inst, "log-uniform in [100, 20000]" if mix else
                            "%d x %d" % (n_inst, sizes[0]) if len(set(sizes)) == 1 else str(sizes),
-                           seed, total),
+                           seed, total, BATCH_FORMS.get(bmode, "form %d" % bmode)),
             "roofline": {"bound": "hbm",
-                         "kernel": "k_batch_step" if bmode == 2 else "k_batch_step + k_batch_neigh",
+                         "kernel": BATCH_KERNELS.get(bmode, "batch"),
                          "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_kind,
@@ -485,6 +516,7 @@ def run_paper_variant(F, torch, dev, stream, steps, warmup, flush, n=16000, seed
     torch.cuda.synchronize()
     assert env.error() == 0
     tun = env.tuning()
+    cand, pairs = pair_counts(p, env.state().cpu().numpy(), tun["stencil"])
     env.close()
     ms = [ev0[k].elapsed_time(ev1[k]) for k in range(steps)]
     tot = max_over_ranks(sum(ms), dev)
@@ -499,10 +531,22 @@ def run_paper_variant(F, torch, dev, stream, steps, warmup, flush, n=16000, seed
                         "side), 128 sectors, fov 250 deg, continuous (acceleration, rotation) "
                         "actions, observation 128 distances + speed" % (n, p["side"],
                                                                          p["view_radius"]),
+            "pairs": pair_rates(cand, pairs, n, tot / steps),
             "roofline": {"bound": "hbm", "kernel": "whole step (4 kernels)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,
                          "traffic": None, "bytes_per_agent": bpa}}
+
+
+def pair_rates(cand: int, pairs: int, n: int, ms_per_step: float):
+    """Pair throughput of a pair-bound workload (a view of hundreds of
+    neighbours): candidate tests and in-range pairs per second and per
+    agent, at the step time given."""
+    s_ = ms_per_step * 1e-3
+    return {"candidate_tests_per_s": cand / s_, "in_range_pairs_per_s": pairs / s_,
+            "candidates_per_agent": cand / max(n, 1), "in_range_per_agent": pairs / max(n, 1),
+            "counted": "at the last timed step's positions; pairs closer than the view radius "
+                       "(float64)"}
 
 
 def run_tag(F, torch, dev, stream, steps, warmup, flush, n=17600, seed=0, world=1):
@@ -534,10 +578,12 @@ def run_tag(F, torch, dev, stream, steps, warmup, flush, n=17600, seed=0, world=
     torch.cuda.synchronize()
     assert env.error() == 0
     tun = env.tuning()
+    cand, pairs = pair_counts(p, env.state().cpu().numpy(), tun["stencil"])
     env.close()
     ms = [ev0[k].elapsed_time(ev1[k]) for k in range(steps)]
     tot = max_over_ranks(sum(ms), dev)
     return {"value": weak_scaling_value(world, n, steps, tot), "unit": UNIT, "agents": n,
+            "pairs": pair_rates(cand, pairs, n, tot / steps),
             "chasers": int(round(0.1 * n)), "ms_per_step": tot / steps,
             "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
             "tuning": tun,
@@ -771,13 +817,13 @@ def main():
                    "actions read in place over NVLink-C2C, the outputs copied out by one "
                    "kernel; synchronous)"}
 
-    batched = single_fused = None
+    batched = batch_of_one = None
     if not args.no_batched:
         batched = run_batched(F, torch, dev, stream, args.steps, args.warmup, flush,
                               seed=rank_seed(rank), world=world,
                               tuning=json.loads(args.batch_tuning) if args.batch_tuning else None)
         # the same 50,000-agent instance as the headline, as a batch of one
-        single_fused = run_batched(F, torch, dev, stream, args.steps, args.warmup, flush,
+        batch_of_one = run_batched(F, torch, dev, stream, args.steps, args.warmup, flush,
                                    seed=rank_seed(rank), sizes=[n], world=world, tune=False)
         # like for like with the headline: its agents as ten 5,000-agent instances
         ten = run_batched(F, torch, dev, stream, args.steps, args.warmup, flush,
@@ -846,7 +892,7 @@ def main():
         }
         if batched is not None:
             line["batched"] = batched
-            line["single_instance_persistent"] = single_fused
+            line["batch_of_one"] = batch_of_one
             line["batched_10_instances"] = ten
         line["plain_small"] = small
         if policy is not None:
@@ -856,6 +902,10 @@ def main():
             line["rollout"] = rollout
             line["tag"] = tag
         if serving is not None:
+            if batched is not None:
+                # saturated serving against the bare batched form (per agent-step)
+                sat = serving["saturated_small_budget"]
+                sat["vs_batched_form"] = sat["agent_steps_per_s"] / batched["value"]
             line["serving"] = serving
 
         if not args.no_cpu_baseline and world == 1:
