@@ -91,6 +91,19 @@ __device__ __forceinline__ int find_inst(const int *pre, int n, int x) {
   return lo;
 }
 
+// Instance of each thread's agent f for a block whose agents start at f0:
+// one thread binary-searches f0's instance and the block shares it; each
+// thread then walks forward from there (a block's agents span few
+// instances).  pre[n] is the total.
+__device__ __forceinline__ int block_inst(const int *pre, int n, int f0, int f, int *sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) *sh = find_inst(pre, n, f0);
+  __syncthreads();
+  int k = *sh;
+  while (k + 1 < n && __ldg(pre + k + 1) <= f) ++k;
+  return k;
+}
+
 // SPLIT: phases A-C only; the neighbour scan runs as the next launch
 // (k_batch_neigh), where it has the registers of a kernel of its own.
 template <int H, int V, bool SPLIT>
@@ -198,18 +211,26 @@ done:
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_bbin_apply(const BatchDev *__restrict__ d,
                                                     const Inst *__restrict__ insts,
-                                                    const int *__restrict__ apre, unsigned *ctr) {
+                                                    const int *__restrict__ apre, unsigned *ctr,
+                                                    float2 *bxy) {
   const BatchDev D = *d;
   const Bufs &B = D.B;
   // the chunk ticket of this step's neighbour launch (the previous step's
   // launch has finished: this kernel starts after it in stream order)
   if (blockIdx.x == 0 && threadIdx.x == 0) ctr[kCtrTicket] = 0;
+  __shared__ int k0;
   unsigned err = 0;
-  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < D.n_total; f += gridDim.x * blockDim.x) {
-    const int k = find_inst(apre, D.n_inst, f);
-    const Inst &I = insts[k];
-    phaseA_agent(I, f - I.agent_base, B.actions + I.agent_base, nullptr, I.reset, B.counts,
-                 B.cellrank, err);
+  const int stride = gridDim.x * blockDim.x;
+  for (int f0 = blockIdx.x * blockDim.x; f0 < D.n_total; f0 += stride) {
+    const int f = f0 + threadIdx.x;
+    const int k = block_inst(apre, D.n_inst, f0, f, &k0);
+    if (f < D.n_total) {
+      const Inst &I = insts[k];
+      const int i = f - I.agent_base;
+      const float4 st = phaseA_agent(I, i, B.actions + I.agent_base, nullptr, I.reset, B.counts,
+                                     B.cellrank, err);
+      bxy[f] = make_float2(st.x, st.y);  // the new position in agent order, for the scatter
+    }
   }
   if (err) atomicOr(B.err, err);
 }
@@ -221,10 +242,11 @@ __global__ void __launch_bounds__(256) k_bbin_scan(const BatchDev *__restrict__ 
   for (int t = blockIdx.x; t < D.n_scan_tiles; t += gridDim.x) phaseB_tile(t, D.B, sm);
 }
 
-// dynamic shared memory: (scan tiles + 1) ints of tile prefix
+// dynamic shared memory: (scan tiles + 1) ints of tile prefix.  Reads the
+// new positions in agent order from bxy (written by k_bbin_apply), so it
+// needs no instance lookup.
 __global__ void __launch_bounds__(256) k_bbin_scatter(const BatchDev *__restrict__ d,
-                                                      const Inst *__restrict__ insts,
-                                                      const int *__restrict__ apre) {
+                                                      const float2 *__restrict__ bxy) {
   extern __shared__ int tp[];
   __shared__ int wsum[33];
   pdl_wait();
@@ -233,9 +255,15 @@ __global__ void __launch_bounds__(256) k_bbin_scatter(const BatchDev *__restrict
   tile_prefix(B, tp, wsum);
   const int stride = gridDim.x * blockDim.x;
   for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < D.n_total; f += stride) {
-    const int k = find_inst(apre, D.n_inst, f);
-    const Inst &I = insts[k];
-    phaseC_agent(f, I.state + (f - I.agent_base), B, tp);
+    const int2 cr = B.cellrank[f];
+    if (!dbg_ok(cr.x >= 0 && cr.x < B.c_total && cr.y >= 0)) continue;
+    const int pos = tp[cr.x / kScanTile] + B.local[cr.x] + cr.y;
+    if ((unsigned)pos >= (unsigned)B.n_total) {  // inconsistent counts: never write out of range
+      atomicOr(B.err, FLOCK_ERR_STATE);
+      continue;
+    }
+    B.sxy[pos] = bxy[f];
+    B.sidx[pos] = f;
   }
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= D.c_total; c += stride)
     phaseC_cell(c, B, tp);
@@ -331,7 +359,7 @@ namespace {
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct BLayout {
-  size_t dev, insts, apre, cpre, ctr, err, cellrank, counts, local, cell_start, tile_sum, sxy,
+  size_t dev, insts, apre, cpre, ctr, err, cellrank, bxy, counts, local, cell_start, tile_sum, sxy,
       sidx, total;
 };
 
@@ -353,6 +381,7 @@ BLayout batch_layout(int mi, int ma, int mc) {
   L.tile_sum = take((size_t)(nT + 1) * 4);
   L.sxy = take((size_t)ma * 8);
   L.sidx = take((size_t)ma * 4);
+  L.bxy = take((size_t)ma * 8);  // mode 4: new positions in agent order
   L.total = o;
   return L;
 }
@@ -624,10 +653,12 @@ static int batch_enqueue(flock_batch *b, cudaStream_t s, int k) {
   if (b->kbin) {
     NvtxRange r("flock:batch_binning");
     const int max_tiles = (b->max_cells + kScanTile - 1) / kScanTile;
-    BCK(launch(false, k_bbin_apply, b->bin_grid, 256, 0, s, dv, (const Inst *)ins, apre, ctr));
+    float2 *bxy = (float2 *)(b->ws + L.bxy);
+    BCK(launch(false, k_bbin_apply, b->bin_grid, 256, 0, s, dv, (const Inst *)ins, apre, ctr,
+               bxy));
     BCK(launch(true, k_bbin_scan, b->scan_grid, 256, 0, s, dv));
     BCK(launch(true, k_bbin_scatter, b->scatter_grid, 256, (size_t)(max_tiles + 1) * 4, s, dv,
-               (const Inst *)ins, apre));
+               (const float2 *)bxy));
   } else {
     const int rc = batch_enqueue_persistent(b, s, dv);
     if (rc) return rc;

@@ -363,9 +363,10 @@ __device__ __forceinline__ int warp_count(int *counts, int g) {
 // ---------------------------------------------------------------------------
 // actions_inst / cactions_inst: the instance's discrete actions, or (when
 // cactions_inst is not null) its continuous ones.
-__device__ __forceinline__ void phaseA_agent(const Inst &I, int i, const int32_t *actions_inst,
-                                             const float2 *cactions_inst, int reset, int *counts,
-                                             int2 *cellrank, unsigned &err) {
+// Returns the agent's new state.
+__device__ __forceinline__ float4 phaseA_agent(const Inst &I, int i, const int32_t *actions_inst,
+                                               const float2 *cactions_inst, int reset,
+                                               int *counts, int2 *cellrank, unsigned &err) {
   float4 st = I.state[i];
   if (!state_ok(st, I)) err |= FLOCK_ERR_STATE;
   if (!reset) {
@@ -375,8 +376,9 @@ __device__ __forceinline__ void phaseA_agent(const Inst &I, int i, const int32_t
     I.state[i] = st;
   }
   const int g = I.cell_base + lrow(I, cell_of(st.y, I)) * I.nc + cell_of(st.x, I);
-  if (!dbg_ok(g >= I.cell_base && g < I.cell_base + I.ncells)) return;
+  if (!dbg_ok(g >= I.cell_base && g < I.cell_base + I.ncells)) return st;
   cellrank[I.agent_base + i] = make_int2(g, warp_count(counts, g));
+  return st;
 }
 
 // ---------------------------------------------------------------------------
