@@ -116,8 +116,9 @@ typedef struct flock_tuning {
   int lanes;   /* mode 2: lanes per agent, 1, 2, 4 or 32 (0: 32 when an agent
                   has 256 or more candidates in its stencil cells on average,
                   else 4 up to 32,768 agents, 2 up to 524,288, else 1); the
-                  lanes of an agent share its candidates.  Mode 1 and the
-                  policy step use 1. */
+                  lanes of an agent share its candidates.  Mode 1 uses 1.
+                  Batch, modes 3 and 4: 1, 2 or 4 for the neighbour launch (0:
+                  by the batch's maximum agent count, as above); mode 2: 1. */
 } flock_tuning;
 
 /* Constants the library derives from flock_params (host, double precision

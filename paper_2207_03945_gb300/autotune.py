@@ -30,7 +30,8 @@ CANDIDATES = (
 BATCH_CANDIDATES = tuple(
     [{"stencil": st, "mode": 2} for st in (1, 2)] +
     [{"stencil": st, "mode": m, "block": blk} for st in (1, 2) for m in (3, 4)
-     for blk in (64, 128, 256)])
+     for blk in (64, 128, 256)] +
+    [{"stencil": 1, "mode": 4, "block": 128, "lanes": ln} for ln in (1, 2, 4)])
 
 
 def _hold(torch):

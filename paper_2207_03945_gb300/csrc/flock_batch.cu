@@ -275,10 +275,13 @@ __global__ void __launch_bounds__(256) k_bbin_scatter(const BatchDev *__restrict
 // binning ends) and keeps its copy of the instance descriptor while
 // consecutive chunks stay in one instance.  A step whose binning launch gave
 // up at a grid barrier (FLOCK_ERR_TIMEOUT latched) is left unobserved.
-template <int H, int V>
+// LPA lanes per agent: a chunk is 32 / LPA agents (more lanes keep more warps
+// busy when the batch holds few agents).
+template <int H, int V, int LPA>
 __global__ void __launch_bounds__(256) k_batch_neigh(const BatchDev *__restrict__ d,
                                                      Inst *insts, const int *cpre,
                                                      unsigned *ctr) {
+  constexpr int A = 32 / LPA;
   extern __shared__ __align__(16) char smem[];
   pdl_wait();
   const BatchDev D = *d;
@@ -286,9 +289,9 @@ __global__ void __launch_bounds__(256) k_batch_neigh(const BatchDev *__restrict_
   if (ld_acquire(B.err) & FLOCK_ERR_TIMEOUT) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int v = V == 8 ? 8 : insts[0].v;
-  char *wbase = smem + (size_t)warp * (sizeof(Inst) + direct_warp_bytes(v));
+  char *wbase = smem + (size_t)warp * (sizeof(Inst) + direct_warp_bytes(v, A));
   Inst &sI = *reinterpret_cast<Inst *>(wbase);
-  const DirectArea W = direct_area(wbase + sizeof(Inst), v);
+  const DirectArea W = direct_area(wbase + sizeof(Inst), v, A);
   unsigned err = 0;
   int cur = -1;
   for (;;) {
@@ -304,16 +307,16 @@ __global__ void __launch_bounds__(256) k_batch_neigh(const BatchDev *__restrict_
       __syncwarp();
       cur = k;
     }
-    const int gp0 = sI.agent_base + (c - cpre[k]) * 32;
-    const int gp1 = min(gp0 + 32, sI.agent_base + sI.n);
-    phaseD_direct<H, V, true, 1, false, true>(sI, gp0, gp1, B, W, err);
+    const int gp0 = sI.agent_base + (c - cpre[k]) * A;
+    const int gp1 = min(gp0 + A, sI.agent_base + sI.n);
+    phaseD_direct<H, V, true, LPA, false, true>(sI, gp0, gp1, B, W, err);
     if (sI.reset && gp0 == sI.agent_base && lane == 0) insts[k].reset = 0;
   }
   if (err) atomicOr(B.err, err);
 }
 
-static size_t neigh_smem(int v, int block) {
-  return (size_t)(block / 32) * (sizeof(Inst) + direct_warp_bytes(v));
+static size_t neigh_smem(int v, int block, int lanes) {
+  return (size_t)(block / 32) * (sizeof(Inst) + direct_warp_bytes(v, 32 / lanes));
 }
 
 // Dynamic shared memory of the persistent kernel: the scan tile or the prefix
@@ -344,10 +347,14 @@ static KFn batch_kernel(int halo, int v, int layout, bool split) {
   return v8 ? k_batch_step<2, 8, false> : k_batch_step<2, 0, false>;
 }
 
-static NFn neigh_kernel(int halo, int v, int layout) {
+static NFn neigh_kernel(int halo, int v, int layout, int lanes) {
   const bool v8 = v == 8 && layout == 0;
-  if (halo == 1) return v8 ? k_batch_neigh<1, 8> : k_batch_neigh<1, 0>;
-  return v8 ? k_batch_neigh<2, 8> : k_batch_neigh<2, 0>;
+  static const NFn t[2][2][3] = {
+      {{k_batch_neigh<1, 0, 1>, k_batch_neigh<1, 0, 2>, k_batch_neigh<1, 0, 4>},
+       {k_batch_neigh<1, 8, 1>, k_batch_neigh<1, 8, 2>, k_batch_neigh<1, 8, 4>}},
+      {{k_batch_neigh<2, 0, 1>, k_batch_neigh<2, 0, 2>, k_batch_neigh<2, 0, 4>},
+       {k_batch_neigh<2, 8, 1>, k_batch_neigh<2, 8, 2>, k_batch_neigh<2, 8, 4>}}};
+  return t[halo - 1][v8 ? 1 : 0][lanes == 1 ? 0 : (lanes == 2 ? 1 : 2)];
 }
 
 }  // namespace flock
@@ -401,6 +408,7 @@ struct flock_batch {
   bool split;      // the neighbour scan is a launch of its own (modes 3, 4)
   bool kbin;       // binning by three kernels (mode 4)
   int nblock;      // threads per block of the neighbour launch
+  int lanes;       // lanes per agent of the neighbour launch (chunks of 32 / lanes agents)
   int neigh_grid;  // blocks of the split form's neighbour launch (all resident)
   int bin_grid, scan_grid, scatter_grid;  // mode 4 binning kernels (grid-stride)
   unsigned spin_limit;
@@ -481,8 +489,17 @@ extern "C" int env_batch_create(int mi, int ma, int mc, const flock_tuning *t, v
     delete b;
     return FLOCK_EINVAL;
   }
+  // lanes per agent (the separate neighbour launch): as for one environment,
+  // by the most agents the batch holds; the one-launch form takes one
+  b->lanes = !b->split ? 1 : (b->tuning.lanes ? b->tuning.lanes
+                                               : (ma <= 32768 ? 4 : (ma <= 524288 ? 2 : 1)));
+  if (b->lanes != 1 && b->lanes != 2 && b->lanes != 4) {
+    delete b;
+    return FLOCK_EINVAL;
+  }
   b->tuning.mode = b->mode;
   b->tuning.block = b->nblock;
+  b->tuning.lanes = b->lanes;
   b->lay = batch_layout(mi, ma, mc);
   if (!ws || ((uintptr_t)ws & 255) || ws_bytes < b->lay.total) { delete b; return FLOCK_ENOSPACE; }
   b->ws = (char *)ws;
@@ -571,7 +588,7 @@ extern "C" int env_batch_set(flock_batch *b, int n_inst, const flock_params *par
     cpre[k] = (int)nchunk;
     na += I.n;
     ncell += I.ncells;
-    nchunk += (I.n + 31) / 32;
+    nchunk += (I.n + 32 / b->lanes - 1) / (32 / b->lanes);
     if (na > b->max_agents || ncell > b->max_cells) return FLOCK_EINVAL;
   }
   apre[n_inst] = (int)na;
@@ -592,8 +609,8 @@ extern "C" int env_batch_set(flock_batch *b, int n_inst, const flock_params *par
       b->grid = b->bin_grid;
     }
     if (b->split) {
-      NFn nf = neigh_kernel(b->halo, v, layout);
-      const size_t nsm = neigh_smem(v, b->nblock);
+      NFn nf = neigh_kernel(b->halo, v, layout, b->lanes);
+      const size_t nsm = neigh_smem(v, b->nblock, b->lanes);
       int pn = 0;
       BCK(cudaFuncSetAttribute(nf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsm));
       BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pn, nf, b->nblock, nsm));
@@ -665,8 +682,8 @@ static int batch_enqueue(flock_batch *b, cudaStream_t s, int k) {
   }
   if (b->split) {
     NvtxRange r("flock:batch_neighbours");
-    BCK(launch(b->kbin, neigh_kernel(b->halo, b->v, b->layout), b->neigh_grid,
-               b->nblock, neigh_smem(b->v, b->nblock), s, dv, ins, cpre, ctr));
+    BCK(launch(b->kbin, neigh_kernel(b->halo, b->v, b->layout, b->lanes), b->neigh_grid,
+               b->nblock, neigh_smem(b->v, b->nblock, b->lanes), s, dv, ins, cpre, ctr));
   }
   if (b->timing) BCK(cudaEventRecordWithFlags(b->ev[1], s, cudaEventRecordExternal));
   return FLOCK_OK;

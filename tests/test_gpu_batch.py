@@ -251,7 +251,9 @@ def test_benchmark_mix_sampled_rows(mode):
 
 @pytest.mark.parametrize("tuning", [{"mode": 3, "block": 64}, {"mode": 3, "block": 256},
                                     {"mode": 4, "block": 64}, {"mode": 4, "block": 256},
-                                    {"mode": 4, "stencil": 2, "block": 128}],
+                                    {"mode": 4, "stencil": 2, "block": 128},
+                                    {"mode": 4, "lanes": 1}, {"mode": 4, "lanes": 2},
+                                    {"mode": 3, "lanes": 4, "stencil": 2}],
                          ids=lambda d: "-".join("%s%s" % kv for kv in d.items()))
 def test_neighbour_launch_block_sizes(tuning):
     """Every block size of the separate neighbour launch (the autotuner's
