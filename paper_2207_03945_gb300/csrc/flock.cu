@@ -28,6 +28,8 @@ __global__ void __launch_bounds__(256) k_apply_bin(const Inst *__restrict__ gI, 
     phaseA_agent(sI, i, B.actions + sI.agent_base, B.cactions ? B.cactions + sI.agent_base : nullptr,
                  reset, B.counts, B.cellrank, err);
   if (err) atomicOr(B.err, err);
+  // the policy step: the network's operand image, read four kernels later
+  if (B.wimg) policy_image(B.wblob, B.wimg, i, gridDim.x * blockDim.x);
 }
 
 __global__ void __launch_bounds__(256) k_scan(Bufs B) {
@@ -87,67 +89,66 @@ __global__ void k_neighbours_direct(const Inst *__restrict__ gI, Bufs B) {
 // the step's observations: the neighbour scan leaves each agent's
 // observation as a BF16 row in the workspace (48 bytes, resident in L2), and
 // this kernel runs the network on the tensor cores (mma.sync m16n8k16, FP32
-// accumulate), 32 agents per warp, and writes the greedy actions (largest
-// logit, lowest index on ties) and optionally the logits.  The weights are
-// staged in shared memory once per block; blocks walk the agents with a
-// grid-stride loop.  (A fused form that ran the network in the neighbour
-// scan's epilogue held 94 registers and 46 KB of shared memory per block,
-// and took 1.67 times the plain step at 100,000 agents.)
+// accumulate), one m-tile of 16 agents per warp and pass, and writes the
+// greedy actions (largest logit, lowest index on ties) and optionally the
+// logits.  Each lane loads its operand fragments itself, the weights from
+// the operand image (31 coalesced 16-byte loads per m-tile, L1-resident; no
+// shared memory, no block barrier); warps walk the agents with a
+// grid-stride loop.  (A fused form that ran the
+// network in the neighbour scan's epilogue held 94 registers and 46 KB of
+// shared memory per block, and took 1.67 times the plain step at 100,000
+// agents.)
 constexpr int kMlpBlock = 256;
+constexpr int kMlpBlocksPerSM = 3;  // at most 80 registers a thread: three blocks on each SM
 
-__global__ void __launch_bounds__(kMlpBlock) k_policy_mlp(const unsigned *__restrict__ pobs, int n,
-                                                          const unsigned short *__restrict__ wblob,
-                                                          int32_t *actions, float *logits) {
-  extern __shared__ __align__(16) char smem[];
-  load_policy(wblob, smem);  // the weights do not depend on the previous kernel
+__global__ void __launch_bounds__(kMlpBlock, kMlpBlocksPerSM)
+    k_policy_mlp(const unsigned *__restrict__ pobs, int n, const uint4 *__restrict__ wimg,
+                 int32_t *actions, float *logits) {
   pdl_wait();
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  PolicyCtx pc = policy_ctx(smem);
-  pc.tile = reinterpret_cast<unsigned short *>(smem + kPolicyBytes + (size_t)warp * kTileBytes);
-  pc.actions = actions;
-  pc.logits = logits;
-  unsigned *row = reinterpret_cast<unsigned *>(pc.tile + lane * kTileS);
-  const int stride = gridDim.x * (kMlpBlock / 32) * 32;
-  for (int base = (blockIdx.x * (kMlpBlock / 32) + warp) * 32; base < n; base += stride) {
-    const int nb = min(32, n - base);
-    // this lane's row: 9 words of values, the rest of the tile row zero
-    uint4 a = make_uint4(0u, 0u, 0u, 0u), b = a, c = a;
-    if (lane < nb) {
-      const uint4 *src = reinterpret_cast<const uint4 *>(pobs + (long long)(base + lane) * kPobsWords);
-      a = src[0];
-      b = src[1];
-      c = src[2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const uint4 *im = wimg + lane;
+  const int stride = gridDim.x * (kMlpBlock / 32) * 16;
+  // A-fragment words of rows g and g + 8 of 16 agents from `base`: BF16
+  // pairs t (columns 2t, 2t + 1), 4 + t (columns 8 + 2t, 9 + 2t) and, for
+  // t = 0, 8 (columns 16, 17); rows past the last agent are zero
+  auto fetch = [&](int base, unsigned (&f)[2][3]) {
+    const int nb = min(16, n - base);
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const int r = g + 8 * m;
+      const bool ok = r < nb;
+      const unsigned *src = pobs + (long long)(base + (ok ? r : 0)) * kPobsWords;
+      f[m][0] = ok ? __ldg(src + t) : 0u;
+      f[m][1] = ok ? __ldg(src + 4 + t) : 0u;
+      f[m][2] = ok && t == 0 ? __ldg(src + 8) : 0u;
     }
-    row[0] = a.x; row[1] = a.y; row[2] = a.z; row[3] = a.w;
-    row[4] = b.x; row[5] = b.y; row[6] = b.z; row[7] = b.w;
-    row[8] = c.x;
+  };
+  int base = (blockIdx.x * (kMlpBlock / 32) + warp) * 16;
+  unsigned f[2][3] = {{0u, 0u, 0u}, {0u, 0u, 0u}};
+  if (base < n) fetch(base, f);
+  for (; base < n; base += stride) {
+    const int nb = min(16, n - base);
+    const unsigned a0[4] = {f[0][0], f[1][0], f[0][1], f[1][1]};
+    const unsigned a1[4] = {f[0][2], f[1][2], 0u, 0u};
+    if ((long long)base + stride < n) fetch(base + stride, f);  // the next rows, in flight meanwhile
+    int alo = 0, ahi = 0;
+    float lg[2][4];
+    policy_mtile(im, a0, a1, alo, ahi, lg);
+    const int rlo = g, rhi = g + 8;
+    if (t == 0) {
+      if (rlo < nb) actions[base + rlo] = alo;
+      if (rhi < nb) actions[base + rhi] = ahi;
+    }
+    if (logits) {
+      const int c4[4] = {2 * t, 2 * t + 1, 8 + 2 * t, 9 + 2 * t};
 #pragma unroll
-    for (int w2 = 9; w2 < kTileS / 2; ++w2) row[w2] = 0u;
-    __syncwarp();
-    const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      int alo = 0, ahi = 0;
-      float lg[2][4];
-      policy_mtile(pc, 16 * mt, alo, ahi, lg);
-      const int rlo = 16 * mt + g, rhi = rlo + 8;
-      if (t == 0) {
-        if (rlo < nb) actions[base + rlo] = alo;
-        if (rhi < nb) actions[base + rhi] = ahi;
-      }
-      if (logits) {
-        const int c4[4] = {2 * t, 2 * t + 1, 8 + 2 * t, 9 + 2 * t};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (c4[j] < 9) {
-            if (rlo < nb) logits[(long long)(base + rlo) * 9 + c4[j]] = lg[0][j];
-            if (rhi < nb) logits[(long long)(base + rhi) * 9 + c4[j]] = lg[1][j];
-          }
+      for (int j = 0; j < 4; ++j) {
+        if (c4[j] < 9) {
+          if (rlo < nb) logits[(long long)(base + rlo) * 9 + c4[j]] = lg[0][j];
+          if (rhi < nb) logits[(long long)(base + rhi) * 9 + c4[j]] = lg[1][j];
         }
       }
     }
-    __syncwarp();
   }
 }
 
@@ -390,8 +391,7 @@ cudaError_t set_kernel_attrs() {
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int want = maxsm - (int)sizeof(Inst) - 1024;
-    const void *fns[] = {(const void *)k_policy_mlp,
-                         (const void *)k_neighbours<1>, (const void *)k_neighbours<2>,
+    const void *fns[] = {(const void *)k_neighbours<1>, (const void *)k_neighbours<2>,
                          (const void *)k_neighbours_direct<1, 0, 1>,
                          (const void *)k_neighbours_direct<2, 0, 1>,
                          (const void *)k_neighbours_direct<1, 8, 1>,
@@ -429,7 +429,7 @@ using namespace flock;
 
 struct Layout {
   size_t state, cellrank, counts, local, cell_start, tile_sum, sxy, sidx, types, stype, inst,
-      err, h_act, h_obs, h_rew, h_coll, pobs, total;
+      err, h_act, h_obs, h_rew, h_coll, pobs, wimg, total;
 };
 
 static Layout make_layout(int n, int C, int D) {
@@ -454,6 +454,7 @@ static Layout make_layout(int n, int C, int D) {
   L.h_rew = take((size_t)n * 4);
   L.h_coll = take((size_t)n * 4);
   L.pobs = take((size_t)n * kPobsWords * 4);  // policy step: BF16 observation rows
+  L.wimg = take(kImgBytes);                    // policy step: the weights' operand image
   L.total = o;
   return L;
 }
@@ -607,7 +608,7 @@ static int create_env(const flock_params *p, const flock_tuning *t, int n, int r
   // 16-byte units of the outputs, one per thread, at most 8 blocks per SM
   const size_t units = ((size_t)n * e->inst.obs_dim * 4 + (size_t)n * 8) / 16;
   e->copy_grid = (int)std::max<size_t>(1, std::min<size_t>((units + 255) / 256, (size_t)sms * 8));
-  e->mlp_grid = sms * 2;  // each block stages the weights once, then walks many agents
+  e->mlp_grid = sms * kMlpBlocksPerSM;  // one resident wave
   e->smemD = e->tuning.mode == 1
                  ? phaseD_smem_bytes(e->inst.cap, e->inst.v, e->tuning.block)
                  : (size_t)(e->tuning.block / 32) *
@@ -650,7 +651,8 @@ extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, v
 // environment's n); the descriptor in the workspace must say the same.
 static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const float2 *cact,
                         float *obs, float *rew, int32_t *coll, int reset,
-                        unsigned *pobs = nullptr, int n_run = -1) {
+                        unsigned *pobs = nullptr, int n_run = -1,
+                        const unsigned short *wblob = nullptr) {
   Bufs B = e->bufs;
   B.actions = act;
   B.cactions = cact;
@@ -658,6 +660,8 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const 
   B.reward = rew;
   B.coll = coll;
   B.pobs = pobs;
+  B.wblob = wblob;
+  B.wimg = wblob ? (uint4 *)(e->ws + e->lay.wimg) : nullptr;
   const Inst *gI = (const Inst *)(e->ws + e->lay.inst);
   const int n = n_run >= 0 ? n_run : e->n;
   B.n_total = n;
@@ -721,22 +725,22 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const 
   return FLOCK_OK;
 }
 
-// The policy step: the step's four kernels, the neighbour scan also writing
-// BF16 observation rows into the workspace, then the network.
+// The policy step: the step's four kernels (the binning kernel also writing
+// the weights' operand image, the neighbour scan also BF16 observation rows
+// into the workspace), then the network.
 static int enqueue_policy_step(flock_env *e, cudaStream_t s, const unsigned short *w,
                                int32_t *act, float *rew, int32_t *coll, float *logits,
                                float *obs) {
   unsigned *pobs = (unsigned *)(e->ws + e->lay.pobs);
-  int rc = enqueue_step(e, s, act, nullptr, obs, rew, coll, 0, pobs);
+  int rc = enqueue_step(e, s, act, nullptr, obs, rew, coll, 0, pobs, -1, w);
   if (rc) return rc;
   const int n = e->n;
   if (n > 0) {
     NvtxRange r("flock:policy_mlp");
-    const size_t smem = kPolicyBytes + (size_t)(kMlpBlock / 32) * kTileBytes;
-    int blocks = (n + kMlpBlock - 1) / kMlpBlock;
+    int blocks = (n + kMlpBlock / 2 - 1) / (kMlpBlock / 2);  // 16 agents a warp
     blocks = blocks < e->mlp_grid ? blocks : e->mlp_grid;
-    CK(launch(true, k_policy_mlp, blocks, kMlpBlock, smem, s, (const unsigned *)pobs, n, w, act,
-              logits));
+    CK(launch(true, k_policy_mlp, blocks, kMlpBlock, 0, s, (const unsigned *)pobs, n,
+              (const uint4 *)(e->ws + e->lay.wimg), act, logits));
   }
   return FLOCK_OK;
 }

@@ -78,6 +78,8 @@ struct Bufs {
   float *reward;
   int32_t *coll;
   unsigned *pobs;  // policy step: BF16 observation rows (kPobsWords per agent, agent order), or null
+  const unsigned short *wblob;  // policy step: the weight blob, whose operand image the
+  uint4 *wimg;                  // binning kernel writes to wimg (both null otherwise)
   int n_total, c_total, n_scan_tiles, pad;
 };
 
@@ -1236,76 +1238,81 @@ __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, c
 // observation), run by k_policy_mlp on the BF16 observation rows the
 // neighbour scan leaves in the workspace.  BF16 operands on the tensor cores
 // (mma.sync m16n8k16), FP32 accumulate; the greedy action (largest logit,
-// lowest index on ties) is written back.  A warp holds its 32 agents'
-// observations as a BF16 tile [32][kTileS]; each layer's accumulators,
-// passed through tanh and rounded to BF16, are the next layer's A fragments
-// without leaving the registers.
+// lowest index on ties) is written back.  The weights reach the lanes as an
+// operand image built from the blob at the start of the step (see
+// policy_image); each layer's accumulators, rounded to BF16 pairs and passed
+// through the hardware BF16 tanh, are the next layer's A fragments without
+// leaving the registers.
 // ---------------------------------------------------------------------------
-constexpr int kW1S = 40, kW2S = 72, kW3S = 72, kTileS = 40;  // padded row strides (bf16)
-constexpr size_t kPolicyBytes = (size_t)(64 * kW1S + 64 * kW2S + 16 * kW3S) * 2 + (64 + 64 + 16) * 4;
-constexpr size_t kTileBytes = (size_t)32 * kTileS * 2;
-static_assert(kPolicyBytes % 16 == 0 && kTileBytes % 16 == 0, "policy smem alignment");
 // offsets in the 5,961-value BF16 blob: W1[64][18] b1[64] W2[64][64] b2[64] W3[9][64] b3[9]
 constexpr int kOffB1 = 64 * 18, kOffW2 = kOffB1 + 64, kOffB2 = kOffW2 + 64 * 64,
               kOffW3 = kOffB2 + 64, kOffB3 = kOffW3 + 9 * 64, kBlobLen = kOffB3 + 9;
+static_assert(kOffB1 % 2 == 0 && kOffW2 % 2 == 0 && kOffB2 % 2 == 0 && kOffW3 % 2 == 0 &&
+                  kOffB3 % 2 == 0,
+              "every matrix and bias of the blob starts on a BF16 pair");
 
-struct PolicyCtx {
-  const unsigned short *W1, *W2, *W3;  // shared memory, bf16 bits, padded rows
-  const float *b1, *b2, *b3;
-  unsigned short *tile;                 // this warp's observation tile
-  int32_t *actions;                     // greedy actions out (agent rows)
-  float *logits;                        // optional: logits out, 9 per agent
-};
+// Operand image: for lane (g, t) = (lane / 4, lane % 4) the 124 words it
+// feeds the forward pass, in the order of use, as 31 uint4 stored
+// lane-interleaved (vector j of lane l at j * 32 + l: a warp-wide load is 512
+// contiguous bytes).  Word ranges per lane:
+//   [0, 24)    layer 1, n-tile nt = s / 3: the B pairs W1[8nt+g][2t, 2t+1],
+//              W1[8nt+g][2t+8, 2t+9] and (t = 0 only) W1[8nt+g][16, 17]
+//   [24, 32)   b1 pair (8nt + 2t, 8nt + 2t + 1) for nt = s - 24
+//   [32, 96)   layer 2, q = s - 32: k-step q / 16, n-tile (q / 2) % 8, the
+//              pair at column offset 8 (q % 2)
+//   [96, 104)  b2 pairs
+//   [104, 120) layer 3, q = s - 104: k-step q / 4, n-tile (q / 2) % 2, pair
+//              q % 2; rows 9-15 of W3 are zero
+//   [120, 124) b3: columns (2t, 2t + 1); (t = 0) column 8 in the low half; 0, 0
+constexpr int kImgWords = 124, kImgVecs = kImgWords / 4;
+constexpr int kImgB1 = 24, kImgL2 = 32, kImgB2 = 96, kImgL3 = 104, kImgB3 = 120;
+constexpr size_t kImgBytes = (size_t)kImgVecs * 32 * 16;
 
-__device__ __forceinline__ float bf16_bits_to_float(unsigned short b) {
-  return __uint_as_float((unsigned)b << 16);
+__device__ __forceinline__ unsigned blob_pair(const unsigned short *__restrict__ blob, int e) {
+  return *reinterpret_cast<const unsigned *>(blob + e);  // e even, blob 4-byte aligned
 }
 
-// Block-cooperative load of the blob into the padded shared layout (call,
-// then __syncthreads).  Padding columns and rows are zero.  Every matrix of
-// the blob starts at an even BF16 offset and has an even row length (18 or
-// 64), so the copy moves BF16 pairs (the blob is 4-byte aligned).
-__device__ __forceinline__ void load_policy(const unsigned short *__restrict__ blob, char *base) {
-  const unsigned *bw = reinterpret_cast<const unsigned *>(blob);
-  unsigned *W1 = reinterpret_cast<unsigned *>(base);  // [64][kW1S / 2]
-  unsigned *W2 = W1 + 64 * (kW1S / 2);                 // [64][kW2S / 2]
-  unsigned *W3 = W2 + 64 * (kW2S / 2);                 // [16][kW3S / 2]
-  float *b1 = reinterpret_cast<float *>(W3 + 16 * (kW3S / 2));
-  float *b2 = b1 + 64, *b3 = b2 + 64;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < 64 * (kW1S / 2); e += nt) {
-    const int n = e / (kW1S / 2), k2 = e - n * (kW1S / 2);
-    W1[e] = k2 < 9 ? __ldg(bw + n * 9 + k2) : 0u;
+__device__ __forceinline__ unsigned image_word(const unsigned short *__restrict__ blob, int s, int g,
+                                               int t) {
+  if (s < kImgB1) {
+    const int nt = s / 3, r = s - 3 * nt, row = (8 * nt + g) * 18;
+    if (r == 0) return blob_pair(blob, row + 2 * t);
+    if (r == 1) return blob_pair(blob, row + 2 * t + 8);
+    return t == 0 ? blob_pair(blob, row + 16) : 0u;
   }
-  for (int e = tid; e < 64 * (kW2S / 2); e += nt) {
-    const int n = e / (kW2S / 2), k2 = e - n * (kW2S / 2);
-    W2[e] = k2 < 32 ? __ldg(bw + kOffW2 / 2 + n * 32 + k2) : 0u;
+  if (s < kImgL2) return blob_pair(blob, kOffB1 + 8 * (s - kImgB1) + 2 * t);
+  if (s < kImgB2) {
+    const int q = s - kImgL2, kk = q >> 4, nt = (q >> 1) & 7, r = q & 1;
+    return blob_pair(blob, kOffW2 + (8 * nt + g) * 64 + 16 * kk + 2 * t + 8 * r);
   }
-  for (int e = tid; e < 16 * (kW3S / 2); e += nt) {
-    const int n = e / (kW3S / 2), k2 = e - n * (kW3S / 2);
-    W3[e] = (n < 9 && k2 < 32) ? __ldg(bw + kOffW3 / 2 + n * 32 + k2) : 0u;
+  if (s < kImgL3) return blob_pair(blob, kOffB2 + 8 * (s - kImgB2) + 2 * t);
+  if (s < kImgB3) {
+    const int q = s - kImgL3, kk = q >> 2, nt = (q >> 1) & 1, r = q & 1, n = 8 * nt + g;
+    return n < 9 ? blob_pair(blob, kOffW3 + n * 64 + 16 * kk + 2 * t + 8 * r) : 0u;
   }
-  for (int e = tid; e < 64; e += nt) {
-    b1[e] = bf16_bits_to_float(blob[kOffB1 + e]);
-    b2[e] = bf16_bits_to_float(blob[kOffB2 + e]);
-  }
-  for (int e = tid; e < 16; e += nt) b3[e] = e < 9 ? bf16_bits_to_float(blob[kOffB3 + e]) : 0.0f;
+  if (s == kImgB3) return blob_pair(blob, kOffB3 + 2 * t);
+  if (s == kImgB3 + 1) return t == 0 ? (unsigned)blob[kOffB3 + 8] : 0u;
+  return 0u;
 }
 
-static_assert(kOffW2 % 2 == 0 && kOffW3 % 2 == 0, "policy matrices start on BF16 pairs");
+// Writes image vectors idx, idx + stride, ... (call with the grid's thread
+// index and size; kImgVecs * 32 vectors in all).
+__device__ __forceinline__ void policy_image(const unsigned short *__restrict__ blob, uint4 *img,
+                                             int idx, int stride) {
+  for (; idx < kImgVecs * 32; idx += stride) {
+    const int j = idx >> 5, l = idx & 31, g = l >> 2, t = l & 3;
+    img[idx] = make_uint4(image_word(blob, 4 * j, g, t), image_word(blob, 4 * j + 1, g, t),
+                          image_word(blob, 4 * j + 2, g, t), image_word(blob, 4 * j + 3, g, t));
+  }
+}
 
-__device__ __forceinline__ PolicyCtx policy_ctx(char *base) {
-  PolicyCtx P;
-  P.W1 = reinterpret_cast<const unsigned short *>(base);
-  P.W2 = P.W1 + 64 * kW1S;
-  P.W3 = P.W2 + 64 * kW2S;
-  P.b1 = reinterpret_cast<const float *>(P.W3 + 16 * kW3S);
-  P.b2 = P.b1 + 64;
-  P.b3 = P.b2 + 64;
-  P.tile = nullptr;
-  P.actions = nullptr;
-  P.logits = nullptr;
-  return P;
+__device__ __forceinline__ unsigned u4c(const uint4 &v, int c) {
+  return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+
+// The two FP32 values of a BF16 pair.
+__device__ __forceinline__ float2 bf16x2_float2(unsigned w) {
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
 }
 
 __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const unsigned (&a)[4], unsigned b0,
@@ -1317,89 +1324,98 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const unsigned (&a
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float tanh_fast(float x) {
-  float y;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 // round-to-nearest-even pair of floats to packed bf16 (lo in the low half)
 __device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const unsigned *>(&v);
 }
 
-__device__ __forceinline__ unsigned lds32(const unsigned short *p) {
-  return *reinterpret_cast<const unsigned *>(p);
+// tanh of a pair of pre-activations: rounded to a bf16 pair, then one
+// hardware approximation for both halves (half the special-function issue
+// of two FP32 tanh); the result is the next layer's packed BF16 operand.
+__device__ __forceinline__ unsigned tanh_pair_bf16(float lo, float hi) {
+  unsigned y;
+  asm("tanh.approx.bf16x2 %0, %1;" : "=r"(y) : "r"(pack_bf16(lo, hi)));
+  return y;
 }
 
-// Forward pass of one m-tile (16 rows, row0 = 0 or 16) of the warp's tile.
-// Returns, for this thread, the greedy action and the 4 logit columns it
-// holds for rows row0 + g and row0 + g + 8 (g = lane / 4).
-__device__ __forceinline__ void policy_mtile(const PolicyCtx &P, int row0, int &act_lo,
-                                             int &act_hi, float (&lg)[2][4]) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  // layer 1: [16 x 32] x W1^T -> [16 x 64]
+// Forward pass of one m-tile (16 agents).  im: this lane's first image
+// vector (vector j at im[32 j]).  a0: this lane's A fragment of observation
+// columns 0-15 (rows g and g + 8); a1: of columns 16-31, where only columns
+// 16 and 17 exist (held by the lanes with t = 0), the rest zero.  Returns,
+// for this lane, the greedy action and the 4 logit columns it holds for rows
+// g and g + 8.
+__device__ __forceinline__ void policy_mtile(const uint4 *__restrict__ im, const unsigned (&a0)[4],
+                                             const unsigned (&a1)[4], int &act_lo, int &act_hi,
+                                             float (&lg)[2][4]) {
+  const int lane = threadIdx.x & 31, t = lane & 3;
+  // layer 1: [16 x 18] x W1^T -> [16 x 64]
   float acc[8][4];
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    const float c0 = P.b1[8 * nt + 2 * t], c1 = P.b1[8 * nt + 2 * t + 1];
-    acc[nt][0] = c0; acc[nt][1] = c1; acc[nt][2] = c0; acc[nt][3] = c1;
-  }
-#pragma unroll
-  for (int kk = 0; kk < 2; ++kk) {
-    const unsigned short *r0 = P.tile + (row0 + g) * kTileS + 16 * kk + 2 * t;
-    const unsigned short *r1 = r0 + 8 * kTileS;
-    const unsigned a[4] = {lds32(r0), lds32(r1), lds32(r0 + 8), lds32(r1 + 8)};
+  {
+    const uint4 b0 = __ldg(im + 32 * 6), b1 = __ldg(im + 32 * 7);
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
-      const unsigned short *w = P.W1 + (8 * nt + g) * kW1S + 16 * kk + 2 * t;
-      mma_bf16_16816(acc[nt], a, lds32(w), lds32(w + 8));
+      const float2 c = bf16x2_float2(u4c(nt < 4 ? b0 : b1, nt & 3));
+      acc[nt][0] = c.x; acc[nt][1] = c.y; acc[nt][2] = c.x; acc[nt][3] = c.y;
+    }
+    uint4 w[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) w[j] = __ldg(im + 32 * j);
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const int s = 3 * nt;
+      mma_bf16_16816(acc[nt], a0, u4c(w[s / 4], s % 4), u4c(w[(s + 1) / 4], (s + 1) % 4));
+      mma_bf16_16816(acc[nt], a1, u4c(w[(s + 2) / 4], (s + 2) % 4), 0u);
     }
   }
   unsigned a2[4][4];
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {
-    a2[kk][0] = pack_bf16(tanh_fast(acc[2 * kk][0]), tanh_fast(acc[2 * kk][1]));
-    a2[kk][1] = pack_bf16(tanh_fast(acc[2 * kk][2]), tanh_fast(acc[2 * kk][3]));
-    a2[kk][2] = pack_bf16(tanh_fast(acc[2 * kk + 1][0]), tanh_fast(acc[2 * kk + 1][1]));
-    a2[kk][3] = pack_bf16(tanh_fast(acc[2 * kk + 1][2]), tanh_fast(acc[2 * kk + 1][3]));
+    a2[kk][0] = tanh_pair_bf16(acc[2 * kk][0], acc[2 * kk][1]);
+    a2[kk][1] = tanh_pair_bf16(acc[2 * kk][2], acc[2 * kk][3]);
+    a2[kk][2] = tanh_pair_bf16(acc[2 * kk + 1][0], acc[2 * kk + 1][1]);
+    a2[kk][3] = tanh_pair_bf16(acc[2 * kk + 1][2], acc[2 * kk + 1][3]);
   }
   // layer 2: [16 x 64] x W2^T -> [16 x 64]
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    const float c0 = P.b2[8 * nt + 2 * t], c1 = P.b2[8 * nt + 2 * t + 1];
-    acc[nt][0] = c0; acc[nt][1] = c1; acc[nt][2] = c0; acc[nt][3] = c1;
-  }
-#pragma unroll
-  for (int kk = 0; kk < 4; ++kk) {
+  {
+    const uint4 b0 = __ldg(im + 32 * 24), b1 = __ldg(im + 32 * 25);
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
-      const unsigned short *w = P.W2 + (8 * nt + g) * kW2S + 16 * kk + 2 * t;
-      mma_bf16_16816(acc[nt], a2[kk], lds32(w), lds32(w + 8));
+      const float2 c = bf16x2_float2(u4c(nt < 4 ? b0 : b1, nt & 3));
+      acc[nt][0] = c.x; acc[nt][1] = c.y; acc[nt][2] = c.x; acc[nt][3] = c.y;
     }
   }
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {
-    a2[kk][0] = pack_bf16(tanh_fast(acc[2 * kk][0]), tanh_fast(acc[2 * kk][1]));
-    a2[kk][1] = pack_bf16(tanh_fast(acc[2 * kk][2]), tanh_fast(acc[2 * kk][3]));
-    a2[kk][2] = pack_bf16(tanh_fast(acc[2 * kk + 1][0]), tanh_fast(acc[2 * kk + 1][1]));
-    a2[kk][3] = pack_bf16(tanh_fast(acc[2 * kk + 1][2]), tanh_fast(acc[2 * kk + 1][3]));
+    uint4 w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[j] = __ldg(im + 32 * (8 + 4 * kk + j));
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+      mma_bf16_16816(acc[nt], a2[kk], u4c(w[nt >> 1], 2 * (nt & 1)),
+                     u4c(w[nt >> 1], 2 * (nt & 1) + 1));
   }
-  // layer 3: [16 x 64] x W3^T -> [16 x 16] (9 logits + padding)
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    a2[kk][0] = tanh_pair_bf16(acc[2 * kk][0], acc[2 * kk][1]);
+    a2[kk][1] = tanh_pair_bf16(acc[2 * kk][2], acc[2 * kk][3]);
+    a2[kk][2] = tanh_pair_bf16(acc[2 * kk + 1][0], acc[2 * kk + 1][1]);
+    a2[kk][3] = tanh_pair_bf16(acc[2 * kk + 1][2], acc[2 * kk + 1][3]);
+  }
+  // layer 3: [16 x 64] x W3^T -> [16 x 16]: 9 logits (columns 9-15 zero)
   float o[2][4];
-#pragma unroll
-  for (int nt = 0; nt < 2; ++nt) {
-    const float c0 = P.b3[8 * nt + 2 * t], c1 = P.b3[8 * nt + 2 * t + 1];
-    o[nt][0] = c0; o[nt][1] = c1; o[nt][2] = c0; o[nt][3] = c1;
+  {
+    const uint4 bb = __ldg(im + 32 * 30);
+    const float2 c = bf16x2_float2(bb.x);  // columns 2t, 2t + 1
+    o[0][0] = c.x; o[0][1] = c.y; o[0][2] = c.x; o[0][3] = c.y;
+    const float2 c8 = bf16x2_float2(bb.y);  // column 8 (t = 0), else zero
+    o[1][0] = c8.x; o[1][1] = c8.y; o[1][2] = c8.x; o[1][3] = c8.y;
   }
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {
-#pragma unroll
-    for (int nt = 0; nt < 2; ++nt) {
-      const unsigned short *w = P.W3 + (8 * nt + g) * kW3S + 16 * kk + 2 * t;
-      mma_bf16_16816(o[nt], a2[kk], lds32(w), lds32(w + 8));
-    }
+    const uint4 w = __ldg(im + 32 * (26 + kk));
+    mma_bf16_16816(o[0], a2[kk], w.x, w.y);
+    mma_bf16_16816(o[1], a2[kk], w.z, w.w);
   }
   // greedy action per row: this thread holds columns 2t, 2t+1, 8+2t, 9+2t
 #pragma unroll
