@@ -271,22 +271,24 @@ __global__ void __launch_bounds__(256) k_bbin_scatter(const BatchDev *__restrict
 
 // Phase D of the split forms, a launch of its own (so the wide direct scan of
 // the standalone kernels has the registers it wants): every warp takes
-// chunks of 32 cell-sorted agents from the shared ticket (zero when the
-// binning ends) and keeps its copy of the instance descriptor while
-// consecutive chunks stay in one instance.  A step whose binning launch gave
-// up at a grid barrier (FLOCK_ERR_TIMEOUT latched) is left unobserved.
+// chunks of 32 / LPA cell-sorted agents, the first by its index in the grid
+// (no atomic round trip before it starts), the rest from a shared ticket
+// (zero when the binning ends; balances the load of a mix of instances),
+// and keeps its copy of the instance descriptor while its chunks stay in one
+// instance.  A step whose persistent binning launch (mode 3) gave up
+// at a grid barrier (FLOCK_ERR_TIMEOUT latched) is left unobserved.
 // LPA lanes per agent: a chunk is 32 / LPA agents (more lanes keep more warps
 // busy when the batch holds few agents).
 template <int H, int V, int LPA>
 __global__ void __launch_bounds__(256) k_batch_neigh(const BatchDev *__restrict__ d,
                                                      Inst *insts, const int *cpre,
-                                                     unsigned *ctr) {
+                                                     unsigned *ctr, int after_barriers) {
   constexpr int A = 32 / LPA;
   extern __shared__ __align__(16) char smem[];
   pdl_wait();
   const BatchDev D = *d;
   const Bufs &B = D.B;
-  if (ld_acquire(B.err) & FLOCK_ERR_TIMEOUT) return;
+  if (after_barriers && (ld_acquire(B.err) & FLOCK_ERR_TIMEOUT)) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int v = V == 8 ? 8 : insts[0].v;
   char *wbase = smem + (size_t)warp * (sizeof(Inst) + direct_warp_bytes(v, A));
@@ -294,11 +296,14 @@ __global__ void __launch_bounds__(256) k_batch_neigh(const BatchDev *__restrict_
   const DirectArea W = direct_area(wbase + sizeof(Inst), v, A);
   unsigned err = 0;
   int cur = -1;
-  for (;;) {
-    int c = 0;
-    if (lane == 0) c = (int)atomicAdd(&ctr[kCtrTicket], 1u);
-    c = __shfl_sync(kFull, c, 0);
-    if (c >= D.n_chunks) break;
+  // first chunk: the warp's index in the grid (a block's warps take
+  // consecutive chunks, no atomic before the first one); later chunks from
+  // the shared ticket, fetched while the current chunk is scanned
+  const int wpb = blockDim.x >> 5, nw = gridDim.x * wpb;
+  int c = blockIdx.x * wpb + warp;
+  while (c < D.n_chunks) {
+    int nxt = 0;
+    if (lane == 0) nxt = nw + (int)atomicAdd(&ctr[kCtrTicket], 1u);
     const int k = find_inst(cpre, D.n_inst, c);
     if (k != cur) {
       const int *src = reinterpret_cast<const int *>(insts + k);
@@ -311,6 +316,7 @@ __global__ void __launch_bounds__(256) k_batch_neigh(const BatchDev *__restrict_
     const int gp1 = min(gp0 + A, sI.agent_base + sI.n);
     phaseD_direct<H, V, true, LPA, false, true>(sI, gp0, gp1, B, W, err);
     if (sI.reset && gp0 == sI.agent_base && lane == 0) insts[k].reset = 0;
+    c = __shfl_sync(kFull, nxt, 0);
   }
   if (err) atomicOr(B.err, err);
 }
@@ -334,7 +340,7 @@ static size_t batch_smem(int v, bool split, int max_tiles) {
 }
 
 using KFn = void (*)(const BatchDev *, Inst *, const int *, const int *, unsigned *, unsigned);
-using NFn = void (*)(const BatchDev *, Inst *, const int *, unsigned *);
+using NFn = void (*)(const BatchDev *, Inst *, const int *, unsigned *, int);
 
 // The V = 8 kernels write observation layout 0 only.
 static KFn batch_kernel(int halo, int v, int layout, bool split) {
@@ -683,7 +689,8 @@ static int batch_enqueue(flock_batch *b, cudaStream_t s, int k) {
   if (b->split) {
     NvtxRange r("flock:batch_neighbours");
     BCK(launch(b->kbin, neigh_kernel(b->halo, b->v, b->layout, b->lanes), b->neigh_grid,
-               b->nblock, neigh_smem(b->v, b->nblock, b->lanes), s, dv, ins, cpre, ctr));
+               b->nblock, neigh_smem(b->v, b->nblock, b->lanes), s, dv, ins, cpre, ctr,
+               b->mode == 3 ? 1 : 0));
   }
   if (b->timing) BCK(cudaEventRecordWithFlags(b->ev[1], s, cudaEventRecordExternal));
   return FLOCK_OK;
