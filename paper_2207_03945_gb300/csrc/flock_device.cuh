@@ -464,14 +464,67 @@ __device__ __forceinline__ void tile_prefix(const Bufs &B, int *tp, int *wsum) {
   block_excl_scan_inplace(tp, B.n_scan_tiles, wsum);
 }
 
-// Phase C for one agent (flattened index f, local index i of instance I):
-// counting-sort scatter of its state into cell order.
-__device__ __forceinline__ void phaseC_agent(int f, const float4 *state_i, const Bufs &B,
-                                             const int *tp) {
-  const int2 cr = B.cellrank[f];
-  if (!dbg_ok(cr.x >= 0 && cr.x < B.c_total && cr.y >= 0)) return;
-  const float4 st = *state_i;
-  const int pos = tp[cr.x / kScanTile] + B.local[cr.x] + cr.y;
+// Whole-grid exclusive scan of the cell counts by one block (the fused
+// scan: the last block of the binning kernel, once every count is final):
+// cell_start[c] = sum of counts[0..c), cell_start[C] = the total, counts
+// zeroed for the next step.  Warp w takes cells [128 G w, 128 G (w + 1)) as
+// G rounds of 32 lanes x 4 cells: coalesced 16-byte loads from L2 (where the
+// count atomics landed), all in flight before the first is used.  The
+// block scans the warps' totals; each warp then walks its rounds in order,
+// a lane's group start being the warp's base, the carry of the earlier
+// rounds and the lane's exclusive prefix within the round.  The counts
+// array is padded with zeros to a multiple of 4 cells and cell_start holds
+// C + 4 entries, so every access is a whole 16-byte group (entries past C
+// hold the total).  Needs C <= 128 G (blockDim.x / 32).  wsum: >= 33 ints
+// of shared memory.
+template <int G>
+__device__ __forceinline__ void scan_cells_block(const Bufs &B, int *wsum) {
+  const int C = B.c_total, C4 = (C + 3) & ~3;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lo = warp * 128 * G + 4 * lane;
+  int4 v[G];
+#pragma unroll
+  for (int j = 0; j < G; ++j) {
+    const int c = lo + 128 * j;
+    v[j] = c < C4 ? __ldcg(reinterpret_cast<const int4 *>(B.counts + c)) : make_int4(0, 0, 0, 0);
+  }
+  int gs[G], t = 0;
+#pragma unroll
+  for (int j = 0; j < G; ++j) {
+    gs[j] = v[j].x + v[j].y + v[j].z + v[j].w;
+    t += gs[j];
+  }
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) t += __shfl_xor_sync(0xffffffffu, t, m);
+  int total = 0;
+  int base = block_excl_scan(lane == 0 ? t : 0, wsum, &total);
+  base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+  for (int j = 0; j < G; ++j) {
+    const int c = lo + 128 * j;
+    int incl = gs[j];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    int run = base + incl - gs[j];
+    base += __shfl_sync(0xffffffffu, incl, 31);
+    int4 st;
+    st.x = run; run += v[j].x;
+    st.y = run; run += v[j].y;
+    st.z = run; run += v[j].z;
+    st.w = run;
+    if (c < C4) {
+      *reinterpret_cast<int4 *>(B.cell_start + c) = st;
+      *reinterpret_cast<int4 *>(B.counts + c) = make_int4(0, 0, 0, 0);
+    }
+  }
+  if (C4 == C && threadIdx.x == 0) B.cell_start[C] = total;
+}
+
+// Writes agent f's sorted entries at position pos.
+__device__ __forceinline__ void scatter_agent(int f, float4 st, int pos, const Bufs &B) {
   if ((unsigned)pos >= (unsigned)B.n_total) {  // inconsistent counts: never write out of range
     atomicOr(B.err, FLOCK_ERR_STATE);
     return;
@@ -479,6 +532,22 @@ __device__ __forceinline__ void phaseC_agent(int f, const float4 *state_i, const
   B.sxy[pos] = make_float2(st.x, st.y);
   B.sidx[pos] = f;
   if (B.stype) B.stype[pos] = B.types[f];
+}
+
+// Phase C after the fused scan: position = cell start + rank in the cell.
+__device__ __forceinline__ void phaseC_agent_final(int f, const float4 *state_i, const Bufs &B) {
+  const int2 cr = B.cellrank[f];
+  if (!dbg_ok(cr.x >= 0 && cr.x < B.c_total && cr.y >= 0)) return;
+  scatter_agent(f, *state_i, B.cell_start[cr.x] + cr.y, B);
+}
+
+// Phase C for one agent (flattened index f, local index i of instance I):
+// counting-sort scatter of its state into cell order.
+__device__ __forceinline__ void phaseC_agent(int f, const float4 *state_i, const Bufs &B,
+                                             const int *tp) {
+  const int2 cr = B.cellrank[f];
+  if (!dbg_ok(cr.x >= 0 && cr.x < B.c_total && cr.y >= 0)) return;
+  scatter_agent(f, *state_i, tp[cr.x / kScanTile] + B.local[cr.x] + cr.y, B);
 }
 
 __device__ __forceinline__ void phaseC_cell(int c, const Bufs &B, const int *tp) {
