@@ -479,7 +479,8 @@ def run_policy(F, torch, dev, stream, steps, warmup, flush, n=100000, seed=0, wo
             "workload": "step + fused policy: %d agents, side %.0f, MLP 18-64-64-9 tanh, BF16 "
                         "weights N(0, 0.1) and activations on tensor cores (mma.sync), FP32 "
                         "accumulate, greedy actions feed the next step" % (n, side),
-            "roofline": {"bound": "hbm", "kernel": "whole step (4 kernels)",
+            "roofline": {"bound": "hbm", "kernel": "whole step (5 kernels: the step's 4 and "
+                                                   "the network)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,
                          "traffic": None,  # a whole-step figure; see profiles/ for the kernel

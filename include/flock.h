@@ -102,8 +102,9 @@ typedef struct flock_tuning {
   int stencil; /* 1: cells of width >= d_v, 3 x 3 stencil; 2: width >= d_v/2, 5 x 5 */
   int tile_w;  /* mode 1: cells per tile along x, 1..64 */
   int tile_h;  /* mode 1: cells per tile along y, 1..8 */
-  int block;   /* threads per block, multiple of 32 in 64..512 (batch, modes
-                  3 and 4: the neighbour launch's block, 64..256) */
+  int block;   /* threads per block, multiple of 32 in 64..512 (0: 128;
+                  batch, modes 3 and 4: the neighbour launch's block,
+                  64..256) */
   int mode;    /* neighbour scan: 1 = tiles of cells staged in shared memory,
                   2 = each warp takes 32 / lanes consecutive cell-sorted agents
                   and reads their stencil cells through the L1 cache.
@@ -114,8 +115,9 @@ typedef struct flock_tuning {
                   instances, then the neighbour launch.  Results are
                   identical. */
   int lanes;   /* mode 2: lanes per agent, 1, 2, 4 or 32 (0: 32 when an agent
-                  has 256 or more candidates in its stencil cells on average,
-                  else 4 up to 32,768 agents, 2 up to 524,288, else 1); the
+                  has 256 or more candidates in its stencil cells on average
+                  or there are at most 4,096 agents, else 4 up to 32,768
+                  agents, 2 up to 524,288, else 1); the
                   lanes of an agent share its candidates.  Mode 1 uses 1.
                   Batch, modes 3 and 4: 1, 2 or 4 for the neighbour launch (0:
                   by the batch's maximum agent count, as above); mode 2: 1. */

@@ -380,20 +380,22 @@ int choose_tuning(const Inst &I, int n, const flock_tuning *req, flock_tuning &t
   t.stencil = I.halo;
   t.mode = r.mode ? r.mode : 2;
   if (t.mode != 1 && t.mode != 2) return FLOCK_EINVAL;
-  t.block = r.block ? r.block : 128;
-  if (t.block < 64 || t.block > 512 || t.block % 32) return FLOCK_EINVAL;
   // lanes per agent: more lanes keep more warps in flight when there are
   // few agents; with many, one lane per agent has the least overhead.  An
   // agent with hundreds of candidates (a view much wider than the spacing of
-  // the agents) gets a whole warp.
+  // the agents), or one of at most 4,096 agents, gets a whole warp.
   const double wc = (double)I.L / I.nc;
   const double cand = n > 0 ? (double)n / ((double)I.L * I.L) * (2.0 * I.halo + 1.0) *
                                   (2.0 * I.halo + 1.0) * wc * wc
                             : 0.0;
   t.lanes = r.lanes ? r.lanes
-                    : (cand >= 256.0 ? 32 : (n <= 32768 ? 4 : (n <= 524288 ? 2 : 1)));
+                    : (cand >= 256.0 || n <= 4096
+                           ? 32
+                           : (n <= 32768 ? 4 : (n <= 524288 ? 2 : 1)));
   if (t.lanes != 1 && t.lanes != 2 && t.lanes != 4 && t.lanes != 32) return FLOCK_EINVAL;
   if (t.mode == 1) t.lanes = 1;
+  t.block = r.block ? r.block : 128;
+  if (t.block < 64 || t.block > 512 || t.block % 32) return FLOCK_EINVAL;
   if (I.kind == 1 && t.mode == 1) return FLOCK_EINVAL;  // tag: direct forms only
   const double w = (double)I.L / I.nc;
   const double per_cell = n > 0 ? (double)n / ((double)I.L * I.L) * w * w : 1.0;

@@ -437,7 +437,31 @@ struct flock_batch {
   int timing;
   cudaEvent_t ev[2];
   bool configured;
+  // Page-locked staging of the uploads (a copy from pageable memory may wait
+  // for the stream, which would stall a caller that keeps steps in flight):
+  // two halves for the set's descriptors and prefixes, used in turn, and one
+  // BatchDev per slot; an event per buffer marks when its copy has left.
+  char *hset = nullptr;
+  size_t hset_half = 0;
+  int hset_cur = 0;
+  cudaEvent_t hset_ev[2] = {nullptr, nullptr};
+  bool hset_used[2] = {false, false};
+  BatchDev *hdev = nullptr;
+  cudaEvent_t hdev_ev[2] = {nullptr, nullptr};
+  bool hdev_used[2] = {false, false};
 };
+
+// Frees what env_batch_create made besides the workspace.
+static void batch_free(flock_batch *b) {
+  for (int k = 0; k < 2; ++k) {
+    if (b->hset_ev[k]) cudaEventDestroy(b->hset_ev[k]);
+    if (b->hdev_ev[k]) cudaEventDestroy(b->hdev_ev[k]);
+  }
+  if (b->hset) cudaFreeHost(b->hset);
+  if (b->hdev) cudaFreeHost(b->hdev);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+}
 
 extern "C" int flock_instance_cells(const flock_params *p, const flock_tuning *t, int *cells) {
   if (!p || !cells) return FLOCK_EINVAL;
@@ -530,9 +554,19 @@ extern "C" int env_batch_create(int mi, int ma, int mc, const flock_tuning *t, v
   if (ce == cudaSuccess) ce = cudaMemsetAsync(b->ws + L.ctr, 0, 64, b->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(b->ws + L.err, 0, 64, b->stream);
   if (ce != cudaSuccess) {
-    cudaStreamDestroy(b->cap_stream);
-    delete b;
+    batch_free(b);
     return cuda_fail(ce, "env_batch_create memset");
+  }
+  b->hset_half = ((size_t)mi * sizeof(Inst) + 2 * ((size_t)mi + 1) * 4 + 255) & ~(size_t)255;
+  ce = cudaHostAlloc((void **)&b->hset, 2 * b->hset_half, cudaHostAllocDefault);
+  if (ce == cudaSuccess) ce = cudaHostAlloc((void **)&b->hdev, 2 * sizeof(BatchDev), cudaHostAllocDefault);
+  for (int k = 0; k < 2 && ce == cudaSuccess; ++k) {
+    ce = cudaEventCreateWithFlags(&b->hset_ev[k], cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&b->hdev_ev[k], cudaEventDisableTiming);
+  }
+  if (ce != cudaSuccess) {
+    batch_free(b);
+    return cuda_fail(ce, "env_batch_create staging");
   }
   *out = b;
   return FLOCK_OK;
@@ -651,12 +685,19 @@ extern "C" int env_batch_set(flock_batch *b, int n_inst, const flock_params *par
   b->apre.swap(apre);
   b->cpre.swap(cpre);
   if (n_inst > 0) {
-    BCK(cudaMemcpyAsync(b->ws + L.insts, b->insts.data(), (size_t)n_inst * sizeof(Inst),
-                        cudaMemcpyHostToDevice, b->stream));
-    BCK(cudaMemcpyAsync(b->ws + L.apre, b->apre.data(), (size_t)(n_inst + 1) * 4,
-                        cudaMemcpyHostToDevice, b->stream));
-    BCK(cudaMemcpyAsync(b->ws + L.cpre, b->cpre.data(), (size_t)(n_inst + 1) * 4,
-                        cudaMemcpyHostToDevice, b->stream));
+    // through the staging half not used last, once its previous copy has left
+    const int h = b->hset_cur ^= 1;
+    if (b->hset_used[h]) BCK(cudaEventSynchronize(b->hset_ev[h]));
+    char *hs = b->hset + (size_t)h * b->hset_half;
+    const size_t bi = (size_t)n_inst * sizeof(Inst), bp = ((size_t)n_inst + 1) * 4;
+    memcpy(hs, b->insts.data(), bi);
+    memcpy(hs + bi, b->apre.data(), bp);
+    memcpy(hs + bi + bp, b->cpre.data(), bp);
+    BCK(cudaMemcpyAsync(b->ws + L.insts, hs, bi, cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaMemcpyAsync(b->ws + L.apre, hs + bi, bp, cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaMemcpyAsync(b->ws + L.cpre, hs + bi + bp, bp, cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaEventRecord(b->hset_ev[h], b->stream));
+    b->hset_used[h] = true;
   }
   b->slot[0].dirty = b->slot[1].dirty = true;  // both descriptors re-uploaded when next used
   b->configured = true;
@@ -743,8 +784,12 @@ extern "C" int env_batch_step(flock_batch *b, const int32_t *act, float *obs, fl
     b->dev.B.obs = obs;
     b->dev.B.reward = rew;
     b->dev.B.coll = coll;
-    BCK(cudaMemcpyAsync((BatchDev *)(b->ws + b->lay.dev) + k, &b->dev, sizeof(BatchDev),
+    if (b->hdev_used[k]) BCK(cudaEventSynchronize(b->hdev_ev[k]));
+    b->hdev[k] = b->dev;
+    BCK(cudaMemcpyAsync((BatchDev *)(b->ws + b->lay.dev) + k, b->hdev + k, sizeof(BatchDev),
                         cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaEventRecord(b->hdev_ev[k], b->stream));
+    b->hdev_used[k] = true;
     q.dirty = false;
   }
   if (!q.graph) {
@@ -843,6 +888,5 @@ extern "C" void env_batch_destroy(flock_batch *b) {
     if (b->ev[k]) cudaEventDestroy(b->ev[k]);
   for (int k = 0; k < 2; ++k)
     if (b->slot[k].graph) cudaGraphExecDestroy(b->slot[k].graph);
-  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-  delete b;
+  batch_free(b);
 }

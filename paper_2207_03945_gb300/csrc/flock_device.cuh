@@ -1014,9 +1014,12 @@ struct DirectArea {
 // Bytes of one warp's area for v sectors and A agents per warp (32 / lanes
 // per agent): the per-sector minima and counts take A rows of v.
 // q: the queue capacity (kQueueWide for the standalone kernels, kQueue for
-// the batched kernel).
+// the batched kernel).  Rounded up to 16 bytes: the warps' areas follow one
+// another and each starts with the float4 queue (one agent per warp with an
+// odd v leaves A v 8 = 8 mod 16).
 __host__ __device__ inline size_t direct_warp_bytes(int v, int A = 32, int q = kQueueWide) {
-  return (size_t)q * 16 + 32 * 8 + 3 * 32 * 4 + 32 + 32 * 4 * 2 + (size_t)A * v * 8;
+  const size_t b = (size_t)q * 16 + 32 * 8 + 3 * 32 * 4 + 32 + 32 * 4 * 2 + (size_t)A * v * 8;
+  return (b + 15) & ~(size_t)15;
 }
 
 __device__ __forceinline__ DirectArea direct_area(char *base, int v, int A = 32,
@@ -1698,8 +1701,8 @@ __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, c
     B.coll[I.agent_base + i] = ncoll;
     if ((long long)nin > I.NMAX) err |= FLOCK_ERR_OVERFLOW;
   }
-  // observation rows (and, with the policy, also BF16 rows of the warp's
-  // tile).  The last entry of a flock row, (speed, heading) (layout 1: the
+  // observation rows (and, in the policy step, also the BF16 rows the
+  // network reads, written by every flock kernel form).  The last entry of a flock row, (speed, heading) (layout 1: the
   // speed), comes from the agent's own lane; the v sector entries of several
   // rows at a time from all lanes, each row's contiguous.  Tag rows are the
   // 2v distances.
@@ -1716,7 +1719,7 @@ __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, c
       if (lay0) *reinterpret_cast<float2 *>(row + 2 * v) = val;
       else row[v] = val.x;
     }
-    if (V == 8 && B.pobs)
+    if (!TAG && B.pobs)
       B.pobs[(long long)(I.agent_base + i) * kPobsWords + v] = pack_bf16(val.x, val.y);
   }
   for (int rb = 0; rb < nb; rb += rpi) {
@@ -1738,7 +1741,7 @@ __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, c
           if (lay0) *reinterpret_cast<float2 *>(row + 2 * e) = val;
           else row[e] = val.x;  // layout 1: the distance only
         }
-        if (V == 8 && B.pobs)
+        if (!TAG && B.pobs)
           B.pobs[(long long)(I.agent_base + ir) * kPobsWords + e] = pack_bf16(val.x, val.y);
       }
     }

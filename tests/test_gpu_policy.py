@@ -115,3 +115,33 @@ def test_policy_needs_eight_segments():
     with pytest.raises(F.FlockError):
         F.env_step_policy(env.env, blob, z, r, z.clone())
     env.close()
+
+
+def test_policy_rows_from_every_kernel_form():
+    """Every flock form of the neighbour scan hands the network the same BF16
+    rows: with 1, 2, 4 and 32 lanes per agent (32 uses the generic-sector
+    kernel) and with the tile form requested, the policy step gives the same
+    logits and actions, bit for bit."""
+    n = 3000
+    side = fi.side_for(n)
+    p = fi.default_params(side)
+    st0 = fi.initial_state(n, side, 9)
+    a0 = fi.random_actions(n, 1, 9)[0]
+    _, blob = weights_dev(3)
+    outs = []
+    for tuning in ({"lanes": 1}, {"lanes": 2}, {"lanes": 4}, {"lanes": 32}, {"mode": 1}, None):
+        env = F.FlockEnv(p, n, device=DEV, tuning=tuning)
+        env.reset(torch.from_numpy(st0).to(DEV))
+        act = torch.from_numpy(a0).to(DEV)
+        rew = torch.empty(n, dtype=torch.float32, device=DEV)
+        coll = torch.empty(n, dtype=torch.int32, device=DEV)
+        logits = torch.empty((n, 9), dtype=torch.float32, device=DEV)
+        F.env_step_policy(env.env, blob, act, rew, coll, logits)
+        torch.cuda.synchronize()
+        assert env.error() == 0, tuning
+        outs.append((tuning, logits.cpu().numpy(), act.cpu().numpy(), rew.cpu().numpy()))
+        env.close()
+    for tuning, lg, ac, rw in outs[1:]:
+        assert np.array_equal(lg, outs[0][1]), tuning
+        assert np.array_equal(ac, outs[0][2]), tuning
+        assert np.array_equal(rw, outs[0][3]), tuning
