@@ -694,6 +694,8 @@ def main():
     ap.add_argument("--agents", type=int, default=N_AGENTS)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-policy", action="store_true")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the 1,000- and 5,000-agent plain steps")
     ap.add_argument("--no-paper", action="store_true",
                     help="skip the paper's own flock variant (16,000 agents, 128 sectors)")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
@@ -840,13 +842,16 @@ def main():
             "workload": "serving: Poisson arrivals 50/s, agents log-uniform in [500, 50000], "
                         "episodes uniform in [100, 2000] steps, 100 GB budget, random actions; "
                         "plus a saturated run (5,000 sessions queued at t=0, more than the run "
-                        "serves, 100 MB budget so that admission binds)"}
+                        "serves, 100 MB budget so that admission binds); clients' initial states "
+                        "made on the host (numpy) at admission, uploaded from page-locked staging"}
     # the other plain-step configurations: 1,000 agents for 100 steps, 5,000
     # agents (the same density) for 1,000 steps
-    small = {"n1000_100_steps": run_plain(F, torch, dev, stream, 1000, 100, args.warmup, flush,
-                                          seed=rank_seed(rank), world=world),
-             "n5000_1000_steps": run_plain(F, torch, dev, stream, 5000, 1000, args.warmup, flush,
-                                           seed=rank_seed(rank), world=world)}
+    small = None
+    if not args.no_small:
+        small = {"n1000_100_steps": run_plain(F, torch, dev, stream, 1000, 100, args.warmup, flush,
+                                              seed=rank_seed(rank), world=world),
+                 "n5000_1000_steps": run_plain(F, torch, dev, stream, 5000, 1000, args.warmup,
+                                               flush, seed=rank_seed(rank), world=world)}
     policy = plain100k = None
     if not args.no_policy:
         policy = run_policy(F, torch, dev, stream, args.steps, args.warmup, flush,
@@ -895,7 +900,8 @@ def main():
             line["batched"] = batched
             line["batch_of_one"] = batch_of_one
             line["batched_10_instances"] = ten
-        line["plain_small"] = small
+        if small is not None:
+            line["plain_small"] = small
         if policy is not None:
             line["policy"] = policy
         if paper is not None:
