@@ -5,7 +5,7 @@ environments of arXiv 2207.03945 Section 4.1) arrive over time.  The server
 admits a waiting session as soon as a slot and enough of the device-memory
 budget are free, keeps every admitted session's state resident in one device
 arena, and advances ALL admitted sessions together, one step per iteration,
-with the batched kernel (one persistent launch per iteration).  A session
+with the batched step (one CUDA graph launch per iteration).  A session
 that arrives while others are running joins at the next iteration; a session
 whose episode is over leaves and frees its slot and memory.  Nothing is
 re-captured when the set changes: only the instance descriptors are
