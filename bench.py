@@ -658,6 +658,27 @@ def run_rollout(F, torch, dev, stream, reps, flush, n=16000, T=128, seed=0, worl
                                  "bytes_per_element": 16}}}
 
 
+def device_initial_state(dev):
+    """Clients' initial states drawn on the device from each session's seed:
+    x, y ~ U[0, side), theta ~ U[0, 2 pi), speed 0.5 (the distribution of
+    flock_inputs.initial_state, from torch's device generator)."""
+    import torch
+    below_two_pi = float(np.nextafter(fi.TWO_PI_F32, np.float32(0)))
+
+    def fn(s):
+        g = torch.Generator(device=dev)
+        g.manual_seed(int(s.seed))
+        side = np.float32(s.params["side"])
+        u = torch.rand((s.n, 3), generator=g, device=dev)
+        st = torch.empty((s.n, 4), dtype=torch.float32, device=dev)
+        st[:, 0:2] = torch.clamp(u[:, 0:2] * float(side),
+                                 max=float(np.nextafter(side, np.float32(0))))
+        st[:, 2] = torch.clamp(u[:, 2] * float(fi.TWO_PI_F32), max=below_two_pi)
+        st[:, 3] = 0.5
+        return st
+    return fn
+
+
 def run_serving(dev, seconds, seed=0, rate=50.0, budget=100 * 10 ** 9, backlog=0):
     """Serving loop with continuous batching: Poisson session arrivals, agent
     counts log-uniform in [500, 50000], episodes of 100..2000 steps, admission
@@ -671,8 +692,7 @@ def run_serving(dev, seconds, seed=0, rate=50.0, budget=100 * 10 ** 9, backlog=0
         for k in range(backlog):
             n = int(round(math.exp(math.log(500) + rng.random() * (math.log(50000) - math.log(500)))))
             arrivals.append((0.0, n, int(rng.integers(100, 2001)), 10 ** 6 + k))
-    srv = serve.FlockServer(budget, state_fn=lambda s: fi.initial_state(s.n, s.params["side"],
-                                                                         s.seed),
+    srv = serve.FlockServer(budget, state_fn=device_initial_state(dev),
                             max_slots=512, arena_agents=8_000_000, max_cells=4_000_000,
                             device=dev)
     st = srv.run(arrivals, duration=seconds)
@@ -842,8 +862,8 @@ def main():
             "workload": "serving: Poisson arrivals 50/s, agents log-uniform in [500, 50000], "
                         "episodes uniform in [100, 2000] steps, 100 GB budget, random actions; "
                         "plus a saturated run (5,000 sessions queued at t=0, more than the run "
-                        "serves, 100 MB budget so that admission binds); clients' initial states "
-                        "made on the host (numpy) at admission, uploaded from page-locked staging"}
+                        "serves, 100 MB budget so that admission binds); initial states drawn "
+                        "on the device from each session's seed at admission"}
     # the other plain-step configurations: 1,000 agents for 100 steps, 5,000
     # agents (the same density) for 1,000 steps
     small = None

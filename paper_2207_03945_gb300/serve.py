@@ -182,8 +182,10 @@ class SessionScheduler:
 class FlockServer:
     """Runs a SessionScheduler against the batched kernel on one GPU.
 
-    state_fn(session) -> (n, 4) float32 initial state of a session (host
-    array, the client's data); params_fn(n) -> parameter dict of a session of
+    state_fn(session) -> (n, 4) float32 initial state of a session: a host
+    array (the client's data, uploaded from page-locked staging) or a tensor
+    on the server's device (drawn there, e.g. from the session's seed; copied
+    into the arena in stream order, no host round trip); params_fn(n) -> parameter dict of a session of
     n agents (default: the library defaults on a square of side
     sqrt(n / 0.1), i.e. density 0.1); action_fn(session, step, out) fills the
     session's int32 actions for one step into the device tensor `out`
@@ -290,12 +292,19 @@ class FlockServer:
         # staging rows may still feed the previous iteration's upload
         if self._upload_pending and self._upload_ev is not None:
             self._upload_ev.synchronize()
+        staged = False
         for s in admitted:
-            st = np.ascontiguousarray(self.state_fn(s), dtype=np.float32)
+            st = self.state_fn(s)
+            if isinstance(st, torch.Tensor) and st.device == self.arena.device:
+                # made on the device: copied in stream order, nothing staged
+                self.arena[s.offset:s.offset + s.n].copy_(st.reshape(s.n, 4))
+                continue
+            st = np.ascontiguousarray(st, dtype=np.float32)
             self._stage[s.offset:s.offset + s.n].numpy()[...] = st
             self.arena[s.offset:s.offset + s.n].copy_(self._stage[s.offset:s.offset + s.n],
                                                       non_blocking=True)
-        if self._upload_ev is not None:
+            staged = True
+        if staged and self._upload_ev is not None:
             self._upload_ev.record()
             self._upload_pending = True
 

@@ -169,3 +169,26 @@ def test_pipelined_results_arrive_one_iteration_later_from_alternating_buffers(m
             assert srv.batch.bufs == [0, 0, 0, 0]
             assert got == [(1, 1), (2, 2), (3, 3), (4, 4)]
         assert a.steps_done == 4 and a.steps_issued == 4
+
+
+def test_device_tensor_initial_states(monkeypatch):
+    """state_fn may return a tensor on the server's device: it is copied into
+    the session's arena rows without staging (nothing waits on an upload
+    event), and host arrays still go through the staging rows."""
+    monkeypatch.setattr(F, "FlockBatch", RecordingBatch)
+    stream = types.SimpleNamespace(synchronize=lambda: None)
+
+    def state_fn(s):
+        v = torch.full((s.n, 4), float(s.sid + 1))
+        return v if s.sid % 2 == 0 else v.numpy()
+
+    srv = serve.FlockServer(10 ** 12, state_fn=state_fn, max_slots=4, arena_agents=100000,
+                            max_cells=100000, device="cpu", stream=stream)
+    ss = [srv.submit(100 + 10 * k, steps=2, seed=k) for k in range(4)]
+    srv.iteration()
+    for s in ss:
+        assert torch.equal(srv.arena[s.offset:s.offset + s.n], torch.full((s.n, 4), float(s.sid + 1)))
+    while srv.sched.active or srv.sched.queue:
+        srv.iteration()
+    srv.close()
+    assert all(s.steps_done == 2 for s in ss)
