@@ -220,7 +220,9 @@ int flock_gae(int T, int n, const float *reward_dev, const float *value_dev, flo
  * the greedy actions (largest logit, lowest index on ties) for the next step.
  * The neighbour scan hands the observations to the network as BF16 rows in
  * the workspace (48 bytes per agent, which stay in L2 at these sizes); the
- * network runs in the step's fifth kernel.
+ * binning kernel copies the weights into a lane-interleaved operand image in
+ * the workspace (15,872 bytes, rebuilt every call, so weights may change
+ * between calls); the network runs in the step's fifth kernel.
  * weights_bf16_dev: 5,961 bfloat16 values, W1[64][18] b1[64] W2[64][64]
  * b2[64] W3[9][64] b3[9], each W row-major [out][in].  Operands are BF16 on
  * the tensor cores, accumulation FP32, tanh the hardware approximation.

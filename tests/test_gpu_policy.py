@@ -145,3 +145,31 @@ def test_policy_rows_from_every_kernel_form():
         assert np.array_equal(lg, outs[0][1]), tuning
         assert np.array_equal(ac, outs[0][2]), tuning
         assert np.array_equal(rw, outs[0][3]), tuning
+
+
+def test_weights_changed_in_place_between_calls():
+    """The step's graph keeps the weights pointer; the operand image is rebuilt
+    from it at every call, so weights updated in place (a training step) are
+    the ones the next call's network uses."""
+    n = 4000
+    side = fi.side_for(n)
+    p = fi.default_params(side)
+    st0 = fi.initial_state(n, side, 13)
+    env = F.FlockEnv(p, n, device=DEV)
+    env.reset(torch.from_numpy(st0).to(DEV))
+    w1, blob = weights_dev(4)
+    w2, blob2 = weights_dev(5)
+    act = torch.from_numpy(fi.random_actions(n, 1, 13)[0]).to(DEV)
+    rew = torch.empty(n, dtype=torch.float32, device=DEV)
+    coll = torch.empty(n, dtype=torch.int32, device=DEV)
+    logits = torch.empty((n, 9), dtype=torch.float32, device=DEV)
+    obs = torch.empty((n, 18), dtype=torch.float32, device=DEV)
+    for w, src in ((w1, None), (w2, blob2)):
+        if src is not None:
+            blob.copy_(src)  # same pointer, new contents
+        F.env_step_policy(env.env, blob, act, rew, coll, logits, obs)
+        torch.cuda.synchronize()
+        ref64 = fp64.mlp_forward(w, obs.cpu().numpy())
+        assert np.abs(logits.cpu().numpy().astype(np.float64) - ref64).max() < LOGIT_TOL
+    assert env.error() == 0
+    env.close()
