@@ -148,6 +148,19 @@ def max_over_ranks(x: float, device=None) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(x: float, device=None) -> float:
+    """Sum of x over the ranks of the default process group (x itself when
+    there is none); a reporting reduction, outside any timed region."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64,
+                     device=device if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def weak_scaling_value(world: int, agents_per_rank: int, steps: int, max_ms: float) -> float:
     """Whole-job agent-steps per second: every rank advanced its own
     agents_per_rank agents `steps` times; the job took the slowest rank's time."""
@@ -679,12 +692,16 @@ def device_initial_state(dev):
     return fn
 
 
-def run_serving(dev, seconds, seed=0, rate=50.0, budget=100 * 10 ** 9, backlog=0):
+def run_serving(dev, seconds, seed=0, rate=50.0, budget=100 * 10 ** 9, backlog=0, rank=0,
+                world=1):
     """Serving loop with continuous batching: Poisson session arrivals, agent
     counts log-uniform in [500, 50000], episodes of 100..2000 steps, admission
     by a device-memory budget, all admitted sessions stepped together by the
     batched kernel each iteration.  backlog > 0 adds that many sessions at
-    t = 0 (saturation)."""
+    t = 0 (saturation).  With several ranks (one GPU each) the job's single
+    arrival stream is placed across them on the host (serve.place_sessions,
+    the same on every rank, no exchange) and each rank serves its share; the
+    rate is the job's agent-steps over the slowest rank's time."""
     from paper_2207_03945_gb300 import serve
     arrivals = fi.session_stream(rate, seconds, seed)
     if backlog:
@@ -692,6 +709,11 @@ def run_serving(dev, seconds, seed=0, rate=50.0, budget=100 * 10 ** 9, backlog=0
         for k in range(backlog):
             n = int(round(math.exp(math.log(500) + rng.random() * (math.log(50000) - math.log(500)))))
             arrivals.append((0.0, n, int(rng.integers(100, 2001)), 10 ** 6 + k))
+    arrivals = sorted(arrivals)
+    offered = len(arrivals)
+    if world > 1:
+        ranks = serve.place_sessions(arrivals, world)
+        arrivals = [a for a, r in zip(arrivals, ranks) if r == rank]
     srv = serve.FlockServer(budget, state_fn=device_initial_state(dev),
                             max_slots=512, arena_agents=8_000_000, max_cells=4_000_000,
                             device=dev)
@@ -699,8 +721,13 @@ def run_serving(dev, seconds, seed=0, rate=50.0, budget=100 * 10 ** 9, backlog=0
     err = srv.batch.error()
     assert err == 0, "device error bits %d" % err
     srv.close()
+    if world > 1:
+        wall = max_over_ranks(st["wall_s"], dev)
+        st["agent_steps_per_s"] = sum_over_ranks(st["agent_steps"], dev) / wall
+        st["placement"] = {"ranks": world, "sessions_this_rank": len(arrivals),
+                           "rule": "least placed work (agents x steps), same on every rank"}
     st.update({"rate_per_s": rate, "budget_bytes": budget, "backlog": backlog,
-               "seconds": seconds, "sessions_offered": len(arrivals)})
+               "seconds": seconds, "sessions_offered": offered})
     return st
 
 
@@ -856,15 +883,18 @@ def main():
     serving = None
     if args.serve_seconds > 0:
         serving = {
-            "as_specified": run_serving(dev, args.serve_seconds, seed=rank_seed(rank)),
+            "as_specified": run_serving(dev, args.serve_seconds, seed=0, rank=rank,
+                                        world=world),
             "saturated_small_budget": run_serving(dev, max(5.0, args.serve_seconds / 2),
-                                                  seed=rank_seed(rank) + 1, budget=10 ** 8,
-                                                  backlog=5000),
+                                                  seed=1, budget=10 ** 8, backlog=5000 * world,
+                                                  rank=rank, world=world),
             "workload": "serving: Poisson arrivals 50/s, agents log-uniform in [500, 50000], "
                         "episodes uniform in [100, 2000] steps, 100 GB budget, random actions; "
                         "plus a saturated run (5,000 sessions queued at t=0, more than the run "
                         "serves, 100 MB budget so that admission binds); initial states drawn "
-                        "on the device from each session's seed at admission"}
+                        "on the device from each session's seed at admission; with N ranks one "
+                        "job-wide arrival stream is placed across them on the host (least placed "
+                        "work) and the saturated backlog is 5,000 per rank"}
     # the other plain-step configurations: 1,000 agents for 100 steps, 5,000
     # agents (the same density) for 1,000 steps
     small = None

@@ -36,6 +36,31 @@ def session_bytes(n_agents: int, n_cells: int) -> int:
     return BYTES_PER_AGENT * n_agents + BYTES_PER_CELL * n_cells + BYTES_PER_SESSION
 
 
+class SessionPlacer:
+    """Host-side placement of sessions across GPUs (one server per GPU, no
+    collective): each arriving session goes to the rank with the least work
+    placed so far (agents x episode steps), the lowest rank on ties.  The
+    placement depends only on the sequence of sessions offered, so every rank
+    computes the same one from the same arrival stream and serves its own
+    share without any exchange."""
+
+    def __init__(self, n_ranks: int):
+        if n_ranks < 1:
+            raise ValueError("n_ranks must be at least 1")
+        self.load = [0] * n_ranks
+
+    def place(self, n_agents: int, steps: int) -> int:
+        r = min(range(len(self.load)), key=lambda k: (self.load[k], k))
+        self.load[r] += int(n_agents) * int(steps)
+        return r
+
+
+def place_sessions(arrivals, n_ranks: int):
+    """Rank of each (t, n, steps, seed) arrival, in the order given."""
+    pl = SessionPlacer(n_ranks)
+    return [pl.place(n, steps) for (_t, n, steps, _seed) in arrivals]
+
+
 @dataclass
 class Session:
     sid: int
