@@ -34,17 +34,30 @@ BATCH_CANDIDATES = tuple(
     [{"stencil": 1, "mode": 4, "block": 128, "lanes": ln} for ln in (1, 2, 4)])
 
 
-def _hold(torch):
-    """Keeps the GPU busy for a few milliseconds so that the timed steps are
-    all queued before the first one starts: the events then measure device
-    time, not the host's launch rate (which bounds small workloads)."""
-    torch.cuda._sleep(8_000_000)
+def _flushed_step_ms(torch, dev, step, acts, abuf, first, count):
+    """Median device time of `count` steps, each after an L2 flush (a write
+    larger than the 129 MB L2, outside the events), as the benchmark times
+    them: candidates are ranked on steps that start with cold caches."""
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(count)]
+    for k in range(count):
+        abuf.copy_(acts[first + k])
+        flush.zero_()
+        ev[k][0].record()
+        step(abuf)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    ms = sorted(a.elapsed_time(b) for a, b in ev)
+    del flush
+    return ms[len(ms) // 2]
 
 
 def _key(torch, dev, n, params):
     name = torch.cuda.get_device_name(dev)
     bucket = 1 << max(0, int(math.ceil(math.log2(max(n, 1)))))
-    return "%s|n<=%d|v=%d" % (name, bucket, int(params["num_segments"]))
+    # "flushed": ranked on L2-flushed steps (entries ranked otherwise are not reused)
+    return "%s|n<=%d|v=%d|flushed" % (name, bucket, int(params["num_segments"]))
 
 
 def _load(path):
@@ -100,16 +113,7 @@ def autotune(params, state0, steps=6, warmup=2, device="cuda", cache=DEFAULT_CAC
             o, r, c = env.step(abuf)
             outs.append((o.clone(), r.clone(), c.clone()))
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        _hold(torch)
-        e0.record()
-        for k in range(warmup, warmup + steps):
-            abuf.copy_(acts[k])
-            env.step(abuf)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
+        ms = _flushed_step_ms(torch, dev, env.step, acts, abuf, warmup, steps)
         tun = env.tuning()
         env.close()
         if ref is None:
@@ -130,7 +134,7 @@ def autotune(params, state0, steps=6, warmup=2, device="cuda", cache=DEFAULT_CAC
     return best[0], report
 
 
-def autotune_batch(params_list, sizes, states, steps=4, warmup=2, device="cuda",
+def autotune_batch(params_list, sizes, states, steps=7, warmup=2, device="cuda",
                    candidates=BATCH_CANDIDATES):
     """Best cell size (stencil) and form (one persistent launch, or binning
     and neighbour scan as two launches) for a batch: times each candidate's
@@ -165,16 +169,7 @@ def autotune_batch(params_list, sizes, states, steps=4, warmup=2, device="cuda",
             o, r, c = b.step(abuf)
             outs.append((o.clone(), r.clone(), c.clone()))
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        _hold(torch)
-        e0.record()
-        for k in range(warmup, warmup + steps):
-            abuf.copy_(acts[k])
-            b.step(abuf)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
+        ms = _flushed_step_ms(torch, dev, b.step, acts, abuf, warmup, steps)
         b.close()
         if ref is None:
             ref, same = outs, True

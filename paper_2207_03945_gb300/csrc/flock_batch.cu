@@ -280,9 +280,8 @@ __global__ void __launch_bounds__(256) k_bbin_scatter(const BatchDev *__restrict
 // LPA lanes per agent: a chunk is 32 / LPA agents (more lanes keep more warps
 // busy when the batch holds few agents).
 template <int H, int V, int LPA>
-__global__ void __launch_bounds__(256) k_batch_neigh(const BatchDev *__restrict__ d,
-                                                     Inst *insts, const int *cpre,
-                                                     unsigned *ctr, int after_barriers) {
+__device__ __forceinline__ void batch_neigh(const BatchDev *__restrict__ d, Inst *insts,
+                                            const int *cpre, unsigned *ctr, int after_barriers) {
   constexpr int A = 32 / LPA;
   extern __shared__ __align__(16) char smem[];
   pdl_wait();
@@ -321,6 +320,25 @@ __global__ void __launch_bounds__(256) k_batch_neigh(const BatchDev *__restrict_
   if (err) atomicOr(B.err, err);
 }
 
+// The launches.  Registers: one lane per agent keeps the compiler's default
+// for blocks of 256 (the large mixes, issue-bound, want the warps: the
+// 256-instance mix takes 179.5 us a step, 181.2 at 80 registers); 2 or 4
+// lanes get 80 registers and no spills (a batch of one 50,000-agent
+// instance 31.6 us a step against 33.6 us at 64 with 24 bytes spilled).
+template <int H, int V>
+__global__ void __launch_bounds__(256) k_batch_neigh1(const BatchDev *__restrict__ d, Inst *insts,
+                                                      const int *cpre, unsigned *ctr,
+                                                      int after_barriers) {
+  batch_neigh<H, V, 1>(d, insts, cpre, ctr, after_barriers);
+}
+
+template <int H, int V, int LPA>
+__global__ void __launch_bounds__(256, 3) k_batch_neigh(const BatchDev *__restrict__ d,
+                                                        Inst *insts, const int *cpre,
+                                                        unsigned *ctr, int after_barriers) {
+  batch_neigh<H, V, LPA>(d, insts, cpre, ctr, after_barriers);
+}
+
 static size_t neigh_smem(int v, int block, int lanes) {
   return (size_t)(block / 32) * (sizeof(Inst) + direct_warp_bytes(v, 32 / lanes));
 }
@@ -356,10 +374,10 @@ static KFn batch_kernel(int halo, int v, int layout, bool split) {
 static NFn neigh_kernel(int halo, int v, int layout, int lanes) {
   const bool v8 = v == 8 && layout == 0;
   static const NFn t[2][2][3] = {
-      {{k_batch_neigh<1, 0, 1>, k_batch_neigh<1, 0, 2>, k_batch_neigh<1, 0, 4>},
-       {k_batch_neigh<1, 8, 1>, k_batch_neigh<1, 8, 2>, k_batch_neigh<1, 8, 4>}},
-      {{k_batch_neigh<2, 0, 1>, k_batch_neigh<2, 0, 2>, k_batch_neigh<2, 0, 4>},
-       {k_batch_neigh<2, 8, 1>, k_batch_neigh<2, 8, 2>, k_batch_neigh<2, 8, 4>}}};
+      {{k_batch_neigh1<1, 0>, k_batch_neigh<1, 0, 2>, k_batch_neigh<1, 0, 4>},
+       {k_batch_neigh1<1, 8>, k_batch_neigh<1, 8, 2>, k_batch_neigh<1, 8, 4>}},
+      {{k_batch_neigh1<2, 0>, k_batch_neigh<2, 0, 2>, k_batch_neigh<2, 0, 4>},
+       {k_batch_neigh1<2, 8>, k_batch_neigh<2, 8, 2>, k_batch_neigh<2, 8, 4>}}};
   return t[halo - 1][v8 ? 1 : 0][lanes == 1 ? 0 : (lanes == 2 ? 1 : 2)];
 }
 
