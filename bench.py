@@ -37,6 +37,9 @@ import flock_inputs as fi  # noqa: E402
 METRIC = "flock agent-steps/sec at 50k agents, batched vs plain; p99 step latency"
 UNIT = "agent-steps/s"
 N_AGENTS = 50000
+# the headline workload, the same words in both arms' config
+PLAIN_WORKLOAD = ("plain flock step, 1 instance, %d agents, side %.1f, density 0.1, view radius "
+                  "5, 8 sectors, fov 250 deg, uniform random actions")
 BYTES_PER_AGENT_STEP = 116  # state in 16 + action 4 + state out 16 + obs 72 + reward 4 + coll 4
 # neighbour scan: reads the agent's sorted position (8), heading and speed (8)
 # and index (4); writes its observation (72), reward (4) and collisions (4)
@@ -302,10 +305,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "plain flock step, 1 instance, 50000 agents, side 707.1, "
-                                   "density 0.1, view radius 5, 8 sectors, fov 250 deg, uniform "
-                                   "random actions (CPU oracle, sampled rows)",
-                       "agents": n, "parallelism": "none"},
+            "config": {"workload": PLAIN_WORKLOAD % (n, fi.side_for(n)),
+                       "agents": n, "parallelism": "single",
+                       "form": "CPU oracle (O(N^2) per observed agent), sampled rows"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -927,9 +929,8 @@ def main():
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "plain flock step, 1 instance, %d agents, side %.1f, density "
-                                   "0.1, view radius 5, 8 sectors, fov 250 deg, uniform random "
-                                   "actions, CUDA graph of 4 kernels" % (n, side),
+            "config": {"workload": PLAIN_WORKLOAD % (n, side),
+                       "form": "CUDA graph of 4 kernels",
                        "agents": n, "tuning": env.tuning(), "tuned_by": tuned_by,
                        "l2": "flushed (512 MiB write) between timed steps",
                        "parallelism": "replicas" if world > 1 else "single"},
