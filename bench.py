@@ -879,9 +879,11 @@ def main():
         batch_of_one = run_batched(F, torch, dev, stream, args.steps, args.warmup, flush,
                                    seed=rank_seed(rank), sizes=[n], world=world, tune=False)
         # like for like with the headline: its agents as ten 5,000-agent instances
+        # the mix's tuned form and block; lanes per agent by these instances' size
+        ten_tuning = {k: v for k, v in (batched["tuning"] or {}).items() if k != "lanes"}
         ten = run_batched(F, torch, dev, stream, args.steps, args.warmup, flush,
                           seed=rank_seed(rank), sizes=[n // 10] * 10, world=world, tune=False,
-                          tuning=batched["tuning"])
+                          tuning=ten_tuning)
     serving = None
     if args.serve_seconds > 0:
         serving = {

@@ -109,8 +109,12 @@ __global__ void k_neighbours(const Inst *__restrict__ gI, Bufs B) {
 }
 
 // LPA lanes per agent: each warp takes 32 / LPA consecutive sorted agents.
-// TAG: the tag environment (two colour channels of sectors).
-template <int H, int V, int LPA, bool TAG = false>
+// TAG: the tag environment (two colour channels of sectors).  COMPACT: the
+// runs across the square's edges walked by one loop instead of nine inlined
+// copies (a warp per agent with a wide view: the paper's flock 126.7 us a
+// step against 141.3, tag 152.2 against 181.5, from fewer instruction-fetch
+// stalls; with few candidates, 1,000 agents, the inlined runs are faster).
+template <int H, int V, int LPA, bool TAG = false, bool COMPACT = false>
 __global__ void k_neighbours_direct(const Inst *__restrict__ gI, Bufs B) {
   extern __shared__ __align__(16) char smem[];
   __shared__ Inst sI;
@@ -124,7 +128,7 @@ __global__ void k_neighbours_direct(const Inst *__restrict__ gI, Bufs B) {
   if (gp0 < sI.n) {
     const int vs = TAG ? 2 * sI.v : sI.v;
     const DirectArea W = direct_area(smem + (size_t)warp * direct_warp_bytes(vs, A), vs, A);
-    phaseD_direct<H, V, true, LPA, TAG>(sI, gp0, min(gp0 + A, sI.n), B, W, err);
+    phaseD_direct<H, V, true, LPA, TAG, COMPACT>(sI, gp0, min(gp0 + A, sI.n), B, W, err);
   }
   if (err) atomicOr(B.err, err);
 }
@@ -374,6 +378,14 @@ int derive(const flock_params &p, int stencil, Inst &I, flock_derived *D) {
 }
 
 // Fill in the launch shape.  Agents per tile aim at 3/4 of the block.
+// Mean candidates an agent tests: the agents in its stencil cells.
+static double candidates_per_agent(const Inst &I, int n) {
+  const double wc = (double)I.L / I.nc;
+  return n > 0 ? (double)n / ((double)I.L * I.L) * (2.0 * I.halo + 1.0) * (2.0 * I.halo + 1.0) *
+                     wc * wc
+               : 0.0;
+}
+
 int choose_tuning(const Inst &I, int n, const flock_tuning *req, flock_tuning &t) {
   flock_tuning r{};
   if (req) r = *req;
@@ -384,10 +396,7 @@ int choose_tuning(const Inst &I, int n, const flock_tuning *req, flock_tuning &t
   // few agents; with many, one lane per agent has the least overhead.  An
   // agent with hundreds of candidates (a view much wider than the spacing of
   // the agents), or one of at most 4,096 agents, gets a whole warp.
-  const double wc = (double)I.L / I.nc;
-  const double cand = n > 0 ? (double)n / ((double)I.L * I.L) * (2.0 * I.halo + 1.0) *
-                                  (2.0 * I.halo + 1.0) * wc * wc
-                            : 0.0;
+  const double cand = candidates_per_agent(I, n);
   t.lanes = r.lanes ? r.lanes
                     : (cand >= 256.0 || n <= 4096
                            ? 32
@@ -459,7 +468,11 @@ cudaError_t set_kernel_attrs() {
                          (const void *)k_neighbours_direct<1, 0, 32>,
                          (const void *)k_neighbours_direct<2, 0, 32>,
                          (const void *)k_neighbours_direct<1, 0, 32, true>,
-                         (const void *)k_neighbours_direct<2, 0, 32, true>};
+                         (const void *)k_neighbours_direct<2, 0, 32, true>,
+                         (const void *)k_neighbours_direct<1, 0, 32, false, true>,
+                         (const void *)k_neighbours_direct<2, 0, 32, false, true>,
+                         (const void *)k_neighbours_direct<1, 0, 32, true, true>,
+                         (const void *)k_neighbours_direct<2, 0, 32, true, true>};
     for (const void *f : fns)
       if (g_attr_err == cudaSuccess) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
@@ -524,6 +537,7 @@ struct flock_env {
   int copy_grid;  // k_copy_out (host-buffer step)
   int mlp_grid;   // k_policy_mlp: blocks at most (grid-stride over the agents)
   bool fused_scan;  // at most kFusedScanCells cells: the binning kernel's last block scans them
+  bool wide;        // 256 or more candidates an agent on average (a view much wider than the spacing)
   size_t smemD;
   int timing;
   cudaEvent_t ev[5];
@@ -657,6 +671,7 @@ static int create_env(const flock_params *p, const flock_tuning *t, int n, int r
   e->copy_grid = (int)std::max<size_t>(1, std::min<size_t>((units + 255) / 256, (size_t)sms * 8));
   e->mlp_grid = sms * kMlpBlocksPerSM;  // one resident wave
   e->fused_scan = e->inst.ncells <= kFusedScanCells;
+  e->wide = candidates_per_agent(e->inst, n) >= 256.0;
   e->smemD = e->tuning.mode == 1
                  ? phaseD_smem_bytes(e->inst.cap, e->inst.v, e->tuning.block)
                  : (size_t)(e->tuning.block / 32) *
@@ -773,7 +788,13 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const 
       // the V = 8 kernels write observation layout 0 only
       const int v8 = e->inst.v == 8 && e->inst.obs_layout == 0 ? 1 : 0;
       const int h = e->inst.halo - 1;
-      const KD k = e->inst.kind == 1 ? kt[h][li] : kd[h][v8][li];
+      // a warp per agent with a wide view (hundreds of candidates): the
+      // compact walk of the wrapping runs
+      static const KD kc[2][2] = {
+          {k_neighbours_direct<1, 0, 32, false, true>, k_neighbours_direct<1, 0, 32, true, true>},
+          {k_neighbours_direct<2, 0, 32, false, true>, k_neighbours_direct<2, 0, 32, true, true>}};
+      const KD k = (lpa == 32 && e->wide) ? kc[h][e->inst.kind == 1 ? 1 : 0]
+                                           : (e->inst.kind == 1 ? kt[h][li] : kd[h][v8][li]);
       CK(launch(pdl, k, blocks, blk, sm, s, gI, B));
     }
   }
