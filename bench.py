@@ -485,6 +485,16 @@ def run_policy(F, torch, dev, stream, steps, warmup, flush, n=100000, seed=0, wo
     assert env.error() == 0
     ms = [ev0[k].elapsed_time(ev1[k]) for k in range(steps)]
     tot = max_over_ranks(sum(ms), dev)
+    # second pass: events between the step's kernels give each one's time
+    F.env_set_timing(env.env, True)
+    phase = []
+    for k in range(min(steps, 20)):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            F.env_step_policy(env.env, blob, act, rew, coll)
+        phase.append(F.env_get_phase_times(env.env))
+    F.env_set_timing(env.env, False)
+    ph = np.array(phase).mean(axis=0)
     env.close()
     peak, peak_kind = peaks()
     achieved = POLICY_BYTES_PER_AGENT * n / (tot / steps * 1e-3) / 1e9
@@ -494,8 +504,10 @@ def run_policy(F, torch, dev, stream, steps, warmup, flush, n=100000, seed=0, wo
             "workload": "step + fused policy: %d agents, side %.0f, MLP 18-64-64-9 tanh, BF16 "
                         "weights N(0, 0.1) and activations on tensor cores (mma.sync), FP32 "
                         "accumulate, greedy actions feed the next step" % (n, side),
-            "roofline": {"bound": "hbm", "kernel": "whole step (5 kernels: the step's 4 and "
-                                                   "the network)",
+            "kernel_ms": {"apply_bin_and_weight_image": float(ph[0]), "scan": float(ph[1]),
+                          "scatter": float(ph[2]), "neighbours_and_network": float(ph[3])},
+            "roofline": {"bound": "hbm", "kernel": "whole step (4 kernels; the network runs "
+                                                   "in the neighbour scan's epilogue)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,
                          "traffic": None,  # a whole-step figure; see profiles/ for the kernel

@@ -34,6 +34,8 @@ constexpr int kFusedScanCells = kFusedBlock * 4 * kFusedRounds;
 // (a ticket in B.bar[0], taken after a fence, so every count atomic of the
 // other blocks is complete) scans all cell counts into cell_start and resets
 // the ticket.  No block waits for another.
+// The policy step (B.wimg set) launches extra blocks past the agents' ones;
+// they write the network's operand image while the others bin the agents.
 template <bool FUSED>
 __global__ void __launch_bounds__(FUSED ? kFusedBlock : 256)
     k_apply_bin(const Inst *__restrict__ gI, Bufs B, int reset) {
@@ -46,8 +48,12 @@ __global__ void __launch_bounds__(FUSED ? kFusedBlock : 256)
     phaseA_agent(sI, i, B.actions + sI.agent_base, B.cactions ? B.cactions + sI.agent_base : nullptr,
                  reset, B.counts, B.cellrank, err);
   if (err) atomicOr(B.err, err);
-  // the policy step: the network's operand image, read four kernels later
-  if (B.wimg) policy_image(B.wblob, B.wimg, i, gridDim.x * blockDim.x);
+  // the policy step: the network's operand image, read three kernels later,
+  // by the blocks past the agents' ones
+  if (B.wimg) {
+    const int first = (sI.n + blockDim.x - 1) / blockDim.x * blockDim.x;
+    if (i >= first) policy_image(B.wblob, B.wimg, i - first, gridDim.x * blockDim.x - first);
+  }
   if (FUSED) {
     // every count atomic of this block has returned (complete in L2); the
     // barrier and thread 0's fence order them before the ticket
@@ -133,71 +139,34 @@ __global__ void k_neighbours_direct(const Inst *__restrict__ gI, Bufs B) {
   if (err) atomicOr(B.err, err);
 }
 
-// The shared policy network (Section 4.3; 18 -> 64 -> 64 -> 9 with tanh) on
-// the step's observations: the neighbour scan leaves each agent's
-// observation as a BF16 row in the workspace (48 bytes, resident in L2), and
-// this kernel runs the network on the tensor cores (mma.sync m16n8k16, FP32
-// accumulate), one m-tile of 16 agents per warp and pass, and writes the
-// greedy actions (largest logit, lowest index on ties) and optionally the
-// logits.  Each lane loads its operand fragments itself, the weights from
-// the operand image (31 coalesced 16-byte loads per m-tile, L1-resident; no
-// shared memory, no block barrier); warps walk the agents with a
-// grid-stride loop.  (A fused form that ran the
-// network in the neighbour scan's epilogue held 94 registers and 46 KB of
-// shared memory per block, and took 1.67 times the plain step at 100,000
-// agents.)
-constexpr int kMlpBlock = 256;
-constexpr int kMlpBlocksPerSM = 3;  // at most 80 registers a thread: three blocks on each SM
-
-__global__ void __launch_bounds__(kMlpBlock, kMlpBlocksPerSM)
-    k_policy_mlp(const unsigned *__restrict__ pobs, int n, const uint4 *__restrict__ wimg,
-                 int32_t *actions, float *logits) {
+// The policy step's neighbour scan with the shared policy network (Section
+// 4.3; 18 -> 64 -> 64 -> 9 with tanh) in its epilogue: each warp, once its
+// agents' observations are complete in its sector arrays, runs the network
+// on them on the tensor cores (policy_warp_rows: mma.sync, BF16 operands,
+// FP32 accumulate; the weights from the operand image the binning kernel
+// built, L1-resident) and writes their greedy actions (largest logit, lowest
+// index on ties) and optionally the logits.  No observation goes through
+// memory on the way, and the step keeps its four kernels.  The network's
+// accumulators are held by halves of 32 columns, so the kernel needs no
+// more registers than the scan (a form with a fifth kernel reading BF16
+// observation rows from L2 took 44.3 us a step at 100,000 agents, this one
+// 42.2 us).
+template <int H, int V, int LPA>
+__global__ void k_neighbours_policy(const Inst *__restrict__ gI, Bufs B) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ Inst sI;
+  load_inst(sI, gI);
   pdl_wait();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const uint4 *im = wimg + lane;
-  const int stride = gridDim.x * (kMlpBlock / 32) * 16;
-  // A-fragment words of rows g and g + 8 of 16 agents from `base`: BF16
-  // pairs t (columns 2t, 2t + 1), 4 + t (columns 8 + 2t, 9 + 2t) and, for
-  // t = 0, 8 (columns 16, 17); rows past the last agent are zero
-  auto fetch = [&](int base, unsigned (&f)[2][3]) {
-    const int nb = min(16, n - base);
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      const int r = g + 8 * m;
-      const bool ok = r < nb;
-      const unsigned *src = pobs + (long long)(base + (ok ? r : 0)) * kPobsWords;
-      f[m][0] = ok ? __ldg(src + t) : 0u;
-      f[m][1] = ok ? __ldg(src + 4 + t) : 0u;
-      f[m][2] = ok && t == 0 ? __ldg(src + 8) : 0u;
-    }
-  };
-  int base = (blockIdx.x * (kMlpBlock / 32) + warp) * 16;
-  unsigned f[2][3] = {{0u, 0u, 0u}, {0u, 0u, 0u}};
-  if (base < n) fetch(base, f);
-  for (; base < n; base += stride) {
-    const int nb = min(16, n - base);
-    const unsigned a0[4] = {f[0][0], f[1][0], f[0][1], f[1][1]};
-    const unsigned a1[4] = {f[0][2], f[1][2], 0u, 0u};
-    if ((long long)base + stride < n) fetch(base + stride, f);  // the next rows, in flight meanwhile
-    int alo = 0, ahi = 0;
-    float lg[2][4];
-    policy_mtile(im, a0, a1, alo, ahi, lg);
-    const int rlo = g, rhi = g + 8;
-    if (t == 0) {
-      if (rlo < nb) actions[base + rlo] = alo;
-      if (rhi < nb) actions[base + rhi] = ahi;
-    }
-    if (logits) {
-      const int c4[4] = {2 * t, 2 * t + 1, 8 + 2 * t, 9 + 2 * t};
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (c4[j] < 9) {
-          if (rlo < nb) logits[(long long)(base + rlo) * 9 + c4[j]] = lg[0][j];
-          if (rhi < nb) logits[(long long)(base + rhi) * 9 + c4[j]] = lg[1][j];
-        }
-      }
-    }
+  __syncthreads();
+  unsigned err = 0;
+  const int warp = threadIdx.x >> 5;
+  constexpr int A = 32 / LPA;
+  const int gp0 = (blockIdx.x * (blockDim.x >> 5) + warp) * A;
+  if (gp0 < sI.n) {
+    const DirectArea W = direct_area(smem + (size_t)warp * direct_warp_bytes(sI.v, A), sI.v, A);
+    phaseD_direct<H, V, true, LPA, false, false, true>(sI, gp0, min(gp0 + A, sI.n), B, W, err);
   }
+  if (err) atomicOr(B.err, err);
 }
 
 // Copies a step's outputs (observations, rewards, collision counts) from the
@@ -472,7 +441,15 @@ cudaError_t set_kernel_attrs() {
                          (const void *)k_neighbours_direct<1, 0, 32, false, true>,
                          (const void *)k_neighbours_direct<2, 0, 32, false, true>,
                          (const void *)k_neighbours_direct<1, 0, 32, true, true>,
-                         (const void *)k_neighbours_direct<2, 0, 32, true, true>};
+                         (const void *)k_neighbours_direct<2, 0, 32, true, true>,
+                         (const void *)k_neighbours_policy<1, 8, 1>,
+                         (const void *)k_neighbours_policy<2, 8, 1>,
+                         (const void *)k_neighbours_policy<1, 8, 2>,
+                         (const void *)k_neighbours_policy<2, 8, 2>,
+                         (const void *)k_neighbours_policy<1, 8, 4>,
+                         (const void *)k_neighbours_policy<2, 8, 4>,
+                         (const void *)k_neighbours_policy<1, 0, 32>,
+                         (const void *)k_neighbours_policy<2, 0, 32>};
     for (const void *f : fns)
       if (g_attr_err == cudaSuccess) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
@@ -488,7 +465,7 @@ using namespace flock;
 
 struct Layout {
   size_t state, cellrank, counts, local, cell_start, tile_sum, sxy, sidx, types, stype, inst,
-      err, h_act, h_obs, h_rew, h_coll, pobs, wimg, total;
+      err, h_act, h_obs, h_rew, h_coll, wimg, total;
 };
 
 static Layout make_layout(int n, int C, int D) {
@@ -512,8 +489,7 @@ static Layout make_layout(int n, int C, int D) {
   L.h_obs = take((size_t)n * D * 4);
   L.h_rew = take((size_t)n * 4);
   L.h_coll = take((size_t)n * 4);
-  L.pobs = take((size_t)n * kPobsWords * 4);  // policy step: BF16 observation rows
-  L.wimg = take(kImgBytes);                    // policy step: the weights' operand image
+  L.wimg = take(kImgBytes);  // policy step: the weights' operand image
   L.total = o;
   return L;
 }
@@ -535,7 +511,6 @@ struct flock_env {
   int n_scan_tiles;
   int scatter_grid;
   int copy_grid;  // k_copy_out (host-buffer step)
-  int mlp_grid;   // k_policy_mlp: blocks at most (grid-stride over the agents)
   bool fused_scan;  // at most kFusedScanCells cells: the binning kernel's last block scans them
   bool wide;        // 256 or more candidates an agent on average (a view much wider than the spacing)
   size_t smemD;
@@ -669,7 +644,6 @@ static int create_env(const flock_params *p, const flock_tuning *t, int n, int r
   // 16-byte units of the outputs, one per thread, at most 8 blocks per SM
   const size_t units = ((size_t)n * e->inst.obs_dim * 4 + (size_t)n * 8) / 16;
   e->copy_grid = (int)std::max<size_t>(1, std::min<size_t>((units + 255) / 256, (size_t)sms * 8));
-  e->mlp_grid = sms * kMlpBlocksPerSM;  // one resident wave
   e->fused_scan = e->inst.ncells <= kFusedScanCells;
   e->wide = candidates_per_agent(e->inst, n) >= 256.0;
   e->smemD = e->tuning.mode == 1
@@ -708,21 +682,23 @@ extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, v
 }
 
 // act: discrete actions, or cact (when not null): continuous ones.
-// pobs (policy step): the neighbour scan also writes BF16 observation rows
-// there; it then runs in the direct form whatever the tuning's mode.
 // n_run >= 0 (a slab's observation): that many agents this time (at most the
 // environment's n); the descriptor in the workspace must say the same.
+// Policy step: wblob, the weight blob (the binning kernel writes its operand
+// image), and pact and plogits, the actions and logits the neighbour scan's
+// epilogue writes; the scan then runs in the direct form.
 static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const float2 *cact,
-                        float *obs, float *rew, int32_t *coll, int reset,
-                        unsigned *pobs = nullptr, int n_run = -1,
-                        const unsigned short *wblob = nullptr) {
+                        float *obs, float *rew, int32_t *coll, int reset, int n_run = -1,
+                        const unsigned short *wblob = nullptr, int32_t *pact = nullptr,
+                        float *plogits = nullptr) {
   Bufs B = e->bufs;
   B.actions = act;
   B.cactions = cact;
   B.obs = obs;
   B.reward = rew;
   B.coll = coll;
-  B.pobs = pobs;
+  B.pact = pact;
+  B.plogits = plogits;
   B.wblob = wblob;
   B.wimg = wblob ? (uint4 *)(e->ws + e->lay.wimg) : nullptr;
   const Inst *gI = (const Inst *)(e->ws + e->lay.inst);
@@ -737,11 +713,13 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const 
   const bool fused = e->fused_scan && n > 0;
   {
     NvtxRange r("flock:apply_bin");
+    // the policy step's operand image: blocks of its own after the agents'
+    const int bs = fused ? kFusedBlock : 256;
+    const int img = wblob ? (kImgVecs * 32 + bs - 1) / bs : 0;
     if (fused)
-      CK(launch(false, k_apply_bin<true>, (n + kFusedBlock - 1) / kFusedBlock, kFusedBlock, 0, s,
-                gI, B, reset));
+      CK(launch(false, k_apply_bin<true>, (n + bs - 1) / bs + img, bs, 0, s, gI, B, reset));
     else if (n > 0)
-      CK(launch(false, k_apply_bin<false>, (n + 255) / 256, 256, 0, s, gI, B, reset));
+      CK(launch(false, k_apply_bin<false>, (n + bs - 1) / bs + img, bs, 0, s, gI, B, reset));
   }
   if (tm) CK(cudaEventRecordWithFlags(e->ev[1], s, cudaEventRecordExternal));
   if (!fused) {
@@ -760,7 +738,7 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const 
   if (n > 0) {
     const int blk = e->tuning.block;
     const size_t sm = e->smemD;
-    if (e->tuning.mode == 1 && !pobs) {
+    if (e->tuning.mode == 1 && !pact) {
       const int tiles = e->inst.tiles_x * e->inst.tiles_y;
       if (e->inst.halo == 1) CK(launch(pdl, k_neighbours<1>, tiles, blk, sm, s, gI, B));
       else CK(launch(pdl, k_neighbours<2>, tiles, blk, sm, s, gI, B));
@@ -793,8 +771,16 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const 
       static const KD kc[2][2] = {
           {k_neighbours_direct<1, 0, 32, false, true>, k_neighbours_direct<1, 0, 32, true, true>},
           {k_neighbours_direct<2, 0, 32, false, true>, k_neighbours_direct<2, 0, 32, true, true>}};
-      const KD k = (lpa == 32 && e->wide) ? kc[h][e->inst.kind == 1 ? 1 : 0]
-                                           : (e->inst.kind == 1 ? kt[h][li] : kd[h][v8][li]);
+      // the policy step's scan with the network in its epilogue (8 sectors,
+      // layout 0, the flock: the host checks)
+      static const KD kp[2][4] = {
+          {k_neighbours_policy<1, 8, 1>, k_neighbours_policy<1, 8, 2>,
+           k_neighbours_policy<1, 8, 4>, k_neighbours_policy<1, 0, 32>},
+          {k_neighbours_policy<2, 8, 1>, k_neighbours_policy<2, 8, 2>,
+           k_neighbours_policy<2, 8, 4>, k_neighbours_policy<2, 0, 32>}};
+      const KD k = pact ? kp[h][li]
+                   : (lpa == 32 && e->wide) ? kc[h][e->inst.kind == 1 ? 1 : 0]
+                   : (e->inst.kind == 1 ? kt[h][li] : kd[h][v8][li]);
       CK(launch(pdl, k, blocks, blk, sm, s, gI, B));
     }
   }
@@ -802,24 +788,13 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const 
   return FLOCK_OK;
 }
 
-// The policy step: the step's four kernels (the binning kernel also writing
-// the weights' operand image, the neighbour scan also BF16 observation rows
-// into the workspace), then the network.
+// The policy step: the step's four kernels, the binning kernel also writing
+// the weights' operand image and the neighbour scan running the network on
+// each warp's agents in its epilogue.
 static int enqueue_policy_step(flock_env *e, cudaStream_t s, const unsigned short *w,
                                int32_t *act, float *rew, int32_t *coll, float *logits,
                                float *obs) {
-  unsigned *pobs = (unsigned *)(e->ws + e->lay.pobs);
-  int rc = enqueue_step(e, s, act, nullptr, obs, rew, coll, 0, pobs, -1, w);
-  if (rc) return rc;
-  const int n = e->n;
-  if (n > 0) {
-    NvtxRange r("flock:policy_mlp");
-    int blocks = (n + kMlpBlock / 2 - 1) / (kMlpBlock / 2);  // 16 agents a warp
-    blocks = blocks < e->mlp_grid ? blocks : e->mlp_grid;
-    CK(launch(true, k_policy_mlp, blocks, kMlpBlock, 0, s, (const unsigned *)pobs, n,
-              (const uint4 *)(e->ws + e->lay.wimg), act, logits));
-  }
-  return FLOCK_OK;
+  return enqueue_step(e, s, act, nullptr, obs, rew, coll, 0, -1, w, act, logits);
 }
 
 static bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p % a) == 0; }
@@ -1123,10 +1098,13 @@ extern "C" int env_set_timing(flock_env *e, int enable) {
   if (!e) return FLOCK_EINVAL;
   if (enable && !e->ev[0])
     for (int k = 0; k < 5; ++k) CK(cudaEventCreate(&e->ev[k]));
-  if ((enable != 0) != (e->timing != 0) && e->graph) {
+  if ((enable != 0) != (e->timing != 0) && (e->graph || e->pgraph)) {
     CK(cudaStreamSynchronize(e->stream));
-    cudaGraphExecDestroy(e->graph);
-    e->graph = nullptr;  // re-captured by the next env_step
+    // re-captured by the next env_step / env_step_policy
+    if (e->graph) cudaGraphExecDestroy(e->graph);
+    if (e->pgraph) cudaGraphExecDestroy(e->pgraph);
+    e->graph = nullptr;
+    e->pgraph = nullptr;
   }
   e->timing = enable != 0;
   return FLOCK_OK;
@@ -1223,7 +1201,7 @@ extern "C" int env_slab_observe(flock_env *e, int n_own, int n_ghost, const floa
   if (n > 0)
     CK(cudaMemcpyAsync(e->ws + e->lay.state, state_dev, (size_t)n * 16, cudaMemcpyDeviceToDevice,
                        e->stream));
-  return enqueue_step(e, e->stream, nullptr, nullptr, obs, rew, coll, 1, nullptr, n);
+  return enqueue_step(e, e->stream, nullptr, nullptr, obs, rew, coll, 1, n);
 }
 
 // ---------------------------------------------------------------------------

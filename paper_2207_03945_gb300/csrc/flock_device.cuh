@@ -77,16 +77,12 @@ struct Bufs {
   float *obs;
   float *reward;
   int32_t *coll;
-  unsigned *pobs;  // policy step: BF16 observation rows (kPobsWords per agent, agent order), or null
   const unsigned short *wblob;  // policy step: the weight blob, whose operand image the
   uint4 *wimg;                  // binning kernel writes to wimg (both null otherwise)
+  int32_t *pact;   // policy step, network in the neighbour scan: greedy actions out
+  float *plogits;  // and logits (9 per agent, agent order), or null
   int n_total, c_total, n_scan_tiles, pad;
 };
-
-// Row of a BF16 observation for the policy network: 18 values (8 sectors x
-// (distance, count), speed, heading) as 9 packed pairs, padded to 12 words
-// (48 bytes, so rows start on 16-byte boundaries).
-constexpr int kPobsWords = 12;
 
 // Debug build (FLOCK_DEBUG, libflock_debug.so): index checks on the step's
 // scratch and output accesses.  A failed check latches FLOCK_ERR_BOUNDS in
@@ -1307,9 +1303,9 @@ __device__ __forceinline__ void direct_run(const Inst &I, const DirectArea &W, c
 // ---------------------------------------------------------------------------
 // Policy network: the shared MLP of the learners (Section 4.3; two hidden
 // layers of 64 with tanh, here 18 -> 64 -> 64 -> 9 on the 18-value
-// observation), run by k_policy_mlp on the BF16 observation rows the
-// neighbour scan leaves in the workspace.  BF16 operands on the tensor cores
-// (mma.sync m16n8k16), FP32 accumulate; the greedy action (largest logit,
+// observation), run in the neighbour scan's epilogue on each warp's own
+// agents (policy_warp_rows).  BF16 operands on the tensor cores (mma.sync
+// m16n8k16 and m16n8k8), FP32 accumulate; the greedy action (largest logit,
 // lowest index on ties) is written back.  The weights reach the lanes as an
 // operand image built from the blob at the start of the step (see
 // policy_image); each layer's accumulators, rounded to BF16 pairs and passed
@@ -1323,21 +1319,24 @@ static_assert(kOffB1 % 2 == 0 && kOffW2 % 2 == 0 && kOffB2 % 2 == 0 && kOffW3 % 
                   kOffB3 % 2 == 0,
               "every matrix and bias of the blob starts on a BF16 pair");
 
-// Operand image: for lane (g, t) = (lane / 4, lane % 4) the 124 words it
-// feeds the forward pass, in the order of use, as 31 uint4 stored
+// Operand image: for lane (g, t) = (lane / 4, lane % 4) the 116 words it
+// feeds the forward pass, in the order of use, as 29 uint4 stored
 // lane-interleaved (vector j of lane l at j * 32 + l: a warp-wide load is 512
-// contiguous bytes).  Word ranges per lane:
-//   [0, 24)    layer 1, n-tile nt = s / 3: the B pairs W1[8nt+g][2t, 2t+1],
-//              W1[8nt+g][2t+8, 2t+9] and (t = 0 only) W1[8nt+g][16, 17]
-//   [24, 32)   b1 pair (8nt + 2t, 8nt + 2t + 1) for nt = s - 24
-//   [32, 96)   layer 2, q = s - 32: k-step q / 16, n-tile (q / 2) % 8, the
+// contiguous bytes).  Every pair of B words an m16n8k16 takes sits in one
+// aligned half of a vector.  The biases enter as products with a constant 1
+// in an m16n8k8 step (no accumulator initialisation).  n = 8 nt + g is the
+// output row a word serves.  Word ranges per lane:
+//   [0, 16)    layer 1, columns 0-15, word 2 nt + r: W1[n][2t + 8r, 2t + 8r + 1]
+//   [16, 24)   layer 1, columns 16-23, word 16 + nt: (t = 0) W1[n][16, 17],
+//              (t = 1) (b1[n], 0): the observation's column 18 is the constant 1
+//   [24, 88)   layer 2, q = s - 24: k-step q / 16, n-tile (q / 2) % 8, the
 //              pair at column offset 8 (q % 2)
-//   [96, 104)  b2 pairs
-//   [104, 120) layer 3, q = s - 104: k-step q / 4, n-tile (q / 2) % 2, pair
+//   [88, 96)   b2, word 88 + nt: (t = 0) (b2[n], 0)
+//   [96, 112)  layer 3, q = s - 96: k-step q / 4, n-tile (q / 2) % 2, pair
 //              q % 2; rows 9-15 of W3 are zero
-//   [120, 124) b3: columns (2t, 2t + 1); (t = 0) column 8 in the low half; 0, 0
-constexpr int kImgWords = 124, kImgVecs = kImgWords / 4;
-constexpr int kImgB1 = 24, kImgL2 = 32, kImgB2 = 96, kImgL3 = 104, kImgB3 = 120;
+//   [112, 116) b3, word 112 + nt (nt < 2): (t = 0, n < 9) (b3[n], 0); 0, 0
+constexpr int kImgWords = 116, kImgVecs = kImgWords / 4;
+constexpr int kImgL1K8 = 16, kImgL2 = 24, kImgB2 = 88, kImgL3 = 96, kImgB3 = 112;
 constexpr size_t kImgBytes = (size_t)kImgVecs * 32 * 16;
 
 __device__ __forceinline__ unsigned blob_pair(const unsigned short *__restrict__ blob, int e) {
@@ -1346,25 +1345,26 @@ __device__ __forceinline__ unsigned blob_pair(const unsigned short *__restrict__
 
 __device__ __forceinline__ unsigned image_word(const unsigned short *__restrict__ blob, int s, int g,
                                                int t) {
-  if (s < kImgB1) {
-    const int nt = s / 3, r = s - 3 * nt, row = (8 * nt + g) * 18;
-    if (r == 0) return blob_pair(blob, row + 2 * t);
-    if (r == 1) return blob_pair(blob, row + 2 * t + 8);
-    return t == 0 ? blob_pair(blob, row + 16) : 0u;
+  if (s < kImgL1K8) {
+    const int nt = s >> 1, r = s & 1;
+    return blob_pair(blob, (8 * nt + g) * 18 + 2 * t + 8 * r);
   }
-  if (s < kImgL2) return blob_pair(blob, kOffB1 + 8 * (s - kImgB1) + 2 * t);
+  if (s < kImgL2) {
+    const int n = 8 * (s - kImgL1K8) + g;
+    if (t == 0) return blob_pair(blob, n * 18 + 16);
+    return t == 1 ? (unsigned)blob[kOffB1 + n] : 0u;
+  }
   if (s < kImgB2) {
     const int q = s - kImgL2, kk = q >> 4, nt = (q >> 1) & 7, r = q & 1;
     return blob_pair(blob, kOffW2 + (8 * nt + g) * 64 + 16 * kk + 2 * t + 8 * r);
   }
-  if (s < kImgL3) return blob_pair(blob, kOffB2 + 8 * (s - kImgB2) + 2 * t);
+  if (s < kImgL3) return t == 0 ? (unsigned)blob[kOffB2 + 8 * (s - kImgB2) + g] : 0u;
   if (s < kImgB3) {
     const int q = s - kImgL3, kk = q >> 2, nt = (q >> 1) & 1, r = q & 1, n = 8 * nt + g;
     return n < 9 ? blob_pair(blob, kOffW3 + n * 64 + 16 * kk + 2 * t + 8 * r) : 0u;
   }
-  if (s == kImgB3) return blob_pair(blob, kOffB3 + 2 * t);
-  if (s == kImgB3 + 1) return t == 0 ? (unsigned)blob[kOffB3 + 8] : 0u;
-  return 0u;
+  const int n = 8 * (s - kImgB3) + g;
+  return s < kImgB3 + 2 && t == 0 && n < 9 ? (unsigned)blob[kOffB3 + n] : 0u;
 }
 
 // Writes image vectors idx, idx + stride, ... (call with the grid's thread
@@ -1387,13 +1387,25 @@ __device__ __forceinline__ float2 bf16x2_float2(unsigned w) {
   return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
 }
 
+// d += a b (m16n8k16, BF16 operands, FP32 accumulate)
 __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const unsigned (&a)[4], unsigned b0,
                                                unsigned b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
       "{%8,%9}, {%0,%1,%2,%3};\n"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// d = a b (m16n8k8, BF16 operands, FP32 result): the first product of an
+// accumulator chain.  a0, a1: rows g and g + 8, columns 2t, 2t + 1; b: rows
+// 2t, 2t + 1 of column g.
+__device__ __forceinline__ void mma_bf16_1688_first(float (&d)[4], unsigned a0, unsigned a1,
+                                                    unsigned b) {
+  const float z = 0.f;
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, "
+      "{%7,%7,%7,%7};\n"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a0), "r"(a1), "r"(b), "f"(z));
 }
 
 // round-to-nearest-even pair of floats to packed bf16 (lo in the low half)
@@ -1411,110 +1423,162 @@ __device__ __forceinline__ unsigned tanh_pair_bf16(float lo, float hi) {
   return y;
 }
 
+constexpr unsigned kOneLo = 0x3f80u;  // BF16 pair (1, 0)
+
+// tanh of four accumulator tiles (n-tiles 4q .. 4q + 3 of a layer, this
+// lane's values) as the next layer's A fragments of k-steps 2q (lo) and
+// 2q + 1 (hi).
+__device__ __forceinline__ void tanh_fragments(const float (&acc)[4][4], unsigned (&lo)[4],
+                                               unsigned (&hi)[4]) {
+  lo[0] = tanh_pair_bf16(acc[0][0], acc[0][1]);
+  lo[1] = tanh_pair_bf16(acc[0][2], acc[0][3]);
+  lo[2] = tanh_pair_bf16(acc[1][0], acc[1][1]);
+  lo[3] = tanh_pair_bf16(acc[1][2], acc[1][3]);
+  hi[0] = tanh_pair_bf16(acc[2][0], acc[2][1]);
+  hi[1] = tanh_pair_bf16(acc[2][2], acc[2][3]);
+  hi[2] = tanh_pair_bf16(acc[3][0], acc[3][1]);
+  hi[3] = tanh_pair_bf16(acc[3][2], acc[3][3]);
+}
+
 // Forward pass of one m-tile (16 agents).  im: this lane's first image
 // vector (vector j at im[32 j]).  a0: this lane's A fragment of observation
-// columns 0-15 (rows g and g + 8); a1: of columns 16-31, where only columns
-// 16 and 17 exist (held by the lanes with t = 0), the rest zero.  Returns,
-// for this lane, the greedy action and the 4 logit columns it holds for rows
-// g and g + 8.
+// columns 0-15 (rows g and g + 8); a8lo, a8hi: its m16n8k8 fragment of
+// columns 16-23 for rows g and g + 8, where column 16, 17 is the row's
+// (speed, heading) pair (t = 0), column 18 the constant 1 (t = 1: the word
+// kOneLo) and the rest zero.  Returns, for this lane, the greedy action and
+// the 4 logit columns it holds for rows g and g + 8.
 __device__ __forceinline__ void policy_mtile(const uint4 *__restrict__ im, const unsigned (&a0)[4],
-                                             const unsigned (&a1)[4], int &act_lo, int &act_hi,
-                                             float (&lg)[2][4]) {
+                                             unsigned a8lo, unsigned a8hi, int &act_lo,
+                                             int &act_hi, float (&lg)[2][4]) {
   const int lane = threadIdx.x & 31, t = lane & 3;
-  // layer 1: [16 x 18] x W1^T -> [16 x 64]
-  float acc[8][4];
-  {
-    const uint4 b0 = __ldg(im + 32 * 6), b1 = __ldg(im + 32 * 7);
+  const unsigned one = t == 0 ? kOneLo : 0u;  // column 0 of a bias step: the constant 1
+  // layer 1: [16 x 19] x [W1 | b1]^T, tanh -> [16 x 64], kept as layer 2's A
+  // fragments (h1[k]: columns 16k .. 16k + 15); by halves of 32 columns, so
+  // that the accumulators take 16 registers
+  unsigned h1[4][4];
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const float2 c = bf16x2_float2(u4c(nt < 4 ? b0 : b1, nt & 3));
-      acc[nt][0] = c.x; acc[nt][1] = c.y; acc[nt][2] = c.x; acc[nt][3] = c.y;
+  for (int hf = 0; hf < 2; ++hf) {
+    const uint4 w0 = __ldg(im + 32 * (2 * hf)), w1 = __ldg(im + 32 * (2 * hf + 1));
+    const uint4 w8 = __ldg(im + 32 * (kImgL1K8 / 4 + hf));
+    float acc[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {  // n-tile 4 hf + j
+      const uint4 &w = j < 2 ? w0 : w1;
+      mma_bf16_1688_first(acc[j], a8lo, a8hi, u4c(w8, j));
+      mma_bf16_16816(acc[j], a0, u4c(w, 2 * (j & 1)), u4c(w, 2 * (j & 1) + 1));
     }
-    uint4 w[6];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) w[j] = __ldg(im + 32 * j);
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const int s = 3 * nt;
-      mma_bf16_16816(acc[nt], a0, u4c(w[s / 4], s % 4), u4c(w[(s + 1) / 4], (s + 1) % 4));
-      mma_bf16_16816(acc[nt], a1, u4c(w[(s + 2) / 4], (s + 2) % 4), 0u);
-    }
+    tanh_fragments(acc, h1[2 * hf], h1[2 * hf + 1]);
   }
-  unsigned a2[4][4];
-#pragma unroll
-  for (int kk = 0; kk < 4; ++kk) {
-    a2[kk][0] = tanh_pair_bf16(acc[2 * kk][0], acc[2 * kk][1]);
-    a2[kk][1] = tanh_pair_bf16(acc[2 * kk][2], acc[2 * kk][3]);
-    a2[kk][2] = tanh_pair_bf16(acc[2 * kk + 1][0], acc[2 * kk + 1][1]);
-    a2[kk][3] = tanh_pair_bf16(acc[2 * kk + 1][2], acc[2 * kk + 1][3]);
-  }
-  // layer 2: [16 x 64] x W2^T -> [16 x 64]
-  {
-    const uint4 b0 = __ldg(im + 32 * 24), b1 = __ldg(im + 32 * 25);
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const float2 c = bf16x2_float2(u4c(nt < 4 ? b0 : b1, nt & 3));
-      acc[nt][0] = c.x; acc[nt][1] = c.y; acc[nt][2] = c.x; acc[nt][3] = c.y;
-    }
-  }
-#pragma unroll
-  for (int kk = 0; kk < 4; ++kk) {
-    uint4 w[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) w[j] = __ldg(im + 32 * (8 + 4 * kk + j));
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-      mma_bf16_16816(acc[nt], a2[kk], u4c(w[nt >> 1], 2 * (nt & 1)),
-                     u4c(w[nt >> 1], 2 * (nt & 1) + 1));
-  }
-#pragma unroll
-  for (int kk = 0; kk < 4; ++kk) {
-    a2[kk][0] = tanh_pair_bf16(acc[2 * kk][0], acc[2 * kk][1]);
-    a2[kk][1] = tanh_pair_bf16(acc[2 * kk][2], acc[2 * kk][3]);
-    a2[kk][2] = tanh_pair_bf16(acc[2 * kk + 1][0], acc[2 * kk + 1][1]);
-    a2[kk][3] = tanh_pair_bf16(acc[2 * kk + 1][2], acc[2 * kk + 1][3]);
-  }
-  // layer 3: [16 x 64] x W3^T -> [16 x 16]: 9 logits (columns 9-15 zero)
+  // layer 2: [16 x 64] x W2^T + b2, tanh, by halves of 32 columns; each half
+  // goes straight into layer 3: [16 x 64] x W3^T + b3 -> [16 x 16], the 9
+  // logits (columns 9-15 zero)
   float o[2][4];
   {
-    const uint4 bb = __ldg(im + 32 * 30);
-    const float2 c = bf16x2_float2(bb.x);  // columns 2t, 2t + 1
-    o[0][0] = c.x; o[0][1] = c.y; o[0][2] = c.x; o[0][3] = c.y;
-    const float2 c8 = bf16x2_float2(bb.y);  // column 8 (t = 0), else zero
-    o[1][0] = c8.x; o[1][1] = c8.y; o[1][2] = c8.x; o[1][3] = c8.y;
+    const uint4 bb = __ldg(im + 32 * (kImgB3 / 4));
+    mma_bf16_1688_first(o[0], one, one, bb.x);
+    mma_bf16_1688_first(o[1], one, one, bb.y);
   }
 #pragma unroll
-  for (int kk = 0; kk < 4; ++kk) {
-    const uint4 w = __ldg(im + 32 * (26 + kk));
-    mma_bf16_16816(o[0], a2[kk], w.x, w.y);
-    mma_bf16_16816(o[1], a2[kk], w.z, w.w);
+  for (int hf = 0; hf < 2; ++hf) {
+    float acc[4][4];
+    const uint4 bv = __ldg(im + 32 * (kImgB2 / 4 + hf));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) mma_bf16_1688_first(acc[j], one, one, u4c(bv, j));
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      const uint4 w0 = __ldg(im + 32 * (kImgL2 / 4 + 4 * kk + 2 * hf));
+      const uint4 w1 = __ldg(im + 32 * (kImgL2 / 4 + 4 * kk + 2 * hf + 1));
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint4 &w = j < 2 ? w0 : w1;
+        mma_bf16_16816(acc[j], h1[kk], u4c(w, 2 * (j & 1)), u4c(w, 2 * (j & 1) + 1));
+      }
+    }
+    unsigned h2[2][4];
+    tanh_fragments(acc, h2[0], h2[1]);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const uint4 w = __ldg(im + 32 * (kImgL3 / 4 + 2 * hf + q));
+      mma_bf16_16816(o[0], h2[q], w.x, w.y);
+      mma_bf16_16816(o[1], h2[q], w.z, w.w);
+    }
   }
-  // greedy action per row: this thread holds columns 2t, 2t+1, 8+2t, 9+2t
+  // greedy action per row (largest logit, lowest column on ties; NaN never
+  // chosen): this thread holds columns 2t, 2t + 1 (logits), 8 + 2t (a logit
+  // for t = 0 only) and 9 + 2t (never one).  The row's maximum over the
+  // quad first, then the lowest column that holds it.
+  const float ninf = -__int_as_float(0x7f800000);
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const float v4[4] = {o[0][2 * h], o[0][2 * h + 1], o[1][2 * h], o[1][2 * h + 1]};
-    const int c4[4] = {2 * t, 2 * t + 1, 8 + 2 * t, 9 + 2 * t};
-    float best = -__int_as_float(0x7f800000);
-    int bi = 16;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      lg[h][j] = v4[j];
-      if (c4[j] < 9 && (v4[j] > best || (v4[j] == best && c4[j] < bi))) {
-        best = v4[j];
-        bi = c4[j];
-      }
-    }
-#pragma unroll
-    for (int m = 1; m <= 2; m <<= 1) {
-      const float ob = __shfl_xor_sync(kFull, best, m);
-      const int oi = __shfl_xor_sync(kFull, bi, m);
-      if (ob > best || (ob == best && oi < bi)) {
-        best = ob;
-        bi = oi;
-      }
-    }
+    const float x0 = o[0][2 * h], x1 = o[0][2 * h + 1], x8 = t == 0 ? o[1][2 * h] : ninf;
+    lg[h][0] = x0;
+    lg[h][1] = x1;
+    lg[h][2] = o[1][2 * h];
+    lg[h][3] = o[1][2 * h + 1];
+    float m = fmaxf(fmaxf(x0, x1), x8);
+    m = fmaxf(m, __shfl_xor_sync(kFull, m, 1));
+    m = fmaxf(m, __shfl_xor_sync(kFull, m, 2));
+    int bi = x0 == m ? 2 * t : (x1 == m ? 2 * t + 1 : (t == 0 && x8 == m ? 8 : 16));
+    bi = min(bi, __shfl_xor_sync(kFull, bi, 1));
+    bi = min(bi, __shfl_xor_sync(kFull, bi, 2));
     if (h == 0) act_lo = bi;
     else act_hi = bi;
+  }
+}
+
+// The network on a warp's own A agents, in the neighbour scan's epilogue:
+// their observation rows go from the warp's sector arrays straight into
+// BF16 A fragments (16 rows an m-tile; rows past the warp's nb agents are
+// zero but for the bias column), and the greedy actions and logits go to
+// the agents' rows.  A row is the observation in BF16: (distance, count)
+// per sector, the range for an empty sector, then (speed, heading).  Every
+// lane of the warp takes part (mma.sync); i and ts are this lane's agent
+// and own state as the scan loaded them (lane r < A holds row r).
+template <int A>
+__device__ __forceinline__ void policy_warp_rows(const Inst &I, const DirectArea &W,
+                                                 const Bufs &B, int i, float2 ts, int nb) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int v = I.v;  // 8 (the host runs the network on 8-sector flocks only)
+  const uint4 *im = B.wimg + lane;
+#pragma unroll 1
+  for (int mt = 0; mt < (A + 15) / 16; ++mt) {
+    unsigned f[2][3];
+    int ir[2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const int r = 16 * mt + g + 8 * m;  // < 32: a lane's index
+      ir[m] = __shfl_sync(kFull, i, r);
+      const float sp = __shfl_sync(kFull, ts.y, r), hd = __shfl_sync(kFull, ts.x, r);
+      const bool ok = r < nb;
+      unsigned w0 = 0u, w1 = 0u;
+      if (ok) {
+        const int c0 = W.cn[r * v + t], c1 = W.cn[r * v + 4 + t];
+        w0 = pack_bf16(c0 ? __uint_as_float(W.md[r * v + t]) : I.RV, (float)c0);
+        w1 = pack_bf16(c1 ? __uint_as_float(W.md[r * v + 4 + t]) : I.RV, (float)c1);
+      }
+      f[m][0] = w0;
+      f[m][1] = w1;
+      f[m][2] = t == 0 ? (ok ? pack_bf16(sp, hd) : 0u) : (t == 1 ? kOneLo : 0u);
+    }
+    const unsigned a0[4] = {f[0][0], f[1][0], f[0][1], f[1][1]};
+    int alo = 0, ahi = 0;
+    float lg[2][4];
+    policy_mtile(im, a0, f[0][2], f[1][2], alo, ahi, lg);
+    const int rlo = 16 * mt + g, rhi = rlo + 8;
+    if (t == 0) {
+      if (rlo < nb) B.pact[I.agent_base + ir[0]] = alo;
+      if (rhi < nb) B.pact[I.agent_base + ir[1]] = ahi;
+    }
+    if (B.plogits) {
+      const int c4[4] = {2 * t, 2 * t + 1, 8 + 2 * t, 9 + 2 * t};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (c4[j] < 9) {
+          if (rlo < nb) B.plogits[(long long)(I.agent_base + ir[0]) * 9 + c4[j]] = lg[0][j];
+          if (rhi < nb) B.plogits[(long long)(I.agent_base + ir[1]) * 9 + c4[j]] = lg[1][j];
+        }
+      }
+    }
   }
 }
 
@@ -1530,11 +1594,15 @@ __device__ __forceinline__ void policy_mtile(const uint4 *__restrict__ im, const
 // batched kernels, whose mix of small instances wraps often, run faster with
 // the smaller instruction footprint; a single large instance rarely wraps and
 // runs faster fully unrolled).
-template <int H, int V, bool PIECES = true, int LPA = 1, bool TAG = false, bool COMPACT = false>
+// POLICY: the policy step's network runs in the epilogue on the warp's own
+// agents (policy_warp_rows) and writes their actions and logits.
+template <int H, int V, bool PIECES = true, int LPA = 1, bool TAG = false, bool COMPACT = false,
+          bool POLICY = false>
 __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
                               const DirectArea &W, unsigned &err) {
   static_assert(LPA == 1 || LPA == 2 || LPA == 4 || LPA == 32, "lanes per agent");
   static_assert(!TAG || V == 0, "tag uses the generic sector count");
+  static_assert(!POLICY || !TAG, "the network reads flock observations");
   constexpr int A = 32 / LPA;
   const int lane = threadIdx.x & 31;
   const int slot = lane & (A - 1);
@@ -1701,50 +1769,41 @@ __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, c
     B.coll[I.agent_base + i] = ncoll;
     if ((long long)nin > I.NMAX) err |= FLOCK_ERR_OVERFLOW;
   }
-  // observation rows (and, in the policy step, also the BF16 rows the
-  // network reads, written by every flock kernel form).  The last entry of a flock row, (speed, heading) (layout 1: the
-  // speed), comes from the agent's own lane; the v sector entries of several
-  // rows at a time from all lanes, each row's contiguous.  Tag rows are the
-  // 2v distances.
-  const int P = TAG ? 2 * v : v;  // entries per row from the sector arrays
-  const int rpi = P <= 32 ? 32 / P : 1;
-  const int my_r = P <= 32 ? lane / P : 0, my_e = P <= 32 ? lane % P : lane;
+  // observation rows (when asked for).  The last entry of a flock row,
+  // (speed, heading) (layout 1: the speed), comes from the agent's own lane;
+  // the v sector entries of several rows at a time from all lanes, each
+  // row's contiguous.  Tag rows are the 2v distances.
   float *obs = B.obs ? B.obs + I.obs_base : nullptr;
-  // the V = 8 kernels serve layout 0 only (the host picks V = 0 for layout 1)
-  const bool lay0 = V == 8 || I.obs_layout == 0;
-  if (!TAG && have && lane < A) {
-    const float2 val = make_float2(ts.y, ts.x);
-    if (obs) {
+  if (obs) {
+    const int P = TAG ? 2 * v : v;  // entries per row from the sector arrays
+    const int rpi = P <= 32 ? 32 / P : 1;
+    const int my_r = P <= 32 ? lane / P : 0, my_e = P <= 32 ? lane % P : lane;
+    // the V = 8 kernels serve layout 0 only (the host picks V = 0 for layout 1)
+    const bool lay0 = V == 8 || I.obs_layout == 0;
+    if (!TAG && have && lane < A) {
+      const float2 val = make_float2(ts.y, ts.x);
       float *row = obs + (long long)i * I.obs_dim;
       if (lay0) *reinterpret_cast<float2 *>(row + 2 * v) = val;
       else row[v] = val.x;
     }
-    if (!TAG && B.pobs)
-      B.pobs[(long long)(I.agent_base + i) * kPobsWords + v] = pack_bf16(val.x, val.y);
-  }
-  for (int rb = 0; rb < nb; rb += rpi) {
-    const int r = min(rb + my_r, 31);
-    const int ir = __shfl_sync(kFull, i, r);
-    const bool hr = __shfl_sync(kFull, have, r);  // a ghost's row gets no output
-    if (rb + my_r < nb && my_r < rpi && hr) {
-      for (int e = my_e; e < P; e += 32) {
-        if (TAG) {
+    for (int rb = 0; rb < nb; rb += rpi) {
+      const int r = min(rb + my_r, 31);
+      const int ir = __shfl_sync(kFull, i, r);
+      const bool hr = __shfl_sync(kFull, have, r);  // a ghost's row gets no output
+      if (rb + my_r < nb && my_r < rpi && hr) {
+        for (int e = my_e; e < P; e += 32) {
           const int ck = W.cn[r * vs + e];
-          if (obs)
-            obs[(long long)ir * I.obs_dim + e] = ck ? __uint_as_float(W.md[r * vs + e]) : I.RV;
-          continue;
-        }
-        const int ck = W.cn[r * v + e];
-        const float2 val = make_float2(ck ? __uint_as_float(W.md[r * v + e]) : I.RV, (float)ck);
-        if (obs) {
+          const float d = ck ? __uint_as_float(W.md[r * vs + e]) : I.RV;
           float *row = obs + (long long)ir * I.obs_dim;
-          if (lay0) *reinterpret_cast<float2 *>(row + 2 * e) = val;
-          else row[e] = val.x;  // layout 1: the distance only
+          if (TAG || !lay0) row[e] = d;  // tag: the channel distances; layout 1: the distance only
+          else *reinterpret_cast<float2 *>(row + 2 * e) = make_float2(d, (float)ck);
         }
-        if (!TAG && B.pobs)
-          B.pobs[(long long)(I.agent_base + ir) * kPobsWords + e] = pack_bf16(val.x, val.y);
       }
     }
+  }
+  if (POLICY) {
+    __syncwarp();
+    policy_warp_rows<A>(I, W, B, i, ts, nb);
   }
   __syncwarp();
 }
