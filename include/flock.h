@@ -218,11 +218,11 @@ int flock_gae(int T, int n, const float *reward_dev, const float *value_dev, flo
  * 18 -> 64 -> 64 -> 9 with tanh, as the 18-value observation needs; needs
  * num_segments == 8 and obs_layout 0), then overwrites actions_inout_dev with
  * the greedy actions (largest logit, lowest index on ties) for the next step.
- * The neighbour scan hands the observations to the network as BF16 rows in
- * the workspace (48 bytes per agent, which stay in L2 at these sizes); the
- * binning kernel copies the weights into a lane-interleaved operand image in
- * the workspace (15,872 bytes, rebuilt every call, so weights may change
- * between calls); the network runs in the step's fifth kernel.
+ * The network runs in the neighbour scan's epilogue: each warp feeds its own
+ * agents' observations to it straight from its registers and shared memory
+ * (as BF16), so the step keeps its four kernels.  The binning launch copies
+ * the weights into a lane-interleaved operand image in the workspace (14,848
+ * bytes, rebuilt every call, so weights may change between calls).
  * weights_bf16_dev: 5,961 bfloat16 values, W1[64][18] b1[64] W2[64][64]
  * b2[64] W3[9][64] b3[9], each W row-major [out][in].  Operands are BF16 on
  * the tensor cores, accumulation FP32, tanh the hardware approximation.
