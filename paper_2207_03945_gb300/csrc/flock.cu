@@ -518,6 +518,8 @@ struct flock_env {
   cudaEvent_t ev[5];
   cudaGraphExec_t pgraph;  // step with the policy
   cudaGraphExec_t rgraph;  // a rollout of T steps
+  cudaGraphExec_t hgraph;  // host-buffer step: the step and the copy to mapped buffers
+  const void *h_act, *h_dst[3];
   const void *r_act, *r_obs, *r_rew, *r_coll;
   int r_T, r_cont;
   const void *p_w, *p_act, *p_rew, *p_coll, *p_log, *p_obs;
@@ -986,7 +988,8 @@ extern "C" int env_step_host(flock_env *e, const int32_t *act_h, float *obs_h, f
   // coherently over NVLink-C2C) are read by the binning kernel in place.  The
   // outputs go through the workspace (written in place, their scattered rows
   // crossed the link more slowly than a bulk copy), then to mapped host
-  // buffers by one copy kernel, else by one copy each.
+  // buffers by one copy kernel captured with the step in one graph, else by
+  // one copy each after the step.
   void *da = nullptr;
   if (n > 0 && cudaHostGetDevicePointer(&da, (void *)act_h, 0) == cudaSuccess) {
     act = (const int32_t *)da;
@@ -994,9 +997,13 @@ extern "C" int env_step_host(flock_env *e, const int32_t *act_h, float *obs_h, f
     (void)cudaGetLastError();
     if (n > 0) CK(cudaMemcpyAsync((void *)act, act_h, n * 4, cudaMemcpyHostToDevice, e->stream));
   }
-  int rc = env_step(e, act, obs, rew, coll);
-  if (rc) return rc;
-  if (n > 0) {
+  if (n == 0) {
+    int rc = env_step(e, act, obs, rew, coll);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(e->stream));
+    return FLOCK_OK;
+  }
+  {
     const size_t ob = n * e->inst.obs_dim * 4;
     void *dobs = nullptr, *drew = nullptr, *dcoll = nullptr;
     const bool mapped =
@@ -1016,9 +1023,37 @@ extern "C" int env_step_host(flock_env *e, const int32_t *act_h, float *obs_h, f
       J.bytes[0] = ob;
       J.bytes[1] = n * 4;
       J.bytes[2] = n * 4;
-      CK(launch(true, k_copy_out, e->copy_grid, 256, 0, e->stream, J));
+      // the step and the copy in one graph (the copy under programmatic
+      // dependent launch behind the neighbour scan), kept while the buffers are
+      if (!e->hgraph || e->h_act != act || e->h_dst[0] != dobs || e->h_dst[1] != drew ||
+          e->h_dst[2] != dcoll) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_step(e, e->cap_stream, act, nullptr, obs, rew, coll, 0);
+        cudaError_t le = rc ? cudaSuccess
+                            : launch(true, k_copy_out, e->copy_grid, 256, 0, e->cap_stream, J);
+        cudaError_t ce = cudaStreamEndCapture(e->cap_stream, &g);
+        if (rc || le != cudaSuccess) {
+          if (g) cudaGraphDestroy(g);
+          return rc ? rc : cuda_fail(le, "cudaLaunchKernelEx");
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        ce = install_graph(e->hgraph, g, e->stream);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) {
+          e->h_act = nullptr;  // force a rebuild next time
+          return cuda_fail(ce, "cudaGraphInstantiate");
+        }
+        e->h_act = act;
+        e->h_dst[0] = dobs;
+        e->h_dst[1] = drew;
+        e->h_dst[2] = dcoll;
+      }
+      CK(cudaGraphLaunch(e->hgraph, e->stream));
     } else {
       (void)cudaGetLastError();
+      int rc = env_step(e, act, obs, rew, coll);
+      if (rc) return rc;
       CK(cudaMemcpyAsync(obs_h, obs, ob, cudaMemcpyDeviceToHost, e->stream));
       CK(cudaMemcpyAsync(rew_h, rew, n * 4, cudaMemcpyDeviceToHost, e->stream));
       CK(cudaMemcpyAsync(coll_h, coll, n * 4, cudaMemcpyDeviceToHost, e->stream));
@@ -1098,13 +1133,15 @@ extern "C" int env_set_timing(flock_env *e, int enable) {
   if (!e) return FLOCK_EINVAL;
   if (enable && !e->ev[0])
     for (int k = 0; k < 5; ++k) CK(cudaEventCreate(&e->ev[k]));
-  if ((enable != 0) != (e->timing != 0) && (e->graph || e->pgraph)) {
+  if ((enable != 0) != (e->timing != 0) && (e->graph || e->pgraph || e->hgraph)) {
     CK(cudaStreamSynchronize(e->stream));
-    // re-captured by the next env_step / env_step_policy
+    // re-captured by the next env_step / env_step_policy / env_step_host
     if (e->graph) cudaGraphExecDestroy(e->graph);
     if (e->pgraph) cudaGraphExecDestroy(e->pgraph);
+    if (e->hgraph) cudaGraphExecDestroy(e->hgraph);
     e->graph = nullptr;
     e->pgraph = nullptr;
+    e->hgraph = nullptr;
   }
   e->timing = enable != 0;
   return FLOCK_OK;
@@ -1125,6 +1162,7 @@ extern "C" void env_destroy(flock_env *e) {
   if (e->graph) cudaGraphExecDestroy(e->graph);
   if (e->pgraph) cudaGraphExecDestroy(e->pgraph);
   if (e->rgraph) cudaGraphExecDestroy(e->rgraph);
+  if (e->hgraph) cudaGraphExecDestroy(e->hgraph);
   if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
   delete e;
 }

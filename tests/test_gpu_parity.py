@@ -289,9 +289,10 @@ def test_host_buffer_step_matches_device_step(buffers):
     """Host buffers: page-locked actions are read by the kernels in place
     (mapped host memory) and page-locked outputs written by the copy kernel
     (16-byte stores; 4-byte ones for buffers one element off a 16-byte
-    boundary), pageable ones are copied in and out; the two host steps, then
-    a device step, all match the oracle.  4,999 agents: no buffer is a whole
-    number of 16-byte units."""
+    boundary), captured with the step in one graph that is kept while the
+    buffers are the same; pageable ones are copied in and out; the two host
+    steps, then a device step, all match the oracle.  4,999 agents: no buffer
+    is a whole number of 16-byte units."""
     n = 4999
     side = fi.side_for(n)
     p = fi.default_params(side)
@@ -302,11 +303,16 @@ def test_host_buffer_step_matches_device_step(buffers):
     o, _ = oracle_run(p, st0, acts)
     k = 1 if buffers == "pinned_offset" else 0
     for t in range(2):
-        if buffers != "pageable":
+        # "pinned": the same buffers both times (the step's graph is kept);
+        # "pinned_offset": new buffers each time (the graph is captured again)
+        if buffers != "pageable" and (t == 0 or buffers == "pinned_offset"):
             obs_h = torch.empty(n * 18 + k, dtype=torch.float32).pin_memory()[k:].view(n, 18)
             rew_h = torch.empty(n + k, dtype=torch.float32).pin_memory()[k:]
             coll_h = torch.empty(n + k, dtype=torch.int32).pin_memory()[k:]
-            act_h = torch.from_numpy(acts[t]).pin_memory()
+            act_h = torch.empty(n, dtype=torch.int32).pin_memory()
+        if buffers != "pageable":
+            act_h.copy_(torch.from_numpy(acts[t]))
+            obs_h.fill_(-1.0)
             if t == 0:
                 F.env_step_host(env.env, act_h, obs_h, rew_h, coll_h)
             else:  # the same call through buffers bound once
