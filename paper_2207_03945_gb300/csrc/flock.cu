@@ -114,13 +114,15 @@ __global__ void k_neighbours(const Inst *__restrict__ gI, Bufs B) {
   if (err) atomicOr(B.err, err);
 }
 
-// LPA lanes per agent: each warp takes 32 / LPA consecutive sorted agents.
-// TAG: the tag environment (two colour channels of sectors).  COMPACT: the
+// LPA lanes per agent: each warp takes 32 / LPA consecutive sorted agents
+// (AORDER: consecutive agents in agent order, their observation rows written
+// as one block; the host-buffer step's form, whose outputs are in mapped host
+// memory).  TAG: the tag environment (two colour channels of sectors).  COMPACT: the
 // runs across the square's edges walked by one loop instead of nine inlined
 // copies (a warp per agent with a wide view: the paper's flock 126.7 us a
 // step against 141.3, tag 152.2 against 181.5, from fewer instruction-fetch
 // stalls; with few candidates, 1,000 agents, the inlined runs are faster).
-template <int H, int V, int LPA, bool TAG = false, bool COMPACT = false>
+template <int H, int V, int LPA, bool TAG = false, bool COMPACT = false, bool AORDER = false>
 __global__ void k_neighbours_direct(const Inst *__restrict__ gI, Bufs B) {
   extern __shared__ __align__(16) char smem[];
   __shared__ Inst sI;
@@ -134,7 +136,8 @@ __global__ void k_neighbours_direct(const Inst *__restrict__ gI, Bufs B) {
   if (gp0 < sI.n) {
     const int vs = TAG ? 2 * sI.v : sI.v;
     const DirectArea W = direct_area(smem + (size_t)warp * direct_warp_bytes(vs, A), vs, A);
-    phaseD_direct<H, V, true, LPA, TAG, COMPACT>(sI, gp0, min(gp0 + A, sI.n), B, W, err);
+    phaseD_direct<H, V, true, LPA, TAG, COMPACT, false, AORDER>(sI, gp0, min(gp0 + A, sI.n), B, W,
+                                                                 err);
   }
   if (err) atomicOr(B.err, err);
 }
@@ -449,7 +452,10 @@ cudaError_t set_kernel_attrs() {
                          (const void *)k_neighbours_policy<1, 8, 4>,
                          (const void *)k_neighbours_policy<2, 8, 4>,
                          (const void *)k_neighbours_policy<1, 0, 32>,
-                         (const void *)k_neighbours_policy<2, 0, 32>};
+                         (const void *)k_neighbours_policy<2, 0, 32>,
+                         (const void *)k_neighbours_direct<1, 8, 1, false, false, true>,
+                         (const void *)k_neighbours_direct<1, 8, 2, false, false, true>,
+                         (const void *)k_neighbours_direct<1, 8, 4, false, false, true>};
     for (const void *f : fns)
       if (g_attr_err == cudaSuccess) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
@@ -692,7 +698,7 @@ extern "C" int env_create(const flock_params *p, const flock_tuning *t, int n, v
 static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const float2 *cact,
                         float *obs, float *rew, int32_t *coll, int reset, int n_run = -1,
                         const unsigned short *wblob = nullptr, int32_t *pact = nullptr,
-                        float *plogits = nullptr) {
+                        float *plogits = nullptr, bool aorder = false) {
   Bufs B = e->bufs;
   B.actions = act;
   B.cactions = cact;
@@ -740,7 +746,7 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const 
   if (n > 0) {
     const int blk = e->tuning.block;
     const size_t sm = e->smemD;
-    if (e->tuning.mode == 1 && !pact) {
+    if (e->tuning.mode == 1 && !pact && !aorder) {
       const int tiles = e->inst.tiles_x * e->inst.tiles_y;
       if (e->inst.halo == 1) CK(launch(pdl, k_neighbours<1>, tiles, blk, sm, s, gI, B));
       else CK(launch(pdl, k_neighbours<2>, tiles, blk, sm, s, gI, B));
@@ -780,7 +786,13 @@ static int enqueue_step(flock_env *e, cudaStream_t s, const int32_t *act, const 
            k_neighbours_policy<1, 8, 4>, k_neighbours_policy<1, 0, 32>},
           {k_neighbours_policy<2, 8, 1>, k_neighbours_policy<2, 8, 2>,
            k_neighbours_policy<2, 8, 4>, k_neighbours_policy<2, 0, 32>}};
+      // agent order (host-buffer step; 3 x 3 cells, 8 sectors, layout 0, 1-4
+      // lanes: the caller checks)
+      static const KD ka[3] = {k_neighbours_direct<1, 8, 1, false, false, true>,
+                               k_neighbours_direct<1, 8, 2, false, false, true>,
+                               k_neighbours_direct<1, 8, 4, false, false, true>};
       const KD k = pact ? kp[h][li]
+                   : aorder ? ka[li < 3 ? li : 0]
                    : (lpa == 32 && e->wide) ? kc[h][e->inst.kind == 1 ? 1 : 0]
                    : (e->inst.kind == 1 ? kt[h][li] : kd[h][v8][li]);
       CK(launch(pdl, k, blocks, blk, sm, s, gI, B));
@@ -1023,15 +1035,23 @@ extern "C" int env_step_host(flock_env *e, const int32_t *act_h, float *obs_h, f
       J.bytes[0] = ob;
       J.bytes[1] = n * 4;
       J.bytes[2] = n * 4;
-      // the step and the copy in one graph (the copy under programmatic
-      // dependent launch behind the neighbour scan), kept while the buffers are
+      // One graph, kept while the buffers are the same.  The 8-sector flock
+      // with 1-4 lanes per agent runs its neighbour scan in agent order and
+      // writes the outputs straight into the mapped buffers, whole blocks of
+      // rows at a time, while other warps still compute; otherwise the step
+      // writes the workspace and the copy kernel follows it (under
+      // programmatic dependent launch).
+      const bool ao = e->inst.kind == 0 && e->inst.halo == 1 && e->inst.v == 8 &&
+                      e->inst.obs_layout == 0 && e->tuning.lanes != 32;
       if (!e->hgraph || e->h_act != act || e->h_dst[0] != dobs || e->h_dst[1] != drew ||
           e->h_dst[2] != dcoll) {
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
-        int rc = enqueue_step(e, e->cap_stream, act, nullptr, obs, rew, coll, 0);
-        cudaError_t le = rc ? cudaSuccess
-                            : launch(true, k_copy_out, e->copy_grid, 256, 0, e->cap_stream, J);
+        int rc = ao ? enqueue_step(e, e->cap_stream, act, nullptr, (float *)dobs, (float *)drew,
+                                   (int32_t *)dcoll, 0, -1, nullptr, nullptr, nullptr, true)
+                    : enqueue_step(e, e->cap_stream, act, nullptr, obs, rew, coll, 0);
+        cudaError_t le = rc || ao ? cudaSuccess
+                                  : launch(true, k_copy_out, e->copy_grid, 256, 0, e->cap_stream, J);
         cudaError_t ce = cudaStreamEndCapture(e->cap_stream, &g);
         if (rc || le != cudaSuccess) {
           if (g) cudaGraphDestroy(g);

@@ -1596,13 +1596,23 @@ __device__ __forceinline__ void policy_warp_rows(const Inst &I, const DirectArea
 // runs faster fully unrolled).
 // POLICY: the policy step's network runs in the epilogue on the warp's own
 // agents (policy_warp_rows) and writes their actions and logits.
+// AORDER: [gp0, gp1) are agent indices (flattened), not sorted positions:
+// the warp's agents are consecutive in agent order, so that its observation
+// rows form one contiguous block, which the warp assembles in its queue area
+// and writes with 16-byte stores (the form for outputs in mapped host
+// memory, where scattered rows cross the link slowly).  An agent's own
+// position is read from its state row, and its sorted position (the
+// candidate that is itself) from its cell and rank.  Flock, 8 sectors,
+// layout 0, at most 32 rows of 72 bytes (the queue holds 2,560).
 template <int H, int V, bool PIECES = true, int LPA = 1, bool TAG = false, bool COMPACT = false,
-          bool POLICY = false>
+          bool POLICY = false, bool AORDER = false>
 __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, const Bufs &B,
                               const DirectArea &W, unsigned &err) {
   static_assert(LPA == 1 || LPA == 2 || LPA == 4 || LPA == 32, "lanes per agent");
   static_assert(!TAG || V == 0, "tag uses the generic sector count");
   static_assert(!POLICY || !TAG, "the network reads flock observations");
+  static_assert(!AORDER || (V == 8 && !TAG && !POLICY && LPA != 32 && (32 / LPA) * 72 <= kQueueWide * 16),
+                "agent-order rows: 8-sector flock rows staged in the queue area");
   constexpr int A = 32 / LPA;
   const int lane = threadIdx.x & 31;
   const int slot = lane & (A - 1);
@@ -1615,8 +1625,22 @@ __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, c
   const int nb = gp1 - gp0;
   float xi = 0.f, yi = 0.f;
   float2 ts = make_float2(0.f, 0.f);
-  int i = 0, cx = 0, cy = 0;
-  if (have && dbg_ok(gp >= 0 && gp < B.n_total)) {
+  int i = 0, cx = 0, cy = 0, sp = -1;
+  if (AORDER) {
+    if (have && dbg_ok(gp >= 0 && gp < B.n_total)) {
+      i = gp - I.agent_base;
+      if (!dbg_ok(i >= 0 && i < I.n)) i = 0;
+      const float4 s4 = I.state[i];  // the new position, heading and speed
+      xi = s4.x;
+      yi = s4.y;
+      ts = make_float2(s4.z, s4.w);
+      cx = cell_of(xi, I);
+      cy = cell_of(yi, I);
+      const int2 cr = B.cellrank[gp];
+      if (dbg_ok(cr.x >= 0 && cr.x < B.c_total)) sp = B.cell_start[cr.x] + cr.y;
+    }
+  } else if (have && dbg_ok(gp >= 0 && gp < B.n_total)) {
+    sp = gp;
     const float2 p = B.sxy[gp];
     xi = p.x;
     yi = p.y;
@@ -1678,7 +1702,7 @@ __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, c
   __syncwarp();
   int qn = 0;
   // the agent's own sorted position: its candidate scan skips it
-  const int self = have ? gp : -1;
+  const int self = have ? sp : -1;
   if (!wrap_any) {
 #pragma unroll
     for (int r = 0; r < 2 * H + 1; ++r)
@@ -1774,7 +1798,34 @@ __device__ __forceinline__ void phaseD_direct(const Inst &I, int gp0, int gp1, c
   // the v sector entries of several rows at a time from all lanes, each
   // row's contiguous.  Tag rows are the 2v distances.
   float *obs = B.obs ? B.obs + I.obs_base : nullptr;
-  if (obs) {
+  if (AORDER && obs) {
+    // the warp's nb rows are contiguous from agent i0: assembled in the queue
+    // area (free after the final drain), then stored 16 bytes at a time
+    __syncwarp();  // the drain's last reads of the queue and writes of the sectors
+    const int i0 = gp0 - I.agent_base;
+    float *stage = reinterpret_cast<float *>(W.queue);
+    for (int t = lane; t < nb * 16; t += 32) {
+      const int r = t >> 4, e = (t & 15) >> 1;
+      const int ck = W.cn[r * 8 + e];
+      stage[r * 18 + (t & 15)] =
+          (t & 1) ? (float)ck : (ck ? __uint_as_float(W.md[r * 8 + e]) : I.RV);
+    }
+    if (have && lane < A) {
+      stage[slot * 18 + 16] = ts.y;
+      stage[slot * 18 + 17] = ts.x;
+    }
+    __syncwarp();
+    float *dst = obs + (long long)i0 * 18;
+    const int words = nb * 18;
+    int done = 0;
+    if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+      const float4 *s4 = reinterpret_cast<const float4 *>(stage);
+      float4 *d4 = reinterpret_cast<float4 *>(dst);
+      for (int t = lane; t < words / 4; t += 32) d4[t] = s4[t];
+      done = words & ~3;
+    }
+    for (int t = done + lane; t < words; t += 32) dst[t] = stage[t];
+  } else if (obs) {
     const int P = TAG ? 2 * v : v;  // entries per row from the sector arrays
     const int rpi = P <= 32 ? 32 / P : 1;
     const int my_r = P <= 32 ? lane / P : 0, my_e = P <= 32 ? lane % P : lane;

@@ -333,6 +333,43 @@ def test_host_buffer_step_matches_device_step(buffers):
     env.close()
 
 
+@pytest.mark.parametrize("tuning", [None, {"lanes": 1}, {"lanes": 2}, {"lanes": 4},
+                                    {"lanes": 32}, {"stencil": 2}])
+def test_host_buffer_step_forms_match_device_step(tuning):
+    """The host-buffer step with page-locked buffers runs the neighbour scan
+    in agent order and writes the outputs straight into the mapped buffers
+    (3 x 3 cells, 1-4 lanes per agent), or steps in the workspace and copies
+    (32 lanes, 5 x 5 cells): either way the same bits as the device step, over
+    three steps with the buffers kept (the graph reused).  20,001 agents: the
+    last warp's block of rows is partial and of odd length."""
+    n = 20001
+    side = fi.side_for(n)
+    p = fi.default_params(side)
+    st0 = fi.initial_state(n, side, 31)
+    acts = fi.random_actions(n, 3, 31)
+    dev_env = F.FlockEnv(p, n, device=DEV, tuning=tuning)
+    host_env = F.FlockEnv(p, n, device=DEV, tuning=tuning)
+    dev_env.reset(torch.from_numpy(st0).to(DEV))
+    host_env.reset(torch.from_numpy(st0).to(DEV))
+    obs_h = torch.empty((n, 18), dtype=torch.float32).pin_memory()
+    rew_h = torch.empty(n, dtype=torch.float32).pin_memory()
+    coll_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    act_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    step = F.env_step_host_bind(host_env.env, act_h, obs_h, rew_h, coll_h)
+    for t in range(3):
+        obs, rew, coll = dev_env.step(torch.from_numpy(acts[t]).to(DEV))
+        act_h.copy_(torch.from_numpy(acts[t]))
+        obs_h.fill_(-1.0)
+        step()
+        assert torch.equal(obs_h, obs.cpu()), (tuning, t)
+        assert torch.equal(rew_h, rew.cpu()), (tuning, t)
+        assert torch.equal(coll_h, coll.cpu()), (tuning, t)
+        assert torch.equal(host_env.state(), dev_env.state()), (tuning, t)
+    assert host_env.error() == 0 and dev_env.error() == 0
+    dev_env.close()
+    host_env.close()
+
+
 def test_statistics_at_benchmark_density():
     """Sanity at 100,000 agents: mean in-range neighbours rho*pi*d_v^2 = 7.854,
     collisions rho*pi*(2 d_r)^2 = 0.314 (Poisson, well within 10 sigma)."""
