@@ -879,8 +879,9 @@ def main():
     e2e = {"value": world * n * e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": n * 4, "d2h_bytes_per_step": n * (env.obs_dim + 2) * 4,
            "call": "env_step_host through env_step_host_bind (pinned host buffers: the "
-                   "actions read in place over NVLink-C2C, the outputs copied out by one "
-                   "kernel; synchronous)"}
+                   "actions read in place over NVLink-C2C, the outputs written into the "
+                   "mapped buffers by the neighbour scan in agent order; one graph; "
+                   "synchronous)"}
 
     batched = batch_of_one = None
     if not args.no_batched:

@@ -235,9 +235,13 @@ int env_step_policy(flock_env *env, const uint16_t *weights_bf16_dev, int32_t *a
  * the outputs are in the host buffers.  Page-locked, mapped actions
  * (cudaHostAlloc / pinned tensors; the GPU reaches them coherently over
  * NVLink-C2C on Grace-Blackwell) are read by the step's first kernel in
- * place, others are copied in.  The outputs are written to the workspace,
- * then copied out: to page-locked, mapped output buffers by one copy kernel,
- * to others by one copy per buffer. */
+ * place, others are copied in.  Page-locked, mapped output buffers of a
+ * flock with 8 sectors, observation layout 0, the 3 x 3 stencil and 1-4
+ * lanes per agent are written by the neighbour scan itself, run in agent
+ * order so that each warp stores its block of rows whole; other page-locked
+ * outputs are written to the workspace and copied out by one copy kernel;
+ * pageable ones by one copy per buffer.  The step (and its copy) is one CUDA
+ * graph, kept while the buffers are the same. */
 int env_step_host(flock_env *env, const int32_t *actions_host, float *obs_host,
                   float *reward_host, int32_t *coll_host);
 

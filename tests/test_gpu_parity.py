@@ -333,16 +333,17 @@ def test_host_buffer_step_matches_device_step(buffers):
     env.close()
 
 
-@pytest.mark.parametrize("tuning", [None, {"lanes": 1}, {"lanes": 2}, {"lanes": 4},
-                                    {"lanes": 32}, {"stencil": 2}])
-def test_host_buffer_step_forms_match_device_step(tuning):
+@pytest.mark.parametrize("n,tuning", [(20001, None), (20001, {"lanes": 1}), (20001, {"mode": 1}),
+                                      (20001, {"lanes": 32}), (20001, {"stencil": 2}),
+                                      (150001, {"lanes": 1}), (150001, {"lanes": 2})])
+def test_host_buffer_step_forms_match_device_step(n, tuning):
     """The host-buffer step with page-locked buffers runs the neighbour scan
     in agent order and writes the outputs straight into the mapped buffers
-    (3 x 3 cells, 1-4 lanes per agent), or steps in the workspace and copies
-    (32 lanes, 5 x 5 cells): either way the same bits as the device step, over
-    three steps with the buffers kept (the graph reused).  20,001 agents: the
-    last warp's block of rows is partial and of odd length."""
-    n = 20001
+    (3 x 3 cells, 4 lanes per agent up to 100,000 agents, else the tuning's
+    1 or 2), or steps in the workspace and copies (32 lanes, 5 x 5 cells):
+    either way the same bits as the device step, over three steps with the
+    buffers kept (the graph reused).  20,001 and 150,001 agents: the last
+    warp's block of rows is partial and of odd length."""
     side = fi.side_for(n)
     p = fi.default_params(side)
     st0 = fi.initial_state(n, side, 31)
