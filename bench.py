@@ -706,6 +706,50 @@ def device_initial_state(dev):
     return fn
 
 
+def bare_set_rate(dev, sessions, max_instances, max_agents, max_cells, steps=100, warmup=5):
+    """Agent-steps/s of the batched kernels alone on the given serving
+    sessions' instances: one batch of them with the serving loop's capacities
+    and default launch shape, uniform random actions drawn on the device each
+    step as the loop draws them, `steps` steps back to back timed with CUDA
+    events."""
+    import torch
+    import paper_2207_03945_gb300 as F
+    sizes = [s.n for s in sessions]
+    params = [s.params for s in sessions]
+    total = sum(sizes)
+    cells = sum(F.flock_instance_cells(p) for p in params)
+    b = F.FlockBatch(max_instances, max_agents, max_cells, 18, device=dev)
+    init = device_initial_state(dev)
+    arena = torch.empty((total, 4), dtype=torch.float32, device=dev)
+    views, off = [], 0
+    for s_ in sessions:
+        arena[off:off + s_.n] = init(s_)
+        views.append(arena[off:off + s_.n])
+        off += s_.n
+    b.set(params, sizes, views, reset=[1] * len(sizes))
+    acts = torch.empty(total, dtype=torch.int32, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(12345)
+    for _ in range(warmup):
+        acts.random_(0, 9, generator=gen)
+        b.step(acts)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        acts.random_(0, 9, generator=gen)
+        b.step(acts)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    err = b.error()
+    assert err == 0, "device error bits %d" % err
+    b.close()
+    return {"agent_steps_per_s": total * steps / (ms * 1e-3), "agents": total,
+            "instances": len(sizes), "ms_per_step": ms / steps, "steps": steps}
+
+
 def run_serving(dev, seconds, seed=0, rate=50.0, budget=100 * 10 ** 9, backlog=0, rank=0,
                 world=1):
     """Serving loop with continuous batching: Poisson session arrivals, agent
@@ -728,13 +772,21 @@ def run_serving(dev, seconds, seed=0, rate=50.0, budget=100 * 10 ** 9, backlog=0
     if world > 1:
         ranks = serve.place_sessions(arrivals, world)
         arrivals = [a for a, r in zip(arrivals, ranks) if r == rank]
-    srv = serve.FlockServer(budget, state_fn=device_initial_state(dev),
-                            max_slots=512, arena_agents=8_000_000, max_cells=4_000_000,
-                            device=dev)
+    caps = {"max_slots": 512, "arena_agents": 8_000_000, "max_cells": 4_000_000}
+    srv = serve.FlockServer(budget, state_fn=device_initial_state(dev), device=dev, **caps)
     st = srv.run(arrivals, duration=seconds)
     err = srv.batch.error()
     assert err == 0, "device error bits %d" % err
+    active = list(srv.sched.active)
     srv.close()
+    if backlog and active:
+        # the sessions running at the end, stepped by the batch alone (same
+        # instances, same default launch shape, actions drawn the same way,
+        # steps back to back): the serving loop's cost over the bare kernels
+        bare = bare_set_rate(dev, active, caps["max_slots"], caps["arena_agents"],
+                             caps["max_cells"])
+        st["bare_same_set"] = bare
+        st["vs_bare_same_set"] = st["agent_steps_per_s"] / bare["agent_steps_per_s"]
     if world > 1:
         wall = max_over_ranks(st["wall_s"], dev)
         st["agent_steps_per_s"] = sum_over_ranks(st["agent_steps"], dev) / wall
