@@ -3,7 +3,8 @@ with index checks on their scratch and output accesses, each failed check
 latching FLOCK_ERR_BOUNDS instead of trapping.  Small cases of every launch
 form (single environment: shared-memory tiles, the direct form with 1, 4 and
 32 lanes per agent, both stencils, wrapping squares, a dense cluster, tag;
-the batch in all three forms; the allocation-free step) must give the
+the policy step's scan with the network; the host-buffer step's agent-order
+scan; the batch in all three forms; the allocation-free step) must give the
 oracle's bits with no error bit latched."""
 import numpy as np
 import pytest
@@ -153,3 +154,64 @@ def test_debug_build_static_step(debug_lib):
     _, o, r, c, _ = oracle.step(p, st0, a, threads=0)
     assert np.array_equal(obs.cpu().numpy(), o) and np.array_equal(rew.cpu().numpy(), r)
     assert np.array_equal(coll.cpu().numpy(), c)
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 32])
+def test_debug_build_policy_step(debug_lib, lanes):
+    """The policy step's scan with the network in its epilogue: the
+    environment part gives the oracle's bits, the greedy actions are the
+    argmax of the step's own logits, and no bit is latched."""
+    n = 3000
+    side = fi.side_for(n)
+    p = fi.default_params(side)
+    st0 = fi.initial_state(n, side, 41)
+    a0 = fi.random_actions(n, 1, 41)[0]
+    w = fi.policy_weights(6)
+    blob = torch.from_numpy(w["blob"].view(np.int16)).to(DEV)
+    env = F.FlockEnv(p, n, device=DEV, tuning={"mode": 2, "lanes": lanes})
+    env.reset(torch.from_numpy(st0).to(DEV))
+    act = torch.from_numpy(a0).to(DEV)
+    rew = torch.empty(n, dtype=torch.float32, device=DEV)
+    coll = torch.empty(n, dtype=torch.int32, device=DEV)
+    logits = torch.empty((n, 9), dtype=torch.float32, device=DEV)
+    obs = torch.empty((n, 18), dtype=torch.float32, device=DEV)
+    F.env_step_policy(env.env, blob, act, rew, coll, logits, obs)
+    torch.cuda.synchronize()
+    st, o, r, c, _ = oracle.step(p, st0, a0, threads=0)
+    assert np.array_equal(obs.cpu().numpy(), o) and np.array_equal(rew.cpu().numpy(), r)
+    assert np.array_equal(coll.cpu().numpy(), c)
+    assert np.array_equal(env.state().cpu().numpy(), st)
+    assert np.array_equal(act.cpu().numpy(), np.argmax(logits.cpu().numpy(), axis=1))
+    assert env.error() == 0, "latched bits"
+    env.close()
+
+
+@pytest.mark.parametrize("n,tuning", [(3001, {"mode": 2, "lanes": 4}),
+                                      (120001, {"mode": 2, "lanes": 1})])
+def test_debug_build_host_step_agent_order(debug_lib, n, tuning):
+    """The host-buffer step with page-locked buffers (the neighbour scan in
+    agent order writing the mapped buffers): the oracle's bits, no bit
+    latched.  3,001 agents with 4 lanes per agent; 120,001 with the tuning's
+    one lane (past 100,000 agents the agent-order form keeps it)."""
+    side = fi.side_for(n)
+    p = fi.default_params(side)
+    st0 = fi.initial_state(n, side, 43)
+    a = fi.random_actions(n, 1, 43)[0]
+    env = F.FlockEnv(p, n, device=DEV, tuning=tuning)
+    env.reset(torch.from_numpy(st0).to(DEV))
+    obs_h = torch.empty((n, 18), dtype=torch.float32).pin_memory()
+    rew_h = torch.empty(n, dtype=torch.float32).pin_memory()
+    coll_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    act_h = torch.from_numpy(a).pin_memory()
+    F.env_step_host(env.env, act_h, obs_h, rew_h, coll_h)
+    ref = F.FlockEnv(p, n, device=DEV, tuning=tuning)
+    ref.reset(torch.from_numpy(st0).to(DEV))
+    o, r, c = (x.cpu().numpy() for x in ref.step(torch.from_numpy(a).to(DEV)))
+    if n <= 5000:  # small enough for the oracle too
+        _, o2, r2, c2, _ = oracle.step(p, st0, a, threads=0)
+        assert np.array_equal(o, o2) and np.array_equal(r, r2) and np.array_equal(c, c2)
+    assert np.array_equal(obs_h.numpy(), o) and np.array_equal(rew_h.numpy(), r)
+    assert np.array_equal(coll_h.numpy(), c)
+    assert env.error() == 0 and ref.error() == 0, "latched bits"
+    env.close()
+    ref.close()
