@@ -2,7 +2,8 @@
 outputs and (for a batch) the instance states live inside larger device
 allocations whose margins hold a fixed byte pattern.  After resets and steps
 of single environments (discrete and continuous actions, a ragged agent
-count) and of batches in all three launch forms, every margin is unchanged: no
+count, the policy step, the host-buffer step writing page-locked host
+buffers) and of batches in all three launch forms, every margin is unchanged: no
 write lands outside the buffers handed over through the C ABI.  (An
 out-of-bounds check that needs no sanitizer; nothing here can fault.)"""
 import numpy as np
@@ -25,11 +26,15 @@ PATTERN = 0xA5
 
 
 class Guarded:
-    """nbytes of device memory with PAD guard bytes on each side."""
+    """nbytes of device memory (host=True: page-locked host memory) with PAD
+    guard bytes on each side."""
 
-    def __init__(self, nbytes):
+    def __init__(self, nbytes, host=False):
         self.nbytes = int(nbytes)
-        self.buf = torch.full((self.nbytes + 2 * PAD,), PATTERN, dtype=torch.uint8, device=DEV)
+        if host:
+            self.buf = torch.full((self.nbytes + 2 * PAD,), PATTERN, dtype=torch.uint8).pin_memory()
+        else:
+            self.buf = torch.full((self.nbytes + 2 * PAD,), PATTERN, dtype=torch.uint8, device=DEV)
         self.inner = self.buf[PAD:PAD + self.nbytes]
 
     def as_(self, dtype, shape):
@@ -100,4 +105,54 @@ def test_batch_writes_stay_inside_its_buffers(mode):
     assert F.env_batch_get_error(b) == 0
     F.env_batch_destroy(b)
     for g in (ws, ga, go, gr, gc):
+        assert g.intact()
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 32])
+def test_policy_step_writes_stay_inside_its_buffers(lanes):
+    n = 4999
+    p = fi.default_params(fi.side_for(n))
+    ws = Guarded(F.flock_workspace_bytes(p, n, {"lanes": lanes}))
+    ga, gr, gc, gl, go = (Guarded(n * 4), Guarded(n * 4), Guarded(n * 4), Guarded(n * 36),
+                          Guarded(n * 72))
+    act = ga.as_(torch.int32, (n,))
+    act.copy_(torch.from_numpy(fi.random_actions(n, 1, 35)[0]))
+    rew, coll = gr.as_(torch.float32, (n,)), gc.as_(torch.int32, (n,))
+    logits, obs = gl.as_(torch.float32, (n, 9)), go.as_(torch.float32, (n, 18))
+    w = fi.policy_weights(7)
+    blob = torch.from_numpy(w["blob"].view(np.int16)).to(DEV)
+    env = F.env_create(p, n, ws.inner, tuning={"lanes": lanes})
+    F.env_reset(env, torch.from_numpy(fi.initial_state(n, p["side"], 35)).to(DEV), obs, rew, coll)
+    for _ in range(3):
+        F.env_step_policy(env, blob, act, rew, coll, logits, obs)
+    torch.cuda.synchronize()
+    assert F.env_get_error(env) == 0
+    F.env_destroy(env)
+    for g in (ws, ga, gr, gc, gl, go):
+        assert g.intact()
+
+
+@pytest.mark.parametrize("n,tuning", [(4999, None), (4999, {"lanes": 32}), (120001, {"lanes": 1})])
+def test_host_step_writes_stay_inside_its_host_buffers(n, tuning):
+    """Page-locked host buffers with margins: the agent-order scan (or, with
+    32 lanes, the copy kernel) writes only the rows it is given."""
+    p = fi.default_params(fi.side_for(n))
+    ws = Guarded(F.flock_workspace_bytes(p, n, tuning))
+    go, gr, gc = Guarded(n * 72, True), Guarded(n * 4, True), Guarded(n * 4, True)
+    ga = Guarded(n * 4, True)
+    obs, rew = go.as_(torch.float32, (n, 18)), gr.as_(torch.float32, (n,))
+    coll, act = gc.as_(torch.int32, (n,)), ga.as_(torch.int32, (n,))
+    env = F.env_create(p, n, ws.inner, tuning=tuning)
+    dobs = torch.empty((n, 18), dtype=torch.float32, device=DEV)
+    drew = torch.empty(n, dtype=torch.float32, device=DEV)
+    dcoll = torch.empty(n, dtype=torch.int32, device=DEV)
+    F.env_reset(env, torch.from_numpy(fi.initial_state(n, p["side"], 37)).to(DEV), dobs, drew,
+                dcoll)
+    acts = fi.random_actions(n, 2, 37)
+    for t in range(2):
+        act.copy_(torch.from_numpy(acts[t]))
+        F.env_step_host(env, act, obs, rew, coll)
+    assert F.env_get_error(env) == 0
+    F.env_destroy(env)
+    for g in (ws, go, gr, gc, ga):
         assert g.intact()
