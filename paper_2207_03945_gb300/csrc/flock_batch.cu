@@ -91,13 +91,35 @@ __device__ __forceinline__ int find_inst(const int *pre, int n, int x) {
   return lo;
 }
 
+// The same search by the 32 lanes of a warp together (x the same in every
+// lane, n >= 1): each round the lanes load 32 evenly spaced entries of the
+// range still open, and the last lane whose entry is <= x narrows it to its
+// stretch, so that 1,024 instances take two dependent loads instead of ten.
+// pre is nondecreasing and pre[0] = 0 <= x, so lane 0 always qualifies.
+__device__ __forceinline__ int warp_find_inst(const int *pre, int n, int x) {
+  const int lane = threadIdx.x & 31;
+  int lo = 0, hi = n;  // the answer is in [lo, hi); pre[lo] <= x
+  while (hi - lo > 1) {
+    const int step = (hi - lo + 31) >> 5;
+    const int idx = lo + lane * step;
+    const bool ok = idx < hi && __ldg(pre + idx) <= x;
+    const unsigned m = __ballot_sync(0xffffffffu, ok);
+    lo += (31 - __clz(m)) * step;
+    hi = min(lo + step, hi);
+  }
+  return lo;
+}
+
 // Instance of each thread's agent f for a block whose agents start at f0:
-// one thread binary-searches f0's instance and the block shares it; each
+// the first warp searches f0's instance and the block shares it; each
 // thread then walks forward from there (a block's agents span few
-// instances).  pre[n] is the total.
+// instances).  pre[n] is the total.  Blocks of at least 32 threads.
 __device__ __forceinline__ int block_inst(const int *pre, int n, int f0, int f, int *sh) {
   __syncthreads();
-  if (threadIdx.x == 0) *sh = find_inst(pre, n, f0);
+  if (threadIdx.x < 32) {
+    const int k = warp_find_inst(pre, n, f0);
+    if (threadIdx.x == 0) *sh = k;
+  }
   __syncthreads();
   int k = *sh;
   while (k + 1 < n && __ldg(pre + k + 1) <= f) ++k;
@@ -160,7 +182,7 @@ __global__ void __launch_bounds__(kBatchBlock, SPLIT ? 6 : 1) k_batch_step(const
       if (lane == 0) c = (int)atomicAdd(&ctr[kCtrTicket], 1u);
       c = __shfl_sync(kFull, c, 0);
       if (c >= D.n_chunks) break;
-      const int k = find_inst(cpre, D.n_inst, c);
+      const int k = warp_find_inst(cpre, D.n_inst, c);
       if (k != cur) {
         const int *src = reinterpret_cast<const int *>(insts + k);
         int *dst = reinterpret_cast<int *>(&sI);
@@ -303,7 +325,7 @@ __device__ __forceinline__ void batch_neigh(const BatchDev *__restrict__ d, Inst
   while (c < D.n_chunks) {
     int nxt = 0;
     if (lane == 0) nxt = nw + (int)atomicAdd(&ctr[kCtrTicket], 1u);
-    const int k = find_inst(cpre, D.n_inst, c);
+    const int k = warp_find_inst(cpre, D.n_inst, c);
     if (k != cur) {
       const int *src = reinterpret_cast<const int *>(insts + k);
       int *dst = reinterpret_cast<int *>(&sI);
