@@ -686,21 +686,15 @@ def run_rollout(F, torch, dev, stream, reps, flush, n=16000, T=128, seed=0, worl
 
 
 def device_initial_state(dev):
-    """Clients' initial states drawn on the device from each session's seed:
-    x, y ~ U[0, side), theta ~ U[0, 2 pi), speed 0.5 (the distribution of
-    flock_inputs.initial_state, from torch's device generator, re-seeded per
-    session; the state is built in place with few launches)."""
+    """Clients' initial states drawn on the device from each session's seed by
+    the library's flock_seed_states: x, y ~ U[0, side), theta ~ U[0, 2 pi),
+    speed 0.5 (the distribution of flock_inputs.initial_state), one launch."""
     import torch
-    below_two_pi = float(np.nextafter(fi.TWO_PI_F32, np.float32(0)))
-    g = torch.Generator(device=dev)
+    import paper_2207_03945_gb300 as F
 
     def fn(s):
-        g.manual_seed(int(s.seed))
-        side = np.float32(s.params["side"])
-        st = torch.rand((s.n, 4), generator=g, device=dev)
-        st[:, 0:2].mul_(float(side)).clamp_(max=float(np.nextafter(side, np.float32(0))))
-        st[:, 2].mul_(float(fi.TWO_PI_F32)).clamp_(max=below_two_pi)
-        st[:, 3].fill_(0.5)
+        st = torch.empty((s.n, 4), dtype=torch.float32, device=dev)
+        F.flock_seed_states(st, float(s.params["side"]), int(s.seed), 0.5)
         return st
     return fn
 

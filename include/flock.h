@@ -212,6 +212,22 @@ int env_rollout(flock_env *env, int T, const int32_t *actions_dev, const float *
 int flock_gae(int T, int n, const float *reward_dev, const float *value_dev, float gamma,
               float lambda, float *adv_dev, float *ret_dev, void *stream);
 
+/* Initial states drawn on the device from a seed (an episode's start where
+ * the state lives, e.g. a serving session admitted by seed; the paper leaves
+ * initial conditions open, uniform is this library's reading): row i of the
+ * n x 4 state_dev is (x, y, theta, s) with
+ *   x = min(u(4i) * side, side-),  y = min(u(4i+1) * side, side-),
+ *   theta = min(u(4i+2) * (float)2pi, (float)2pi-),  s = speed,
+ * where v- is the float below v, each product rounded once, and u(k) is
+ * output k (from 0) of SplitMix64 seeded with `seed` (Steele, Lea and Flood,
+ * OOPSLA 2014: z = seed + (k+1) * 0x9E3779B97F4A7C15, then the finaliser
+ * z ^= z >> 30, z *= 0xBF58476D1CE4E5B9, z ^= z >> 27, z *= 0x94D049BB133111EB,
+ * z ^= z >> 31) reduced to its top 24 bits times 2^-24.  state_dev: device
+ * memory, 16-byte aligned; side > 0 and speed finite, else FLOCK_EINVAL.
+ * Enqueues one kernel on `stream` (a cudaStream_t); n == 0 does nothing. */
+int flock_seed_states(float *state_dev, int n, float side, float speed, uint64_t seed,
+                      void *stream);
+
 /* One step whose next actions come from the policy: applies
  * actions_inout_dev, observes, and feeds each agent's observation through the
  * shared policy network (the learners' shared MLP of Section 4.3, here

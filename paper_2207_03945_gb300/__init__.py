@@ -21,6 +21,7 @@ __all__ = [
     "flock_workspace_bytes",
     "flock_derive",
     "env_create", "env_reset", "env_step", "env_step_continuous", "env_rollout", "flock_gae",
+    "flock_seed_states",
     "env_set_types",
     "env_step_host", "env_step_host_bind", "env_get_state", "env_set_state",
     "env_get_error", "env_get_derived", "env_get_tuning", "env_set_timing",
@@ -163,6 +164,17 @@ def flock_gae(reward, value, gamma: float, lam: float, adv, ret, stream=None):
         _ptr(value, torch.float32, (T + 1, n), "value"), ctypes.c_float(gamma),
         ctypes.c_float(lam), _ptr(adv, torch.float32, (T, n), "adv"),
         _ptr(ret, torch.float32, (T, n), "ret"), _stream(stream)))
+
+
+def flock_seed_states(state, side: float, seed: int, speed: float = 0.5, stream=None):
+    """Initial states drawn on the device from a seed (see flock.h): state is
+    an (n, 4) float32 CUDA tensor, filled in place with x, y ~ U[0, side),
+    theta ~ U[0, 2 pi) and the given speed, from SplitMix64 outputs of seed."""
+    torch = _torch()
+    n = int(state.shape[0])
+    _abi.check(_abi.lib.flock_seed_states(
+        _ptr(state, torch.float32, (n, 4), "state"), n, ctypes.c_float(side),
+        ctypes.c_float(speed), ctypes.c_uint64(int(seed) & 0xFFFFFFFFFFFFFFFF), _stream(stream)))
 
 
 def env_set_types(env, types):

@@ -106,6 +106,7 @@ def _load(path=LIB_PATH):
         "env_step": [vp, vp, vp, vp, vp],
         "env_step_continuous": [vp, vp, vp, vp, vp],
         "env_rollout": [vp, ctypes.c_int, vp, vp, vp, vp, vp],
+        "flock_seed_states": [vp, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_uint64, vp],
         "flock_gae": [ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_float, ctypes.c_float, vp, vp,
                       vp],
         "env_step_host": [vp, vp, vp, vp, vp],

@@ -18,6 +18,9 @@
 // HBM-bound: 16 bytes per (step, agent).
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <cstdint>
+
 #include "flock.h"
 #include "flock_host.h"
 
@@ -70,6 +73,38 @@ __global__ void __launch_bounds__(kGaeBlock) k_gae(int T, int n, const float *__
   }
 }
 
+// Initial states from a seed (a serving session's episode start, drawn where
+// the state lives).  Random numbers: SplitMix64 (Steele, Lea and Flood,
+// "Fast splittable pseudorandom number generators", OOPSLA 2014): output k of
+// seed S mixes S + (k + 1) * 0x9E3779B97F4A7C15 through the variant-13
+// finaliser, so each output is computed on its own; agent i takes outputs
+// 4i, 4i + 1 and 4i + 2 (the fourth is unused), and a uniform in [0, 1) is
+// the output's top 24 bits times 2^-24 (exact in FP32).  A thread per agent.
+__device__ __forceinline__ unsigned long long splitmix64_out(unsigned long long seed,
+                                                             unsigned long long k) {
+  unsigned long long z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ float unit24(unsigned long long x) {
+  return __uint2float_rn((unsigned)(x >> 40)) * 0x1p-24f;  // 24 bits: exact
+}
+
+__global__ void __launch_bounds__(256) k_seed_states(float4 *state, int n, float side,
+                                                     float side_below, float two_pi,
+                                                     float two_pi_below, float speed,
+                                                     unsigned long long seed) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned long long k = 4ull * (unsigned long long)i;
+  const float x = fminf(__fmul_rn(unit24(splitmix64_out(seed, k)), side), side_below);
+  const float y = fminf(__fmul_rn(unit24(splitmix64_out(seed, k + 1)), side), side_below);
+  const float th = fminf(__fmul_rn(unit24(splitmix64_out(seed, k + 2)), two_pi), two_pi_below);
+  state[i] = make_float4(x, y, th, speed);
+}
+
 }  // namespace flock
 
 using namespace flock;
@@ -87,4 +122,18 @@ extern "C" int flock_gae(int T, int n, const float *reward, const float *value, 
                                                         ret);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? FLOCK_OK : cuda_fail(e, "k_gae launch");
+}
+
+extern "C" int flock_seed_states(float *state, int n, float side, float speed, uint64_t seed,
+                                 void *stream) {
+  NvtxRange nvtx_range("flock:seed_states");
+  if (n < 0 || !(side > 0.0f) || !std::isfinite(side) || !std::isfinite(speed)) return FLOCK_EINVAL;
+  if (n == 0) return FLOCK_OK;
+  if (!state || (reinterpret_cast<uintptr_t>(state) & 15)) return FLOCK_EINVAL;
+  const float two_pi = (float)(2.0 * 3.14159265358979323846);
+  k_seed_states<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
+      reinterpret_cast<float4 *>(state), n, side, std::nextafter(side, 0.0f), two_pi,
+      std::nextafter(two_pi, 0.0f), speed, (unsigned long long)seed);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? FLOCK_OK : cuda_fail(e, "k_seed_states launch");
 }
