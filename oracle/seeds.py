@@ -9,11 +9,14 @@ number generators", OOPSLA 2014), written here from that published
 definition: output k of seed S is the finaliser applied to
 S + (k + 1) * 0x9E3779B97F4A7C15 (all arithmetic modulo 2^64).
 
-Parity unpinned for the generator's exact stream (no published test vector is
-at hand offline); its outputs are pinned by distribution properties in
-``tests/test_seed_states.py`` (ranges, moments, uniformity of bins, the
-independence of the three columns), and the CUDA path must equal this module
-bit for bit.
+Pins (``tests/test_seed_states.py``): every output, run backwards through the
+finaliser step by step (the xor-shifts and the multiplications by odd
+constants each inverted on its own), gives back its counter; and the draws
+have the properties of a uniform draw (ranges, moments, flat histograms of
+single columns and of pairs, which a bare counter without the finaliser
+fails).  The constants themselves are those of the published definition as
+written here; no published output of the generator was at hand offline to
+compare against.  The CUDA path must equal this module bit for bit.
 """
 from __future__ import annotations
 

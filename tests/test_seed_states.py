@@ -1,10 +1,12 @@
 """Initial states drawn from a seed (flock_seed_states).
 
 CPU: the oracle's restatement (oracle/seeds.py, SplitMix64 from its published
-definition) is pinned by what a uniform draw must satisfy: every value in its
-range, the moments of U[0, 1), flat histograms, flat histograms of pairs
-(the three columns of an agent and consecutive agents: a generator without
-its finaliser, a bare Weyl sequence, fails these), and determinism by seed.
+definition) is pinned by its outputs run backwards through the finaliser
+(each step inverted on its own) to the counter they came from, and by what a
+uniform draw must satisfy: every value in its range, the moments of U[0, 1),
+flat histograms, flat histograms of pairs (the three columns of an agent and
+consecutive agents: a generator without its finaliser, a bare Weyl sequence,
+fails these), and determinism by seed.
 GPU: the kernel equals the oracle bit for bit, and bad arguments are refused
 before any launch."""
 import numpy as np
@@ -77,6 +79,39 @@ def test_bare_weyl_sequence_fails_the_pair_test():
     h = np.bincount(cells, minlength=g * g)
     e = len(a) / (g * g)
     assert ((h - e) ** 2 / e).sum() > 10 * g * g
+
+
+def _unxorshift(y: int, s: int) -> int:
+    """Inverse of z -> z ^ (z >> s) on 64-bit words: the top s bits are
+    unchanged, each further block of s bits follows from the ones above it."""
+    x = y
+    for _ in range(64 // s + 1):
+        x = y ^ (x >> s)
+    return x
+
+
+def _unfinalise(z: int) -> int:
+    """The finaliser of each output run backwards, step by step: the xor-shifts
+    by 31, 27 and 30 undone as above, the multiplications by the two odd
+    constants undone by their inverses modulo 2^64."""
+    M = 1 << 64
+    z = _unxorshift(z, 31)
+    z = (z * pow(0x94D049BB133111EB, -1, M)) % M
+    z = _unxorshift(z, 27)
+    z = (z * pow(0xBF58476D1CE4E5B9, -1, M)) % M
+    return _unxorshift(z, 30)
+
+
+def test_outputs_invert_to_the_weyl_sequence():
+    """Each output run backwards through the finaliser gives back the counter
+    seed + (k + 1) * 0x9E3779B97F4A7C15: a dropped or altered step of the
+    forward mix (a shift, a multiplication, the counter) fails this."""
+    rng = np.random.Generator(np.random.PCG64(5))
+    for seed in [0, 1, 2 ** 63 + 5, 2 ** 64 - 1] + [int(x) for x in rng.integers(0, 2 ** 63, 4)]:
+        k = np.arange(50, dtype=np.uint64) * np.uint64(97)
+        out = seeds.splitmix64(seed, k)
+        for kk, z in zip(k.tolist(), out.tolist()):
+            assert _unfinalise(int(z)) == (seed + (kk + 1) * 0x9E3779B97F4A7C15) % (1 << 64)
 
 
 def test_seed_determines_the_draw():
