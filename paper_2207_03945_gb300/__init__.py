@@ -437,31 +437,30 @@ def env_batch_set_rows(batch, params_c, n_agents, arena, rows, reset=None):
     the device): instance k's state is arena[rows[k] : rows[k] + n_agents[k]].
     params_c: FlockParams structs (from params_from_dict, built once per
     instance).  For callers that change the set often, such as the serving
-    loop: one check of the arena and of the row ranges, no per-instance tensor
-    checks or dict conversions."""
-    import numpy as np
+    loop: one pass over the instances in plain Python and ctypes arrays, no
+    per-instance tensor checks, dict conversions or numpy round trips."""
     torch = _torch()
     if not isinstance(arena, torch.Tensor) or arena.dim() != 2 or arena.shape[1] != 4:
         raise FlockError("arena must be an (R, 4) tensor")
     k = len(params_c)
-    n = np.asarray(n_agents, dtype=np.int64).reshape(-1)
-    r = np.asarray(rows, dtype=np.int64).reshape(-1)
-    if len(n) != k or len(r) != k:
+    if len(n_agents) != k or len(rows) != k:
         raise FlockError("params, agent counts and rows differ in length")
-    if k and (n.min() < 0 or r.min() < 0 or int((r + n).max()) > arena.shape[0]):
-        raise FlockError("row range outside the arena")
-    if any(not isinstance(q, _abi.FlockParams) for q in params_c):
-        raise FlockError("params_c must be FlockParams structs")
+    cap = int(arena.shape[0])
+    nn = [int(x) for x in n_agents]
+    rr = [int(x) for x in rows]
+    fp = _abi.FlockParams
+    for q, n_, r_ in zip(params_c, nn, rr):
+        if n_ < 0 or r_ < 0 or r_ + n_ > cap:
+            raise FlockError("row range outside the arena")
+        if not isinstance(q, fp):
+            raise FlockError("params_c must be FlockParams structs")
     base = _ptr(arena, torch.float32, name="arena").value
-    P = (_abi.FlockParams * max(k, 1))(*params_c)
-    N = np.ascontiguousarray(n, dtype=np.int32) if k else np.zeros(1, np.int32)
-    S = (base + 16 * r).astype(np.uint64) if k else np.zeros(1, np.uint64)
-    R = (np.asarray([bool(x) for x in reset], dtype=np.int32) if reset is not None and k
-         else np.zeros(max(k, 1), np.int32))
-    _abi.check(_abi.lib.env_batch_set(batch.handle, k, P,
-                                      N.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                                      S.ctypes.data_as(ctypes.POINTER(ctypes.c_void_p)),
-                                      R.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+    m = max(k, 1)
+    P = (fp * m)(*params_c)
+    N = (ctypes.c_int * m)(*nn)
+    S = (ctypes.c_void_p * m)(*[base + 16 * r_ for r_ in rr])
+    R = (ctypes.c_int * m)(*([1 if x else 0 for x in reset] if reset is not None else []))
+    _abi.check(_abi.lib.env_batch_set(batch.handle, k, P, N, S, R))
     batch.states = [arena]  # keep the arena alive while active
 
 
